@@ -1,0 +1,222 @@
+"""CPU FP64 oracle for the SIDM scattering step -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never calls it and shares no code with it.
+
+The arithmetic lives in ``sidm_oracle.cpp`` (plain C++17, FP64, no FMA
+contraction); this module compiles it into ``liboracle.so`` on first use and
+wraps it with ctypes.  Each wrapped function cites the passage of Zier et al.
+(AREPO-2 SIDM) it restates; see the C++ header comment for the readings taken
+where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sidm_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (g++, -O2, OpenMP, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off",
+                               "-fno-fast-math", "-fPIC", "-shared", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Config(C.Structure):
+    _fields_ = [("n_ngb", C.c_int), ("ngb_tol", C.c_int), ("c_sidm", C.c_double),
+                ("box", C.c_double), ("kernel", C.c_int), ("fixed_h", C.c_double),
+                ("use_tree", C.c_int), ("n_threads", C.c_int)]
+
+
+class Sigma(C.Structure):
+    _fields_ = [("kind", C.c_int), ("sigma0", C.c_double), ("w", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_active", C.c_int64), ("n_candidate_pairs", C.c_int64),
+                ("n_accepted", C.c_int64), ("n_p_ge_1", C.c_int64),
+                ("n_h_nonconv", C.c_int64), ("n_dir_fail", C.c_int64),
+                ("e_before", C.c_double), ("e_after", C.c_double),
+                ("p_before", C.c_double * 3), ("p_after", C.c_double * 3),
+                ("sum_p", C.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["p_before"] = list(self.p_before)
+        d["p_after"] = list(self.p_after)
+        return d
+
+
+def _p(a, t):
+    return a.ctypes.data_as(C.POINTER(t)) if a is not None else None
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            dp, u32p, i64p, u8p, i8p, u64p, ip = (C.POINTER(C.c_double), C.POINTER(C.c_uint32),
+                                                    C.POINTER(C.c_int64), C.POINTER(C.c_uint8),
+                                                    C.POINTER(C.c_int8), C.POINTER(C.c_uint64),
+                                                    C.POINTER(C.c_int))
+            L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            L.orc_uniform53.argtypes = [C.c_uint32, C.c_uint32]
+            L.orc_uniform53.restype = C.c_double
+            L.orc_kernel_w.argtypes = [C.c_int, C.c_double, C.c_double]
+            L.orc_kernel_w.restype = C.c_double
+            L.orc_sigma_over_m.argtypes = [C.POINTER(Sigma), C.c_double]
+            L.orc_sigma_over_m.restype = C.c_double
+            L.orc_directed_probability.argtypes = [C.c_int, C.POINTER(Sigma), C.c_double, dp, dp,
+                                                   C.c_double, C.c_double, C.c_double]
+            L.orc_directed_probability.restype = C.c_double
+            L.orc_direction.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, dp]
+            L.orc_direction.restype = C.c_int
+            L.orc_kick.argtypes = [C.c_double, C.c_double, dp, dp, dp]
+            L.orc_initial_h.argtypes = [C.c_double, C.c_int64, C.c_int]
+            L.orc_initial_h.restype = C.c_double
+            L.orc_counts.argtypes = [C.c_int64, dp, C.c_double, C.c_int, C.c_int64, i64p, dp, i64p]
+            L.orc_h_for.argtypes = [C.POINTER(Config), C.c_int64, dp, C.c_int64, i64p, dp, i64p, ip]
+            L.orc_step.argtypes = [C.POINTER(Config), C.c_int64, dp, dp, dp, u32p, u8p, i8p,
+                                   C.c_double, C.POINTER(Sigma), C.c_uint64, C.c_uint64, dp, dp,
+                                   C.c_int64, u32p, u64p, dp, i64p, C.POINTER(Stats)]
+            L.orc_step.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def make_config(n_ngb=32, ngb_tol=5, c_sidm=0.1, box=0.0, kernel=0, fixed_h=0.0,
+                use_tree=1, n_threads=0) -> Config:
+    return Config(int(n_ngb), int(ngb_tol), float(c_sidm), float(box), int(kernel),
+                  float(fixed_h), int(use_tree), int(n_threads))
+
+
+def make_sigma(kind=0, sigma0=1.0, w=1.0) -> Sigma:
+    return Sigma(int(kind), float(sigma0), float(w))
+
+
+# ------------------------------------------------------------ primitives ---
+
+def philox4x32_10(key, ctr) -> np.ndarray:
+    """Philox-4x32-10 block (Salmon et al., SC'11)."""
+    k = np.ascontiguousarray(key, np.uint32)
+    c = np.ascontiguousarray(ctr, np.uint32)
+    o = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(_p(k, C.c_uint32), _p(c, C.c_uint32), _p(o, C.c_uint32))
+    return o
+
+
+def uniform53(wa: int, wb: int) -> float:
+    return lib().orc_uniform53(int(wa), int(wb))
+
+
+def kernel_w(r: float, h: float, kernel: int = 0) -> float:
+    """Cubic spline W_CS (kernel 0) or top-hat W_TH (kernel 1), Sec. 4.2."""
+    return lib().orc_kernel_w(int(kernel), float(r), float(h))
+
+
+def sigma_over_m(vrel: float, kind=0, sigma0=1.0, w=1.0) -> float:
+    s = make_sigma(kind, sigma0, w)
+    return lib().orc_sigma_over_m(C.byref(s), float(vrel))
+
+
+def directed_probability(m_j, v_i, v_j, r2, h_i, dt_i, kernel=0, kind=0, sigma0=1.0, w=1.0):
+    """P(i|j) of Eq. 3 with the rate of Eq. 2 and g_ij of Eq. 4."""
+    s = make_sigma(kind, sigma0, w)
+    vi = np.ascontiguousarray(v_i, np.float64)
+    vj = np.ascontiguousarray(v_j, np.float64)
+    return lib().orc_directed_probability(int(kernel), C.byref(s), float(m_j), _p(vi, C.c_double),
+                                          _p(vj, C.c_double), float(r2), float(h_i), float(dt_i))
+
+
+def direction(seed: int, step: int, a: int, b: int):
+    e = np.zeros(3)
+    ok = lib().orc_direction(seed, step, a, b, _p(e, C.c_double))
+    return e, bool(ok)
+
+
+def kick(mi, mj, vi, vj, e):
+    """Elastic centre-of-momentum kick, Sec. 4.1 (eps = 1)."""
+    vi = np.array(vi, np.float64)
+    vj = np.array(vj, np.float64)
+    e = np.ascontiguousarray(e, np.float64)
+    lib().orc_kick(float(mi), float(mj), _p(vi, C.c_double), _p(vj, C.c_double), _p(e, C.c_double))
+    return vi, vj
+
+
+def initial_h(l_ext: float, n: int, n_ngb: int) -> float:
+    return lib().orc_initial_h(float(l_ext), int(n), int(n_ngb))
+
+
+def counts(pos, h, query=None, box=0.0, use_tree=True) -> np.ndarray:
+    """Neighbour counts #{j != i : r_ij < h_i} for the query particles."""
+    pos = np.ascontiguousarray(pos, np.float64)
+    n = pos.shape[0]
+    q = np.arange(n, dtype=np.int64) if query is None else np.ascontiguousarray(query, np.int64)
+    hh = np.ascontiguousarray(np.broadcast_to(np.asarray(h, np.float64), q.shape), np.float64)
+    out = np.zeros(q.shape[0], np.int64)
+    lib().orc_counts(n, _p(pos, C.c_double), float(box), int(use_tree), q.shape[0],
+                     _p(q, C.c_int64), _p(hh, C.c_double), _p(out, C.c_int64))
+    return out
+
+
+def h_for(pos, query, n_ngb=32, ngb_tol=5, box=0.0, use_tree=True, n_threads=0):
+    """h_SI by bisection for the query particles (Sec. 4.2/4.5)."""
+    pos = np.ascontiguousarray(pos, np.float64)
+    q = np.ascontiguousarray(query, np.int64)
+    cfg = make_config(n_ngb, ngb_tol, 0.1, box, 0, 0.0, int(use_tree), n_threads)
+    h = np.zeros(q.shape[0])
+    cnt = np.zeros(q.shape[0], np.int64)
+    nc = np.zeros(q.shape[0], np.int32)
+    lib().orc_h_for(C.byref(cfg), pos.shape[0], _p(pos, C.c_double), q.shape[0], _p(q, C.c_int64),
+                    _p(h, C.c_double), _p(cnt, C.c_int64), nc.ctypes.data_as(C.POINTER(C.c_int)))
+    return h, cnt, nc
+
+
+def step(pos, vel, mass, ids, active, bins, dt_max, *, n_ngb=32, ngb_tol=5, c_sidm=0.1,
+         box=0.0, kernel=0, fixed_h=0.0, sigma_kind=0, sigma0=1.0, w=1.0, seed=0, step=0,
+         use_tree=True, n_threads=0, max_pairs=None, h_init=None, dtlim_init=None):
+    """One scattering step (Sec. 4); returns a dict with the new velocities,
+    h and dt-limits (active particles updated, others from *_init or 0/inf),
+    the accepted pairs sorted by (ord, a, b), and the step statistics."""
+    pos = np.ascontiguousarray(pos, np.float64)
+    n = pos.shape[0]
+    vel = np.array(vel, np.float64, order="C", copy=True)
+    mass = np.ascontiguousarray(mass, np.float64)
+    ids = np.ascontiguousarray(ids, np.uint32)
+    act = None if active is None else np.ascontiguousarray(active, np.uint8)
+    bins = np.ascontiguousarray(bins, np.int8)
+    h = np.zeros(n) if h_init is None else np.array(h_init, np.float64, copy=True)
+    dl = np.full(n, np.inf) if dtlim_init is None else np.array(dtlim_init, np.float64, copy=True)
+    cap = (4 * n + 16) if max_pairs is None else int(max_pairs)
+    ab = np.zeros((cap, 2), np.uint32)
+    ords = np.zeros(cap, np.uint64)
+    pp = np.zeros(cap, np.float64)
+    npairs = C.c_int64(0)
+    st = Stats()
+    cfg = make_config(n_ngb, ngb_tol, c_sidm, box, kernel, fixed_h, int(use_tree), n_threads)
+    sg = make_sigma(sigma_kind, sigma0, w)
+    rc = lib().orc_step(C.byref(cfg), n, _p(pos, C.c_double), _p(vel, C.c_double),
+                        _p(mass, C.c_double), _p(ids, C.c_uint32), _p(act, C.c_uint8),
+                        _p(bins, C.c_int8), float(dt_max), C.byref(sg), int(seed), int(step),
+                        _p(h, C.c_double), _p(dl, C.c_double), cap, _p(ab, C.c_uint32),
+                        _p(ords, C.c_uint64), _p(pp, C.c_double), C.byref(npairs), C.byref(st))
+    if rc != 0:
+        raise ValueError("oracle step: invalid arguments")
+    k = min(npairs.value, cap)
+    return {"vel": vel, "h": h, "dtlim": dl, "pairs_ab": ab[:k].copy(), "pairs_ord": ords[:k].copy(),
+            "pairs_p": pp[:k].copy(), "n_pairs": npairs.value, "stats": st.as_dict()}
