@@ -223,6 +223,8 @@ struct KdTree {
     return s;
   }
 
+  // Calls f(j, r2) for every j != i with r2 < h*h; f returns false to stop
+  // the walk early.  Nearer children are visited first.
   template <class F>
   void for_each_within(const Cloud& c, int64_t i, double h, F&& f) const {
     const double hh = h * h;
@@ -238,11 +240,13 @@ struct KdTree {
           const int64_t j = order[t];
           if (j == i) continue;
           const double r2 = separation_r2(c, i, j);
-          if (r2 < hh) f(j, r2);
+          if (r2 < hh && !f(j, r2)) return;
         }
       } else {
-        stack.push_back(nd.left);
-        stack.push_back(nd.right);
+        const double dl = box_distance(c, nodes[nd.left], p);
+        const double dr = box_distance(c, nodes[nd.right], p);
+        if (dl <= dr) { stack.push_back(nd.right); stack.push_back(nd.left); }
+        else { stack.push_back(nd.left); stack.push_back(nd.right); }
       }
     }
   }
@@ -251,19 +255,31 @@ struct KdTree {
 struct Search {
   const Cloud& c;
   const KdTree* tree;   // null: brute force
+  // f(j, r2) returns false to stop early
   template <class F>
-  void within(int64_t i, double h, F&& f) const {
+  void within_until(int64_t i, double h, F&& f) const {
     if (tree) { tree->for_each_within(c, i, h, f); return; }
     const double hh = h * h;
     for (int64_t j = 0; j < c.n; ++j) {
       if (j == i) continue;
       const double r2 = separation_r2(c, i, j);
-      if (r2 < hh) f(j, r2);
+      if (r2 < hh && !f(j, r2)) return;
     }
+  }
+  template <class F>
+  void within(int64_t i, double h, F&& f) const {
+    within_until(i, h, [&](int64_t j, double r2) { f(j, r2); return true; });
   }
   int64_t count_within(int64_t i, double h) const {
     int64_t k = 0;
     within(i, h, [&](int64_t, double) { ++k; });
+    return k;
+  }
+  // min(c_i(h), cap): the bisection only compares the count with the band,
+  // so counting may stop once it exceeds the band.
+  int64_t count_capped(int64_t i, double h, int64_t cap) const {
+    int64_t k = 0;
+    within_until(i, h, [&](int64_t, double) { return ++k < cap; });
     return k;
   }
 };
@@ -287,7 +303,7 @@ double bisect_h(const Search& s, int64_t i, double h0, int n_ngb, int tol, int* 
   *nonconv = 1;
   int64_t c = 0;
   for (int it = 0; it < 128; ++it) {
-    c = s.count_within(i, h);
+    c = s.count_capped(i, h, (int64_t)n_ngb + tol + 1);
     if (c >= n_ngb - tol && c <= n_ngb + tol) { *nonconv = 0; break; }
     if (c < n_ngb - tol) {
       lo = h;
