@@ -1,0 +1,342 @@
+"""Benchmark of the SIDM scattering step on one B300 (or N independent replicas).
+
+Workload: isolated Hernquist halo, N = 2^20, N_ngb = 64 +- 5, constant
+sigma/m = 1, open boundaries, FP64, power-of-two timestep bins with ~10 % of
+the particles active per finest step (step s of a 100-step cycle uses the
+active set of finest step s).  One bench step = one complete scattering step
+(keys, sort, structure, h_SI search, pairs + draws + Eq. 9, kicks) on the
+step's active set.  Metric: particle updates (active particles) per second.
+
+    python bench.py [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own halo replica on its own GPU
+(independent problems, no data-path collective): value = all ranks'
+updates / the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SIDM particle-updates/s (search+scatter)"
+UNIT = "particle-updates/s"
+CYCLE = 100
+
+# Algorithmic HBM bytes of each phase, per particle (n) and per active
+# particle (a): the data the phase must read and write once (FP64 state,
+# 4-byte ids/indices, 1-byte flags).  Derivation in the design doc.
+PHASE_BYTES = {
+    "keys": (56.0, 0.0),        # bbox read 24, keys read 24, key+index write 8
+    "sort": (96.0, 0.0),        # 4 passes x (hist read 4 + scatter read 8 + write 8) + index
+    "structure": (190.0, 0.0),  # gather 66 read, key-order state 97 written, leaf boxes ~27
+    "search": (16.0, 56.0),     # FP32 positions once; own state 40 read, h 16 written
+    "pairs": (0.0, 92.0),       # own state 84 read, Eq. 9 limit 8 written
+    "resolve": (0.0, 0.0),      # per accepted pair, reported separately
+}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6400.0)), "measured"
+    return 6400.0, "fallback"
+
+
+def _workload(seed_offset=0):
+    from paper_2607_05504_b300 import inputs as I
+    w = I.hernquist_2pow20(seed=1 + seed_offset)
+    masks = np.stack([I.active_at_step(w["bins"], s) for s in range(CYCLE)])
+    return w, masks
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            os.remove(self.path)
+        except Exception:
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except Exception:
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def run_reference(args) -> None:
+    """The oracle as it stands, on the host cores, on the same workload: each
+    step runs the full oracle step on a bounded sample of the step's active set."""
+    import oracle
+    oracle.build()
+    w, masks = _workload()
+    p, bins = w["particles"], w["bins"]
+    cap = 1 << 14
+    rng = np.random.default_rng(0)
+
+    def sample(s):
+        a = masks[s].copy()
+        idx = np.nonzero(a)[0]
+        if idx.size > cap:
+            a[:] = 0
+            a[rng.choice(idx, cap, replace=False)] = 1
+        return a
+
+    vel = p.vel.copy()
+    for k in range(args.warmup):
+        s = k % CYCLE
+        oracle.step(p.pos, vel, p.mass, p.ids, sample(s), bins, w["dt_max"], n_ngb=64, seed=0, step=s)
+    upd, t0 = 0, time.perf_counter()
+    for k in range(args.steps):
+        s = (args.warmup + k) % CYCLE
+        a = sample(s)
+        r = oracle.step(p.pos, vel, p.mass, p.ids, a, bins, w["dt_max"], n_ngb=64, seed=0, step=s)
+        vel = r["vel"]
+        upd += int(a.sum())
+    dt = time.perf_counter() - t0
+    v = upd / dt
+    cores = os.cpu_count()
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "hernquist-2^20 (N_ngb 64, sigma/m 1, ~10% active, 100-step bin cycle)",
+                       "l2": "host run"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"full oracle step per bench step, active set capped at {cap} "
+                                       "(seeded subset) of the step's active particles"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, masks, budget_s=12.0) -> dict:
+    import oracle
+    oracle.build()
+    p, bins = w["particles"], w["bins"]
+    upd, t0, k = 0, time.perf_counter(), 0
+    vel = p.vel.copy()
+    while k < CYCLE - 1 and (time.perf_counter() - t0) < budget_s:
+        s = 1 + k
+        r = oracle.step(p.pos, vel, p.mass, p.ids, masks[s], bins, w["dt_max"], n_ngb=64, seed=0, step=s)
+        vel = r["vel"]
+        upd += int(masks[s].sum())
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": upd / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"finest steps 1..{k} of the 100-step cycle ({upd} active updates, {dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import torch
+    from paper_2607_05504_b300 import sidm
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    w, masks = _workload(seed_offset=rank)
+    p, bins = w["particles"], w["bins"]
+    n = p.n
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    masks_d = torch.from_numpy(masks).to(dev)
+    bins_d = torch.from_numpy(bins).to(dev)
+    pos_d = torch.from_numpy(p.pos).to(dev)
+    vel_d = torch.from_numpy(p.vel).to(dev)
+    ids_d = torch.from_numpy(p.ids.view(np.int32)).to(dev)
+    mass_d = torch.from_numpy(p.mass).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
+
+    ctx = sidm.Context(n_ngb=64, box=0.0, stream=stream.cuda_stream, device=local, n_max=n)
+    ctx.set_particles(pos_d, vel_d, ids_d, mass=mass_d)
+    sg = sidm.SigmaModel(sidm.SIGMA_CONST, 1.0, 1.0)
+
+    def step(k):
+        s = k % CYCLE
+        sidm.sidm_step(ctx.handle, masks_d[s], bins_d, w["dt_max"], sg, 0, None)
+        return int(masks[s].sum())
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    upd = 0
+    l0 = ctx.kernel_launches
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()                       # L2 flush between timed steps (untimed)
+            ev[k][0].record(stream)
+            upd += step(args.warmup + k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = ctx.kernel_launches - l0
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist:
+        import torch.distributed as D
+        tt = torch.tensor([t_ms, float(upd)], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        D.all_reduce(mx, op=D.ReduceOp.MAX)
+        D.all_reduce(tt, op=D.ReduceOp.SUM)
+        t_all, upd_all = float(mx[0]), float(tt[1])
+        D.barrier()
+    else:
+        t_all, upd_all = t_ms, float(upd)
+    value = upd_all / (t_all * 1e-3)
+
+    # ---- roofline: phase times of the same steps, CUDA events on the library's stream
+    pctx = sidm.Context(n_ngb=64, box=0.0, stream=stream.cuda_stream, device=local, n_max=n,
+                        profile=True)
+    pctx.set_particles(pos_d, vel_d, ids_d, mass=mass_d)
+    phase_sum = {k: 0.0 for k in sidm.PHASES}
+    n_act_sum = 0
+    reps = min(args.steps, CYCLE)
+    for k in range(reps):
+        flush.zero_()
+        s = (args.warmup + k) % CYCLE
+        sidm.sidm_step(pctx.handle, masks_d[s], bins_d, w["dt_max"], sg, 0, None)
+        for name, ms in pctx.phase_times().items():
+            phase_sum[name] += ms
+        n_act_sum += int(masks[s].sum())
+    pctx.close()
+    hbm_peak, peak_kind = _peaks()
+    dom = max(phase_sum, key=phase_sum.get)
+    per_n, per_a = PHASE_BYTES[dom]
+    bytes_per_step = per_n * n + per_a * (n_act_sum / reps)
+    avg_ms = phase_sum[dom] / reps
+    achieved = bytes_per_step / (avg_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "kernel": dom,
+                "peak_kind": peak_kind,
+                "phase_ms_per_step": {k: v / reps for k, v in phase_sum.items()},
+                "phase_share": {k: v / sum(phase_sum.values()) for k, v in phase_sum.items()}}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+        pos_h, vel_h, ids_h, mass_h = pin(p.pos), pin(p.vel), pin(p.ids), pin(p.mass)
+        masks_h = [pin(masks[s]) for s in range(CYCLE)]
+        bins_h = pin(bins)
+        out_v = pin(np.empty((n, 3)))
+        ectx = sidm.Context(n_ngb=64, box=0.0, device=local, n_max=n)
+        K2 = min(args.steps, 20)
+        ectx.set_particles(pos_h, vel_h, ids_h, mass=mass_h)
+        sidm.sidm_step(ectx.handle, masks_h[1], bins_h, w["dt_max"], sg, 0, None)
+        sidm.sidm_get_particles(ectx.handle, out_v)
+        eu, t0 = 0, time.perf_counter()
+        for k in range(K2):
+            s = (args.warmup + k) % CYCLE
+            sidm.sidm_set_particles(ectx.handle, pos_h, vel_h, mass_h, 0.0, ids_h)
+            sidm.sidm_step(ectx.handle, masks_h[s], bins_h, w["dt_max"], sg, 0, None)
+            sidm.sidm_get_particles(ectx.handle, out_v)
+            eu += int(masks[s].sum())
+        et = time.perf_counter() - t0
+        ectx.close()
+        e2e = {"value": eu / et, "unit": UNIT,
+               "h2d_bytes_per_step": int(n * (24 + 24 + 8 + 4) + n + n),
+               "d2h_bytes_per_step": int(n * 24)}
+
+    cb = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cb = cpu_baseline(w, masks)
+
+    ctx.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_all / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "hernquist-2^20 (N_ngb 64, sigma/m 1, open, ~10% active "
+                                       "per finest step, 100-step bin cycle)",
+                           "n": n, "mean_active": upd / args.steps,
+                           "parallelism": f"replicas{world}" if world > 1 else "single",
+                           "l2": "flushed between timed steps (256 MB write)"},
+                "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist:
+        import torch.distributed as D
+        D.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * sidm.h -- C ABI of the B300 SIDM scattering-step library (libsidm.so).
+ *
+ * The library runs, on one CUDA device, the per-timestep Monte-Carlo
+ * scattering step for self-interacting dark matter of Zier et al., "A Novel
+ * Implementation of Self-Interacting Dark Matter in AREPO-2":
+ *
+ *   - for every active particle i, the search radius h_i that encloses
+ *     N_ngb +- tol other particles, active or inactive (Sec. 4.2, Sec. 4.5);
+ *   - the pair probability P(i|j) = 1/2 m_j (sigma/m)(v_ij) |v_i - v_j|
+ *     W(|x_j - x_i|, h_i) dt_i (Eqs. 2-4, cubic spline or top-hat W, Sec. 4.2;
+ *     constant or Yukawa-like sigma/m, Sec. 5.2);
+ *   - one Philox-4x32-10 draw per unordered candidate pair against
+ *     P_pair = P(i|j)[i active, j in N(i)] + P(j|i)[j active, i in N(j)];
+ *   - elastic isotropic centre-of-momentum kicks (Sec. 4.1), several per
+ *     particle per step, applied in ascending (ord, min id, max id) order so
+ *     that each kick sees the velocities left by the earlier ones (Sec. 4.4);
+ *   - the per-pair timestep limit of Eq. 9.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: SIDM_OK (0), a positive warning (the call took effect),
+ *     or a negative error (see sidm_status).  sidm_error_string() names it.
+ *   - ptr_kind: SIDM_HOST (0) for host memory, SIDM_DEVICE (1) for device
+ *     memory of the context's device.  Inputs are copied; the caller keeps
+ *     ownership of every pointer it passes and may reuse it after the call
+ *     returns (host inputs) or after the context's stream has passed the
+ *     call (device inputs).
+ *   - Layouts: positions and velocities are n x 3 row-major FP64 arrays
+ *     (x0 y0 z0 x1 y1 z1 ...); masses FP64; ids uint32, unique.
+ *   - All device work is issued on the context's stream.  sidm_step() does
+ *     not wait for the device unless `stats` is non-NULL; errors detected on
+ *     the device (a bounded loop that gave up, a full pair buffer) are
+ *     latched in the context and returned by the next call that waits:
+ *     sidm_step() with stats, sidm_sync(), sidm_get_particles(),
+ *     sidm_timestep_limits(), sidm_get_pairs().
+ *   - One context is used by one host thread at a time.
+ */
+#ifndef SIDM_H
+#define SIDM_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SIDM_API __attribute__((visibility("default")))
+#else
+#define SIDM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sidm_ctx sidm_ctx;
+
+typedef enum {
+  SIDM_OK = 0,
+  SIDM_WARN_H_NOT_CONVERGED = 1, /* a bisection hit its evaluation cap (the last h is kept) */
+  SIDM_WARN_P_GE_1 = 2,          /* some P_pair >= 1 (accepted; dt too large for Eq. 9)    */
+  SIDM_WARN_DIRECTION = 4,       /* a direction draw exhausted its 64 tries (e = +z used)   */
+  SIDM_ERR_INVALID_ARG = -1,
+  SIDM_ERR_OOM = -2,
+  SIDM_ERR_CUDA = -3,
+  SIDM_ERR_DEVICE_LIMIT = -4,    /* a bounded device loop or buffer gave up; step not valid */
+  SIDM_ERR_NOT_READY = -5        /* sidm_step before sidm_set_particles                     */
+} sidm_status;
+
+enum { SIDM_HOST = 0, SIDM_DEVICE = 1 };
+enum { SIDM_KERNEL_CUBIC = 0, SIDM_KERNEL_TOPHAT = 1 };
+enum { SIDM_SIGMA_CONST = 0, SIDM_SIGMA_YUKAWA = 1 };
+enum { SIDM_FP64_PLAIN = 0 };
+
+typedef struct {
+  int n_ngb;            /* target neighbour number N_ngb (paper: 32)                     */
+  int ngb_tol;          /* accepted band N_ngb +- ngb_tol (paper: 5)                      */
+  double c_sidm;        /* C_SIDM of Eq. 9 (paper: 0.1)                                   */
+  double box;           /* > 0: periodic cube [0, box)^3; 0: open boundaries              */
+  int kernel;           /* SIDM_KERNEL_CUBIC (fiducial) or SIDM_KERNEL_TOPHAT              */
+  int precision;        /* SIDM_FP64_PLAIN                                                */
+  double fixed_h;       /* > 0: every active particle uses this h (no bisection); 0: adaptive */
+  int64_t n_max;        /* capacity in particles (0: sized by the first sidm_set_particles) */
+  int64_t pair_capacity;/* accepted-pair buffer (0: 2 n_max + 4096)                        */
+  void* stream;         /* cudaStream_t for all work; NULL: a stream owned by the context */
+  int device;           /* CUDA device ordinal (-1: the current device)                   */
+  int profile;          /* 1: time the phases of every step with CUDA events              */
+} sidm_config;
+
+/* Fills `cfg` with the paper's fiducial values (N_ngb 32 +- 5, C_SIDM 0.1,
+ * cubic spline, open boundaries, FP64, adaptive h, current device). */
+SIDM_API void sidm_default_config(sidm_config* cfg);
+
+typedef struct {
+  int kind;             /* SIDM_SIGMA_CONST or SIDM_SIGMA_YUKAWA                           */
+  double sigma0;        /* sigma/m, or sigma0/m of sigma0/m / (1 + (v/w)^2)^2 (Sec. 5.2)    */
+  double w;             /* velocity scale w of the Yukawa-like law                         */
+} sidm_sigma_model;
+
+typedef struct {
+  int64_t n_active;            /* particles active in the step                              */
+  int64_t n_candidate_pairs;   /* unordered candidate pairs drawn                            */
+  int64_t n_accepted;          /* accepted pairs (kicks applied)                             */
+  int64_t n_rounds;            /* resolver rounds of vertex-disjoint pairs                   */
+  int64_t n_p_ge_1;            /* candidate pairs with P_pair >= 1                           */
+  int64_t n_h_nonconv;         /* bisections that hit the evaluation cap                     */
+  int64_t n_dir_fail;          /* direction draws that exhausted their tries                 */
+  int64_t max_multiplicity;    /* most kicks received by one particle in the step            */
+  double sum_p;                /* sum of P_pair over candidate pairs                         */
+  double e_before, e_after;    /* total kinetic energy, compensated sums                     */
+  double p_before[3], p_after[3]; /* total momentum                                         */
+  int32_t status;              /* bitwise OR of warnings / latched error of this step        */
+  int32_t reserved;
+} sidm_step_stats;
+
+/* Creates a context on cfg->device.  Returns SIDM_ERR_INVALID_ARG for
+ * n_ngb < 1, ngb_tol < 0, ngb_tol >= n_ngb, c_sidm <= 0, box < 0, unknown
+ * kernel or precision; SIDM_ERR_CUDA if the device cannot be used. */
+SIDM_API int sidm_create(const sidm_config* cfg, sidm_ctx** out);
+
+/* Loads n particles (replaces any previous set).  pos, vel: n x 3; mass:
+ * n values, or NULL to give every particle `mass_scalar`; ids: n unique
+ * uint32 (they key the random draws, Philox counter words 2-3).  With a
+ * periodic box every coordinate must lie in [0, box).  The buffers grow if
+ * n exceeds the capacity.  Resets h to 0 and the dt limits to +inf. */
+SIDM_API int sidm_set_particles(sidm_ctx* ctx, int64_t n, const double* pos, const double* vel,
+                       const double* mass, double mass_scalar, const uint32_t* ids,
+                       int ptr_kind);
+
+/* Replaces the velocities only (n must equal the loaded count). */
+SIDM_API int sidm_set_velocities(sidm_ctx* ctx, const double* vel, int ptr_kind);
+
+/* One scattering step (the whole path above).
+ *   active_mask: n bytes, nonzero = active; NULL = all particles active.
+ *   dt_bins:     n int8 bins, dt_i = dt_max * 2^-bin_i (power-of-two
+ *                individual timesteps); NULL = bin 0 for every particle.
+ *   Either pointer may be host or device memory (detected per call).
+ *   sigma:       cross-section model.
+ *   seed:        Philox key; the context's step counter (starts at 0, +1 per
+ *                successful call) is Philox counter word 0.
+ *   stats:       NULL, or receives the step statistics (waits for the step).
+ * The step reads start-of-step velocities for every probability and
+ * applies the accepted kicks in (ord, min id, max id) order. */
+SIDM_API int sidm_step(sidm_ctx* ctx, const uint8_t* active_mask, const int8_t* dt_bins, double dt_max,
+              const sidm_sigma_model* sigma, uint64_t seed, sidm_step_stats* stats);
+
+/* Waits for the context's stream; returns the latched device status. */
+SIDM_API int sidm_sync(sidm_ctx* ctx);
+
+/* Copies the current velocities (n x 3) and, if h_out is non-NULL, the
+ * last h of every particle (0 for particles never active). */
+SIDM_API int sidm_get_particles(sidm_ctx* ctx, double* vel_out, double* h_out, int ptr_kind);
+
+/* Copies the Eq. 9 limit of every particle from its last active step
+ * (+inf before its first active step, and when no neighbour moves
+ * relative to it). */
+SIDM_API int sidm_timestep_limits(sidm_ctx* ctx, double* dt_limit_out, int ptr_kind);
+
+/* Accepted pairs of the last step in application order: ab[2k] = min id,
+ * ab[2k+1] = max id, ord[k] = the 64-bit order key; up to `cap` entries,
+ * *n_out = the total.  Host pointers. */
+SIDM_API int sidm_get_pairs(sidm_ctx* ctx, uint32_t* ab, uint64_t* ord, int64_t cap, int64_t* n_out);
+
+/* Step counter (resume support: the random stream is a pure function of
+ * (seed, step counter, ids), so restoring the particles and the counter
+ * reproduces a run bit for bit). */
+SIDM_API int sidm_get_step(const sidm_ctx* ctx, uint64_t* step);
+SIDM_API int sidm_set_step(sidm_ctx* ctx, uint64_t step);
+
+/* Phase times (milliseconds, CUDA events on the context's stream) of the
+ * last step of a context created with profile = 1; waits for the stream.
+ * ms[k] for k < min(n, SIDM_N_PHASES): 0 keys (bounding box, start radius,
+ * spatial keys), 1 sort, 2 structure (key-order copy, active list, box
+ * tree), 3 search (h_SI), 4 pairs (probabilities, draws, Eq. 9),
+ * 5 resolve (kicks).  Returns SIDM_ERR_INVALID_ARG without profiling. */
+#define SIDM_N_PHASES 6
+SIDM_API int sidm_phase_times(sidm_ctx* ctx, float* ms, int n);
+
+/* Kernels launched by the context so far (all of them are this library's). */
+SIDM_API int64_t sidm_kernel_launches(const sidm_ctx* ctx);
+
+SIDM_API const char* sidm_error_string(int status);
+
+/* Frees every device buffer of the context (waits for its stream). */
+SIDM_API void sidm_destroy(sidm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIDM_H */

@@ -1,0 +1,539 @@
+// C ABI of the SIDM scattering-step library: context, buffers, validation and
+// the order of the kernels of one step.
+//
+// Step (all on the context's stream, no host round trip unless statistics
+// are requested):
+//   bounding box -> start radius / key transform -> 30-bit spatial keys ->
+//   radix sort -> key-order copy of the state + active list -> 32-ary box
+//   tree -> h_SI per active particle -> candidate pairs, probabilities and
+//   draws, Eq. 9 limits -> canonical application of the accepted kicks.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sidm_internal.cuh"
+
+using namespace sidm;
+
+struct sidm_ctx {
+  sidm_config cfg{};
+  int device = 0;
+  int sms = 148;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t n = 0, cap = 0, pair_cap = 0;
+  uint64_t step = 0;
+  bool loaded = false;
+
+  // user order
+  double *pos = nullptr, *vel = nullptr, *mass = nullptr, *h_user = nullptr, *dtlim = nullptr;
+  uint32_t* ids = nullptr;
+  uint8_t* act = nullptr;
+  int8_t* bins = nullptr;
+  // sort
+  uint32_t *keys = nullptr, *keys_alt = nullptr;
+  int32_t *vals = nullptr, *vals_alt = nullptr;
+  void* sort_tmp = nullptr;
+  // key order
+  Sorted so{};
+  int32_t* act_list = nullptr;
+  Tree tree{};
+  // per step
+  StepParams* params = nullptr;
+  unsigned long long* mm = nullptr;
+  DevStats* dstats = nullptr;
+  unsigned* latched = nullptr;
+  int* work = nullptr;
+  PairRec* pairs = nullptr;
+  int32_t *head = nullptr, *next = nullptr, *mult = nullptr;
+  uint8_t* pflags = nullptr;
+  double *cons_partial = nullptr, *cons = nullptr;
+  // pinned host staging
+  DevStats* h_stats = nullptr;
+  double* h_cons = nullptr;
+  unsigned* h_latched = nullptr;
+  std::vector<void*> allocs;
+  // instrumentation
+  int64_t launches = 0;
+  cudaEvent_t ev[SIDM_N_PHASES + 1] = {};
+  bool have_events = false;
+  bool timed_step = false;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return SIDM_ERR_OOM;
+  return SIDM_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_);   \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <class T>
+cudaError_t dalloc(sidm_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  c->allocs.push_back(q);
+  *p = (T*)q;
+  return cudaSuccess;
+}
+
+void free_buffers(sidm_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  c->cap = 0;
+  c->pair_cap = 0;
+}
+
+__global__ void fill_kernel(double* p, int64_t n, double v) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+__global__ void latch_kernel(const DevStats* st, unsigned* latched) {
+  if (threadIdx.x == 0 && st->status) atomicOr(latched, st->status);
+}
+
+void fill(double* p, int64_t n, double v, cudaStream_t s) {
+  if (n > 0) fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, v);
+}
+
+int ensure_capacity(sidm_ctx* c, int64_t n) {
+  int64_t want = std::max<int64_t>(n, c->cfg.n_max);
+  if (want <= c->cap && c->allocs.size()) return SIDM_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  free_buffers(c);
+  want = std::max<int64_t>(want, 64);
+  const int64_t pc = c->cfg.pair_capacity > 0 ? c->cfg.pair_capacity : 2 * want + 4096;
+  Tree& t = c->tree;
+  t.levels = tree_levels_for(want, t.count);
+  int64_t nodes = 0;
+  for (int l = 0; l < t.levels; ++l) {
+    t.offset[l] = nodes;
+    nodes += t.count[l];
+  }
+  CK(dalloc(c, &c->pos, 3 * want));
+  CK(dalloc(c, &c->vel, 3 * want));
+  CK(dalloc(c, &c->mass, want));
+  CK(dalloc(c, &c->h_user, want));
+  CK(dalloc(c, &c->dtlim, want));
+  CK(dalloc(c, &c->ids, want));
+  CK(dalloc(c, &c->act, want));
+  CK(dalloc(c, &c->bins, want));
+  CK(dalloc(c, &c->keys, want));
+  CK(dalloc(c, &c->keys_alt, want));
+  CK(dalloc(c, &c->vals, want));
+  CK(dalloc(c, &c->vals_alt, want));
+  CK(dalloc(c, (char**)&c->sort_tmp, radix_sort_temp_bytes(want)));
+  Sorted& so = c->so;
+  CK(dalloc(c, &so.x, want));
+  CK(dalloc(c, &so.y, want));
+  CK(dalloc(c, &so.z, want));
+  CK(dalloc(c, &so.vx, want));
+  CK(dalloc(c, &so.vy, want));
+  CK(dalloc(c, &so.vz, want));
+  CK(dalloc(c, &so.m, want));
+  CK(dalloc(c, &so.h, want));
+  CK(dalloc(c, &so.dt, want));
+  CK(dalloc(c, &so.f, want));
+  CK(dalloc(c, &so.id, want));
+  CK(dalloc(c, &so.act, want));
+  CK(dalloc(c, &so.orig, want));
+  CK(dalloc(c, &c->act_list, want));
+  CK(dalloc(c, &t.lo, nodes));
+  CK(dalloc(c, &t.hi, nodes));
+  CK(dalloc(c, &c->params, 1));
+  CK(dalloc(c, &c->mm, 8));
+  CK(dalloc(c, &c->dstats, 1));
+  CK(dalloc(c, &c->latched, 1));
+  CK(dalloc(c, &c->work, 8));
+  CK(dalloc(c, &c->pairs, pc));
+  CK(dalloc(c, &c->head, want));
+  CK(dalloc(c, &c->mult, want));
+  CK(dalloc(c, &c->next, 2 * pc));
+  CK(dalloc(c, &c->pflags, pc));
+  CK(dalloc(c, &c->cons_partial, 4 * conserved_blocks()));
+  CK(dalloc(c, &c->cons, 8));
+  CK(cudaMemsetAsync(c->head, 0xFF, want * sizeof(int32_t), c->stream));
+  CK(cudaMemsetAsync(c->mult, 0, want * sizeof(int32_t), c->stream));
+  CK(cudaMemsetAsync(c->latched, 0, sizeof(unsigned), c->stream));
+  c->cap = want;
+  c->pair_cap = pc;
+  return SIDM_OK;
+}
+
+cudaMemcpyKind copy_kind_in(int ptr_kind) {
+  return ptr_kind == SIDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind copy_kind_out(int ptr_kind) {
+  return ptr_kind == SIDM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int status_from_bits(unsigned bits) {
+  if (bits & ST_ERR_MASK) return SIDM_ERR_DEVICE_LIMIT;
+  int w = 0;
+  if (bits & ST_H_NONCONV) w |= SIDM_WARN_H_NOT_CONVERGED;
+  if (bits & ST_P_GE_1) w |= SIDM_WARN_P_GE_1;
+  if (bits & ST_DIR_FAIL) w |= SIDM_WARN_DIRECTION;
+  return w;
+}
+
+// Waits for the stream and returns (and clears) the latched device status.
+int wait_and_collect(sidm_ctx* c) {
+  CK(cudaMemcpyAsync(c->h_latched, c->latched, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemsetAsync(c->latched, 0, sizeof(unsigned), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return status_from_bits(*c->h_latched);
+}
+
+}  // namespace
+
+extern "C" {
+
+void sidm_default_config(sidm_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->n_ngb = 32;
+  cfg->ngb_tol = 5;
+  cfg->c_sidm = 0.1;
+  cfg->box = 0.0;
+  cfg->kernel = SIDM_KERNEL_CUBIC;
+  cfg->precision = SIDM_FP64_PLAIN;
+  cfg->fixed_h = 0.0;
+  cfg->n_max = 0;
+  cfg->pair_capacity = 0;
+  cfg->stream = nullptr;
+  cfg->device = -1;
+}
+
+int sidm_create(const sidm_config* cfg, sidm_ctx** out) {
+  if (!cfg || !out) return SIDM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cfg->n_ngb < 1 || cfg->ngb_tol < 0 || cfg->ngb_tol >= cfg->n_ngb ||
+      cfg->n_ngb + cfg->ngb_tol + 2 > 256 || !(cfg->c_sidm > 0.0) || !(cfg->box >= 0.0) ||
+      !std::isfinite(cfg->box) || (cfg->kernel != SIDM_KERNEL_CUBIC && cfg->kernel != SIDM_KERNEL_TOPHAT) ||
+      cfg->precision != SIDM_FP64_PLAIN || !(cfg->fixed_h >= 0.0) || cfg->n_max < 0 ||
+      cfg->pair_capacity < 0)
+    return SIDM_ERR_INVALID_ARG;
+  sidm_ctx* c = new (std::nothrow) sidm_ctx();
+  if (!c) return SIDM_ERR_OOM;
+  c->cfg = *cfg;
+  int dev = cfg->device;
+  if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) { delete c; return SIDM_ERR_CUDA; }
+  c->device = dev;
+  DeviceGuard g(dev);
+  if (cudaFree(nullptr) != cudaSuccess) { delete c; return SIDM_ERR_CUDA; }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cfg->stream) {
+    c->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return SIDM_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  if (cudaMallocHost(&c->h_stats, sizeof(DevStats)) != cudaSuccess ||
+      cudaMallocHost(&c->h_cons, 8 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&c->h_latched, sizeof(unsigned)) != cudaSuccess) {
+    sidm_destroy(c);
+    return SIDM_ERR_OOM;
+  }
+  if (cfg->profile) {
+    for (int k = 0; k <= SIDM_N_PHASES; ++k)
+      if (cudaEventCreate(&c->ev[k]) != cudaSuccess) { sidm_destroy(c); return SIDM_ERR_CUDA; }
+    c->have_events = true;
+  }
+  if (cfg->n_max > 0) {
+    const int r = ensure_capacity(c, cfg->n_max);
+    if (r != SIDM_OK) { sidm_destroy(c); return r; }
+  }
+  *out = c;
+  return SIDM_OK;
+}
+
+int sidm_phase_times(sidm_ctx* c, float* ms, int n) {
+  if (!c || !ms || n < 0 || !c->have_events || !c->timed_step) return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  CK(cudaEventSynchronize(c->ev[SIDM_N_PHASES]));
+  for (int k = 0; k < n && k < SIDM_N_PHASES; ++k) CK(cudaEventElapsedTime(&ms[k], c->ev[k], c->ev[k + 1]));
+  return SIDM_OK;
+}
+
+int64_t sidm_kernel_launches(const sidm_ctx* c) { return c ? c->launches : -1; }
+
+int sidm_set_particles(sidm_ctx* c, int64_t n, const double* pos, const double* vel,
+                       const double* mass, double mass_scalar, const uint32_t* ids, int ptr_kind) {
+  if (!c || n < 0 || n > (int64_t)1 << 31 || (n > 0 && (!pos || !vel || !ids)) ||
+      (ptr_kind != SIDM_HOST && ptr_kind != SIDM_DEVICE) || (!mass && !(mass_scalar > 0.0)))
+    return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  int r = ensure_capacity(c, n);
+  if (r != SIDM_OK) return r;
+  const cudaMemcpyKind k = copy_kind_in(ptr_kind);
+  if (n > 0) {
+    CK(cudaMemcpyAsync(c->pos, pos, 3 * n * sizeof(double), k, c->stream));
+    CK(cudaMemcpyAsync(c->vel, vel, 3 * n * sizeof(double), k, c->stream));
+    CK(cudaMemcpyAsync(c->ids, ids, n * sizeof(uint32_t), k, c->stream));
+    if (mass) CK(cudaMemcpyAsync(c->mass, mass, n * sizeof(double), k, c->stream));
+    else fill(c->mass, n, mass_scalar, c->stream);
+    fill(c->h_user, n, 0.0, c->stream);
+    fill(c->dtlim, n, INFINITY, c->stream);
+  }
+  // periodic box: every coordinate in [0, box)
+  if (c->cfg.box > 0.0 && n > 0) {
+    launch_bbox(c->pos, n, c->mm, c->stream);
+    unsigned long long hm[6];
+    CK(cudaMemcpyAsync(hm, c->mm, sizeof(hm), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k2 = 0; k2 < 3; ++k2) {
+      const double lo = ordered_to_dbl(hm[k2]), hi = ordered_to_dbl(hm[3 + k2]);
+      if (!(lo >= 0.0) || !(hi < c->cfg.box)) {
+        c->loaded = false;
+        return SIDM_ERR_INVALID_ARG;
+      }
+    }
+  }
+  CK(cudaGetLastError());
+  c->n = n;
+  c->loaded = true;
+  return SIDM_OK;
+}
+
+int sidm_set_velocities(sidm_ctx* c, const double* vel, int ptr_kind) {
+  if (!c || !c->loaded || !vel || (ptr_kind != SIDM_HOST && ptr_kind != SIDM_DEVICE))
+    return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (c->n > 0)
+    CK(cudaMemcpyAsync(c->vel, vel, 3 * c->n * sizeof(double), copy_kind_in(ptr_kind), c->stream));
+  return SIDM_OK;
+}
+
+int sidm_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins, double dt_max,
+              const sidm_sigma_model* sigma, uint64_t seed, sidm_step_stats* stats) {
+  if (!c || !sigma) return SIDM_ERR_INVALID_ARG;
+  if (!c->loaded) return SIDM_ERR_NOT_READY;
+  if (!(dt_max > 0.0) || !std::isfinite(dt_max) || !(sigma->sigma0 >= 0.0) ||
+      !std::isfinite(sigma->sigma0) ||
+      (sigma->kind != SIDM_SIGMA_CONST && sigma->kind != SIDM_SIGMA_YUKAWA) ||
+      (sigma->kind == SIDM_SIGMA_YUKAWA && !(sigma->w > 0.0)))
+    return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  const int64_t n = c->n;
+  cudaStream_t s = c->stream;
+  if (n > 0) {
+    if (active_mask)
+      CK(cudaMemcpyAsync(c->act, active_mask, n, is_device_ptr(active_mask)
+                                                      ? cudaMemcpyDeviceToDevice
+                                                      : cudaMemcpyHostToDevice, s));
+    else
+      CK(cudaMemsetAsync(c->act, 1, n, s));
+    if (dt_bins)
+      CK(cudaMemcpyAsync(c->bins, dt_bins, n, is_device_ptr(dt_bins) ? cudaMemcpyDeviceToDevice
+                                                                     : cudaMemcpyHostToDevice, s));
+    else
+      CK(cudaMemsetAsync(c->bins, 0, n, s));
+  }
+  CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), s));
+  CK(cudaMemsetAsync(c->work, 0, 8 * sizeof(int), s));
+  int64_t& L = c->launches;
+  if (stats) L += launch_conserved(c->vel, c->mass, n, c->cons_partial, c->cons, s);
+  const bool prof = c->have_events && n > 0;
+  auto mark = [&](int k) {
+    if (prof) cudaEventRecord(c->ev[k], s);
+  };
+  c->timed_step = prof;
+  if (n > 0) {
+    mark(0);
+    L += launch_bbox(c->pos, n, c->mm, s);
+    L += launch_params(c->mm, c->params, c->cfg.box, n, c->cfg.n_ngb, s);
+    L += launch_keys(c->pos, n, c->params, c->cfg.box, c->keys, c->vals, s);
+    mark(1);
+    L += radix_sort_pairs(c->keys, c->vals, c->keys_alt, c->vals_alt, n, 30, c->sort_tmp, s);
+    mark(2);
+    L += launch_permute(c->vals, n, c->pos, c->vel, c->mass, c->ids, c->act, c->bins, dt_max,
+                        c->so, c->act_list, c->dstats, s);
+    Tree t = c->tree;
+    t.levels = tree_levels_for(n, t.count);
+    int64_t off = 0;
+    for (int l = 0; l < t.levels; ++l) { t.offset[l] = off; off += t.count[l]; }
+    L += launch_tree(c->so, n, t, s);
+    mark(3);
+    L += launch_search(c->so, t, n, c->act_list, c->params, c->cfg.box, c->cfg.n_ngb,
+                       c->cfg.ngb_tol, c->cfg.fixed_h, c->h_user, c->dstats, c->work, s);
+    mark(4);
+    PairArgs pa;
+    pa.kernel = c->cfg.kernel;
+    pa.sigma_kind = sigma->kind;
+    pa.sigma0 = sigma->sigma0;
+    pa.w = sigma->kind == SIDM_SIGMA_YUKAWA ? sigma->w : 1.0;
+    pa.c_sidm = c->cfg.c_sidm;
+    pa.box = c->cfg.box;
+    pa.seed = seed;
+    pa.step = (uint32_t)c->step;
+    pa.pair_cap = c->pair_cap;
+    L += launch_pairs(c->so, t, n, c->act_list, pa, c->pairs, c->dtlim, c->dstats, c->work + 1, s);
+    mark(5);
+    L += launch_resolve(c->pairs, c->pair_cap, c->vel, c->mass, c->head, c->next, c->pflags,
+                        c->mult, seed, (uint32_t)c->step, c->dstats, s);
+    mark(6);
+  }
+  latch_kernel<<<1, 32, 0, s>>>(c->dstats, c->latched);
+  L += 1;
+  CK(cudaGetLastError());
+  c->step += 1;
+  if (!stats) return SIDM_OK;
+  L += launch_conserved(c->vel, c->mass, n, c->cons_partial, c->cons + 4, s);
+  CK(cudaMemcpyAsync(c->h_stats, c->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->h_cons, c->cons, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  const int st = wait_and_collect(c);
+  const DevStats& d = *c->h_stats;
+  std::memset(stats, 0, sizeof(*stats));
+  stats->n_active = (int64_t)d.n_active;
+  stats->n_candidate_pairs = (int64_t)d.n_cand;
+  stats->n_accepted = (int64_t)d.n_acc;
+  stats->n_rounds = (int64_t)d.n_rounds;
+  stats->n_p_ge_1 = (int64_t)d.n_pge1;
+  stats->n_h_nonconv = (int64_t)d.n_nonconv;
+  stats->n_dir_fail = (int64_t)d.n_dirfail;
+  stats->max_multiplicity = (int64_t)d.max_mult;
+  stats->sum_p = d.sum_p;
+  stats->e_before = c->h_cons[0];
+  stats->p_before[0] = c->h_cons[1];
+  stats->p_before[1] = c->h_cons[2];
+  stats->p_before[2] = c->h_cons[3];
+  stats->e_after = c->h_cons[4];
+  stats->p_after[0] = c->h_cons[5];
+  stats->p_after[1] = c->h_cons[6];
+  stats->p_after[2] = c->h_cons[7];
+  stats->status = st;
+  return st;
+}
+
+int sidm_sync(sidm_ctx* c) {
+  if (!c) return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  return wait_and_collect(c);
+}
+
+int sidm_get_particles(sidm_ctx* c, double* vel_out, double* h_out, int ptr_kind) {
+  if (!c || !c->loaded || (!vel_out && !h_out) || (ptr_kind != SIDM_HOST && ptr_kind != SIDM_DEVICE))
+    return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  const cudaMemcpyKind k = copy_kind_out(ptr_kind);
+  if (c->n > 0) {
+    if (vel_out) CK(cudaMemcpyAsync(vel_out, c->vel, 3 * c->n * sizeof(double), k, c->stream));
+    if (h_out) CK(cudaMemcpyAsync(h_out, c->h_user, c->n * sizeof(double), k, c->stream));
+  }
+  return wait_and_collect(c);
+}
+
+int sidm_timestep_limits(sidm_ctx* c, double* out, int ptr_kind) {
+  if (!c || !c->loaded || !out || (ptr_kind != SIDM_HOST && ptr_kind != SIDM_DEVICE))
+    return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (c->n > 0)
+    CK(cudaMemcpyAsync(out, c->dtlim, c->n * sizeof(double), copy_kind_out(ptr_kind), c->stream));
+  return wait_and_collect(c);
+}
+
+int sidm_get_pairs(sidm_ctx* c, uint32_t* ab, uint64_t* ord, int64_t cap, int64_t* n_out) {
+  if (!c || !c->loaded || cap < 0 || (cap > 0 && (!ab || !ord))) return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  CK(cudaMemcpyAsync(c->h_stats, c->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const int64_t total = (int64_t)c->h_stats->n_acc;
+  const int64_t stored = std::min<int64_t>(total, c->pair_cap);
+  std::vector<PairRec> h(stored);
+  if (stored > 0)
+    CK(cudaMemcpy(h.data(), c->pairs, stored * sizeof(PairRec), cudaMemcpyDeviceToHost));
+  std::sort(h.begin(), h.end(), [](const PairRec& x, const PairRec& y) {
+    if (x.ord != y.ord) return x.ord < y.ord;
+    if (x.a != y.a) return x.a < y.a;
+    return x.b < y.b;
+  });
+  for (int64_t k = 0; k < stored && k < cap; ++k) {
+    ab[2 * k] = h[k].a;
+    ab[2 * k + 1] = h[k].b;
+    ord[k] = h[k].ord;
+  }
+  if (n_out) *n_out = total;
+  return total > c->pair_cap ? SIDM_ERR_DEVICE_LIMIT : wait_and_collect(c);
+}
+
+int sidm_get_step(const sidm_ctx* c, uint64_t* step) {
+  if (!c || !step) return SIDM_ERR_INVALID_ARG;
+  *step = c->step;
+  return SIDM_OK;
+}
+
+int sidm_set_step(sidm_ctx* c, uint64_t step) {
+  if (!c) return SIDM_ERR_INVALID_ARG;
+  c->step = step;
+  return SIDM_OK;
+}
+
+const char* sidm_error_string(int status) {
+  switch (status) {
+    case SIDM_OK: return "ok";
+    case SIDM_WARN_H_NOT_CONVERGED: return "warning: h bisection hit its evaluation cap";
+    case SIDM_WARN_P_GE_1: return "warning: a pair probability reached 1 (timestep above the Eq. 9 limit)";
+    case SIDM_WARN_DIRECTION: return "warning: a direction draw exhausted its tries";
+    case SIDM_ERR_INVALID_ARG: return "invalid argument";
+    case SIDM_ERR_OOM: return "out of device memory";
+    case SIDM_ERR_CUDA: return "CUDA error";
+    case SIDM_ERR_DEVICE_LIMIT: return "a bounded device loop or buffer gave up (search capacity, traversal stack, pair buffer or resolver rounds); the step is not valid";
+    case SIDM_ERR_NOT_READY: return "no particles loaded";
+    default:
+      if (status > 0) return "several warnings";
+      return "unknown status";
+  }
+}
+
+void sidm_destroy(sidm_ctx* c) {
+  if (!c) return;
+  {
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_buffers(c);
+    if (c->h_stats) cudaFreeHost(c->h_stats);
+    if (c->h_cons) cudaFreeHost(c->h_cons);
+    if (c->h_latched) cudaFreeHost(c->h_latched);
+    for (int k = 0; k <= SIDM_N_PHASES; ++k)
+      if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  }
+  delete c;
+}
+
+}  // extern "C"

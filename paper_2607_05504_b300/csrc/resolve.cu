@@ -1,0 +1,163 @@
+// Application of the accepted pairs (Sec. 4.1 kick, Sec. 4.4 multiple
+// scatters with immediate updates).
+//
+// The canonical result is the sequential pass over the accepted pairs in
+// ascending (ord, a, b) order, each kick reading the velocities left by the
+// earlier ones.  The resolver reaches the same result in rounds: in a round
+// every unapplied pair that precedes all other unapplied pairs at both of its
+// particles is applied.  Such pairs share no particle, and every particle
+// still meets its pairs in key order, so the velocities equal those of the
+// sequential pass bit for bit.  (This is the single-device counterpart of the
+// paper's rule that no particle is modified concurrently, Sec. 4.5.)
+//
+// Direction: Marsaglia (1972) -- x1, x2 uniform in (-1, 1) from the Philox
+// streams 1, 2, ... of the pair, accepted when 0 < s = x1^2 + x2^2 < 1, then
+// e = (2 x1 sqrt(1-s), 2 x2 sqrt(1-s), 1 - 2 s).
+// Kick: v_com = (m_a v_a + m_b v_b)/M, g = |v_a - v_b|,
+//       v_a' = v_com + (m_b g / M) e,  v_b' = v_com - (m_a g / M) e.
+#include "sidm_internal.cuh"
+
+namespace sidm {
+
+namespace {
+
+constexpr int RT = 1024;
+
+__device__ __forceinline__ bool key_less(const PairRec& x, const PairRec& y) {
+  if (x.ord != y.ord) return x.ord < y.ord;
+  if (x.a != y.a) return x.a < y.a;
+  return x.b < y.b;
+}
+
+// true if no other unapplied pair at particle e precedes pair p
+__device__ bool first_at(int64_t p, const PairRec& rp, int32_t e, const int32_t* head,
+                         const int32_t* next, const PairRec* pairs, const volatile uint8_t* flags) {
+  for (int32_t slot = head[e]; slot >= 0; slot = next[slot]) {
+    const int64_t q = slot >> 1;
+    if (q == p || (flags[q] & 1)) continue;
+    if (key_less(pairs[q], rp)) return false;
+  }
+  return true;
+}
+
+__device__ void kick(const PairRec& r, double* vel, const double* mass, uint32_t k0, uint32_t k1,
+                     uint32_t step, unsigned* dirfail) {
+  double e0 = 0.0, e1 = 0.0, e2 = 1.0;
+  bool found = false;
+  for (uint32_t t = 0; t < DIRECTION_TRIES && !found; ++t) {
+    const U4 w = philox10(k0, k1, step, 1u + t, r.a, r.b);
+    const double x1 = 2.0 * unit53(w.x, w.y) - 1.0;
+    const double x2 = 2.0 * unit53(w.z, w.w) - 1.0;
+    const double s = x1 * x1 + x2 * x2;
+    if (s > 0.0 && s < 1.0) {
+      const double k = 2.0 * sqrt(1.0 - s);
+      e0 = x1 * k;
+      e1 = x2 * k;
+      e2 = 1.0 - 2.0 * s;
+      found = true;
+    }
+  }
+  if (!found) atomicAdd(dirfail, 1u);
+  double* va = vel + 3 * (int64_t)r.ia;
+  double* vb = vel + 3 * (int64_t)r.ib;
+  const double ma = mass[r.ia], mb = mass[r.ib];
+  const double M = ma + mb;
+  const double ax = va[0], ay = va[1], az = va[2];
+  const double bx = vb[0], by = vb[1], bz = vb[2];
+  const double cx = ((ma * ax) + (mb * bx)) / M;
+  const double cy = ((ma * ay) + (mb * by)) / M;
+  const double cz = ((ma * az) + (mb * bz)) / M;
+  const double dx = ax - bx, dy = ay - by, dz = az - bz;
+  const double g = sqrt((dx * dx + dy * dy) + dz * dz);
+  const double fa = (mb * g) / M, fb = (ma * g) / M;
+  va[0] = cx + fa * e0;
+  va[1] = cy + fa * e1;
+  va[2] = cz + fa * e2;
+  vb[0] = cx - fb * e0;
+  vb[1] = cy - fb * e1;
+  vb[2] = cz - fb * e2;
+}
+
+__global__ void __launch_bounds__(RT) resolve_kernel(const PairRec* __restrict__ pairs,
+                                                     int64_t cap, double* vel,
+                                                     const double* __restrict__ mass,
+                                                     int32_t* head, int32_t* next, uint8_t* flags,
+                                                     int32_t* mult, uint32_t k0, uint32_t k1,
+                                                     uint32_t step, DevStats* st) {
+  __shared__ unsigned s_dirfail;
+  __shared__ int s_max;
+  const int t = threadIdx.x;
+  if (t == 0) { s_dirfail = 0; s_max = 0; }
+  const unsigned long long nall = st->n_acc;
+  if (nall > (unsigned long long)cap) {
+    if (t == 0) atomicOr(&st->status, (unsigned)ST_ERR_PAIR_OVERFLOW);
+    return;
+  }
+  const int64_t na = (int64_t)nall;
+  for (int64_t p = t; p < na; p += RT) {
+    flags[p] = 0;
+    const int32_t ea = pairs[p].ia, eb = pairs[p].ib;
+    next[2 * p] = atomicExch(&head[ea], (int32_t)(2 * p));
+    next[2 * p + 1] = atomicExch(&head[eb], (int32_t)(2 * p + 1));
+    atomicAdd(&mult[ea], 1);
+    atomicAdd(&mult[eb], 1);
+  }
+  __syncthreads();
+  int rounds = 0;
+  bool done = false;
+  for (; rounds < RESOLVE_MAX_ROUNDS; ++rounds) {
+    int left = 0;
+    for (int64_t p = t; p < na; p += RT) {
+      if (flags[p] & 1) continue;
+      left = 1;
+      const PairRec rp = pairs[p];
+      if (first_at(p, rp, rp.ia, head, next, pairs, flags) &&
+          first_at(p, rp, rp.ib, head, next, pairs, flags))
+        flags[p] = 2;
+    }
+    if (!__syncthreads_or(left)) { done = true; break; }
+    for (int64_t p = t; p < na; p += RT) {
+      if (flags[p] == 2) {
+        kick(pairs[p], vel, mass, k0, k1, step, &s_dirfail);
+        flags[p] = 1;
+      }
+    }
+    __syncthreads();
+  }
+  if (!done) {
+    // the cap was reached with pairs left
+    int left = 0;
+    for (int64_t p = t; p < na; p += RT) left |= !(flags[p] & 1);
+    if (__syncthreads_or(left) && t == 0) atomicOr(&st->status, (unsigned)ST_ERR_ROUNDS);
+  }
+  int mm = 0;
+  for (int64_t p = t; p < na; p += RT) mm = max(mm, max(mult[pairs[p].ia], mult[pairs[p].ib]));
+  atomicMax(&s_max, mm);
+  __syncthreads();
+  for (int64_t p = t; p < na; p += RT) {
+    head[pairs[p].ia] = -1;
+    head[pairs[p].ib] = -1;
+    mult[pairs[p].ia] = 0;
+    mult[pairs[p].ib] = 0;
+  }
+  if (t == 0) {
+    st->n_rounds = (unsigned long long)rounds;
+    st->max_mult = (unsigned long long)s_max;
+    if (s_dirfail) {
+      st->n_dirfail = s_dirfail;
+      atomicOr(&st->status, (unsigned)ST_DIR_FAIL);
+    }
+  }
+}
+
+}  // namespace
+
+int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* mass,
+                    int32_t* head, int32_t* next, uint8_t* flags, int32_t* mult, uint64_t seed,
+                    uint32_t step, DevStats* st, cudaStream_t s) {
+  resolve_kernel<<<1, RT, 0, s>>>(pairs, pair_cap, vel, mass, head, next, flags, mult,
+                                  (uint32_t)seed, (uint32_t)(seed >> 32), step, st);
+  return 1;
+}
+
+}  // namespace sidm

@@ -1,0 +1,220 @@
+// Internal declarations of the SIDM scattering-step library: device data
+// layout, shared device helpers and the launchers of every kernel.
+//
+// The library is compiled with -fmad=false: every FP64 expression on the
+// exact path is one IEEE round-to-nearest operation per operator, in the
+// order written, so that its results are a function of the inputs alone.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sidm.h"
+
+namespace sidm {
+
+// ------------------------------------------------------------------ limits
+constexpr int WARP = 32;
+constexpr int LEAF = 32;                 // particles per tree leaf (one per lane)
+constexpr int MAX_LEVELS = 8;            // 32-ary levels: 32^8 leaves >> any n
+constexpr int BISECT_MAX_EVALS = 128;    // neighbour-count evaluations per particle
+constexpr int SEARCH_CAP = 1024;         // gathered candidates per query (shared memory)
+constexpr int SEARCH_STACK = 256;        // traversal stack per warp
+constexpr int RADIUS_MAX_ITERS = 24;     // gather-radius adjustments per query
+constexpr int RESOLVE_MAX_ROUNDS = 4096; // resolver rounds
+constexpr int DIRECTION_TRIES = 64;      // Marsaglia rejection tries
+
+// device status bits (latched per step)
+enum : uint32_t {
+  ST_H_NONCONV = 1u,
+  ST_P_GE_1 = 2u,
+  ST_DIR_FAIL = 4u,
+  ST_ERR_SEARCH_CAP = 1u << 8,    // a query needed more than SEARCH_CAP candidates
+  ST_ERR_STACK = 1u << 9,         // traversal stack overflow
+  ST_ERR_RADIUS = 1u << 10,       // gather radius adjustment did not settle
+  ST_ERR_PAIR_OVERFLOW = 1u << 11,// accepted-pair buffer full
+  ST_ERR_ROUNDS = 1u << 12,       // resolver did not finish within its round cap
+  ST_ERR_MASK = 0xFF00u
+};
+
+// Step parameters computed on the device (no host round trip).
+struct StepParams {
+  double lo[3], hi[3];     // bounding box of the positions
+  double l_ext;            // box side (periodic) or largest extent (open)
+  double h0;               // bisection start radius
+  float centre[3];         // key transform centre (open boundaries)
+  float key_scale;         // asinh scale s
+  float key_inv_norm;      // 1 / asinh(R / s)
+  float key_radius;        // R
+};
+
+// Device counters of one step.
+struct DevStats {
+  unsigned long long n_active, n_cand, n_acc, n_rounds, n_pge1, n_nonconv, n_dirfail, max_mult;
+  double sum_p;
+  unsigned int status;
+  unsigned int pad;
+};
+
+struct PairRec {
+  unsigned long long ord;  // words 2,3 of the stream-0 draw
+  uint32_t a, b;           // ids, a < b
+  int32_t ia, ib;          // user-order indices of the a- and b-particle
+};
+
+// ------------------------------------------------------------------ Philox
+// Philox-4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds, each two
+// 32x32 -> 64-bit products of counter words 0 and 2 with fixed multipliers;
+// the high halves are xor-ed with counter words 1, 3 and the key, the key is
+// advanced by two Weyl increments between rounds.
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox10(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
+                                       uint32_t c2, uint32_t c3) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// 53 random bits -> [0, 1), exact in FP64: top 27 bits of one word, top 26 of the other.
+__device__ __forceinline__ double unit53(uint32_t a, uint32_t b) {
+  return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * 0x1.0p-53;
+}
+
+// ---------------------------------------------------------------- geometry
+// Minimum-image component of x_j - x_i (box > 0), one rounding per operation.
+__device__ __forceinline__ double min_image(double d, double box, double half) {
+  if (box > 0.0) {
+    if (d > half) d = d - box;
+    else if (d < -half) d = d + box;
+  }
+  return d;
+}
+
+// Squared separation in the fixed order (dx dx + dy dy) + dz dz.
+__device__ __forceinline__ double sep2(double xi, double yi, double zi, double xj, double yj,
+                                       double zj, double box, double half) {
+  const double dx = min_image(xj - xi, box, half);
+  const double dy = min_image(yj - yi, box, half);
+  const double dz = min_image(zj - zi, box, half);
+  return (dx * dx + dy * dy) + dz * dz;
+}
+
+// Kernel normalisation K / h^3 with K = 8/pi (cubic spline) or 3/(4 pi) (top-hat).
+__device__ __forceinline__ double kernel_norm(int kernel, double h) {
+  const double k = kernel == SIDM_KERNEL_TOPHAT ? 3.0 / (4.0 * 3.141592653589793)
+                                                : 8.0 / 3.141592653589793;
+  return k / ((h * h) * h);
+}
+
+// Kernel shape f(q), q = r/h < 1: cubic spline 1 - 6q^2 + 6q^3 (q <= 1/2),
+// 2(1-q)^3 (q > 1/2); top-hat 1.
+__device__ __forceinline__ double kernel_shape(int kernel, double q) {
+  if (kernel == SIDM_KERNEL_TOPHAT) return 1.0;
+  if (q <= 0.5) return (1.0 - 6.0 * (q * q)) + 6.0 * ((q * q) * q);
+  const double u = 1.0 - q;
+  return 2.0 * ((u * u) * u);
+}
+
+__device__ __forceinline__ double sigma_over_m(int kind, double s0, double w, double v) {
+  if (kind == SIDM_SIGMA_YUKAWA) {
+    const double t = 1.0 + (v * v) / (w * w);
+    return s0 / (t * t);
+  }
+  return s0;
+}
+
+// Order-preserving map of a double to uint64 (for atomicMin/atomicMax).
+__device__ __forceinline__ unsigned long long dbl_to_ordered(double x) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__host__ __device__ inline double ordered_to_dbl(unsigned long long u) {
+  u = (u >> 63) ? (u & 0x7FFFFFFFFFFFFFFFull) : ~u;
+  double d;
+  memcpy(&d, &u, sizeof(d));
+  return d;
+}
+
+// --------------------------------------------------------- device buffers
+struct Tree {
+  int levels;                 // number of levels (level 0 = leaves)
+  int64_t count[MAX_LEVELS];  // nodes per level
+  int64_t offset[MAX_LEVELS]; // first node of each level in lo/hi
+  float4* lo;                 // per node: min corner (w unused), rounded down
+  float4* hi;                 // per node: max corner, rounded up
+};
+
+struct Sorted {               // particle state in key order
+  double *x, *y, *z;
+  double *vx, *vy, *vz;
+  double *m;
+  double *h;                  // h of active particles (this step)
+  double *dt;                 // dt_i of the particle
+  float4* f;                  // FP32 copy of the position (w = 0)
+  uint32_t* id;
+  uint8_t* act;
+  int32_t* orig;              // user-order index
+};
+
+// ---------------------------------------------------------------- launchers
+// sort.cu
+size_t radix_sort_temp_bytes(int64_t n);
+int radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_alt, int32_t* vals_alt,
+                      int64_t n, int key_bits, void* temp, cudaStream_t s);
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
+                        cudaStream_t s);
+size_t exclusive_scan_temp_bytes(int64_t n);
+
+// build.cu
+int launch_bbox(const double* pos, int64_t n, unsigned long long* mm, cudaStream_t s);
+int launch_params(const unsigned long long* mm, StepParams* p, double box, int64_t n,
+                   int n_ngb, cudaStream_t s);
+int launch_keys(const double* pos, int64_t n, const StepParams* p, double box, uint32_t* keys,
+                 int32_t* vals, cudaStream_t s);
+int launch_permute(const int32_t* perm, int64_t n, const double* pos, const double* vel,
+                    const double* mass, const uint32_t* ids, const uint8_t* act,
+                    const int8_t* bins, double dt_max, Sorted so, int32_t* act_list,
+                    DevStats* st, cudaStream_t s);
+int launch_tree(const Sorted& so, int64_t n, Tree& t, cudaStream_t s);
+int tree_levels_for(int64_t n, int64_t count[MAX_LEVELS]);
+
+// search.cu
+int launch_search(const Sorted& so, const Tree& t, int64_t n, const int32_t* act_list,
+                   const StepParams* p, double box, int n_ngb, int tol, double fixed_h,
+                   double* h_user, DevStats* st, int* work, cudaStream_t s);
+
+// pairs.cu
+struct PairArgs {
+  int kernel;
+  int sigma_kind;
+  double sigma0, w;
+  double c_sidm;
+  double box;
+  uint64_t seed;
+  uint32_t step;
+  int64_t pair_cap;
+};
+int launch_pairs(const Sorted& so, const Tree& t, int64_t n, const int32_t* act_list,
+                  const PairArgs& a, PairRec* pairs, double* dtlim_user, DevStats* st,
+                  int* work, cudaStream_t s);
+
+// resolve.cu
+int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* mass,
+                    int32_t* head, int32_t* next, uint8_t* flags, int32_t* mult,
+                    uint64_t seed, uint32_t step, DevStats* st, cudaStream_t s);
+int launch_sort_pairs_for_output(PairRec* pairs, int64_t n, cudaStream_t s);
+
+// stats.cu
+int launch_conserved(const double* vel, const double* mass, int64_t n, double* partial,
+                      double* out4, cudaStream_t s);
+int conserved_blocks();
+
+}  // namespace sidm

@@ -1,0 +1,327 @@
+"""Python binding of libsidm.so (include/sidm.h) -- argument marshalling only.
+
+Every step of the scattering path runs in the CUDA library; this module only
+converts numpy arrays / torch tensors to pointers and status codes to
+exceptions.  It never computes any part of the step itself and has no CPU
+fallback: if the library cannot be loaded, :func:`lib` raises.
+
+The functions ``sidm_*`` mirror the C entry points one to one; :class:`Context`
+is a convenience wrapper that owns one ``sidm_ctx``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+HOST, DEVICE = 0, 1
+KERNEL_CUBIC, KERNEL_TOPHAT = 0, 1
+SIGMA_CONST, SIGMA_YUKAWA = 0, 1
+
+OK = 0
+WARN_H_NOT_CONVERGED, WARN_P_GE_1, WARN_DIRECTION = 1, 2, 4
+ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_DEVICE_LIMIT, ERR_NOT_READY = -1, -2, -3, -4, -5
+
+
+class SidmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {error_string(status)} (status {status})")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("n_ngb", C.c_int), ("ngb_tol", C.c_int), ("c_sidm", C.c_double),
+                ("box", C.c_double), ("kernel", C.c_int), ("precision", C.c_int),
+                ("fixed_h", C.c_double), ("n_max", C.c_int64), ("pair_capacity", C.c_int64),
+                ("stream", C.c_void_p), ("device", C.c_int), ("profile", C.c_int)]
+
+
+class SigmaModel(C.Structure):
+    _fields_ = [("kind", C.c_int), ("sigma0", C.c_double), ("w", C.c_double)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("n_active", C.c_int64), ("n_candidate_pairs", C.c_int64),
+                ("n_accepted", C.c_int64), ("n_rounds", C.c_int64), ("n_p_ge_1", C.c_int64),
+                ("n_h_nonconv", C.c_int64), ("n_dir_fail", C.c_int64),
+                ("max_multiplicity", C.c_int64), ("sum_p", C.c_double),
+                ("e_before", C.c_double), ("e_after", C.c_double),
+                ("p_before", C.c_double * 3), ("p_after", C.c_double * 3),
+                ("status", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d["p_before"] = list(self.p_before)
+        d["p_after"] = list(self.p_after)
+        return d
+
+
+# names of every entry point declared in include/sidm.h
+ENTRY_POINTS = ("sidm_default_config", "sidm_create", "sidm_set_particles",
+                "sidm_set_velocities", "sidm_step", "sidm_sync", "sidm_get_particles",
+                "sidm_timestep_limits", "sidm_get_pairs", "sidm_get_step", "sidm_set_step",
+                "sidm_phase_times", "sidm_kernel_launches", "sidm_error_string", "sidm_destroy")
+
+N_PHASES = 6
+PHASES = ("keys", "sort", "structure", "search", "pairs", "resolve")
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libsidm.so (building it first if sources are newer and nvcc exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not _build.up_to_date():
+            if os.path.exists(_build.NVCC):
+                _build.build()
+            elif not os.path.exists(path):
+                raise ImportError(f"libsidm.so not found at {path} and nvcc unavailable")
+        L = C.CDLL(path)
+        vp, i64, dp = C.c_void_p, C.c_int64, C.c_double
+        L.sidm_default_config.argtypes = [C.POINTER(Config)]
+        L.sidm_default_config.restype = None
+        L.sidm_create.argtypes = [C.POINTER(Config), C.POINTER(vp)]
+        L.sidm_set_particles.argtypes = [vp, i64, vp, vp, vp, dp, vp, C.c_int]
+        L.sidm_set_velocities.argtypes = [vp, vp, C.c_int]
+        L.sidm_step.argtypes = [vp, vp, vp, dp, C.POINTER(SigmaModel), C.c_uint64,
+                                C.POINTER(StepStats)]
+        L.sidm_sync.argtypes = [vp]
+        L.sidm_get_particles.argtypes = [vp, vp, vp, C.c_int]
+        L.sidm_timestep_limits.argtypes = [vp, vp, C.c_int]
+        L.sidm_get_pairs.argtypes = [vp, vp, vp, i64, C.POINTER(i64)]
+        L.sidm_get_step.argtypes = [vp, C.POINTER(C.c_uint64)]
+        L.sidm_set_step.argtypes = [vp, C.c_uint64]
+        L.sidm_phase_times.argtypes = [vp, C.POINTER(C.c_float), C.c_int]
+        L.sidm_kernel_launches.argtypes = [vp]
+        L.sidm_error_string.argtypes = [C.c_int]
+        L.sidm_error_string.restype = C.c_char_p
+        L.sidm_destroy.argtypes = [vp]
+        L.sidm_destroy.restype = None
+        for name in ENTRY_POINTS:
+            fn = getattr(L, name)
+            if name not in ("sidm_default_config", "sidm_error_string", "sidm_destroy"):
+                fn.restype = C.c_int
+        L.sidm_kernel_launches.restype = C.c_int64
+        _lib = L
+        return L
+
+
+def error_string(status: int) -> str:
+    return lib().sidm_error_string(int(status)).decode()
+
+
+def _check(status: int, what: str) -> int:
+    if status < 0:
+        raise SidmError(status, what)
+    return status
+
+
+def _ptr(a):
+    """(pointer, ptr_kind) of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None, HOST
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, HOST
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), (DEVICE if a.is_cuda else HOST)
+    raise TypeError(type(a))
+
+
+# ------------------------------------------------------- C entry points ---
+
+def sidm_default_config() -> Config:
+    c = Config()
+    lib().sidm_default_config(C.byref(c))
+    return c
+
+
+def sidm_create(cfg: Config) -> int:
+    h = C.c_void_p()
+    _check(lib().sidm_create(C.byref(cfg), C.byref(h)), "sidm_create")
+    return h.value
+
+
+def sidm_set_particles(ctx, pos, vel, mass, mass_scalar, ids) -> int:
+    n = int(pos.shape[0])
+    pp, kind = _ptr(pos)
+    return _check(lib().sidm_set_particles(ctx, n, pp, _ptr(vel)[0], _ptr(mass)[0],
+                                           float(mass_scalar), _ptr(ids)[0], kind),
+                  "sidm_set_particles")
+
+
+def sidm_set_velocities(ctx, vel) -> int:
+    p, kind = _ptr(vel)
+    return _check(lib().sidm_set_velocities(ctx, p, kind), "sidm_set_velocities")
+
+
+def sidm_step(ctx, active_mask, dt_bins, dt_max, sigma: SigmaModel, seed, stats=None) -> int:
+    return _check(lib().sidm_step(ctx, _ptr(active_mask)[0], _ptr(dt_bins)[0], float(dt_max),
+                                  C.byref(sigma), int(seed),
+                                  C.byref(stats) if stats is not None else None), "sidm_step")
+
+
+def sidm_sync(ctx) -> int:
+    return _check(lib().sidm_sync(ctx), "sidm_sync")
+
+
+def sidm_get_particles(ctx, vel_out, h_out=None) -> int:
+    p, kind = _ptr(vel_out)
+    return _check(lib().sidm_get_particles(ctx, p, _ptr(h_out)[0], kind), "sidm_get_particles")
+
+
+def sidm_timestep_limits(ctx, out) -> int:
+    p, kind = _ptr(out)
+    return _check(lib().sidm_timestep_limits(ctx, p, kind), "sidm_timestep_limits")
+
+
+def sidm_get_pairs(ctx, ab, ord_, cap) -> int:
+    n = C.c_int64(0)
+    _check(lib().sidm_get_pairs(ctx, _ptr(ab)[0], _ptr(ord_)[0], int(cap), C.byref(n)),
+           "sidm_get_pairs")
+    return n.value
+
+
+def sidm_get_step(ctx) -> int:
+    s = C.c_uint64(0)
+    _check(lib().sidm_get_step(ctx, C.byref(s)), "sidm_get_step")
+    return s.value
+
+
+def sidm_set_step(ctx, step) -> int:
+    return _check(lib().sidm_set_step(ctx, int(step)), "sidm_set_step")
+
+
+def sidm_phase_times(ctx) -> list:
+    ms = (C.c_float * N_PHASES)()
+    _check(lib().sidm_phase_times(ctx, ms, N_PHASES), "sidm_phase_times")
+    return list(ms)
+
+
+def sidm_kernel_launches(ctx) -> int:
+    return int(lib().sidm_kernel_launches(ctx))
+
+
+def sidm_destroy(ctx) -> None:
+    if ctx:
+        lib().sidm_destroy(ctx)
+
+
+# ------------------------------------------------------------- wrapper ---
+
+class Context:
+    """One library context.  Host (numpy) and device (torch CUDA) inputs both
+    work; outputs are numpy arrays unless device tensors are passed in."""
+
+    def __init__(self, n_ngb=32, ngb_tol=5, c_sidm=0.1, box=0.0, kernel=KERNEL_CUBIC,
+                 fixed_h=0.0, n_max=0, pair_capacity=0, stream=None, device=-1, profile=False):
+        cfg = sidm_default_config()
+        cfg.n_ngb, cfg.ngb_tol, cfg.c_sidm, cfg.box = int(n_ngb), int(ngb_tol), float(c_sidm), float(box)
+        cfg.kernel, cfg.fixed_h, cfg.n_max = int(kernel), float(fixed_h), int(n_max)
+        cfg.pair_capacity = int(pair_capacity)
+        cfg.stream = stream
+        cfg.device = int(device)
+        cfg.profile = int(bool(profile))
+        self.cfg = cfg
+        self.handle = sidm_create(cfg)
+        self.n = 0
+
+    def close(self):
+        if self.handle:
+            sidm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_particles(self, pos, vel, ids, mass=None, mass_scalar=0.0):
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, np.float64)
+            vel = np.ascontiguousarray(vel, np.float64)
+            ids = np.ascontiguousarray(ids, np.uint32)
+            mass = None if mass is None else np.ascontiguousarray(mass, np.float64)
+        self._keep = (pos, vel, ids, mass)
+        sidm_set_particles(self.handle, pos, vel, mass, mass_scalar, ids)
+        self.n = int(pos.shape[0])
+
+    def set_velocities(self, vel):
+        if isinstance(vel, np.ndarray):
+            vel = np.ascontiguousarray(vel, np.float64)
+        sidm_set_velocities(self.handle, vel)
+
+    def step(self, dt_max, active=None, bins=None, sigma0=1.0, sigma_kind=SIGMA_CONST, w=1.0,
+             seed=0, stats=True):
+        if isinstance(active, np.ndarray):
+            active = np.ascontiguousarray(active, np.uint8)
+        if isinstance(bins, np.ndarray):
+            bins = np.ascontiguousarray(bins, np.int8)
+        sg = SigmaModel(int(sigma_kind), float(sigma0), float(w))
+        st = StepStats() if stats else None
+        status = sidm_step(self.handle, active, bins, dt_max, sg, seed, st)
+        if st is not None:
+            d = st.as_dict()
+            d["return"] = status
+            return d
+        return status
+
+    def sync(self):
+        return sidm_sync(self.handle)
+
+    def velocities(self):
+        v = np.empty((self.n, 3))
+        h = np.empty(self.n)
+        sidm_get_particles(self.handle, v, h)
+        return v, h
+
+    def timestep_limits(self):
+        out = np.empty(self.n)
+        sidm_timestep_limits(self.handle, out)
+        return out
+
+    def pairs(self, cap=None):
+        cap = (4 * self.n + 16) if cap is None else int(cap)
+        ab = np.zeros((cap, 2), np.uint32)
+        ords = np.zeros(cap, np.uint64)
+        n = sidm_get_pairs(self.handle, ab, ords, cap)
+        k = min(n, cap)
+        return ab[:k].copy(), ords[:k].copy()
+
+    def phase_times(self) -> dict:
+        return dict(zip(PHASES, sidm_phase_times(self.handle)))
+
+    @property
+    def kernel_launches(self) -> int:
+        return sidm_kernel_launches(self.handle)
+
+    @property
+    def step_counter(self) -> int:
+        return sidm_get_step(self.handle)
+
+    @step_counter.setter
+    def step_counter(self, v: int):
+        sidm_set_step(self.handle, v)

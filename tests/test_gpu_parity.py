@@ -1,0 +1,213 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+The FP64 plain form must reproduce the oracle exactly: the same h for every
+active particle, the same Eq. 9 limits, the same accepted pairs (ids and
+order keys) and the same velocities.  The bound stated for velocities is
+1e-12 relative; the path is built to be bit-identical, and these tests
+assert bit equality (a relative-difference report is printed on failure).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_05504_b300 import inputs as I
+from paper_2607_05504_b300 import sidm
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_step(ctx, p, act, bins, dt_max, **kw):
+    st = ctx.step(dt_max, act, bins, sigma0=kw.get("sigma0", 1.0),
+                  sigma_kind=kw.get("sigma_kind", 0), w=kw.get("w", 1.0), seed=kw.get("seed", 0))
+    v, h = ctx.velocities()
+    return {"vel": v, "h": h, "dtlim": ctx.timestep_limits(), "pairs": ctx.pairs(), "stats": st}
+
+
+def _compare(g, o, act, what=""):
+    act = np.ones(g["h"].shape[0], bool) if act is None else act.astype(bool)
+    gs, os_ = g["stats"], o["stats"]
+    assert gs["n_active"] == os_["n_active"], what
+    assert gs["n_h_nonconv"] == os_["n_h_nonconv"], what
+    bad = np.nonzero(g["h"][act] != o["h"][act])[0]
+    assert bad.size == 0, f"{what}: h differs at {bad.size} particles, e.g. {g['h'][act][bad[:3]]} vs {o['h'][act][bad[:3]]}"
+    assert gs["n_candidate_pairs"] == os_["n_candidate_pairs"], what
+    assert gs["n_p_ge_1"] == os_["n_p_ge_1"], what
+    ab, ords = g["pairs"]
+    assert gs["n_accepted"] == o["n_pairs"], what
+    assert np.array_equal(ab, o["pairs_ab"]), what
+    assert np.array_equal(ords, o["pairs_ord"]), what
+    dl_g, dl_o = g["dtlim"][act], o["dtlim"][act]
+    assert np.array_equal(dl_g, dl_o), what
+    if not np.array_equal(g["vel"], o["vel"]):
+        rel = np.abs(g["vel"] - o["vel"]) / np.maximum(np.abs(o["vel"]), 1e-300)
+        pytest.fail(f"{what}: velocities differ, max rel {rel.max():.3e}")
+    assert math.isclose(gs["sum_p"], os_["sum_p"], rel_tol=1e-9, abs_tol=1e-300)
+    assert abs(gs["e_after"] - os_["e_after"]) <= 1e-13 * abs(os_["e_after"]) + 1e-300
+
+
+def run_pair(p, act, bins, dt_max, *, n_ngb=32, ngb_tol=5, kernel=0, fixed_h=0.0, steps=1,
+             seed=0, sigma_kind=0, sigma0=1.0, w=1.0, c_sidm=0.1, device_inputs=False):
+    ctx = sidm.Context(n_ngb=n_ngb, ngb_tol=ngb_tol, c_sidm=c_sidm, box=p.box, kernel=kernel,
+                       fixed_h=fixed_h)
+    if device_inputs:
+        import torch
+        ctx.set_particles(torch.from_numpy(p.pos).cuda(), torch.from_numpy(p.vel).cuda(),
+                          torch.from_numpy(p.ids.astype(np.int32)).cuda(),
+                          mass=torch.from_numpy(p.mass).cuda())
+    else:
+        ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    vel = p.vel.copy()
+    h = np.zeros(p.n)
+    dl = np.full(p.n, np.inf)
+    for k in range(steps):
+        a = act(k) if callable(act) else act
+        o = oracle.step(p.pos, vel, p.mass, p.ids, a, bins, dt_max, n_ngb=n_ngb, ngb_tol=ngb_tol,
+                        c_sidm=c_sidm, box=p.box, kernel=kernel, fixed_h=fixed_h,
+                        sigma_kind=sigma_kind, sigma0=sigma0, w=w, seed=seed, step=k,
+                        h_init=h, dtlim_init=dl)
+        g = _gpu_step(ctx, p, a, bins, dt_max, sigma_kind=sigma_kind, sigma0=sigma0, w=w, seed=seed)
+        _compare(g, o, a, f"step {k}")
+        vel, h, dl = o["vel"], o["h"], o["dtlim"]
+        # outputs of inactive particles keep their previous values
+        assert np.array_equal(g["h"], h) and np.array_equal(g["dtlim"], dl)
+    ctx.close()
+    return g, o
+
+
+def test_box_small_all_active():
+    p = I.uniform_box(4096, 1.0, 1.0, 3)
+    g, o = run_pair(p, None, np.zeros(p.n, np.int8), 0.05)
+    assert o["n_pairs"] > 50
+
+
+def test_box_32cubed_workload():
+    w = I.box_32cubed()
+    p = w["particles"]
+    g, o = run_pair(p, None, w["bins"], w["dt_max"])
+    assert 1400 < o["n_pairs"] < 1900
+    assert abs(g["stats"]["e_after"] - g["stats"]["e_before"]) <= 1e-13 * g["stats"]["e_before"]
+
+
+def test_halo_partial_activity_random_ids_unequal_masses():
+    p = I.hernquist_halo(20000, 5, ids="random")
+    rng = np.random.default_rng(1)
+    p.mass = p.mass * rng.uniform(0.5, 1.5, p.n)
+    bins = rng.integers(0, 4, p.n).astype(np.int8)
+    act = (rng.random(p.n) < 0.3).astype(np.uint8)
+    run_pair(p, act, bins, 0.2, n_ngb=64)
+
+
+def test_yukawa_tophat_box():
+    p = I.uniform_box(3000, 2.0, 1.5, 4, ids="random")
+    run_pair(p, None, np.zeros(p.n, np.int8), 0.3, kernel=1, sigma_kind=1, sigma0=5.0, w=1.2)
+
+
+def test_fixed_h_hook():
+    p = I.uniform_box(2000, 1.0, 1.0, 5)
+    run_pair(p, None, np.zeros(p.n, np.int8), 0.02, fixed_h=0.12)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 38, 39, 40, 70, 1000, 1025, 4097])
+@pytest.mark.parametrize("box", [1.0, 0.0])
+def test_ragged_and_tiny_sizes(n, box):
+    p = I.uniform_box(n, 1.0, 1.0, 100 + n)
+    p.box = box
+    run_pair(p, None, np.zeros(n, np.int8), 0.1)
+
+
+def test_no_active_particles():
+    p = I.uniform_box(3000, 1.0, 1.0, 6)
+    g, o = run_pair(p, np.zeros(p.n, np.uint8), np.zeros(p.n, np.int8), 0.1)
+    assert o["n_pairs"] == 0 and np.array_equal(g["vel"], p.vel)
+
+
+def test_several_steps_with_changing_activity():
+    p = I.uniform_box(6000, 1.0, 1.0, 7, ids="random")
+    rng = np.random.default_rng(2)
+    masks = [(rng.random(p.n) < f).astype(np.uint8) for f in (1.0, 0.3, 0.05, 0.6)]
+    bins = rng.integers(0, 3, p.n).astype(np.int8)
+    run_pair(p, lambda k: masks[k], bins, 0.15, steps=4, seed=12345678901)
+
+
+def test_lattice_without_admissible_count():
+    g_ = np.arange(8) / 8.0
+    x, y, z = np.meshgrid(g_, g_, g_, indexing="ij")
+    pos = np.stack([x.ravel(), y.ravel(), z.ravel()], 1)
+    n = pos.shape[0]
+    p = I.Particles(pos, np.random.default_rng(0).normal(size=(n, 3)), np.full(n, 1.0 / n),
+                    np.arange(n, dtype=np.uint32), 1.0)
+    g, o = run_pair(p, None, np.zeros(n, np.int8), 0.1, n_ngb=22, ngb_tol=1)
+    assert o["stats"]["n_h_nonconv"] == n
+    assert g["stats"]["return"] & sidm.WARN_H_NOT_CONVERGED
+
+
+def test_probabilities_above_one():
+    p = I.uniform_box(2000, 1.0, 1.0, 8)
+    g, o = run_pair(p, None, np.zeros(p.n, np.int8), 20.0)
+    assert o["stats"]["n_p_ge_1"] > 0
+    assert g["stats"]["return"] & sidm.WARN_P_GE_1
+
+
+def test_device_inputs_match_host_inputs():
+    import torch
+    p = I.uniform_box(5000, 1.0, 1.0, 9)
+    run_pair(p, None, np.zeros(p.n, np.int8), 0.1, device_inputs=True)
+
+
+def test_resume_is_bit_identical():
+    p = I.uniform_box(4000, 1.0, 1.0, 10, ids="random")
+    bins = np.zeros(p.n, np.int8)
+    a = sidm.Context(box=1.0)
+    a.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    a.step(0.2, None, bins, seed=9)
+    v1, _ = a.velocities()
+    a.step(0.2, None, bins, seed=9)
+    v2, _ = a.velocities()
+    b = sidm.Context(box=1.0)
+    b.set_particles(p.pos, v1, p.ids, mass=p.mass)
+    b.step_counter = 1
+    b.step(0.2, None, bins, seed=9)
+    v2b, _ = b.velocities()
+    assert np.array_equal(v2, v2b) and not np.array_equal(v1, v2)
+
+
+def test_invalid_inputs_are_rejected():
+    ctx = sidm.Context(box=1.0)
+    with pytest.raises(sidm.SidmError) as e:
+        ctx.step(0.1)
+    assert e.value.status == sidm.ERR_NOT_READY
+    p = I.uniform_box(100, 1.0, 1.0, 11)
+    bad = p.pos.copy()
+    bad[3, 1] = 1.0
+    with pytest.raises(sidm.SidmError) as e:
+        ctx.set_particles(bad, p.vel, p.ids, mass=p.mass)
+    assert e.value.status == sidm.ERR_INVALID_ARG
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    for dt in (0.0, -1.0, float("inf")):
+        with pytest.raises(sidm.SidmError):
+            ctx.step(dt)
+    with pytest.raises(sidm.SidmError):
+        ctx.step(0.1, sigma_kind=1, w=0.0)
+
+
+@pytest.fixture(scope="module")
+def hernquist_full():
+    return I.hernquist_2pow20()
+
+
+@pytest.mark.parametrize("s", [1, 2])
+def test_hernquist_2pow20_full_size(hernquist_full, s):
+    """The halo workload at full size (N = 2^20, N_ngb = 64, open boundaries,
+    power-of-two bins) in the configuration the benchmark times."""
+    w = hernquist_full
+    p, bins = w["particles"], w["bins"]
+    act = I.active_at_step(bins, s)
+    ctx = sidm.Context(n_ngb=64, box=0.0)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    ctx.step_counter = s
+    o = oracle.step(p.pos, p.vel, p.mass, p.ids, act, bins, w["dt_max"], n_ngb=64, seed=w["seed"],
+                    step=s)
+    g = _gpu_step(ctx, p, act, bins, w["dt_max"], seed=w["seed"])
+    _compare(g, o, act, f"hernquist step {s}")
