@@ -213,7 +213,10 @@ def main():
     p, bins = w["particles"], w["bins"]
     n = p.n
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    # a non-default stream shared by torch and the library: the events that
+    # time the steps are recorded on the stream the library launches on
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     masks_d = torch.from_numpy(masks).to(dev)
     bins_d = torch.from_numpy(bins).to(dev)
     pos_d = torch.from_numpy(p.pos).to(dev)

@@ -48,9 +48,10 @@ def _compare(g, o, act, what=""):
 
 
 def run_pair(p, act, bins, dt_max, *, n_ngb=32, ngb_tol=5, kernel=0, fixed_h=0.0, steps=1,
-             seed=0, sigma_kind=0, sigma0=1.0, w=1.0, c_sidm=0.1, device_inputs=False):
+             seed=0, sigma_kind=0, sigma0=1.0, w=1.0, c_sidm=0.1, device_inputs=False,
+             pair_capacity=0):
     ctx = sidm.Context(n_ngb=n_ngb, ngb_tol=ngb_tol, c_sidm=c_sidm, box=p.box, kernel=kernel,
-                       fixed_h=fixed_h)
+                       fixed_h=fixed_h, pair_capacity=pair_capacity)
     if device_inputs:
         import torch
         ctx.set_particles(torch.from_numpy(p.pos).cuda(), torch.from_numpy(p.vel).cuda(),
@@ -145,9 +146,23 @@ def test_lattice_without_admissible_count():
 
 def test_probabilities_above_one():
     p = I.uniform_box(2000, 1.0, 1.0, 8)
-    g, o = run_pair(p, None, np.zeros(p.n, np.int8), 20.0)
+    g, o = run_pair(p, None, np.zeros(p.n, np.int8), 20.0, pair_capacity=200000)
     assert o["stats"]["n_p_ge_1"] > 0
     assert g["stats"]["return"] & sidm.WARN_P_GE_1
+
+
+def test_full_pair_buffer_is_reported_and_nothing_is_kicked():
+    """A bounded buffer that fills makes the step return SIDM_ERR_DEVICE_LIMIT
+    and leaves the velocities untouched (no partial application)."""
+    p = I.uniform_box(3000, 1.0, 1.0, 12)
+    ctx = sidm.Context(box=1.0, pair_capacity=5)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    with pytest.raises(sidm.SidmError) as e:
+        ctx.step(0.5)
+    assert e.value.status == sidm.ERR_DEVICE_LIMIT
+    v, _ = ctx.velocities()
+    assert np.array_equal(v, p.vel)
+    ctx.close()
 
 
 def test_device_inputs_match_host_inputs():
