@@ -61,7 +61,8 @@ typedef enum {
   SIDM_ERR_OOM = -2,
   SIDM_ERR_CUDA = -3,
   SIDM_ERR_DEVICE_LIMIT = -4,    /* a bounded device loop or buffer gave up; step not valid */
-  SIDM_ERR_NOT_READY = -5        /* sidm_step before sidm_set_particles                     */
+  SIDM_ERR_NOT_READY = -5,       /* sidm_step before sidm_set_particles                     */
+  SIDM_ERR_TOO_LARGE = -6        /* input beyond the fixed scratch of a no-allocation call  */
 } sidm_status;
 
 enum { SIDM_HOST = 0, SIDM_DEVICE = 1 };
@@ -175,6 +176,54 @@ SIDM_API int sidm_phase_times(sidm_ctx* ctx, float* ms, int n);
 
 /* Kernels launched by the context so far (all of them are this library's). */
 SIDM_API int64_t sidm_kernel_launches(const sidm_ctx* ctx);
+
+/* ---- Kick application without any device allocation ----------------------
+ * The paper has no counterpart to this entry point: it exists for callers
+ * that cannot let a library allocate device memory -- simulation codes that
+ * reserve all GPU memory in their own pool at start-up, or that call in from
+ * a place where a cudaMalloc would synchronise the whole device or is not
+ * allowed.  It applies a given list of accepted pairs to velocities exactly
+ * as the kick phase of sidm_step() does (each particle meets its pairs in
+ * ascending (ord, a, b) order; direction from Philox (seed, step, 1 + t, a,
+ * b); elastic kick), so its result equals sidm_step()'s velocities for the
+ * pairs sidm_get_pairs() reports.
+ *
+ * Memory: all scratch lives in one fixed array inside the library (a
+ * file-scope __device__ array of 10.25 MiB), which every GPU that loads
+ * the library holds until the process exits.  Hence the fixed maxima below;
+ * larger inputs are rejected with SIDM_ERR_TOO_LARGE before any GPU work.
+ * Nothing is allocated: no cudaMalloc, cudaFree or allocating library call.
+ *
+ * Arguments (all device pointers of the current device):
+ *   pairs   n_pairs records; ia, ib are indices into vel / mass, a, b the
+ *           ids used in the random counter (as sidm_get_pairs() reports them
+ *           for ids equal to the indices), ord the order key;
+ *   vel     n x 3 FP64 velocities, updated in place; mass: n FP64 masses;
+ *   seed, step: the Philox key and the step counter of the draw;
+ *   stream: cudaStream_t (NULL: the legacy default stream).
+ * Returns SIDM_OK (or SIDM_WARN_DIRECTION); SIDM_ERR_TOO_LARGE for
+ * n > SIDM_NOALLOC_MAX_PARTICLES or n_pairs > SIDM_NOALLOC_MAX_PAIRS;
+ * SIDM_ERR_INVALID_ARG for NULL pointers, negative sizes, or a pair whose
+ * index lies outside [0, n) or names one particle twice (checked on the
+ * device; then no velocity is changed); SIDM_ERR_CUDA on a CUDA failure.
+ * The call waits for the stream before it returns.
+ *
+ * Set-up: the first call on each device looks up the device address of the
+ * scratch array (with that device current); make that first call before
+ * any stream capture.  Every call shares the one array per device and
+ * clears the parts it uses at the start; calls that overlap on the GPU
+ * (different streams or host threads, same device) race on it and must not
+ * be issued. */
+#define SIDM_NOALLOC_MAX_PARTICLES (1 << 20)
+#define SIDM_NOALLOC_MAX_PAIRS (1 << 18)
+typedef struct {
+  uint64_t ord;   /* order key of the pair                 */
+  uint32_t a, b;  /* ids of the two particles, a < b         */
+  int32_t ia, ib; /* indices of the a- and b-particle         */
+} sidm_pair;
+SIDM_API int sidm_apply_pairs_noalloc(const sidm_pair* pairs, int64_t n_pairs, double* vel,
+                                      const double* mass, int64_t n, uint64_t seed,
+                                      uint64_t step, void* stream);
 
 SIDM_API const char* sidm_error_string(int status);
 

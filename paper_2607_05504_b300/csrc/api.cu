@@ -514,6 +514,9 @@ const char* sidm_error_string(int status) {
     case SIDM_ERR_CUDA: return "CUDA error";
     case SIDM_ERR_DEVICE_LIMIT: return "a bounded device loop or buffer gave up (search capacity, traversal stack, pair buffer or resolver rounds); the step is not valid";
     case SIDM_ERR_NOT_READY: return "no particles loaded";
+    case SIDM_ERR_TOO_LARGE:
+      return "input exceeds the fixed scratch of the no-allocation entry point "
+             "(at most SIDM_NOALLOC_MAX_PARTICLES particles and SIDM_NOALLOC_MAX_PAIRS pairs)";
     default:
       if (status > 0) return "several warnings";
       return "unknown status";

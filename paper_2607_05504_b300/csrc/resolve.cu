@@ -160,4 +160,14 @@ int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* 
   return 1;
 }
 
+// The same kernel for the no-allocation entry point: every scratch pointer
+// (head, next, flags, mult, st) is supplied by the caller.
+void launch_resolve_with_scratch(const PairRec* pairs, int64_t pair_cap, double* vel,
+                                 const double* mass, int32_t* head, int32_t* next, uint8_t* flags,
+                                 int32_t* mult, uint64_t seed, uint32_t step, DevStats* st,
+                                 cudaStream_t s) {
+  resolve_kernel<<<1, RT, 0, s>>>(pairs, pair_cap, vel, mass, head, next, flags, mult,
+                                  (uint32_t)seed, (uint32_t)(seed >> 32), step, st);
+}
+
 }  // namespace sidm

@@ -211,6 +211,10 @@ int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* 
                     int32_t* head, int32_t* next, uint8_t* flags, int32_t* mult,
                     uint64_t seed, uint32_t step, DevStats* st, cudaStream_t s);
 int launch_sort_pairs_for_output(PairRec* pairs, int64_t n, cudaStream_t s);
+void launch_resolve_with_scratch(const PairRec* pairs, int64_t pair_cap, double* vel,
+                                 const double* mass, int32_t* head, int32_t* next, uint8_t* flags,
+                                 int32_t* mult, uint64_t seed, uint32_t step, DevStats* st,
+                                 cudaStream_t s);
 
 // stats.cu
 int launch_conserved(const double* vel, const double* mass, int64_t n, double* partial,

@@ -25,6 +25,10 @@ SIGMA_CONST, SIGMA_YUKAWA = 0, 1
 OK = 0
 WARN_H_NOT_CONVERGED, WARN_P_GE_1, WARN_DIRECTION = 1, 2, 4
 ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_DEVICE_LIMIT, ERR_NOT_READY = -1, -2, -3, -4, -5
+ERR_TOO_LARGE = -6
+NOALLOC_MAX_PARTICLES, NOALLOC_MAX_PAIRS = 1 << 20, 1 << 18
+# record layout of sidm_pair (include/sidm.h)
+PAIR_DTYPE = np.dtype([("ord", "<u8"), ("a", "<u4"), ("b", "<u4"), ("ia", "<i4"), ("ib", "<i4")])
 
 
 class SidmError(RuntimeError):
@@ -64,7 +68,8 @@ class StepStats(C.Structure):
 ENTRY_POINTS = ("sidm_default_config", "sidm_create", "sidm_set_particles",
                 "sidm_set_velocities", "sidm_step", "sidm_sync", "sidm_get_particles",
                 "sidm_timestep_limits", "sidm_get_pairs", "sidm_get_step", "sidm_set_step",
-                "sidm_phase_times", "sidm_kernel_launches", "sidm_error_string", "sidm_destroy")
+                "sidm_phase_times", "sidm_kernel_launches", "sidm_error_string", "sidm_destroy",
+                "sidm_apply_pairs_noalloc")
 
 N_PHASES = 6
 PHASES = ("keys", "sort", "structure", "search", "pairs", "resolve")
@@ -110,6 +115,7 @@ def lib():
         L.sidm_error_string.restype = C.c_char_p
         L.sidm_destroy.argtypes = [vp]
         L.sidm_destroy.restype = None
+        L.sidm_apply_pairs_noalloc.argtypes = [vp, i64, vp, vp, i64, C.c_uint64, C.c_uint64, vp]
         for name in ENTRY_POINTS:
             fn = getattr(L, name)
             if name not in ("sidm_default_config", "sidm_error_string", "sidm_destroy"):
@@ -221,6 +227,15 @@ def sidm_kernel_launches(ctx) -> int:
 def sidm_destroy(ctx) -> None:
     if ctx:
         lib().sidm_destroy(ctx)
+
+
+def sidm_apply_pairs_noalloc(pairs, n_pairs, vel, mass, n, seed, step, stream=None) -> int:
+    """Kicks of the given accepted pairs applied to ``vel`` in place, with no
+    device allocation (fixed scratch inside the library; device pointers or
+    CUDA tensors).  Returns the status (negative statuses raise)."""
+    return _check(lib().sidm_apply_pairs_noalloc(_ptr(pairs)[0], int(n_pairs), _ptr(vel)[0],
+                                                 _ptr(mass)[0], int(n), int(seed), int(step),
+                                                 stream), "sidm_apply_pairs_noalloc")
 
 
 # ------------------------------------------------------------- wrapper ---
