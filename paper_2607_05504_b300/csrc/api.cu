@@ -40,6 +40,9 @@ struct sidm_ctx {
   // key order
   Sorted so{};
   int32_t* act_list = nullptr;
+  int32_t* nb_list = nullptr;   // [n][nb_stride] neighbour lists of the active particles
+  int32_t* nb_count = nullptr;  // [n] list length, or -1
+  int nb_stride = 0;
   Tree tree{};
   // per step
   StepParams* params = nullptr;
@@ -50,6 +53,7 @@ struct sidm_ctx {
   PairRec* pairs = nullptr;
   int32_t *head = nullptr, *next = nullptr, *mult = nullptr;
   uint8_t* pflags = nullptr;
+  int32_t* pending = nullptr;   // 2 x pair capacity: pending pairs of the resolver rounds
   double *cons_partial = nullptr, *cons = nullptr;
   // pinned host staging
   DevStats* h_stats = nullptr;
@@ -157,10 +161,15 @@ int ensure_capacity(sidm_ctx* c, int64_t n) {
   CK(dalloc(c, &so.h, want));
   CK(dalloc(c, &so.dt, want));
   CK(dalloc(c, &so.f, want));
+  CK(dalloc(c, &so.vm, want));
+  CK(dalloc(c, &so.hb, want));
   CK(dalloc(c, &so.id, want));
   CK(dalloc(c, &so.act, want));
   CK(dalloc(c, &so.orig, want));
   CK(dalloc(c, &c->act_list, want));
+  c->nb_stride = c->cfg.n_ngb + c->cfg.ngb_tol;
+  CK(dalloc(c, &c->nb_count, want));
+  CK(dalloc(c, &c->nb_list, want * (int64_t)c->nb_stride));
   CK(dalloc(c, &t.lo, nodes));
   CK(dalloc(c, &t.hi, nodes));
   CK(dalloc(c, &c->params, 1));
@@ -173,6 +182,7 @@ int ensure_capacity(sidm_ctx* c, int64_t n) {
   CK(dalloc(c, &c->mult, want));
   CK(dalloc(c, &c->next, 2 * pc));
   CK(dalloc(c, &c->pflags, pc));
+  CK(dalloc(c, &c->pending, 2 * pc));
   CK(dalloc(c, &c->cons_partial, 4 * conserved_blocks()));
   CK(dalloc(c, &c->cons, 8));
   CK(cudaMemsetAsync(c->head, 0xFF, want * sizeof(int32_t), c->stream));
@@ -390,7 +400,8 @@ int sidm_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins, do
     L += launch_tree(c->so, n, t, s);
     mark(3);
     L += launch_search(c->so, t, n, c->act_list, c->params, c->cfg.box, c->cfg.n_ngb,
-                       c->cfg.ngb_tol, c->cfg.fixed_h, c->h_user, c->dstats, c->work, s);
+                       c->cfg.ngb_tol, c->cfg.fixed_h, c->h_user, c->nb_list, c->nb_count,
+                       c->nb_stride, c->dstats, c->work, c->sms, s);
     mark(4);
     PairArgs pa;
     pa.kernel = c->cfg.kernel;
@@ -402,10 +413,11 @@ int sidm_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins, do
     pa.seed = seed;
     pa.step = (uint32_t)c->step;
     pa.pair_cap = c->pair_cap;
-    L += launch_pairs(c->so, t, n, c->act_list, pa, c->pairs, c->dtlim, c->dstats, c->work + 1, s);
+    L += launch_pairs(c->so, t, n, c->act_list, c->nb_list, c->nb_count, c->nb_stride, pa,
+                      c->pairs, c->dtlim, c->dstats, c->work + 1, c->sms, s);
     mark(5);
     L += launch_resolve(c->pairs, c->pair_cap, c->vel, c->mass, c->head, c->next, c->pflags,
-                        c->mult, seed, (uint32_t)c->step, c->dstats, s);
+                        c->mult, c->pending, seed, (uint32_t)c->step, c->dstats, c->sms, s);
     mark(6);
   }
   latch_kernel<<<1, 32, 0, s>>>(c->dstats, c->latched);

@@ -159,15 +159,18 @@ __global__ void __launch_bounds__(BT) permute_kernel(
     so.x[s] = x;
     so.y[s] = y;
     so.z[s] = z;
-    so.f[s] = make_float4((float)x, (float)y, (float)z, 0.f);
-    so.vx[s] = vel[3 * o];
-    so.vy[s] = vel[3 * o + 1];
-    so.vz[s] = vel[3 * o + 2];
-    so.m[s] = mass[o];
+    const double dt = ldexp(dt_max, -(int)bins[o]);
+    const double vx = vel[3 * o], vy = vel[3 * o + 1], vz = vel[3 * o + 2], m = mass[o];
+    so.f[s] = make_float4((float)x, (float)y, (float)z, __double2float_ru(dt));
+    so.vx[s] = vx;
+    so.vy[s] = vy;
+    so.vz[s] = vz;
+    so.vm[s] = make_float4((float)vx, (float)vy, (float)vz, __double2float_ru(m));
+    so.m[s] = m;
     so.id[s] = ids[o];
     a = act[o] != 0;
     so.act[s] = a ? 1 : 0;
-    so.dt[s] = ldexp(dt_max, -(int)bins[o]);
+    so.dt[s] = dt;
     so.h[s] = 0.0;
     so.orig[s] = (int32_t)o;
   }

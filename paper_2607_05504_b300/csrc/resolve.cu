@@ -150,14 +150,159 @@ __global__ void __launch_bounds__(RT) resolve_kernel(const PairRec* __restrict__
   }
 }
 
+// ---- step path: isolated pairs in parallel, the rest in rounds ----------
+//
+// A pair whose two particles take part in no other accepted pair commutes
+// with every other kick, so it is applied at once by any thread.  Only the
+// remaining ("pending") pairs go through the rounds, and each round visits
+// only the pairs still pending.
+
+constexpr int GT = 256;
+
+__global__ void __launch_bounds__(GT) count_kernel(const PairRec* __restrict__ pairs, int64_t cap,
+                                                   int32_t* mult, const DevStats* st) {
+  const unsigned long long nall = st->n_acc;
+  if (nall > (unsigned long long)cap) return;
+  for (int64_t p = blockIdx.x * (int64_t)GT + threadIdx.x; p < (int64_t)nall;
+       p += (int64_t)gridDim.x * GT) {
+    atomicAdd(&mult[pairs[p].ia], 1);
+    atomicAdd(&mult[pairs[p].ib], 1);
+  }
+}
+
+__global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ pairs, int64_t cap,
+                                                   double* vel, const double* __restrict__ mass,
+                                                   int32_t* head, int32_t* next, uint8_t* flags,
+                                                   const int32_t* __restrict__ mult,
+                                                   int32_t* pending, uint32_t k0, uint32_t k1,
+                                                   uint32_t step, DevStats* st) {
+  __shared__ unsigned s_dirfail;
+  __shared__ int s_max;
+  if (threadIdx.x == 0) { s_dirfail = 0; s_max = 0; }
+  __syncthreads();
+  const unsigned long long nall = st->n_acc;
+  const int lane = threadIdx.x & 31;
+  int mm = 0;
+  if (nall <= (unsigned long long)cap) {
+    const int64_t na = (int64_t)nall;
+    const int64_t stride = (int64_t)gridDim.x * GT;
+    // uniform trip count per warp (ballots below)
+    for (int64_t base = blockIdx.x * (int64_t)GT + (threadIdx.x & ~31); base < na; base += stride) {
+      const int64_t p = base + lane;
+      bool pend = false;
+      if (p < na) {
+        const PairRec r = pairs[p];
+        const int ma = mult[r.ia], mb = mult[r.ib];
+        mm = max(mm, max(ma, mb));
+        if (ma == 1 && mb == 1) {
+          kick(r, vel, mass, k0, k1, step, &s_dirfail);
+        } else {
+          pend = true;
+          flags[p] = 0;
+          next[2 * p] = atomicExch(&head[r.ia], (int32_t)(2 * p));
+          next[2 * p + 1] = atomicExch(&head[r.ib], (int32_t)(2 * p + 1));
+        }
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, pend);
+      if (m) {
+        unsigned long long at = 0;
+        const int leader = __ffs(m) - 1;
+        if (lane == leader) at = atomicAdd(&st->n_pending, (unsigned long long)__popc(m));
+        at = __shfl_sync(0xffffffffu, at, leader);
+        if (pend) pending[at + __popc(m & ((1u << lane) - 1u))] = (int32_t)p;
+      }
+    }
+  }
+  atomicMax(&s_max, mm);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_max) atomicMax(&st->max_mult, (unsigned long long)s_max);
+    if (s_dirfail) {
+      atomicAdd(&st->n_dirfail, (unsigned long long)s_dirfail);
+      atomicOr(&st->status, (unsigned)ST_DIR_FAIL);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RT) rounds_kernel(const PairRec* __restrict__ pairs, int64_t cap,
+                                                    double* vel, const double* __restrict__ mass,
+                                                    const int32_t* head, const int32_t* next,
+                                                    uint8_t* flags, int32_t* pend_a,
+                                                    int32_t* pend_b, uint32_t k0, uint32_t k1,
+                                                    uint32_t step, DevStats* st) {
+  __shared__ unsigned s_dirfail;
+  __shared__ int s_n;
+  const int t = threadIdx.x;
+  if (t == 0) s_dirfail = 0;
+  __syncthreads();
+  if (st->n_acc > (unsigned long long)cap) return;
+  int npend = (int)st->n_pending;
+  int32_t* cur = pend_a;
+  int32_t* nxt = pend_b;
+  int rounds = 0;
+  while (npend > 0 && rounds < RESOLVE_MAX_ROUNDS) {
+    for (int k = t; k < npend; k += RT) {
+      const int64_t p = cur[k];
+      const PairRec rp = pairs[p];
+      if (first_at(p, rp, rp.ia, head, next, pairs, flags) &&
+          first_at(p, rp, rp.ib, head, next, pairs, flags))
+        flags[p] = 2;
+    }
+    if (t == 0) s_n = 0;
+    __syncthreads();
+    for (int k = t; k < npend; k += RT) {
+      const int64_t p = cur[k];
+      if (flags[p] == 2) {
+        kick(pairs[p], vel, mass, k0, k1, step, &s_dirfail);
+        flags[p] = 1;
+      } else {
+        nxt[atomicAdd(&s_n, 1)] = (int32_t)p;
+      }
+    }
+    __syncthreads();
+    npend = s_n;
+    int32_t* tmp = cur; cur = nxt; nxt = tmp;
+    ++rounds;
+    __syncthreads();
+  }
+  if (t == 0) {
+    if (npend > 0) atomicOr(&st->status, (unsigned)ST_ERR_ROUNDS);
+    st->n_rounds = (unsigned long long)rounds;
+    if (s_dirfail) {
+      atomicAdd(&st->n_dirfail, (unsigned long long)s_dirfail);
+      atomicOr(&st->status, (unsigned)ST_DIR_FAIL);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(GT) reset_kernel(const PairRec* __restrict__ pairs, int64_t cap,
+                                                   int32_t* head, int32_t* mult,
+                                                   const DevStats* st) {
+  const unsigned long long nall = st->n_acc;
+  if (nall > (unsigned long long)cap) return;
+  for (int64_t p = blockIdx.x * (int64_t)GT + threadIdx.x; p < (int64_t)nall;
+       p += (int64_t)gridDim.x * GT) {
+    head[pairs[p].ia] = -1;
+    head[pairs[p].ib] = -1;
+    mult[pairs[p].ia] = 0;
+    mult[pairs[p].ib] = 0;
+  }
+}
+
 }  // namespace
 
 int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* mass,
-                    int32_t* head, int32_t* next, uint8_t* flags, int32_t* mult, uint64_t seed,
-                    uint32_t step, DevStats* st, cudaStream_t s) {
-  resolve_kernel<<<1, RT, 0, s>>>(pairs, pair_cap, vel, mass, head, next, flags, mult,
-                                  (uint32_t)seed, (uint32_t)(seed >> 32), step, st);
-  return 1;
+                   int32_t* head, int32_t* next, uint8_t* flags, int32_t* mult, int32_t* pending,
+                   uint64_t seed, uint32_t step, DevStats* st, int sms, cudaStream_t s) {
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const unsigned g = (unsigned)(sms * 4);
+  count_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, mult, st);
+  split_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, vel, mass, head, next, flags, mult, pending, k0,
+                                k1, step, st);
+  rounds_kernel<<<1, RT, 0, s>>>(pairs, pair_cap, vel, mass, head, next, flags, pending,
+                                 pending + pair_cap, k0, k1, step, st);
+  reset_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, head, mult, st);
+  return 4;
 }
 
 // The same kernel for the no-allocation entry point: every scratch pointer

@@ -18,7 +18,7 @@ constexpr int WARP = 32;
 constexpr int LEAF = 32;                 // particles per tree leaf (one per lane)
 constexpr int MAX_LEVELS = 8;            // 32-ary levels: 32^8 leaves >> any n
 constexpr int BISECT_MAX_EVALS = 128;    // neighbour-count evaluations per particle
-constexpr int SEARCH_CAP = 1024;         // gathered candidates per query (shared memory)
+constexpr int SEARCH_CAP = 896;          // gathered candidates per query (shared memory)
 constexpr int SEARCH_STACK = 256;        // traversal stack per warp
 constexpr int RADIUS_MAX_ITERS = 24;     // gather-radius adjustments per query
 constexpr int RESOLVE_MAX_ROUNDS = 4096; // resolver rounds
@@ -51,6 +51,7 @@ struct StepParams {
 // Device counters of one step.
 struct DevStats {
   unsigned long long n_active, n_cand, n_acc, n_rounds, n_pge1, n_nonconv, n_dirfail, max_mult;
+  unsigned long long n_pending;   // accepted pairs that share a particle with another
   double sum_p;
   unsigned int status;
   unsigned int pad;
@@ -158,7 +159,9 @@ struct Sorted {               // particle state in key order
   double *m;
   double *h;                  // h of active particles (this step)
   double *dt;                 // dt_i of the particle
-  float4* f;                  // FP32 copy of the position (w = 0)
+  float4* f;                  // FP32 position (round to nearest); w = dt_i rounded up
+  float4* vm;                 // FP32 velocity (round to nearest); w = m rounded up
+  float2* hb;                 // h of active particles rounded down / up
   uint32_t* id;
   uint8_t* act;
   int32_t* orig;              // user-order index
@@ -188,8 +191,9 @@ int tree_levels_for(int64_t n, int64_t count[MAX_LEVELS]);
 
 // search.cu
 int launch_search(const Sorted& so, const Tree& t, int64_t n, const int32_t* act_list,
-                   const StepParams* p, double box, int n_ngb, int tol, double fixed_h,
-                   double* h_user, DevStats* st, int* work, cudaStream_t s);
+                  const StepParams* p, double box, int n_ngb, int tol, double fixed_h,
+                  double* h_user, int32_t* nb_list, int32_t* nb_count, int nb_stride,
+                  DevStats* st, int* work, int sms, cudaStream_t s);
 
 // pairs.cu
 struct PairArgs {
@@ -203,14 +207,15 @@ struct PairArgs {
   int64_t pair_cap;
 };
 int launch_pairs(const Sorted& so, const Tree& t, int64_t n, const int32_t* act_list,
-                  const PairArgs& a, PairRec* pairs, double* dtlim_user, DevStats* st,
-                  int* work, cudaStream_t s);
+                 const int32_t* nb_list, const int32_t* nb_count, int nb_stride,
+                 const PairArgs& a, PairRec* pairs, double* dtlim_user, DevStats* st,
+                 int* work, int sms, cudaStream_t s);
 
 // resolve.cu
 int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* mass,
-                    int32_t* head, int32_t* next, uint8_t* flags, int32_t* mult,
-                    uint64_t seed, uint32_t step, DevStats* st, cudaStream_t s);
-int launch_sort_pairs_for_output(PairRec* pairs, int64_t n, cudaStream_t s);
+                   int32_t* head, int32_t* next, uint8_t* flags, int32_t* mult,
+                   int32_t* pending, uint64_t seed, uint32_t step, DevStats* st, int sms,
+                   cudaStream_t s);
 void launch_resolve_with_scratch(const PairRec* pairs, int64_t pair_cap, double* vel,
                                  const double* mass, int32_t* head, int32_t* next, uint8_t* flags,
                                  int32_t* mult, uint64_t seed, uint32_t step, DevStats* st,

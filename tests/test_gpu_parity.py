@@ -43,7 +43,9 @@ def _compare(g, o, act, what=""):
     if not np.array_equal(g["vel"], o["vel"]):
         rel = np.abs(g["vel"] - o["vel"]) / np.maximum(np.abs(o["vel"]), 1e-300)
         pytest.fail(f"{what}: velocities differ, max rel {rel.max():.3e}")
-    assert math.isclose(gs["sum_p"], os_["sum_p"], rel_tol=1e-9, abs_tol=1e-300)
+    # sum_p is a statistic: pairs whose draw is decided on the FP32 upper
+    # bound contribute their FP32 estimate (relative error < 1e-5)
+    assert math.isclose(gs["sum_p"], os_["sum_p"], rel_tol=1e-5, abs_tol=1e-30)
     assert abs(gs["e_after"] - os_["e_after"]) <= 1e-13 * abs(os_["e_after"]) + 1e-300
 
 
