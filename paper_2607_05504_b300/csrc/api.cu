@@ -51,9 +51,7 @@ struct sidm_ctx {
   unsigned* latched = nullptr;
   int* work = nullptr;
   PairRec* pairs = nullptr;
-  int32_t *head = nullptr, *next = nullptr, *mult = nullptr;
-  uint8_t* pflags = nullptr;
-  int32_t* pending = nullptr;   // 2 x pair capacity: pending pairs of the resolver rounds
+  ResolveBuffers rb{};          // per-particle segments and cursors of the resolver
   double *cons_partial = nullptr, *cons = nullptr;
   // pinned host staging
   DevStats* h_stats = nullptr;
@@ -178,15 +176,21 @@ int ensure_capacity(sidm_ctx* c, int64_t n) {
   CK(dalloc(c, &c->latched, 1));
   CK(dalloc(c, &c->work, 8));
   CK(dalloc(c, &c->pairs, pc));
-  CK(dalloc(c, &c->head, want));
-  CK(dalloc(c, &c->mult, want));
-  CK(dalloc(c, &c->next, 2 * pc));
-  CK(dalloc(c, &c->pflags, pc));
-  CK(dalloc(c, &c->pending, 2 * pc));
+  ResolveBuffers& rb = c->rb;
+  CK(dalloc(c, &rb.mult, want));
+  CK(dalloc(c, &rb.seg_off, want));
+  CK(dalloc(c, &rb.fill, want));
+  CK(dalloc(c, &rb.cursor, want));
+  CK(dalloc(c, &rb.seg, 2 * pc));
+  CK(dalloc(c, &rb.touched, 2 * pc));
+  CK(dalloc(c, &rb.pending, pc));
+  CK(dalloc(c, &rb.flags, pc));
   CK(dalloc(c, &c->cons_partial, 4 * conserved_blocks()));
   CK(dalloc(c, &c->cons, 8));
-  CK(cudaMemsetAsync(c->head, 0xFF, want * sizeof(int32_t), c->stream));
-  CK(cudaMemsetAsync(c->mult, 0, want * sizeof(int32_t), c->stream));
+  CK(cudaMemsetAsync(rb.mult, 0, want * sizeof(int32_t), c->stream));
+  CK(cudaMemsetAsync(rb.seg_off, 0xFF, want * sizeof(int32_t), c->stream));
+  CK(cudaMemsetAsync(rb.fill, 0, want * sizeof(int32_t), c->stream));
+  CK(cudaMemsetAsync(rb.cursor, 0, want * sizeof(int32_t), c->stream));
   CK(cudaMemsetAsync(c->latched, 0, sizeof(unsigned), c->stream));
   c->cap = want;
   c->pair_cap = pc;
@@ -416,8 +420,10 @@ int sidm_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins, do
     L += launch_pairs(c->so, t, n, c->act_list, c->nb_list, c->nb_count, c->nb_stride, pa,
                       c->pairs, c->dtlim, c->dstats, c->work + 1, c->sms, s);
     mark(5);
-    L += launch_resolve(c->pairs, c->pair_cap, c->vel, c->mass, c->head, c->next, c->pflags,
-                        c->mult, c->pending, seed, (uint32_t)c->step, c->dstats, c->sms, s);
+    const int nr = launch_resolve(c->pairs, c->pair_cap, c->vel, c->mass, c->rb, seed,
+                                  (uint32_t)c->step, c->dstats, c->sms, s);
+    if (nr < 0) return SIDM_ERR_CUDA;
+    L += nr;
     mark(6);
   }
   latch_kernel<<<1, 32, 0, s>>>(c->dstats, c->latched);

@@ -150,14 +150,75 @@ __global__ void __launch_bounds__(RT) resolve_kernel(const PairRec* __restrict__
   }
 }
 
-// ---- step path: isolated pairs in parallel, the rest in rounds ----------
+// ---- step path: dataflow application ------------------------------------
 //
-// A pair whose two particles take part in no other accepted pair commutes
-// with every other kick, so it is applied at once by any thread.  Only the
-// remaining ("pending") pairs go through the rounds, and each round visits
-// only the pairs still pending.
+// 1. count: accepted pairs per particle.
+// 2. split: a pair whose two particles take part in no other accepted pair
+//    commutes with every other kick and is applied at once; the others are
+//    "pending".  Each particle of a pending pair gets a segment of its pairs.
+// 3. fill + sort: the segments are filled and sorted by key (ord, a, b), and
+//    every particle gets a cursor at its first segment entry.
+// 4. dataflow: a pending pair is ready when it sits at the cursor of both of
+//    its particles, i.e. when every earlier pair of both particles has been
+//    applied.  Ready pairs are applied and advance the two cursors (release
+//    store after the kick; acquire load before reading velocities), so every
+//    particle meets its pairs in key order -- the sequential result.  The
+//    grid is launched cooperatively (all blocks resident); the globally first
+//    unapplied pair is always ready, so the passes make progress.  A bounded
+//    number of passes guards against a stuck state (error flag).
+// 5. reset the per-particle arrays that were touched.
 
 constexpr int GT = 256;
+constexpr int DATAFLOW_MAX_PASSES = 1 << 22;
+
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// The kick of a pending pair, with the velocities read and written through
+// L2 (other SMs apply the neighbouring kicks).
+__device__ void kick_l2(const PairRec& r, double* vel, const double* mass, uint32_t k0,
+                        uint32_t k1, uint32_t step, unsigned* dirfail) {
+  double e0 = 0.0, e1 = 0.0, e2 = 1.0;
+  bool found = false;
+  for (uint32_t t = 0; t < DIRECTION_TRIES && !found; ++t) {
+    const U4 w = philox10(k0, k1, step, 1u + t, r.a, r.b);
+    const double x1 = 2.0 * unit53(w.x, w.y) - 1.0;
+    const double x2 = 2.0 * unit53(w.z, w.w) - 1.0;
+    const double s = x1 * x1 + x2 * x2;
+    if (s > 0.0 && s < 1.0) {
+      const double k = 2.0 * sqrt(1.0 - s);
+      e0 = x1 * k;
+      e1 = x2 * k;
+      e2 = 1.0 - 2.0 * s;
+      found = true;
+    }
+  }
+  if (!found) atomicAdd(dirfail, 1u);
+  double* va = vel + 3 * (int64_t)r.ia;
+  double* vb = vel + 3 * (int64_t)r.ib;
+  const double ma = mass[r.ia], mb = mass[r.ib];
+  const double M = ma + mb;
+  const double ax = __ldcg(va), ay = __ldcg(va + 1), az = __ldcg(va + 2);
+  const double bx = __ldcg(vb), by = __ldcg(vb + 1), bz = __ldcg(vb + 2);
+  const double cx = ((ma * ax) + (mb * bx)) / M;
+  const double cy = ((ma * ay) + (mb * by)) / M;
+  const double cz = ((ma * az) + (mb * bz)) / M;
+  const double dx = ax - bx, dy = ay - by, dz = az - bz;
+  const double g = sqrt((dx * dx + dy * dy) + dz * dz);
+  const double fa = (mb * g) / M, fb = (ma * g) / M;
+  __stcg(va, cx + fa * e0);
+  __stcg(va + 1, cy + fa * e1);
+  __stcg(va + 2, cz + fa * e2);
+  __stcg(vb, cx - fb * e0);
+  __stcg(vb + 1, cy - fb * e1);
+  __stcg(vb + 2, cz - fb * e2);
+}
 
 __global__ void __launch_bounds__(GT) count_kernel(const PairRec* __restrict__ pairs, int64_t cap,
                                                    int32_t* mult, const DevStats* st) {
@@ -170,11 +231,19 @@ __global__ void __launch_bounds__(GT) count_kernel(const PairRec* __restrict__ p
   }
 }
 
+// claim a segment for particle e (first claimant allocates mult[e] slots)
+__device__ __forceinline__ void claim_segment(int32_t e, const int32_t* mult, int32_t* seg_off,
+                                              int32_t* touched, DevStats* st) {
+  if (atomicCAS(&seg_off[e], -1, -2) == -1) {
+    const unsigned long long base = atomicAdd(&st->n_seg, (unsigned long long)mult[e]);
+    seg_off[e] = (int32_t)base;
+    touched[atomicAdd(&st->n_touched, 1ull)] = e;
+  }
+}
+
 __global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ pairs, int64_t cap,
                                                    double* vel, const double* __restrict__ mass,
-                                                   int32_t* head, int32_t* next, uint8_t* flags,
-                                                   const int32_t* __restrict__ mult,
-                                                   int32_t* pending, uint32_t k0, uint32_t k1,
+                                                   ResolveBuffers b, uint32_t k0, uint32_t k1,
                                                    uint32_t step, DevStats* st) {
   __shared__ unsigned s_dirfail;
   __shared__ int s_max;
@@ -186,21 +255,20 @@ __global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ p
   if (nall <= (unsigned long long)cap) {
     const int64_t na = (int64_t)nall;
     const int64_t stride = (int64_t)gridDim.x * GT;
-    // uniform trip count per warp (ballots below)
     for (int64_t base = blockIdx.x * (int64_t)GT + (threadIdx.x & ~31); base < na; base += stride) {
       const int64_t p = base + lane;
       bool pend = false;
       if (p < na) {
         const PairRec r = pairs[p];
-        const int ma = mult[r.ia], mb = mult[r.ib];
+        const int ma = b.mult[r.ia], mb = b.mult[r.ib];
         mm = max(mm, max(ma, mb));
         if (ma == 1 && mb == 1) {
           kick(r, vel, mass, k0, k1, step, &s_dirfail);
         } else {
           pend = true;
-          flags[p] = 0;
-          next[2 * p] = atomicExch(&head[r.ia], (int32_t)(2 * p));
-          next[2 * p + 1] = atomicExch(&head[r.ib], (int32_t)(2 * p + 1));
+          b.flags[p] = 0;
+          claim_segment(r.ia, b.mult, b.seg_off, b.touched, st);
+          claim_segment(r.ib, b.mult, b.seg_off, b.touched, st);
         }
       }
       const uint32_t m = __ballot_sync(0xffffffffu, pend);
@@ -209,7 +277,7 @@ __global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ p
         const int leader = __ffs(m) - 1;
         if (lane == leader) at = atomicAdd(&st->n_pending, (unsigned long long)__popc(m));
         at = __shfl_sync(0xffffffffu, at, leader);
-        if (pend) pending[at + __popc(m & ((1u << lane) - 1u))] = (int32_t)p;
+        if (pend) b.pending[at + __popc(m & ((1u << lane) - 1u))] = (int32_t)p;
       }
     }
   }
@@ -224,50 +292,83 @@ __global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ p
   }
 }
 
-__global__ void __launch_bounds__(RT) rounds_kernel(const PairRec* __restrict__ pairs, int64_t cap,
-                                                    double* vel, const double* __restrict__ mass,
-                                                    const int32_t* head, const int32_t* next,
-                                                    uint8_t* flags, int32_t* pend_a,
-                                                    int32_t* pend_b, uint32_t k0, uint32_t k1,
-                                                    uint32_t step, DevStats* st) {
-  __shared__ unsigned s_dirfail;
-  __shared__ int s_n;
-  const int t = threadIdx.x;
-  if (t == 0) s_dirfail = 0;
-  __syncthreads();
+__global__ void __launch_bounds__(GT) fill_kernel(const PairRec* __restrict__ pairs, int64_t cap,
+                                                  ResolveBuffers b, const DevStats* st) {
   if (st->n_acc > (unsigned long long)cap) return;
-  int npend = (int)st->n_pending;
-  int32_t* cur = pend_a;
-  int32_t* nxt = pend_b;
-  int rounds = 0;
-  while (npend > 0 && rounds < RESOLVE_MAX_ROUNDS) {
-    for (int k = t; k < npend; k += RT) {
-      const int64_t p = cur[k];
-      const PairRec rp = pairs[p];
-      if (first_at(p, rp, rp.ia, head, next, pairs, flags) &&
-          first_at(p, rp, rp.ib, head, next, pairs, flags))
-        flags[p] = 2;
+  const int64_t np = (int64_t)st->n_pending;
+  for (int64_t k = blockIdx.x * (int64_t)GT + threadIdx.x; k < np; k += (int64_t)gridDim.x * GT) {
+    const int32_t p = b.pending[k];
+    const int32_t ea = pairs[p].ia, eb = pairs[p].ib;
+    b.seg[b.seg_off[ea] + atomicAdd(&b.fill[ea], 1)] = p;
+    b.seg[b.seg_off[eb] + atomicAdd(&b.fill[eb], 1)] = p;
+  }
+}
+
+__device__ __forceinline__ bool key_less_id(const PairRec* pairs, int32_t x, int32_t y) {
+  return key_less(pairs[x], pairs[y]);
+}
+
+// insertion sort of each particle's segment by key
+__global__ void __launch_bounds__(GT) segsort_kernel(const PairRec* __restrict__ pairs,
+                                                     int64_t cap, ResolveBuffers b,
+                                                     const DevStats* st) {
+  if (st->n_acc > (unsigned long long)cap) return;
+  const int64_t nt = (int64_t)st->n_touched;
+  for (int64_t k = blockIdx.x * (int64_t)GT + threadIdx.x; k < nt; k += (int64_t)gridDim.x * GT) {
+    const int32_t e = b.touched[k];
+    int32_t* sg = b.seg + b.seg_off[e];
+    const int len = b.mult[e];
+    for (int i = 1; i < len; ++i) {
+      const int32_t x = sg[i];
+      int j = i - 1;
+      while (j >= 0 && key_less_id(pairs, x, sg[j])) {
+        sg[j + 1] = sg[j];
+        --j;
+      }
+      sg[j + 1] = x;
     }
-    if (t == 0) s_n = 0;
-    __syncthreads();
-    for (int k = t; k < npend; k += RT) {
-      const int64_t p = cur[k];
-      if (flags[p] == 2) {
-        kick(pairs[p], vel, mass, k0, k1, step, &s_dirfail);
-        flags[p] = 1;
-      } else {
-        nxt[atomicAdd(&s_n, 1)] = (int32_t)p;
+  }
+}
+
+__global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict__ pairs, int64_t cap,
+                                                      double* vel, const double* __restrict__ mass,
+                                                      ResolveBuffers b, uint32_t k0, uint32_t k1,
+                                                      uint32_t step, DevStats* st) {
+  __shared__ unsigned s_dirfail;
+  __shared__ int s_passes;
+  if (threadIdx.x == 0) { s_dirfail = 0; s_passes = 0; }
+  __syncthreads();
+  if (st->n_acc <= (unsigned long long)cap) {
+    const int64_t np = (int64_t)st->n_pending;
+    const int64_t gsize = (int64_t)gridDim.x * GT;
+    const int64_t t0 = blockIdx.x * (int64_t)GT + threadIdx.x;
+    int pass = 0;
+    bool left = t0 < np;
+    for (; left && pass < DATAFLOW_MAX_PASSES; ++pass) {
+      left = false;
+      for (int64_t k = t0; k < np; k += gsize) {
+        const int32_t p = b.pending[k];
+        if (b.flags[p]) continue;
+        const PairRec r = pairs[p];
+        const int ca = ld_acquire(&b.cursor[r.ia]);
+        const int cb = ld_acquire(&b.cursor[r.ib]);
+        if (b.seg[b.seg_off[r.ia] + ca] == p && b.seg[b.seg_off[r.ib] + cb] == p) {
+          kick_l2(r, vel, mass, k0, k1, step, &s_dirfail);
+          __threadfence();
+          st_release(&b.cursor[r.ia], ca + 1);
+          st_release(&b.cursor[r.ib], cb + 1);
+          b.flags[p] = 1;
+        } else {
+          left = true;
+        }
       }
     }
-    __syncthreads();
-    npend = s_n;
-    int32_t* tmp = cur; cur = nxt; nxt = tmp;
-    ++rounds;
-    __syncthreads();
+    if (left) atomicOr(&st->status, (unsigned)ST_ERR_ROUNDS);
+    atomicMax(&s_passes, pass);
   }
-  if (t == 0) {
-    if (npend > 0) atomicOr(&st->status, (unsigned)ST_ERR_ROUNDS);
-    st->n_rounds = (unsigned long long)rounds;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicMax(&st->n_rounds, (unsigned long long)s_passes);
     if (s_dirfail) {
       atomicAdd(&st->n_dirfail, (unsigned long long)s_dirfail);
       atomicOr(&st->status, (unsigned)ST_DIR_FAIL);
@@ -276,34 +377,60 @@ __global__ void __launch_bounds__(RT) rounds_kernel(const PairRec* __restrict__ 
 }
 
 __global__ void __launch_bounds__(GT) reset_kernel(const PairRec* __restrict__ pairs, int64_t cap,
-                                                   int32_t* head, int32_t* mult,
-                                                   const DevStats* st) {
+                                                   ResolveBuffers b, const DevStats* st) {
   const unsigned long long nall = st->n_acc;
   if (nall > (unsigned long long)cap) return;
-  for (int64_t p = blockIdx.x * (int64_t)GT + threadIdx.x; p < (int64_t)nall;
-       p += (int64_t)gridDim.x * GT) {
-    head[pairs[p].ia] = -1;
-    head[pairs[p].ib] = -1;
-    mult[pairs[p].ia] = 0;
-    mult[pairs[p].ib] = 0;
+  const int64_t stride = (int64_t)gridDim.x * GT;
+  const int64_t t0 = blockIdx.x * (int64_t)GT + threadIdx.x;
+  for (int64_t p = t0; p < (int64_t)nall; p += stride) {
+    b.mult[pairs[p].ia] = 0;
+    b.mult[pairs[p].ib] = 0;
   }
+  const int64_t nt = (int64_t)st->n_touched;
+  for (int64_t k = t0; k < nt; k += stride) {
+    const int32_t e = b.touched[k];
+    b.seg_off[e] = -1;
+    b.fill[e] = 0;
+    b.cursor[e] = 0;
+  }
+}
+
+int dataflow_grid(int sms) {
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, dataflow_kernel, GT, 0) != cudaSuccess ||
+        v < 1)
+      v = 1;
+    per_sm = v;
+  }
+  return per_sm * sms;
 }
 
 }  // namespace
 
 int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* mass,
-                   int32_t* head, int32_t* next, uint8_t* flags, int32_t* mult, int32_t* pending,
-                   uint64_t seed, uint32_t step, DevStats* st, int sms, cudaStream_t s) {
-  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+                   const ResolveBuffers& b, uint64_t seed, uint32_t step, DevStats* st, int sms,
+                   cudaStream_t s) {
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   const unsigned g = (unsigned)(sms * 4);
-  count_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, mult, st);
-  split_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, vel, mass, head, next, flags, mult, pending, k0,
-                                k1, step, st);
-  rounds_kernel<<<1, RT, 0, s>>>(pairs, pair_cap, vel, mass, head, next, flags, pending,
-                                 pending + pair_cap, k0, k1, step, st);
-  reset_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, head, mult, st);
-  return 4;
+  count_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, b.mult, st);
+  split_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, vel, mass, b, k0, k1, step, st);
+  fill_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, b, st);
+  segsort_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, b, st);
+  // cooperative launch: every block resident, as the passes wait on each other
+  ResolveBuffers bb = b;
+  PairRec* pp = pairs;
+  int64_t cap = pair_cap;
+  void* args[] = {(void*)&pp, (void*)&cap, (void*)&vel, (void*)&mass, (void*)&bb,
+                  (void*)&k0, (void*)&k1, (void*)&step, (void*)&st};
+  if (cudaLaunchCooperativeKernel((const void*)dataflow_kernel, dim3(dataflow_grid(sms)),
+                                  dim3(GT), args, 0, s) != cudaSuccess)
+    return -1;
+  reset_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, b, st);
+  return 6;
 }
+
 
 // The same kernel for the no-allocation entry point: every scratch pointer
 // (head, next, flags, mult, st) is supplied by the caller.

@@ -52,6 +52,8 @@ struct StepParams {
 struct DevStats {
   unsigned long long n_active, n_cand, n_acc, n_rounds, n_pge1, n_nonconv, n_dirfail, max_mult;
   unsigned long long n_pending;   // accepted pairs that share a particle with another
+  unsigned long long n_seg;       // segment slots handed out to particles of pending pairs
+  unsigned long long n_touched;   // particles of pending pairs
   double sum_p;
   unsigned int status;
   unsigned int pad;
@@ -212,9 +214,18 @@ int launch_pairs(const Sorted& so, const Tree& t, int64_t n, const int32_t* act_
                  int* work, int sms, cudaStream_t s);
 
 // resolve.cu
+struct ResolveBuffers {
+  int32_t* mult;      // [n] accepted pairs per particle (0 between steps)
+  int32_t* seg_off;   // [n] start of the particle's pair segment (-1 between steps)
+  int32_t* fill;      // [n] segment fill counter (0 between steps)
+  int32_t* cursor;    // [n] first unapplied entry of the segment (0 between steps)
+  int32_t* seg;       // [2 cap] pair ids, one segment per particle, sorted by key
+  int32_t* touched;   // [2 cap] particles that own a segment
+  int32_t* pending;   // [cap] pairs that share a particle with another pair
+  uint8_t* flags;     // [cap] applied flags
+};
 int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* mass,
-                   int32_t* head, int32_t* next, uint8_t* flags, int32_t* mult,
-                   int32_t* pending, uint64_t seed, uint32_t step, DevStats* st, int sms,
+                   const ResolveBuffers& b, uint64_t seed, uint32_t step, DevStats* st, int sms,
                    cudaStream_t s);
 void launch_resolve_with_scratch(const PairRec* pairs, int64_t pair_cap, double* vel,
                                  const double* mass, int32_t* head, int32_t* next, uint8_t* flags,
