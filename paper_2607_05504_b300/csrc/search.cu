@@ -3,24 +3,27 @@
 // its neighbour list N(i) = {j != i : r_ij^2 < h_i^2}.
 //
 // One warp per active particle i:
-//   1. Bounds.  Every separation is first taken in FP32 from the FP32 copies
-//      of the positions.  Those copies lie within 2^-24 |x| of the FP64
-//      values, so the true separation r lies in [lo, hi] with
-//      lo = r32 (1 - 2^-20) - E, hi = r32 (1 + 2^-20) + E,
-//      E = 2^-21 (max|x_i| + L) + 2^-21 r32 (generous over the rounding of
-//      coordinates, differences, squares, sums and the square root).
-//   2. Radius T: in the key-order window of 256 particles around i, the
-//      K-th smallest upper bound hi, K = N_ngb + tol + 1 (found by
-//      bisection on the float bit pattern).  K particles have r <= T.
-//   3. Gather: every particle with lo <= T goes into a shared-memory list as
-//      (lo, hi, index).  If more than SEARCH_CAP qualify, T shrinks
-//      (count-verified) and the gather repeats.
+//   1. Bounds.  Separations are first taken in FP32 from the FP32 copies of
+//      the positions (within 2^-24 |x| of the FP64 values), so the true
+//      separation r of a candidate with FP32 separation s lies in
+//      [lo(s), hi(s)], lo(s) = s (1 - c) - e, hi(s) = s (1 + c) + e with
+//      c = 2^-20 + 2^-21 and e = 2^-21 (max|x_i| + L) (generous over the
+//      rounding of coordinates, differences, squares, sums).  Every test
+//      "surely inside / surely outside radius H" becomes one comparison of
+//      the FP32 squared separation with a threshold computed once per H.
+//   2. Radius T: from the key-order window of 256 particles around i, an
+//      upper bound (within ~2 % above) of the K-th smallest hi,
+//      K = N_ngb + tol + 1: K particles have r <= T.
+//   3. Gather: every particle whose lower bound is <= T goes into a
+//      shared-memory list (FP32 squared separation, index).  If more than
+//      SEARCH_CAP qualify, T shrinks (count-verified) and the gather repeats.
 //   4. Bisection on the neighbour count c(h) = #{j : r^2 < h h}, in the same
 //      order of exactly rounded operations from the same start h0 as a
-//      direct count: for h h > T^2 the count is at least K (above the band);
-//      otherwise entries with hi below h count, entries with lo at or above h
-//      do not, and the rare entries whose bounds straddle h are decided on the
-//      exact FP64 r^2, computed in the fixed order (dx dx + dy dy) + dz dz.
+//      direct count: for h > T the count is at least K (above the band);
+//      otherwise entries surely inside count, entries surely outside do not,
+//      and the rare entries in between are decided on the exact FP64 r^2,
+//      computed in the fixed order (dx dx + dy dy) + dz dz.  Doubling and
+//      halving h are exact exponent steps; midpoints are one FP64 addition.
 //   5. The members of N(i) are written to the neighbour list of i (when the
 //      list is complete and fits); otherwise the list is marked for a direct
 //      tree walk in the pair kernel.
@@ -37,6 +40,8 @@ constexpr int NWIN = 8;               // window of 8 * 32 particles
 constexpr int CHUNK = 4;              // queries per work-counter increment
 constexpr float REL = 9.5367431640625e-07f;   // 2^-20
 constexpr float ABS = 4.76837158203125e-07f;  // 2^-21
+constexpr float CREL = REL + ABS;             // relative part of the bounds
+constexpr float SQ = 4.76837158203125e-07f;   // 2^-21: slack on squared thresholds
 
 struct SearchArgs {
   Sorted so;
@@ -60,30 +65,56 @@ __device__ __forceinline__ int warp_sum(int v) {
   return v;
 }
 
-struct Bounds {
-  float lo, hi;
-};
+// FP32 squared-separation thresholds for a radius H given by its FP32
+// bounds Hlo <= H <= Hhi:  s2 < in2 -> r < H surely;  s2 >= out2 -> r >= H surely.
+// (directed rounding throughout; SQ covers the rounding of s2 itself)
+__device__ __forceinline__ float thr_in2(float Hlo, float eq) {
+  const float x = __fdiv_rd(__fsub_rd(Hlo, eq), 1.0f + CREL);
+  return x > 0.0f ? __fmul_rd(__fmul_rd(x, x), 1.0f - SQ) : 0.0f;
+}
+__device__ __forceinline__ float thr_out2(float Hhi, float eq) {
+  const float x = __fdiv_ru(__fadd_ru(Hhi, eq), 1.0f - CREL);
+  return __fmul_ru(__fmul_ru(x, x), 1.0f + SQ);
+}
+// upper bound hi(s) of the true separation for FP32 squared separation s2
+__device__ __forceinline__ float upper_from_s2(float s2, float eq) {
+  return __fmul_ru(__fadd_ru(__fmul_ru(__fsqrt_ru(s2), 1.0f + CREL), eq), 1.0f + SQ);
+}
 
-// Separation bounds of particle j from the query (FP32), see the header.
-__device__ __forceinline__ Bounds sep_bounds(const float4& q, const float4& b, float box,
-                                             float eq) {
-  const float r = sqrtf(sep2f(q, b, box));
-  const float e = eq + ABS * r;
-  Bounds o;
-  o.lo = fmaxf(r * (1.0f - REL) - e, 0.0f);
-  o.hi = r * (1.0f + REL) + e;
-  return o;
+// FP32 bounds of a positive double by bit manipulation (exact, no FP64 ops)
+__device__ __forceinline__ void float_bounds(double h, float* lo, float* hi) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(h);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -125 || e > 126) {
+    *lo = __double2float_rd(h);
+    *hi = __double2float_ru(h);
+    return;
+  }
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const unsigned int fb = ((unsigned int)(e + 127) << 23) | (unsigned int)(m >> 29);
+  *lo = __uint_as_float(fb);
+  *hi = (m & 0x1FFFFFFFull) ? __uint_as_float(fb + 1u) : *lo;
+}
+
+// exact 2 h and h / 2 (exponent steps; FP64 multiply where that is not exact)
+__device__ __forceinline__ double twice(double h) {
+  const long long b = __double_as_longlong(h);
+  const int ef = (int)((b >> 52) & 0x7FF);
+  return (ef >= 1 && ef < 2046) ? __longlong_as_double(b + (1ll << 52)) : 2.0 * h;
+}
+__device__ __forceinline__ double half_of(double h) {
+  const long long b = __double_as_longlong(h);
+  const int ef = (int)((b >> 52) & 0x7FF);
+  return (ef > 1 && ef < 2047) ? __longlong_as_double(b - (1ll << 52)) : 0.5 * h;
 }
 
 __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
-  __shared__ float s_lo[SW][SEARCH_CAP];
-  __shared__ float s_hi[SW][SEARCH_CAP];
+  __shared__ float s_r2[SW][SEARCH_CAP];
   __shared__ int32_t s_j[SW][SEARCH_CAP];
   __shared__ int s_stack[SW][SEARCH_STACK];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  float* lst_lo = s_lo[warp];
-  float* lst_hi = s_hi[warp];
+  float* lst_r2 = s_r2[warp];
   int32_t* lst_j = s_j[warp];
   int* stack = s_stack[warp];
   const Sorted& so = A.so;
@@ -107,76 +138,74 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
     if (q >= n_act) break;
     const int64_t qi = q++;
     const int64_t s = A.act_list[qi];
-    const double xi = so.x[s], yi = so.y[s], zi = so.z[s];
     const float4 fi = so.f[s];
     const float eq = ABS * (fmaxf(fmaxf(fabsf(fi.x), fabsf(fi.y)), fabsf(fi.z)) + boxf);
     double h;
     int len = 0;
-    float T = INFINITY;  // gather radius (all j with lo <= T are in the list)
+    float T = INFINITY;  // every j with r <= T (and more) is in the list
 
     if (A.fixed_h > 0.0) {
       h = A.fixed_h;
-      // gather N(i) directly with radius h
-      T = __double2float_ru(h) * (1.0f + REL);
+      float hl, hu;
+      float_bounds(h, &hl, &hu);
+      T = hu;
     } else if (n - 1 >= K) {
       // ---- 2. radius T from the key-order window
       const int64_t W = (int64_t)NWIN * 32 < n ? (int64_t)NWIN * 32 : n;
       int64_t w0 = s - W / 2;
       if (w0 > n - W) w0 = n - W;
       if (w0 < 0) w0 = 0;
-      float hv[NWIN];
+      float wv[NWIN];
       float vmin = INFINITY, vmax = 0.0f;
 #pragma unroll
       for (int k = 0; k < NWIN; ++k) {
-        hv[k] = INFINITY;
+        wv[k] = INFINITY;
         const int64_t j = w0 + k * 32 + lane;
         if (j < w0 + W && j != s) {
-          hv[k] = sep_bounds(fi, so.f[j], boxf, eq).hi;
-          vmin = fminf(vmin, hv[k]);
-          vmax = fmaxf(vmax, hv[k]);
+          wv[k] = sep2f(fi, so.f[j], boxf);
+          vmin = fminf(vmin, wv[k]);
+          vmax = fmaxf(vmax, wv[k]);
         }
       }
       for (int o = 16; o > 0; o >>= 1) {
         vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
         vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
       }
-      // smallest T (bit pattern bisection) with #{hv <= T} >= K
+      // bit-pattern bisection for t with #{wv <= t} >= K; stop within 2^-6
       uint32_t blo = __float_as_uint(vmin), bhi = __float_as_uint(vmax);
-      if (blo > 0) --blo;                        // count(blo) < K unless ties
-      for (int it = 0; it < 40 && bhi - blo > 1; ++it) {
+      if (blo > 0) --blo;
+      for (int it = 0; it < 32 && bhi - blo > (1u << 17); ++it) {
         const uint32_t mid = blo + ((bhi - blo) >> 1);
         const float tm = __uint_as_float(mid);
         int c = 0;
 #pragma unroll
-        for (int k = 0; k < NWIN; ++k) c += hv[k] <= tm ? 1 : 0;
+        for (int k = 0; k < NWIN; ++k) c += wv[k] <= tm ? 1 : 0;
         c = warp_sum(c);
         if (c >= K) bhi = mid; else blo = mid;
       }
-      T = __uint_as_float(bhi);
+      T = upper_from_s2(__uint_as_float(bhi), eq);
     }
 
-    // ---- 3. gather every j with lo <= T (shrink T while the list overflows)
+    // ---- 3. gather every j whose lower bound is <= T
     bool complete = true;
     for (int attempt = 0;; ++attempt) {
       len = 0;
-      const float Tg = T * (1.0f + REL);
-      // covers every particle whose lower bound can be <= Tg (see the header)
+      const float g2 = T < INFINITY ? thr_out2(T * (1.0f + REL), eq) : INFINITY;
       const float rad = (T + 2.0f * eq) * (1.0f + 4.0f * REL);
       const float rad2 = rad < INFINITY ? rad * rad : INFINITY;
       const bool ok = traverse(A.t, fi, rad2, boxf, stack, [&](int leaf) {
         const int64_t j = (int64_t)leaf * LEAF + lane;
+        float s2 = 0.0f;
         bool keep = false;
-        Bounds b{0.f, 0.f};
         if (j < n && j != s) {
-          b = sep_bounds(fi, so.f[j], boxf, eq);
-          keep = b.lo <= Tg;
+          s2 = sep2f(fi, so.f[j], boxf);
+          keep = s2 < g2;
         }
         const uint32_t m = __ballot_sync(0xffffffffu, keep);
         if (keep) {
           const int at = len + __popc(m & lt);
           if (at < SEARCH_CAP) {
-            lst_lo[at] = b.lo;
-            lst_hi[at] = b.hi;
+            lst_r2[at] = s2;
             lst_j[at] = (int32_t)j;
           }
         }
@@ -202,12 +231,13 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
       float Tn = T * cbrtf(0.5f * (float)SEARCH_CAP / (float)len);
       bool verified = false;
       for (int inner = 0; inner < RADIUS_MAX_ITERS; ++inner) {
-        int c = 0;
+        const float in2 = thr_in2(Tn, eq);
         const float radn = (Tn + 2.0f * eq) * (1.0f + 4.0f * REL);
+        int c = 0;
         const bool ok2 = traverse(A.t, fi, radn * radn, boxf, stack, [&](int leaf) {
           const int64_t j = (int64_t)leaf * LEAF + lane;
           bool in = false;
-          if (j < n && j != s) in = sep_bounds(fi, so.f[j], boxf, eq).hi <= Tn;
+          if (j < n && j != s) in = sep2f(fi, so.f[j], boxf) < in2;
           c += __popc(__ballot_sync(0xffffffffu, in));
         });
         if (!ok2) { status |= ST_ERR_STACK; break; }
@@ -224,61 +254,74 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
     }
 
     // ---- 4. bisection on the exact neighbour count
-    const double R2 = (double)T * (double)T;   // K particles have r^2 < R2 (exact product)
+    const double xi = so.x[s], yi = so.y[s], zi = so.z[s];
     auto exact_r2 = [&](int k) {
       const int64_t j = lst_j[k];
       return sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half);
     };
-    // count of r^2 < h h over the list (exact), for h h <= R2
-    auto count_below = [&](double hh, float hl, float hu) {
+    // #{r^2 < h h} over the list (exact); requires h <= T (1 + 2^-22)
+    auto count_below = [&](double hv, float hl, float hu) {
+      const float in2 = thr_in2(hl, eq), out2 = thr_out2(hu, eq);
       int c = 0;
+      bool amb = false;
       for (int k = lane; k < len; k += 32) {
-        const float lo = lst_lo[k], hi = lst_hi[k];
-        if (hi < hl) ++c;
-        else if (lo < hu) c += exact_r2(k) < hh ? 1 : 0;
+        const float v = lst_r2[k];
+        c += v < in2 ? 1 : 0;
+        amb |= (v >= in2) && (v < out2);
+      }
+      if (__any_sync(0xffffffffu, amb)) {
+        const double hh = hv * hv;
+        for (int k = lane; k < len; k += 32) {
+          const float v = lst_r2[k];
+          if (v >= in2 && v < out2) c += exact_r2(k) < hh ? 1 : 0;
+        }
       }
       return warp_sum(c);
     };
+    const bool window_bound = !(A.fixed_h > 0.0) && (n - 1 >= K);
     if (!(A.fixed_h > 0.0)) {
       h = h0;
       double blo = 0.0, bhi = 0.0;
       bool have_hi = false, conv = false;
       for (int it = 0; it < BISECT_MAX_EVALS; ++it) {
-        const double hh = h * h;
+        float hl, hu;
+        float_bounds(h, &hl, &hu);
         int c;
-        if (n - 1 >= K && hh > R2) {
-          c = hi_band + 1;
+        if (window_bound && hl > T) {
+          c = hi_band + 1;   // K particles lie within T < h
         } else {
-          c = count_below(hh, __double2float_rd(h), __double2float_ru(h));
+          c = count_below(h, hl, hu);
         }
         if (c >= lo_band && c <= hi_band) { conv = true; break; }
         if (c < lo_band) {
           blo = h;
-          h = have_hi ? 0.5 * (blo + bhi) : 2.0 * h;
+          h = have_hi ? half_of(blo + bhi) : twice(h);
         } else {
           bhi = h;
           have_hi = true;
-          h = 0.5 * (blo + bhi);
+          h = half_of(blo + bhi);
         }
       }
       if (!conv) ++nonconv;
     }
 
     // ---- 5. neighbour list
-    const double hh = h * h;
-    const float hl = __double2float_rd(h), hu = __double2float_ru(h);
+    float hl, hu;
+    float_bounds(h, &hl, &hu);
     int* out = A.nb_list + qi * (int64_t)A.nb_stride;
     int cnt = -1;
-    const bool list_covers = complete && (n - 1 < K || A.fixed_h > 0.0 || hh <= R2);
+    const bool list_covers = complete && (!window_bound || !(hl > T));
     if (list_covers) {
+      const float in2 = thr_in2(hl, eq), out2 = thr_out2(hu, eq);
+      const double hh = h * h;
       cnt = 0;
       for (int k0 = 0; k0 < len; k0 += 32) {
         const int k = k0 + lane;
         bool in = false;
         if (k < len) {
-          const float lo = lst_lo[k], hi = lst_hi[k];
-          if (hi < hl) in = true;
-          else if (lo < hu) in = exact_r2(k) < hh;
+          const float v = lst_r2[k];
+          if (v < in2) in = true;
+          else if (v < out2) in = exact_r2(k) < hh;
         }
         const uint32_t m = __ballot_sync(0xffffffffu, in);
         if (in) {
@@ -315,7 +358,7 @@ int launch_search(const Sorted& so, const Tree& t, int64_t n, const int32_t* act
   if (n <= 0) return 0;
   SearchArgs a{so, t, n, act_list, p, box, n_ngb, tol, fixed_h, h_user,
                nb_list, nb_count, nb_stride, st, work};
-  int64_t blocks = (int64_t)sms * 8;
+  int64_t blocks = (int64_t)sms * 12;
   const int64_t need = (n + SW - 1) / SW;
   if (blocks > need) blocks = need;
   search_kernel<<<(unsigned)blocks, ST, 0, s>>>(a);
