@@ -142,6 +142,35 @@ SIDM_API int sidm_set_velocities(sidm_ctx* ctx, const double* vel, int ptr_kind)
 SIDM_API int sidm_step(sidm_ctx* ctx, const uint8_t* active_mask, const int8_t* dt_bins, double dt_max,
               const sidm_sigma_model* sigma, uint64_t seed, sidm_step_stats* stats);
 
+/* ---- Many independent haloes in one context ------------------------------
+ * The particle arrays of sidm_set_particles may hold several independent
+ * haloes (e.g. a batch of requests of different sizes), each a contiguous
+ * segment: halo k is particles [offsets[k], offsets[k+1]).  Every halo gets
+ * its own neighbour structure, start radius, cross-section model, random
+ * key and step counter, so a halo's results are bit-identical to a context
+ * that holds that halo alone with the same parameters; no pair ever joins
+ * particles of two haloes.  One sidm_step_haloes() call steps all haloes
+ * with one sequence of kernel launches.
+ *
+ * sidm_set_haloes: n_halos in [1, 4096]; offsets[0] = 0, offsets[n_halos] =
+ * the loaded particle count, non-decreasing (empty haloes are allowed).
+ * Must follow sidm_set_particles (which resets the context to one halo). */
+typedef struct {
+  double dt_max;              /* dt_i = dt_max 2^-bin_i for the halo's particles        */
+  sidm_sigma_model sigma;     /* cross-section model of the halo                       */
+  uint64_t seed;              /* Philox key of the halo                                */
+  uint64_t step;              /* step counter of the halo (Philox counter word 0)      */
+} sidm_halo_params;
+
+SIDM_API int sidm_set_haloes(sidm_ctx* ctx, int32_t n_halos, const int64_t* offsets);
+
+/* One scattering step of every halo; params[k] (host array of n_halos)
+ * holds halo k's parameters.  active_mask, dt_bins and stats as for
+ * sidm_step.  (sidm_step applies one parameter set, with the context's step
+ * counter, to every halo.) */
+SIDM_API int sidm_step_haloes(sidm_ctx* ctx, const uint8_t* active_mask, const int8_t* dt_bins,
+                              const sidm_halo_params* params, sidm_step_stats* stats);
+
 /* Waits for the context's stream; returns the latched device status. */
 SIDM_API int sidm_sync(sidm_ctx* ctx);
 

@@ -1,14 +1,16 @@
-// C ABI of the SIDM scattering-step library: context, buffers, validation and
-// the order of the kernels of one step.
+// C ABI of the SIDM scattering-step library: context, buffers, haloes,
+// validation and the order of the kernels of one step.
 //
 // Step (all on the context's stream, no host round trip unless statistics
 // are requested):
-//   bounding box -> start radius / key transform -> 30-bit spatial keys ->
-//   radix sort -> key-order copy of the state + active list -> 32-ary box
-//   tree -> h_SI per active particle -> candidate pairs, probabilities and
-//   draws, Eq. 9 limits -> canonical application of the accepted kicks.
+//   halo table upload -> bounding box per halo -> start radius / key
+//   transform per halo -> halo-prefixed spatial keys -> radix sort ->
+//   key-order copy of the state + active list -> 32-ary box tree per halo ->
+//   h_SI per active particle -> candidate pairs, probabilities and draws,
+//   Eq. 9 limits -> canonical application of the accepted kicks.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -31,6 +33,7 @@ struct sidm_ctx {
   // user order
   double *pos = nullptr, *vel = nullptr, *mass = nullptr, *h_user = nullptr, *dtlim = nullptr;
   uint32_t* ids = nullptr;
+  int32_t* halo_of = nullptr;   // halo of each particle
   uint8_t* act = nullptr;
   int8_t* bins = nullptr;
   // sort
@@ -43,10 +46,14 @@ struct sidm_ctx {
   int32_t* nb_list = nullptr;   // [n][nb_stride] neighbour lists of the active particles
   int32_t* nb_count = nullptr;  // [n] list length, or -1
   int nb_stride = 0;
-  Tree tree{};
+  // haloes and their trees
+  std::vector<Halo> halos;      // host copy (layout + per-step parameters)
+  Halo* d_halos = nullptr;
+  int halo_cap = 0;
+  Forest forest{};
+  int64_t node_cap = 0;
+  float4 *node_lo = nullptr, *node_hi = nullptr;
   // per step
-  StepParams* params = nullptr;
-  unsigned long long* mm = nullptr;
   DevStats* dstats = nullptr;
   unsigned* latched = nullptr;
   int* work = nullptr;
@@ -106,11 +113,20 @@ void free_buffers(sidm_ctx* c) {
   c->allocs.clear();
   c->cap = 0;
   c->pair_cap = 0;
+  c->halo_cap = 0;
+  c->node_cap = 0;
+  c->d_halos = nullptr;
+  c->node_lo = c->node_hi = nullptr;
 }
 
 __global__ void fill_kernel(double* p, int64_t n, double v) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) p[i] = v;
+}
+
+__global__ void fill_halo_kernel(int32_t* halo_of, int64_t start, int64_t n, int k) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) halo_of[start + i] = k;
 }
 
 __global__ void latch_kernel(const DevStats* st, unsigned* latched) {
@@ -128,19 +144,13 @@ int ensure_capacity(sidm_ctx* c, int64_t n) {
   free_buffers(c);
   want = std::max<int64_t>(want, 64);
   const int64_t pc = c->cfg.pair_capacity > 0 ? c->cfg.pair_capacity : 2 * want + 4096;
-  Tree& t = c->tree;
-  t.levels = tree_levels_for(want, t.count);
-  int64_t nodes = 0;
-  for (int l = 0; l < t.levels; ++l) {
-    t.offset[l] = nodes;
-    nodes += t.count[l];
-  }
   CK(dalloc(c, &c->pos, 3 * want));
   CK(dalloc(c, &c->vel, 3 * want));
   CK(dalloc(c, &c->mass, want));
   CK(dalloc(c, &c->h_user, want));
   CK(dalloc(c, &c->dtlim, want));
   CK(dalloc(c, &c->ids, want));
+  CK(dalloc(c, &c->halo_of, want));
   CK(dalloc(c, &c->act, want));
   CK(dalloc(c, &c->bins, want));
   CK(dalloc(c, &c->keys, want));
@@ -164,14 +174,11 @@ int ensure_capacity(sidm_ctx* c, int64_t n) {
   CK(dalloc(c, &so.id, want));
   CK(dalloc(c, &so.act, want));
   CK(dalloc(c, &so.orig, want));
+  CK(dalloc(c, &so.halo, want));
   CK(dalloc(c, &c->act_list, want));
   c->nb_stride = c->cfg.n_ngb + c->cfg.ngb_tol;
   CK(dalloc(c, &c->nb_count, want));
   CK(dalloc(c, &c->nb_list, want * (int64_t)c->nb_stride));
-  CK(dalloc(c, &t.lo, nodes));
-  CK(dalloc(c, &t.hi, nodes));
-  CK(dalloc(c, &c->params, 1));
-  CK(dalloc(c, &c->mm, 8));
   CK(dalloc(c, &c->dstats, 1));
   CK(dalloc(c, &c->latched, 1));
   CK(dalloc(c, &c->work, 8));
@@ -194,6 +201,86 @@ int ensure_capacity(sidm_ctx* c, int64_t n) {
   CK(cudaMemsetAsync(c->latched, 0, sizeof(unsigned), c->stream));
   c->cap = want;
   c->pair_cap = pc;
+  return SIDM_OK;
+}
+
+// Plain device buffers outside the capacity set (grown on demand).
+template <class T>
+cudaError_t grow(sidm_ctx* c, T** p, int64_t* have, int64_t need) {
+  if (*p && *have >= need) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  if (*p) {
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), (void*)*p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  return dalloc(c, p, (size_t)need);
+}
+
+// largest e (<= 60) with 8^e * n_ngb <= 4 n
+int start_exponent(int64_t n, int n_ngb) {
+  int e = 0;
+  while (e < 60 && std::ldexp((double)n_ngb, 3 * (e + 1)) <= 4.0 * (double)n) ++e;
+  return e;
+}
+
+// Halo layout from segment offsets (host): particle ranges, tree levels and
+// node offsets (level-major), start-radius exponents; fills halo_of.
+int layout_haloes(sidm_ctx* c, int n_halos, const int64_t* off) {
+  std::vector<Halo>& H = c->halos;
+  H.assign(n_halos, Halo{});
+  Forest& f = c->forest;
+  std::memset(f.level_nodes, 0, sizeof(f.level_nodes));
+  f.max_levels = 0;
+  for (int k = 0; k < n_halos; ++k) {
+    Halo& h = H[k];
+    h.start = off[k];
+    h.n = off[k + 1] - off[k];
+    h.levels = tree_levels_for(h.n, h.node_cnt);
+    for (int l = h.levels; l < MAX_LEVELS; ++l) h.node_cnt[l] = 0;
+    h.e0 = start_exponent(h.n, c->cfg.n_ngb);
+    for (int l = 0; l < MAX_LEVELS; ++l) f.level_nodes[l] += h.node_cnt[l];
+    f.max_levels = std::max(f.max_levels, h.levels);
+  }
+  int64_t base = 0;
+  for (int l = 0; l < MAX_LEVELS; ++l) {
+    int64_t run = base;
+    for (int k = 0; k < n_halos; ++k) {
+      H[k].node_off[l] = run;
+      run += H[k].node_cnt[l];
+    }
+    base += f.level_nodes[l];
+  }
+  int bits = 0;
+  while ((1 << bits) < n_halos) ++bits;
+  f.n_halos = n_halos;
+  f.halo_bits = n_halos > 1 ? bits : 0;
+  int64_t have = c->node_cap;
+  CK(grow(c, &c->node_lo, &have, std::max<int64_t>(base, 1)));
+  have = c->node_cap;
+  CK(grow(c, &c->node_hi, &have, std::max<int64_t>(base, 1)));
+  c->node_cap = std::max<int64_t>(c->node_cap, std::max<int64_t>(base, 1));
+  int64_t hc = c->halo_cap;
+  CK(grow(c, &c->d_halos, &hc, std::max(n_halos, 1)));
+  c->halo_cap = std::max(c->halo_cap, std::max(n_halos, 1));
+  f.lo = c->node_lo;
+  f.hi = c->node_hi;
+  f.halos = c->d_halos;
+  for (int k = 0; k < n_halos; ++k)
+    if (H[k].n > 0)
+      fill_halo_kernel<<<(unsigned)((H[k].n + 255) / 256), 256, 0, c->stream>>>(
+          c->halo_of, H[k].start, H[k].n, k);
+  CK(cudaGetLastError());
+  return SIDM_OK;
+}
+
+// Uploads the halo table (pageable copy: the host vector may change after).
+int upload_haloes(sidm_ctx* c) {
+  if (c->halos.empty()) return SIDM_OK;
+  CK(cudaMemcpyAsync(c->d_halos, c->halos.data(), c->halos.size() * sizeof(Halo),
+                     cudaMemcpyHostToDevice, c->stream));
   return SIDM_OK;
 }
 
@@ -228,6 +315,117 @@ int wait_and_collect(sidm_ctx* c) {
   CK(cudaMemsetAsync(c->latched, 0, sizeof(unsigned), c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return status_from_bits(*c->h_latched);
+}
+
+bool valid_sigma(const sidm_sigma_model& s) {
+  return (s.sigma0 >= 0.0) && std::isfinite(s.sigma0) &&
+         (s.kind == SIDM_SIGMA_CONST || (s.kind == SIDM_SIGMA_YUKAWA && s.w > 0.0 && std::isfinite(s.w)));
+}
+
+void set_step_params(Halo& h, double dt_max, const sidm_sigma_model& s, uint64_t seed,
+                     uint64_t step) {
+  h.dt_max = dt_max;
+  h.sigma_kind = s.kind;
+  h.sigma0 = s.sigma0;
+  h.w = s.kind == SIDM_SIGMA_YUKAWA ? s.w : 1.0;
+  h.seed = seed;
+  h.step = (uint32_t)step;
+}
+
+// The kernels of one step over every halo (the halo table is set).
+int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
+             sidm_step_stats* stats) {
+  const int64_t n = c->n;
+  cudaStream_t s = c->stream;
+  if (n > 0) {
+    if (active_mask)
+      CK(cudaMemcpyAsync(c->act, active_mask, n, is_device_ptr(active_mask)
+                                                      ? cudaMemcpyDeviceToDevice
+                                                      : cudaMemcpyHostToDevice, s));
+    else
+      CK(cudaMemsetAsync(c->act, 1, n, s));
+    if (dt_bins)
+      CK(cudaMemcpyAsync(c->bins, dt_bins, n, is_device_ptr(dt_bins) ? cudaMemcpyDeviceToDevice
+                                                                     : cudaMemcpyHostToDevice, s));
+    else
+      CK(cudaMemsetAsync(c->bins, 0, n, s));
+  }
+  const int r0 = upload_haloes(c);
+  if (r0 != SIDM_OK) return r0;
+  CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), s));
+  CK(cudaMemsetAsync(c->work, 0, 8 * sizeof(int), s));
+  int64_t& L = c->launches;
+  if (stats) L += launch_conserved(c->vel, c->mass, n, c->cons_partial, c->cons, s);
+  const bool prof = c->have_events && n > 0;
+  auto mark = [&](int k) {
+    if (prof) cudaEventRecord(c->ev[k], s);
+  };
+  c->timed_step = prof;
+  const int nh = (int)c->halos.size();
+  const Forest& F = c->forest;
+  if (n > 0) {
+    mark(0);
+    L += launch_bbox(c->pos, c->halo_of, n, c->d_halos, nh, s);
+    L += launch_params(c->d_halos, nh, c->cfg.box, s);
+    L += launch_keys(c->pos, c->halo_of, n, c->d_halos, F.halo_bits, c->cfg.box, c->keys,
+                     c->vals, s);
+    mark(1);
+    const int mb = (30 - F.halo_bits) / 3;
+    L += radix_sort_pairs(c->keys, c->vals, c->keys_alt, c->vals_alt, n, F.halo_bits + 3 * mb,
+                          c->sort_tmp, s);
+    mark(2);
+    L += launch_permute(c->vals, n, c->pos, c->vel, c->mass, c->ids, c->halo_of, c->act,
+                        c->bins, c->d_halos, c->so, c->act_list, c->dstats, s);
+    L += launch_forest(c->so, F, s);
+    mark(3);
+    L += launch_search(c->so, F, n, c->act_list, c->cfg.box, c->cfg.n_ngb, c->cfg.ngb_tol,
+                       c->cfg.fixed_h, c->h_user, c->nb_list, c->nb_count, c->nb_stride,
+                       c->dstats, c->work, c->sms, s);
+    mark(4);
+    PairArgs pa;
+    pa.kernel = c->cfg.kernel;
+    pa.c_sidm = c->cfg.c_sidm;
+    pa.box = c->cfg.box;
+    pa.pair_cap = c->pair_cap;
+    L += launch_pairs(c->so, F, n, c->act_list, c->nb_list, c->nb_count, c->nb_stride, pa,
+                      c->pairs, c->dtlim, c->dstats, c->work + 1, c->sms, s);
+    mark(5);
+    const int nr = launch_resolve(c->pairs, c->pair_cap, c->vel, c->mass, c->halo_of,
+                                  c->d_halos, c->rb, c->dstats, c->sms, s);
+    if (nr < 0) return SIDM_ERR_CUDA;
+    L += nr;
+    mark(6);
+  }
+  latch_kernel<<<1, 32, 0, s>>>(c->dstats, c->latched);
+  L += 1;
+  CK(cudaGetLastError());
+  c->step += 1;
+  if (!stats) return SIDM_OK;
+  L += launch_conserved(c->vel, c->mass, n, c->cons_partial, c->cons + 4, s);
+  CK(cudaMemcpyAsync(c->h_stats, c->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->h_cons, c->cons, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  const int st = wait_and_collect(c);
+  const DevStats& d = *c->h_stats;
+  std::memset(stats, 0, sizeof(*stats));
+  stats->n_active = (int64_t)d.n_active;
+  stats->n_candidate_pairs = (int64_t)d.n_cand;
+  stats->n_accepted = (int64_t)d.n_acc;
+  stats->n_rounds = (int64_t)d.n_rounds;
+  stats->n_p_ge_1 = (int64_t)d.n_pge1;
+  stats->n_h_nonconv = (int64_t)d.n_nonconv;
+  stats->n_dir_fail = (int64_t)d.n_dirfail;
+  stats->max_multiplicity = (int64_t)d.max_mult;
+  stats->sum_p = d.sum_p;
+  stats->e_before = c->h_cons[0];
+  stats->p_before[0] = c->h_cons[1];
+  stats->p_before[1] = c->h_cons[2];
+  stats->p_before[2] = c->h_cons[3];
+  stats->e_after = c->h_cons[4];
+  stats->p_after[0] = c->h_cons[5];
+  stats->p_after[1] = c->h_cons[6];
+  stats->p_after[2] = c->h_cons[7];
+  stats->status = st;
+  return st;
 }
 
 }  // namespace
@@ -324,24 +522,37 @@ int sidm_set_particles(sidm_ctx* c, int64_t n, const double* pos, const double* 
     fill(c->h_user, n, 0.0, c->stream);
     fill(c->dtlim, n, INFINITY, c->stream);
   }
+  c->loaded = false;
+  const int64_t off[2] = {0, n};
+  r = layout_haloes(c, 1, off);
+  if (r != SIDM_OK) return r;
   // periodic box: every coordinate in [0, box)
   if (c->cfg.box > 0.0 && n > 0) {
-    launch_bbox(c->pos, n, c->mm, c->stream);
+    r = upload_haloes(c);
+    if (r != SIDM_OK) return r;
+    launch_bbox(c->pos, c->halo_of, n, c->d_halos, 1, c->stream);
     unsigned long long hm[6];
-    CK(cudaMemcpyAsync(hm, c->mm, sizeof(hm), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(hm, (const char*)c->d_halos + offsetof(Halo, mm), sizeof(hm),
+                       cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    for (int k2 = 0; k2 < 3; ++k2) {
-      const double lo = ordered_to_dbl(hm[k2]), hi = ordered_to_dbl(hm[3 + k2]);
-      if (!(lo >= 0.0) || !(hi < c->cfg.box)) {
-        c->loaded = false;
-        return SIDM_ERR_INVALID_ARG;
-      }
+    for (int a = 0; a < 3; ++a) {
+      const double lo = ordered_to_dbl(hm[a]), hi = ordered_to_dbl(hm[3 + a]);
+      if (!(lo >= 0.0) || !(hi < c->cfg.box)) return SIDM_ERR_INVALID_ARG;
     }
   }
   CK(cudaGetLastError());
   c->n = n;
   c->loaded = true;
   return SIDM_OK;
+}
+
+int sidm_set_haloes(sidm_ctx* c, int32_t n_halos, const int64_t* offsets) {
+  if (!c || !c->loaded || n_halos < 1 || n_halos > (1 << 12) || !offsets) return SIDM_ERR_INVALID_ARG;
+  if (offsets[0] != 0 || offsets[n_halos] != c->n) return SIDM_ERR_INVALID_ARG;
+  for (int k = 0; k < n_halos; ++k)
+    if (offsets[k + 1] < offsets[k]) return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  return layout_haloes(c, n_halos, offsets);
 }
 
 int sidm_set_velocities(sidm_ctx* c, const double* vel, int ptr_kind) {
@@ -357,105 +568,26 @@ int sidm_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins, do
               const sidm_sigma_model* sigma, uint64_t seed, sidm_step_stats* stats) {
   if (!c || !sigma) return SIDM_ERR_INVALID_ARG;
   if (!c->loaded) return SIDM_ERR_NOT_READY;
-  if (!(dt_max > 0.0) || !std::isfinite(dt_max) || !(sigma->sigma0 >= 0.0) ||
-      !std::isfinite(sigma->sigma0) ||
-      (sigma->kind != SIDM_SIGMA_CONST && sigma->kind != SIDM_SIGMA_YUKAWA) ||
-      (sigma->kind == SIDM_SIGMA_YUKAWA && !(sigma->w > 0.0)))
-    return SIDM_ERR_INVALID_ARG;
+  if (!(dt_max > 0.0) || !std::isfinite(dt_max) || !valid_sigma(*sigma)) return SIDM_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
-  const int64_t n = c->n;
-  cudaStream_t s = c->stream;
-  if (n > 0) {
-    if (active_mask)
-      CK(cudaMemcpyAsync(c->act, active_mask, n, is_device_ptr(active_mask)
-                                                      ? cudaMemcpyDeviceToDevice
-                                                      : cudaMemcpyHostToDevice, s));
-    else
-      CK(cudaMemsetAsync(c->act, 1, n, s));
-    if (dt_bins)
-      CK(cudaMemcpyAsync(c->bins, dt_bins, n, is_device_ptr(dt_bins) ? cudaMemcpyDeviceToDevice
-                                                                     : cudaMemcpyHostToDevice, s));
-    else
-      CK(cudaMemsetAsync(c->bins, 0, n, s));
+  for (Halo& h : c->halos) set_step_params(h, dt_max, *sigma, seed, c->step);
+  return run_step(c, active_mask, dt_bins, stats);
+}
+
+int sidm_step_haloes(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
+                     const sidm_halo_params* params, sidm_step_stats* stats) {
+  if (!c || !params) return SIDM_ERR_INVALID_ARG;
+  if (!c->loaded) return SIDM_ERR_NOT_READY;
+  for (size_t k = 0; k < c->halos.size(); ++k) {
+    const sidm_halo_params& p = params[k];
+    if (!(p.dt_max > 0.0) || !std::isfinite(p.dt_max) || !valid_sigma(p.sigma))
+      return SIDM_ERR_INVALID_ARG;
   }
-  CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), s));
-  CK(cudaMemsetAsync(c->work, 0, 8 * sizeof(int), s));
-  int64_t& L = c->launches;
-  if (stats) L += launch_conserved(c->vel, c->mass, n, c->cons_partial, c->cons, s);
-  const bool prof = c->have_events && n > 0;
-  auto mark = [&](int k) {
-    if (prof) cudaEventRecord(c->ev[k], s);
-  };
-  c->timed_step = prof;
-  if (n > 0) {
-    mark(0);
-    L += launch_bbox(c->pos, n, c->mm, s);
-    L += launch_params(c->mm, c->params, c->cfg.box, n, c->cfg.n_ngb, s);
-    L += launch_keys(c->pos, n, c->params, c->cfg.box, c->keys, c->vals, s);
-    mark(1);
-    L += radix_sort_pairs(c->keys, c->vals, c->keys_alt, c->vals_alt, n, 30, c->sort_tmp, s);
-    mark(2);
-    L += launch_permute(c->vals, n, c->pos, c->vel, c->mass, c->ids, c->act, c->bins, dt_max,
-                        c->so, c->act_list, c->dstats, s);
-    Tree t = c->tree;
-    t.levels = tree_levels_for(n, t.count);
-    int64_t off = 0;
-    for (int l = 0; l < t.levels; ++l) { t.offset[l] = off; off += t.count[l]; }
-    L += launch_tree(c->so, n, t, s);
-    mark(3);
-    L += launch_search(c->so, t, n, c->act_list, c->params, c->cfg.box, c->cfg.n_ngb,
-                       c->cfg.ngb_tol, c->cfg.fixed_h, c->h_user, c->nb_list, c->nb_count,
-                       c->nb_stride, c->dstats, c->work, c->sms, s);
-    mark(4);
-    PairArgs pa;
-    pa.kernel = c->cfg.kernel;
-    pa.sigma_kind = sigma->kind;
-    pa.sigma0 = sigma->sigma0;
-    pa.w = sigma->kind == SIDM_SIGMA_YUKAWA ? sigma->w : 1.0;
-    pa.c_sidm = c->cfg.c_sidm;
-    pa.box = c->cfg.box;
-    pa.seed = seed;
-    pa.step = (uint32_t)c->step;
-    pa.pair_cap = c->pair_cap;
-    L += launch_pairs(c->so, t, n, c->act_list, c->nb_list, c->nb_count, c->nb_stride, pa,
-                      c->pairs, c->dtlim, c->dstats, c->work + 1, c->sms, s);
-    mark(5);
-    const int nr = launch_resolve(c->pairs, c->pair_cap, c->vel, c->mass, c->rb, seed,
-                                  (uint32_t)c->step, c->dstats, c->sms, s);
-    if (nr < 0) return SIDM_ERR_CUDA;
-    L += nr;
-    mark(6);
-  }
-  latch_kernel<<<1, 32, 0, s>>>(c->dstats, c->latched);
-  L += 1;
-  CK(cudaGetLastError());
-  c->step += 1;
-  if (!stats) return SIDM_OK;
-  L += launch_conserved(c->vel, c->mass, n, c->cons_partial, c->cons + 4, s);
-  CK(cudaMemcpyAsync(c->h_stats, c->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(c->h_cons, c->cons, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  const int st = wait_and_collect(c);
-  const DevStats& d = *c->h_stats;
-  std::memset(stats, 0, sizeof(*stats));
-  stats->n_active = (int64_t)d.n_active;
-  stats->n_candidate_pairs = (int64_t)d.n_cand;
-  stats->n_accepted = (int64_t)d.n_acc;
-  stats->n_rounds = (int64_t)d.n_rounds;
-  stats->n_p_ge_1 = (int64_t)d.n_pge1;
-  stats->n_h_nonconv = (int64_t)d.n_nonconv;
-  stats->n_dir_fail = (int64_t)d.n_dirfail;
-  stats->max_multiplicity = (int64_t)d.max_mult;
-  stats->sum_p = d.sum_p;
-  stats->e_before = c->h_cons[0];
-  stats->p_before[0] = c->h_cons[1];
-  stats->p_before[1] = c->h_cons[2];
-  stats->p_before[2] = c->h_cons[3];
-  stats->e_after = c->h_cons[4];
-  stats->p_after[0] = c->h_cons[5];
-  stats->p_after[1] = c->h_cons[6];
-  stats->p_after[2] = c->h_cons[7];
-  stats->status = st;
-  return st;
+  DeviceGuard g(c->device);
+  for (size_t k = 0; k < c->halos.size(); ++k)
+    set_step_params(c->halos[k], params[k].dt_max, params[k].sigma, params[k].seed,
+                    params[k].step);
+  return run_step(c, active_mask, dt_bins, stats);
 }
 
 int sidm_sync(sidm_ctx* c) {

@@ -38,7 +38,7 @@ constexpr float FLT_TINY = 7.888609052210118e-31f;  // 2^-100
 
 struct PairKArgs {
   Sorted so;
-  Tree t;
+  Forest f;
   int64_t n;
   const int32_t* act_list;
   const int32_t* nb_list;
@@ -108,14 +108,10 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
   int* stack = s_stack[warp];
   const Sorted& so = A.so;
   const PairArgs& P = A.a;
-  const int64_t n = A.n;
   const int64_t n_act = (int64_t)A.st->n_active;
   const double box = P.box, half = 0.5 * P.box;
   const float boxf = (float)P.box;
-  const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
-  const int kind = P.sigma_kind, kern = P.kernel;
-  const float s0f = __double2float_ru(P.sigma0);
-  const float wf = (float)P.w;
+  const int kern = P.kernel;
   const float knorm_up = __double2float_ru(kern == SIDM_KERNEL_TOPHAT
                                                ? 3.0 / (4.0 * 3.141592653589793)
                                                : 8.0 / 3.141592653589793);
@@ -133,6 +129,15 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
     if (q >= n_act) break;
     const int64_t qi = q++;
     const int64_t s = A.act_list[qi];
+    // the query's halo: its particles, cross-section model, random key and step
+    const Halo& H = A.f.halos[so.halo[s]];
+    const int64_t hs = H.start, hn = H.n;
+    const uint32_t k0 = (uint32_t)H.seed, k1 = (uint32_t)(H.seed >> 32);
+    const uint32_t step = H.step;
+    const int kind = H.sigma_kind;
+    const double sigma0 = H.sigma0, wv = H.w;
+    const float s0f = __double2float_ru(sigma0);
+    const float wf = (float)wv;
     const double xi = so.x[s], yi = so.y[s], zi = so.z[s];
     const double vxi = so.vx[s], vyi = so.vy[s], vzi = so.vz[s];
     const double mi = so.m[s], hi = so.h[s], dti = so.dt[s];
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
           pu *= (1.0f + SLACK);
           const bool i_is_a = idi < idj;
           const uint32_t a = i_is_a ? idi : idj, b = i_is_a ? idj : idi;
-          const U4 w = philox10(k0, k1, P.step, 0u, a, b);
+          const U4 w = philox10(k0, k1, step, 0u, a, b);
           const double u = unit53(w.x, w.y);
           double pp = (double)pc;
           if (tiny || u < (double)pu) {
@@ -215,7 +220,7 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
             const double r2 = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half);
             const double ddx = vxi - so.vx[j], ddy = vyi - so.vy[j], ddz = vzi - so.vz[j];
             const double vrel = sqrt((ddx * ddx + ddy * ddy) + ddz * ddz);
-            const double sg = sigma_over_m(kind, P.sigma0, P.w, vrel);
+            const double sg = sigma_over_m(kind, sigma0, wv, vrel);
             const double mj = so.m[j];
             const double qq = sqrt(r2) / hi;
             const double p_i = ((((0.5 * mj) * sg) * vrel) * (wni * kernel_shape(kern, qq))) * dti;
@@ -262,7 +267,7 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
     auto exact_g = [&](int64_t j) {
       const double ddx = vxi - so.vx[j], ddy = vyi - so.vy[j], ddz = vzi - so.vz[j];
       const double vrel = sqrt((ddx * ddx + ddy * ddy) + ddz * ddz);
-      return vrel * sigma_over_m(kind, P.sigma0, P.w, vrel);
+      return vrel * sigma_over_m(kind, sigma0, wv, vrel);
     };
 
     double vs_max = 0.0;
@@ -300,10 +305,11 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
       // direct walk with radius h_i (list incomplete): exact membership
       const float rad = (__double2float_ru(hi) + 2.0f * eq) * (1.0f + 4.0f * REL);
       double mine = 0.0;
-      const bool ok = traverse(A.t, fi, rad * rad, boxf, stack, [&](int leaf) {
-        const int64_t j = (int64_t)leaf * LEAF + lane;
+      const bool ok = traverse(A.f, H, fi, rad * rad, boxf, stack, [&](int leaf) {
+        const int64_t jl = (int64_t)leaf * LEAF + lane;
+        const int64_t j = hs + jl;
         bool in = false;
-        if (j < n && j != s) {
+        if (jl < hn && j != s) {
           const float r = sqrtf(sep2f(fi, so.f[j], boxf));
           const float e = eq + ABS * r;
           const float rlo = fmaxf(r * (1.0f - REL) - e, 0.0f);
@@ -340,12 +346,12 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
 
 }  // namespace
 
-int launch_pairs(const Sorted& so, const Tree& t, int64_t n, const int32_t* act_list,
+int launch_pairs(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
                  const int32_t* nb_list, const int32_t* nb_count, int nb_stride,
                  const PairArgs& a, PairRec* pairs, double* dtlim_user, DevStats* st, int* work,
                  int sms, cudaStream_t s) {
   if (n <= 0) return 0;
-  PairKArgs k{so, t, n, act_list, nb_list, nb_count, nb_stride, a, pairs, dtlim_user, st, work};
+  PairKArgs k{so, f, n, act_list, nb_list, nb_count, nb_stride, a, pairs, dtlim_user, st, work};
   int64_t blocks = (int64_t)sms * 8;
   const int64_t need = (n + PW - 1) / PW;
   if (blocks > need) blocks = need;

@@ -243,8 +243,9 @@ __device__ __forceinline__ void claim_segment(int32_t e, const int32_t* mult, in
 
 __global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ pairs, int64_t cap,
                                                    double* vel, const double* __restrict__ mass,
-                                                   ResolveBuffers b, uint32_t k0, uint32_t k1,
-                                                   uint32_t step, DevStats* st) {
+                                                   ResolveBuffers b,
+                                                   const int32_t* __restrict__ halo_of,
+                                                   const Halo* __restrict__ halos, DevStats* st) {
   __shared__ unsigned s_dirfail;
   __shared__ int s_max;
   if (threadIdx.x == 0) { s_dirfail = 0; s_max = 0; }
@@ -263,7 +264,8 @@ __global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ p
         const int ma = b.mult[r.ia], mb = b.mult[r.ib];
         mm = max(mm, max(ma, mb));
         if (ma == 1 && mb == 1) {
-          kick(r, vel, mass, k0, k1, step, &s_dirfail);
+          const Halo& H = halos[halo_of[r.ia]];
+          kick(r, vel, mass, (uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, &s_dirfail);
         } else {
           pend = true;
           b.flags[p] = 0;
@@ -332,8 +334,10 @@ __global__ void __launch_bounds__(GT) segsort_kernel(const PairRec* __restrict__
 
 __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict__ pairs, int64_t cap,
                                                       double* vel, const double* __restrict__ mass,
-                                                      ResolveBuffers b, uint32_t k0, uint32_t k1,
-                                                      uint32_t step, DevStats* st) {
+                                                      ResolveBuffers b,
+                                                      const int32_t* __restrict__ halo_of,
+                                                      const Halo* __restrict__ halos,
+                                                      DevStats* st) {
   __shared__ unsigned s_dirfail;
   __shared__ int s_passes;
   if (threadIdx.x == 0) { s_dirfail = 0; s_passes = 0; }
@@ -353,7 +357,8 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
         const int ca = ld_acquire(&b.cursor[r.ia]);
         const int cb = ld_acquire(&b.cursor[r.ib]);
         if (b.seg[b.seg_off[r.ia] + ca] == p && b.seg[b.seg_off[r.ib] + cb] == p) {
-          kick_l2(r, vel, mass, k0, k1, step, &s_dirfail);
+          const Halo& H = halos[halo_of[r.ia]];
+          kick_l2(r, vel, mass, (uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, &s_dirfail);
           __threadfence();
           st_release(&b.cursor[r.ia], ca + 1);
           st_release(&b.cursor[r.ib], cb + 1);
@@ -410,20 +415,19 @@ int dataflow_grid(int sms) {
 }  // namespace
 
 int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* mass,
-                   const ResolveBuffers& b, uint64_t seed, uint32_t step, DevStats* st, int sms,
-                   cudaStream_t s) {
-  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+                   const int32_t* halo_of, const Halo* halos, const ResolveBuffers& b,
+                   DevStats* st, int sms, cudaStream_t s) {
   const unsigned g = (unsigned)(sms * 4);
   count_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, b.mult, st);
-  split_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, vel, mass, b, k0, k1, step, st);
+  split_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, vel, mass, b, halo_of, halos, st);
   fill_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, b, st);
   segsort_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, b, st);
   // cooperative launch: every block resident, as the passes wait on each other
   ResolveBuffers bb = b;
   PairRec* pp = pairs;
   int64_t cap = pair_cap;
-  void* args[] = {(void*)&pp, (void*)&cap, (void*)&vel, (void*)&mass, (void*)&bb,
-                  (void*)&k0, (void*)&k1, (void*)&step, (void*)&st};
+  void* args[] = {(void*)&pp,      (void*)&cap,   (void*)&vel, (void*)&mass,
+                  (void*)&bb,      (void*)&halo_of, (void*)&halos, (void*)&st};
   if (cudaLaunchCooperativeKernel((const void*)dataflow_kernel, dim3(dataflow_grid(sms)),
                                   dim3(GT), args, 0, s) != cudaSuccess)
     return -1;

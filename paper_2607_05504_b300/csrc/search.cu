@@ -45,10 +45,9 @@ constexpr float SQ = 4.76837158203125e-07f;   // 2^-21: slack on squared thresho
 
 struct SearchArgs {
   Sorted so;
-  Tree t;
+  Forest f;
   int64_t n;
   const int32_t* act_list;
-  const StepParams* p;
   double box;
   int n_ngb, tol;
   double fixed_h;
@@ -118,13 +117,11 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
   int32_t* lst_j = s_j[warp];
   int* stack = s_stack[warp];
   const Sorted& so = A.so;
-  const int64_t n = A.n;
   const int64_t n_act = (int64_t)A.st->n_active;
   const double box = A.box, half = 0.5 * A.box;
   const float boxf = (float)A.box;
   const int K = A.n_ngb + A.tol + 1;
   const int lo_band = A.n_ngb - A.tol, hi_band = A.n_ngb + A.tol;
-  const double h0 = A.p->h0;
   uint32_t status = 0;
   int nonconv = 0;
 
@@ -138,6 +135,8 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
     if (q >= n_act) break;
     const int64_t qi = q++;
     const int64_t s = A.act_list[qi];
+    const Halo& H = A.f.halos[so.halo[s]];
+    const int64_t hs = H.start, hn = H.n;   // the query's halo: [hs, hs + hn)
     const float4 fi = so.f[s];
     const float eq = ABS * (fmaxf(fmaxf(fabsf(fi.x), fabsf(fi.y)), fabsf(fi.z)) + boxf);
     double h;
@@ -149,12 +148,12 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
       float hl, hu;
       float_bounds(h, &hl, &hu);
       T = hu;
-    } else if (n - 1 >= K) {
+    } else if (hn - 1 >= K) {
       // ---- 2. radius T from the key-order window
-      const int64_t W = (int64_t)NWIN * 32 < n ? (int64_t)NWIN * 32 : n;
+      const int64_t W = (int64_t)NWIN * 32 < hn ? (int64_t)NWIN * 32 : hn;
       int64_t w0 = s - W / 2;
-      if (w0 > n - W) w0 = n - W;
-      if (w0 < 0) w0 = 0;
+      if (w0 > hs + hn - W) w0 = hs + hn - W;
+      if (w0 < hs) w0 = hs;
       float wv[NWIN];
       float vmin = INFINITY, vmax = 0.0f;
 #pragma unroll
@@ -193,11 +192,12 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
       const float g2 = T < INFINITY ? thr_out2(T * (1.0f + REL), eq) : INFINITY;
       const float rad = (T + 2.0f * eq) * (1.0f + 4.0f * REL);
       const float rad2 = rad < INFINITY ? rad * rad : INFINITY;
-      const bool ok = traverse(A.t, fi, rad2, boxf, stack, [&](int leaf) {
-        const int64_t j = (int64_t)leaf * LEAF + lane;
+      const bool ok = traverse(A.f, H, fi, rad2, boxf, stack, [&](int leaf) {
+        const int64_t jl = (int64_t)leaf * LEAF + lane;
+        const int64_t j = hs + jl;
         float s2 = 0.0f;
         bool keep = false;
-        if (j < n && j != s) {
+        if (jl < hn && j != s) {
           s2 = sep2f(fi, so.f[j], boxf);
           keep = s2 < g2;
         }
@@ -234,10 +234,11 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
         const float in2 = thr_in2(Tn, eq);
         const float radn = (Tn + 2.0f * eq) * (1.0f + 4.0f * REL);
         int c = 0;
-        const bool ok2 = traverse(A.t, fi, radn * radn, boxf, stack, [&](int leaf) {
-          const int64_t j = (int64_t)leaf * LEAF + lane;
+        const bool ok2 = traverse(A.f, H, fi, radn * radn, boxf, stack, [&](int leaf) {
+          const int64_t jl = (int64_t)leaf * LEAF + lane;
+          const int64_t j = hs + jl;
           bool in = false;
-          if (j < n && j != s) in = sep2f(fi, so.f[j], boxf) < in2;
+          if (jl < hn && j != s) in = sep2f(fi, so.f[j], boxf) < in2;
           c += __popc(__ballot_sync(0xffffffffu, in));
         });
         if (!ok2) { status |= ST_ERR_STACK; break; }
@@ -278,9 +279,9 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
       }
       return warp_sum(c);
     };
-    const bool window_bound = !(A.fixed_h > 0.0) && (n - 1 >= K);
+    const bool window_bound = !(A.fixed_h > 0.0) && (hn - 1 >= K);
     if (!(A.fixed_h > 0.0)) {
-      h = h0;
+      h = H.h0;
       double blo = 0.0, bhi = 0.0;
       bool have_hi = false, conv = false;
       for (int it = 0; it < BISECT_MAX_EVALS; ++it) {
@@ -351,12 +352,12 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
 
 }  // namespace
 
-int launch_search(const Sorted& so, const Tree& t, int64_t n, const int32_t* act_list,
-                  const StepParams* p, double box, int n_ngb, int tol, double fixed_h,
-                  double* h_user, int32_t* nb_list, int32_t* nb_count, int nb_stride,
-                  DevStats* st, int* work, int sms, cudaStream_t s) {
+int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
+                  double box, int n_ngb, int tol, double fixed_h, double* h_user,
+                  int32_t* nb_list, int32_t* nb_count, int nb_stride, DevStats* st, int* work,
+                  int sms, cudaStream_t s) {
   if (n <= 0) return 0;
-  SearchArgs a{so, t, n, act_list, p, box, n_ngb, tol, fixed_h, h_user,
+  SearchArgs a{so, f, n, act_list, box, n_ngb, tol, fixed_h, h_user,
                nb_list, nb_count, nb_stride, st, work};
   int64_t blocks = (int64_t)sms * 12;
   const int64_t need = (n + SW - 1) / SW;

@@ -37,15 +37,29 @@ enum : uint32_t {
   ST_ERR_MASK = 0xFF00u
 };
 
-// Step parameters computed on the device (no host round trip).
-struct StepParams {
-  double lo[3], hi[3];     // bounding box of the positions
-  double l_ext;            // box side (periodic) or largest extent (open)
-  double h0;               // bisection start radius
-  float centre[3];         // key transform centre (open boundaries)
-  float key_scale;         // asinh scale s
-  float key_inv_norm;      // 1 / asinh(R / s)
-  float key_radius;        // R
+// One halo: an independent set of particles, contiguous in user order and
+// in key order, with its own bounding box, start radius, key transform,
+// tree, cross-section model, random key and step counter.  A context holds
+// one or more haloes; a single particle set is a context with one halo.
+struct Halo {
+  // layout (host, at configuration)
+  int64_t start, n;                 // particle range (same in user and key order)
+  int64_t node_off[MAX_LEVELS];     // first node of each tree level (level 0 = leaves)
+  int64_t node_cnt[MAX_LEVELS];     // nodes per level
+  int32_t levels;                   // tree levels (0 for an empty halo)
+  int32_t e0;                       // start radius h0 = l_ext 2^-e0 (8^e0 N_ngb <= 4 n)
+  // per step (host)
+  double dt_max, sigma0, w;
+  int32_t sigma_kind;
+  uint32_t step;                    // Philox counter word 0
+  uint64_t seed;                    // Philox key
+  // per step (device)
+  unsigned long long mm[6];         // ordered bounding-box accumulators (min xyz, max xyz)
+  double l_ext, h0;
+  float centre[3];                  // key transform centre (open boundaries)
+  float key_scale;                  // asinh scale s
+  float key_inv_norm;               // 1 / asinh(R / s)
+  float pad;
 };
 
 // Device counters of one step.
@@ -147,10 +161,15 @@ __host__ __device__ inline double ordered_to_dbl(unsigned long long u) {
 }
 
 // --------------------------------------------------------- device buffers
-struct Tree {
-  int levels;                 // number of levels (level 0 = leaves)
-  int64_t count[MAX_LEVELS];  // nodes per level
-  int64_t offset[MAX_LEVELS]; // first node of each level in lo/hi
+// Trees of all haloes: node boxes in level-major arrays (all haloes' level-0
+// nodes, then all level-1 nodes, ...); a halo's nodes of level l are
+// [node_off[l], node_off[l] + node_cnt[l]).
+struct Forest {
+  const Halo* halos;
+  int32_t n_halos;
+  int32_t halo_bits;          // key prefix bits (0 for one halo)
+  int32_t max_levels;         // deepest tree
+  int64_t level_nodes[MAX_LEVELS];  // nodes of all haloes per level
   float4* lo;                 // per node: min corner (w unused), rounded down
   float4* hi;                 // per node: max corner, rounded up
 };
@@ -167,6 +186,7 @@ struct Sorted {               // particle state in key order
   uint32_t* id;
   uint8_t* act;
   int32_t* orig;              // user-order index
+  int32_t* halo;              // halo of the particle
 };
 
 // ---------------------------------------------------------------- launchers
@@ -179,36 +199,32 @@ int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* t
 size_t exclusive_scan_temp_bytes(int64_t n);
 
 // build.cu
-int launch_bbox(const double* pos, int64_t n, unsigned long long* mm, cudaStream_t s);
-int launch_params(const unsigned long long* mm, StepParams* p, double box, int64_t n,
-                   int n_ngb, cudaStream_t s);
-int launch_keys(const double* pos, int64_t n, const StepParams* p, double box, uint32_t* keys,
-                 int32_t* vals, cudaStream_t s);
+int launch_bbox(const double* pos, const int32_t* halo_of, int64_t n, Halo* halos,
+                int n_halos, cudaStream_t s);
+int launch_params(Halo* halos, int n_halos, double box, cudaStream_t s);
+int launch_keys(const double* pos, const int32_t* halo_of, int64_t n, const Halo* halos,
+                int halo_bits, double box, uint32_t* keys, int32_t* vals, cudaStream_t s);
 int launch_permute(const int32_t* perm, int64_t n, const double* pos, const double* vel,
-                    const double* mass, const uint32_t* ids, const uint8_t* act,
-                    const int8_t* bins, double dt_max, Sorted so, int32_t* act_list,
-                    DevStats* st, cudaStream_t s);
-int launch_tree(const Sorted& so, int64_t n, Tree& t, cudaStream_t s);
+                   const double* mass, const uint32_t* ids, const int32_t* halo_of,
+                   const uint8_t* act, const int8_t* bins, const Halo* halos, Sorted so,
+                   int32_t* act_list, DevStats* st, cudaStream_t s);
+int launch_forest(const Sorted& so, const Forest& f, cudaStream_t s);
 int tree_levels_for(int64_t n, int64_t count[MAX_LEVELS]);
 
 // search.cu
-int launch_search(const Sorted& so, const Tree& t, int64_t n, const int32_t* act_list,
-                  const StepParams* p, double box, int n_ngb, int tol, double fixed_h,
-                  double* h_user, int32_t* nb_list, int32_t* nb_count, int nb_stride,
-                  DevStats* st, int* work, int sms, cudaStream_t s);
+int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
+                  double box, int n_ngb, int tol, double fixed_h, double* h_user,
+                  int32_t* nb_list, int32_t* nb_count, int nb_stride, DevStats* st, int* work,
+                  int sms, cudaStream_t s);
 
 // pairs.cu
 struct PairArgs {
   int kernel;
-  int sigma_kind;
-  double sigma0, w;
   double c_sidm;
   double box;
-  uint64_t seed;
-  uint32_t step;
   int64_t pair_cap;
 };
-int launch_pairs(const Sorted& so, const Tree& t, int64_t n, const int32_t* act_list,
+int launch_pairs(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
                  const int32_t* nb_list, const int32_t* nb_count, int nb_stride,
                  const PairArgs& a, PairRec* pairs, double* dtlim_user, DevStats* st,
                  int* work, int sms, cudaStream_t s);
@@ -225,8 +241,8 @@ struct ResolveBuffers {
   uint8_t* flags;     // [cap] applied flags
 };
 int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* mass,
-                   const ResolveBuffers& b, uint64_t seed, uint32_t step, DevStats* st, int sms,
-                   cudaStream_t s);
+                   const int32_t* halo_of, const Halo* halos, const ResolveBuffers& b,
+                   DevStats* st, int sms, cudaStream_t s);
 void launch_resolve_with_scratch(const PairRec* pairs, int64_t pair_cap, double* vel,
                                  const double* mass, int32_t* head, int32_t* next, uint8_t* flags,
                                  int32_t* mult, uint64_t seed, uint32_t step, DevStats* st,

@@ -48,15 +48,18 @@ __device__ __forceinline__ float test_radius2(double R, const float4& q, float b
   return r * r;
 }
 
-// Visits every leaf whose box meets the sphere; leaf_fn(leaf) is called by
-// the whole warp.  Returns false if the stack overflowed (visit incomplete).
+// Visits every leaf of halo H whose box meets the sphere; leaf_fn(leaf) is
+// called by the whole warp with the halo-local leaf index (particles
+// H.start + 32 leaf + lane, below H.start + H.n).  Returns false if the
+// stack overflowed (visit incomplete).
 template <class LeafFn>
-__device__ __forceinline__ bool traverse(const Tree& t, const float4& q, float rad2, float box,
-                                         int* stack, LeafFn&& leaf_fn) {
+__device__ __forceinline__ bool traverse(const Forest& f, const Halo& H, const float4& q,
+                                         float rad2, float box, int* stack, LeafFn&& leaf_fn) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
+  if (H.levels <= 0) return true;
   int top = 1;
-  if (lane == 0) stack[0] = (t.levels - 1) << 28;
+  if (lane == 0) stack[0] = (H.levels - 1) << 28;
   __syncwarp();
   bool ok = true;
   while (top > 0) {
@@ -69,9 +72,9 @@ __device__ __forceinline__ bool traverse(const Tree& t, const float4& q, float r
     } else {
       const int64_t child = (int64_t)idx * 32 + lane;
       bool hit = false;
-      if (child < t.count[level - 1]) {
-        const int64_t c = t.offset[level - 1] + child;
-        hit = box_hits(t.lo[c], t.hi[c], q.x, q.y, q.z, rad2, box);
+      if (child < H.node_cnt[level - 1]) {
+        const int64_t c = H.node_off[level - 1] + child;
+        hit = box_hits(f.lo[c], f.hi[c], q.x, q.y, q.z, rad2, box);
       }
       const uint32_t m = __ballot_sync(0xffffffffu, hit);
       const int k = __popc(m);

@@ -106,20 +106,24 @@ def hernquist_df(E: np.ndarray) -> np.ndarray:
     return br / (8.0 * math.sqrt(2.0) * math.pi ** 3 * (1.0 - q2) ** 2.5)
 
 
-def _sample_speeds(rng, psi: np.ndarray, df) -> np.ndarray:
+def _sample_speeds(rng, psi: np.ndarray, df, psi0: float) -> np.ndarray:
     """Rejection-sample speeds v in [0, sqrt(2 psi)] with density
-    v^2 f(psi - v^2/2), per particle."""
+    v^2 f(psi - v^2/2), per particle.  The envelope max_y y^2 f(psi(1-y^2))
+    is tabulated once on a log grid of psi0 - psi (psi0 = psi at the centre,
+    where the distribution function diverges) and taken, with a margin, as
+    the larger of the two bracketing table values."""
     n = psi.shape[0]
     vesc = np.sqrt(2.0 * psi)
-    grid = np.linspace(0.0, 1.0, 97)[1:]
-    gmax = np.zeros(n)
-    chunk = 1 << 16
-    for s in range(0, n, chunk):
-        y = grid[None, :]
-        ps = psi[s:s + chunk, None]
-        g = y * y * df(ps * (1.0 - y * y))
-        gmax[s:s + chunk] = g.max(axis=1)
-    gmax *= 1.5
+    y = np.linspace(0.0, 1.0, 193)[1:][None, :]
+    d = np.maximum(psi0 - psi, 1e-300)
+    dg = np.geomspace(d.min() * 0.999, d.max() * 1.001, 4096)
+    pg = psi0 - dg
+    tab = np.empty(pg.shape[0])
+    for s in range(0, pg.shape[0], 256):
+        ps = pg[s:s + 256, None]
+        tab[s:s + 256] = (y * y * df(ps * (1.0 - y * y))).max(axis=1)
+    idx = np.clip(np.searchsorted(dg, d), 1, dg.shape[0] - 1)
+    gmax = 1.5 * np.maximum(tab[idx - 1], tab[idx])
     out = np.empty(n)
     todo = np.arange(n)
     while todo.size:
@@ -143,7 +147,7 @@ def hernquist_halo(n: int, seed: int = 1, r_trunc: float = 100.0,
     r = sx / (1.0 - sx)
     pos = _isotropic(rng, r)
     psi = 1.0 / (1.0 + r)
-    v = _sample_speeds(rng, psi, hernquist_df)
+    v = _sample_speeds(rng, psi, hernquist_df, 1.0)
     vel = _isotropic(rng, v)
     mass = np.full(n, xmax / n)
     return Particles(pos, vel, mass, _ids(rng, n, ids), 0.0,
@@ -198,7 +202,7 @@ def nfw_halo(n: int, seed: int = 2, c: float = 10.0, ids: str = "arange") -> Par
     def df(e):
         return np.interp(np.clip(e, emin, emax), E, f) * (e > 0)
 
-    v = _sample_speeds(rng, psi, df)
+    v = _sample_speeds(rng, psi, df, float(psi_g.max()))
     vel = _isotropic(rng, v)
     mass = np.full(n, 1.0 / n)
     vc_rs = math.sqrt((math.log(2.0) - 0.5) / mu_c)    # circular speed at r_s
@@ -232,14 +236,17 @@ def timestep_bins(p: Particles, density, sigma_over_m: float, n_ngb: int,
     v = np.maximum(np.linalg.norm(p.vel, axis=1), 1e-12)
     t = (3.0 * n_ngb * c_sidm / 16.0) / (density(r) * sigma_over_m * 2.0 * v)
     lt = np.log2(t)
+    sub = lt if lt.shape[0] <= 20000 else np.random.default_rng(0).choice(lt, 20000, replace=False)
     best = None
-    for ldt in np.linspace(lt.min(), lt.max() + n_bins, 2000):
-        b = np.ceil(ldt - lt).clip(0, n_bins - 1)
+    for ldt in np.linspace(lt.min(), lt.max() + n_bins, 1000):
+        b = np.ceil(ldt - sub).clip(0, n_bins - 1)
         frac = float(np.mean(np.exp2(b - (n_bins - 1))))
         score = abs(frac - target_active)
         if best is None or score < best[0]:
-            best = (score, float(2.0 ** ldt), b)
-    return best[2].astype(np.int8), best[1]
+            best = (score, float(ldt))
+    ldt = best[1]
+    bins = np.ceil(ldt - lt).clip(0, n_bins - 1)
+    return bins.astype(np.int8), float(2.0 ** ldt)
 
 
 def active_at_step(bins: np.ndarray, s: int) -> np.ndarray:
@@ -271,3 +278,33 @@ def hernquist_2pow20(seed: int = 1, n: int = 1 << 20) -> dict:
     bins, dt_max = timestep_bins(p, hernquist_density, 1.0, 64)
     return {"name": f"hernquist-2^{int(math.log2(n))}", "particles": p, "n_ngb": 64,
             "sigma0": 1.0, "dt_max": dt_max, "bins": bins, "steps": 100, "seed": 0}
+
+
+def hernquist_batch(n_halos: int = 512, seed: int = 1000, log2_n=(12.0, 18.0),
+                    sigma_range=(0.1, 10.0), n_ngb: int = 64) -> list:
+    """Independent Hernquist haloes with N log-uniform in 2^[log2_n] and
+    sigma/m log-uniform in sigma_range; halo k has seed seed + k, its own
+    power-of-two bins and dt_max (10 % mean activity)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.round(2.0 ** rng.uniform(log2_n[0], log2_n[1], n_halos)).astype(np.int64)
+    sig = 10.0 ** rng.uniform(math.log10(sigma_range[0]), math.log10(sigma_range[1]), n_halos)
+    out = []
+    for k in range(n_halos):
+        p = hernquist_halo(int(sizes[k]), seed + 1 + k)
+        bins, dt = timestep_bins(p, hernquist_density, float(sig[k]), n_ngb)
+        out.append({"particles": p, "bins": bins, "dt_max": dt, "sigma0": float(sig[k]),
+                    "seed": seed + k})
+    return out
+
+
+def pack(haloes: list) -> tuple:
+    """Concatenates haloes into one particle set; returns (Particles, offsets,
+    bins) with halo k = particles [offsets[k], offsets[k+1])."""
+    ps = [h["particles"] for h in haloes]
+    off = np.zeros(len(ps) + 1, np.int64)
+    off[1:] = np.cumsum([p.n for p in ps])
+    cat = Particles(np.concatenate([p.pos for p in ps]), np.concatenate([p.vel for p in ps]),
+                    np.concatenate([p.mass for p in ps]), np.concatenate([p.ids for p in ps]),
+                    ps[0].box if ps else 0.0, {"kind": "batch"})
+    bins = np.concatenate([h["bins"] for h in haloes]).astype(np.int8)
+    return cat, off, bins

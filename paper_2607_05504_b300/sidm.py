@@ -48,6 +48,11 @@ class SigmaModel(C.Structure):
     _fields_ = [("kind", C.c_int), ("sigma0", C.c_double), ("w", C.c_double)]
 
 
+class HaloParams(C.Structure):
+    _fields_ = [("dt_max", C.c_double), ("sigma", SigmaModel), ("seed", C.c_uint64),
+                ("step", C.c_uint64)]
+
+
 class StepStats(C.Structure):
     _fields_ = [("n_active", C.c_int64), ("n_candidate_pairs", C.c_int64),
                 ("n_accepted", C.c_int64), ("n_rounds", C.c_int64), ("n_p_ge_1", C.c_int64),
@@ -69,7 +74,7 @@ ENTRY_POINTS = ("sidm_default_config", "sidm_create", "sidm_set_particles",
                 "sidm_set_velocities", "sidm_step", "sidm_sync", "sidm_get_particles",
                 "sidm_timestep_limits", "sidm_get_pairs", "sidm_get_step", "sidm_set_step",
                 "sidm_phase_times", "sidm_kernel_launches", "sidm_error_string", "sidm_destroy",
-                "sidm_apply_pairs_noalloc")
+                "sidm_apply_pairs_noalloc", "sidm_set_haloes", "sidm_step_haloes")
 
 N_PHASES = 6
 PHASES = ("keys", "sort", "structure", "search", "pairs", "resolve")
@@ -116,6 +121,8 @@ def lib():
         L.sidm_destroy.argtypes = [vp]
         L.sidm_destroy.restype = None
         L.sidm_apply_pairs_noalloc.argtypes = [vp, i64, vp, vp, i64, C.c_uint64, C.c_uint64, vp]
+        L.sidm_set_haloes.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64)]
+        L.sidm_step_haloes.argtypes = [vp, vp, vp, C.POINTER(HaloParams), C.POINTER(StepStats)]
         for name in ENTRY_POINTS:
             fn = getattr(L, name)
             if name not in ("sidm_default_config", "sidm_error_string", "sidm_destroy"):
@@ -181,6 +188,20 @@ def sidm_step(ctx, active_mask, dt_bins, dt_max, sigma: SigmaModel, seed, stats=
     return _check(lib().sidm_step(ctx, _ptr(active_mask)[0], _ptr(dt_bins)[0], float(dt_max),
                                   C.byref(sigma), int(seed),
                                   C.byref(stats) if stats is not None else None), "sidm_step")
+
+
+def sidm_set_haloes(ctx, offsets) -> int:
+    off = np.ascontiguousarray(offsets, np.int64)
+    return _check(lib().sidm_set_haloes(ctx, int(off.shape[0] - 1),
+                                        off.ctypes.data_as(C.POINTER(C.c_int64))),
+                  "sidm_set_haloes")
+
+
+def sidm_step_haloes(ctx, active_mask, dt_bins, params, stats=None) -> int:
+    arr = (HaloParams * len(params))(*params)
+    return _check(lib().sidm_step_haloes(ctx, _ptr(active_mask)[0], _ptr(dt_bins)[0], arr,
+                                         C.byref(stats) if stats is not None else None),
+                  "sidm_step_haloes")
 
 
 def sidm_sync(ctx) -> int:
@@ -298,6 +319,31 @@ class Context:
         sg = SigmaModel(int(sigma_kind), float(sigma0), float(w))
         st = StepStats() if stats else None
         status = sidm_step(self.handle, active, bins, dt_max, sg, seed, st)
+        if st is not None:
+            d = st.as_dict()
+            d["return"] = status
+            return d
+        return status
+
+    def set_haloes(self, offsets):
+        """Segments the loaded particles into independent haloes:
+        halo k = particles [offsets[k], offsets[k+1])."""
+        sidm_set_haloes(self.handle, offsets)
+
+    def step_haloes(self, params, active=None, bins=None, stats=True):
+        """One step of every halo; params: list of HaloParams or dicts with
+        dt_max, sigma0, sigma_kind, w, seed, step."""
+        if isinstance(active, np.ndarray):
+            active = np.ascontiguousarray(active, np.uint8)
+        if isinstance(bins, np.ndarray):
+            bins = np.ascontiguousarray(bins, np.int8)
+        hp = [p if isinstance(p, HaloParams) else
+              HaloParams(float(p["dt_max"]), SigmaModel(int(p.get("sigma_kind", 0)),
+                                                          float(p.get("sigma0", 1.0)),
+                                                          float(p.get("w", 1.0))),
+                         int(p.get("seed", 0)), int(p.get("step", 0))) for p in params]
+        st = StepStats() if stats else None
+        status = sidm_step_haloes(self.handle, active, bins, hp, st)
         if st is not None:
             d = st.as_dict()
             d["return"] = status
