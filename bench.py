@@ -180,16 +180,141 @@ def cpu_baseline(w, masks, budget_s=12.0) -> dict:
             "sample": f"finest steps 1..{k} of the 100-step cycle ({upd} active updates, {dt:.1f} s)"}
 
 
+def run_batch(args) -> None:
+    """512 independent Hernquist haloes (N log-uniform in [2^12, 2^18], sigma/m
+    log-uniform in [0.1, 10], own seeds, bins and step counters) stepped
+    together (one sidm_step_haloes per step), against the plain per-halo form
+    (one sidm_step per halo) on the same haloes and steps."""
+    import torch
+    from paper_2607_05504_b300 import inputs as I
+    from paper_2607_05504_b300 import sidm
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    haloes = I.hernquist_batch(args.n_halos)
+    p, off, bins = I.pack(haloes)
+    n = p.n
+    bmax = [int(h["bins"].max()) for h in haloes]
+
+    def masks_for(s):
+        return np.concatenate([I.active_at_step(h["bins"], s) for h in haloes])
+
+    steps = args.steps
+    cyc = [masks_for(s) for s in range(args.warmup + steps)]
+    ctx = sidm.Context(n_ngb=64, box=0.0, stream=stream.cuda_stream, n_max=n)
+    ctx.set_particles(torch.from_numpy(p.pos).to(dev), torch.from_numpy(p.vel).to(dev),
+                      torch.from_numpy(p.ids.view(np.int32)).to(dev),
+                      mass=torch.from_numpy(p.mass).to(dev))
+    ctx.set_haloes(off)
+    bins_d = torch.from_numpy(bins).to(dev)
+    masks_d = [torch.from_numpy(m).to(dev) for m in cyc]
+
+    def params(s):
+        return [sidm.HaloParams(h["dt_max"], sidm.SigmaModel(0, h["sigma0"], 1.0), h["seed"], s)
+                for h in haloes]
+
+    prm = [params(s) for s in range(args.warmup + steps)]
+    for s in range(args.warmup):
+        sidm.sidm_step_haloes(ctx.handle, masks_d[s], bins_d, prm[s], None)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    upd = 0
+    e0.record(stream)
+    for k in range(steps):
+        s = args.warmup + k
+        sidm.sidm_step_haloes(ctx.handle, masks_d[s], bins_d, prm[s], None)
+        upd += int(cyc[s].sum())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) * 1e-3
+    ctx.close()
+    # plain per-halo form: one context, each halo loaded then stepped alone
+    pc = sidm.Context(n_ngb=64, box=0.0, stream=stream.cuda_stream, n_max=int(np.diff(off).max()))
+    dev_h = [(torch.from_numpy(h["particles"].pos).to(dev), torch.from_numpy(h["particles"].vel).to(dev),
+              torch.from_numpy(h["particles"].ids.view(np.int32)).to(dev),
+              torch.from_numpy(h["particles"].mass).to(dev), torch.from_numpy(h["bins"]).to(dev))
+             for h in haloes]
+    t_plain, upd_plain = 0.0, 0
+    for k in range(min(steps, 3)):
+        s = args.warmup + k
+        for j, h in enumerate(haloes):
+            pos, vel, ids, mass, hb = dev_h[j]
+            pc.set_particles(pos, vel, ids, mass=mass)
+            mk = torch.from_numpy(I.active_at_step(h["bins"], s)).to(dev)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pc.step_counter = s
+            sidm.sidm_step(pc.handle, mk, hb, h["dt_max"], sidm.SigmaModel(0, h["sigma0"], 1.0),
+                           h["seed"], None)
+            b.record(stream)
+            b.synchronize()
+            t_plain += a.elapsed_time(b) * 1e-3
+            upd_plain += int(mk.sum().item())
+    pc.close()
+    line = {"metric": METRIC, "value": upd / t_batch, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batch of {args.n_halos} Hernquist haloes, N log-uniform in "
+                                   "[2^12, 2^18], sigma/m log-uniform in [0.1, 10], N_ngb 64",
+                       "n": n, "n_halos": args.n_halos, "mean_active": upd / steps},
+            "plain_per_halo": {"value": upd_plain / t_plain, "unit": UNIT,
+                               "steps": min(steps, 3),
+                               "note": "same haloes, one sidm_step per halo (kernel time only)"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args) -> None:
+    """Poisson stream of halo requests served with continuous batching under
+    a device-memory budget; p50/p99 latency and throughput."""
+    import torch
+    from paper_2607_05504_b300 import serving as S
+    torch.cuda.set_device(0)
+    reqs = S.request_stream(args.requests, rate=args.rate, seed=3,
+                            log2_n=(12.0, args.log2_nmax), steps=(10, args.max_steps))
+    budget = args.budget_gb * 1e9
+    per_particle = 700.0
+    eng = S.GpuEngine(capacity=int(budget / per_particle))
+    srv = S.Server(eng, S.Scheduler(budget, per_particle))
+    rep = srv.run(reqs)
+    eng.close()
+    line = {"metric": METRIC, "value": rep.throughput, "unit": UNIT, "n_gpus": 1,
+            "steps": rep.ticks, "warmup": 0, "ms_per_step": 1e3 * rep.wall / max(rep.ticks, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "serving: Poisson halo requests (Hernquist/NFW, const/Yukawa "
+                                   f"sigma), N log-uniform in [2^12, 2^{args.log2_nmax:g}], steps "
+                                   f"log-uniform in [10, {args.max_steps}]",
+                       "rate_per_s": args.rate, "requests": args.requests,
+                       "hbm_budget_gb": args.budget_gb},
+            "latency_s": {"p50": rep.percentile(50), "p99": rep.percentile(99),
+                          "max": max(rep.latencies) if rep.latencies else None},
+            "wall_s": rep.wall}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hernquist", choices=["hernquist", "batch", "serving"])
+    ap.add_argument("--n-halos", type=int, default=512)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--log2-nmax", type=float, default=21.0)
+    ap.add_argument("--max-steps", type=int, default=1000)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.impl == "ours" and args.workload == "batch":
+        return run_batch(args)
+    if args.impl == "ours" and args.workload == "serving":
+        return run_serving(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
