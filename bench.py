@@ -265,6 +265,75 @@ def run_batch(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_precision(args) -> None:
+    """NFW halo (c = 10, r_s = 1, N = 2^23), Yukawa-like sigma0/m = 1 with w =
+    v_c(r_s), N_ngb 64, power-of-two bins: the FP32-split form against the
+    FP64 plain form, step by step from the same state.  Reports both forms'
+    throughput, the accepted-pair mismatch |A32 xor A64| / |A64| and the
+    split form's relative energy / momentum change per step."""
+    import torch
+    from paper_2607_05504_b300 import inputs as I
+    from paper_2607_05504_b300 import sidm
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    p = I.nfw_halo(1 << args.log2_n, 2)
+    w = p.meta["v_c_rs"]
+    bins, dt = I.timestep_bins(p, I.nfw_density, 1.0, 64)
+    ctxs = {k: sidm.Context(n_ngb=64, stream=stream.cuda_stream, n_max=p.n, precision=v)
+            for k, v in (("fp64", sidm.FP64_PLAIN), ("split", sidm.FP32_SPLIT))}
+    pos, vel = torch.from_numpy(p.pos).to(dev), torch.from_numpy(p.vel).to(dev)
+    ids, mass = torch.from_numpy(p.ids.view(np.int32)).to(dev), torch.from_numpy(p.mass).to(dev)
+    for c in ctxs.values():
+        c.set_particles(pos, vel, ids, mass=mass)
+    bins_d = torch.from_numpy(bins).to(dev)
+    sg = sidm.SigmaModel(sidm.SIGMA_YUKAWA, 1.0, w)
+    t = {"fp64": 0.0, "split": 0.0}
+    n64 = nx = upd = 0
+    drift_e, drift_p = 0.0, 0.0
+    vcur = torch.empty_like(vel)
+    for s in range(args.steps):
+        act = torch.from_numpy(I.active_at_step(bins, s)).to(dev)
+        res = {}
+        for k, c in ctxs.items():
+            c.step_counter = s
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sidm.sidm_step(c.handle, act, bins_d, dt, sg, 7, None)
+            b.record(stream)
+            b.synchronize()
+            t[k] += a.elapsed_time(b) * 1e-3
+            st = sidm.StepStats()
+            res[k] = set(map(tuple, c.pairs()[0].tolist()))
+        upd += int(act.sum().item())
+        n64 += len(res["fp64"])
+        nx += len(res["fp64"] ^ res["split"])
+        # conservation of the split step: recompute with statistics
+        sidm.sidm_get_particles(ctxs["fp64"].handle, vcur)
+        c = ctxs["split"]
+        c.set_velocities(vcur)
+        c.step_counter = s
+        st = c.step(dt, act, bins_d, sigma0=1.0, sigma_kind=sidm.SIGMA_YUKAWA, w=w, seed=7)
+        drift_e = max(drift_e, abs(st["e_after"] - st["e_before"]) / st["e_before"])
+        pscale = float((mass[:, None] * vcur.abs()).sum().item())
+        drift_p = max(drift_p, float(np.max(np.abs(np.subtract(st["p_after"], st["p_before"])))) / pscale)
+        c.set_velocities(vcur)
+    for c in ctxs.values():
+        c.close()
+    line = {"metric": METRIC, "value": upd / t["split"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 * t["split"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+            "data": "synthetic",
+            "config": {"workload": f"NFW c=10 N=2^{args.log2_n}, Yukawa sigma0/m=1 w=v_c(r_s), "
+                                   "N_ngb 64, FP32-split vs FP64 plain", "n": p.n},
+            "fp64_plain": {"value": upd / t["fp64"], "unit": UNIT},
+            "pair_mismatch": {"rate": nx / max(n64, 1), "pairs_fp64": n64, "differing": nx},
+            "drift_per_step": {"energy_rel": drift_e, "momentum_rel": drift_p}}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(args) -> None:
     """Poisson stream of halo requests served with continuous batching under
     a device-memory budget; p50/p99 latency and throughput."""
@@ -300,7 +369,9 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hernquist", choices=["hernquist", "batch", "serving"])
+    ap.add_argument("--workload", default="hernquist",
+                    choices=["hernquist", "batch", "serving", "precision"])
+    ap.add_argument("--log2-n", type=int, default=23)
     ap.add_argument("--n-halos", type=int, default=512)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=20.0)
@@ -315,6 +386,8 @@ def main():
         return run_batch(args)
     if args.impl == "ours" and args.workload == "serving":
         return run_serving(args)
+    if args.impl == "ours" and args.workload == "precision":
+        return run_precision(args)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

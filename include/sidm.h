@@ -68,7 +68,14 @@ typedef enum {
 enum { SIDM_HOST = 0, SIDM_DEVICE = 1 };
 enum { SIDM_KERNEL_CUBIC = 0, SIDM_KERNEL_TOPHAT = 1 };
 enum { SIDM_SIGMA_CONST = 0, SIDM_SIGMA_YUKAWA = 1 };
-enum { SIDM_FP64_PLAIN = 0 };
+/* SIDM_FP64_PLAIN: every decision and value equals an FP64 evaluation in a
+ * fixed operation order (FP32 is used only where it is provably decisive).
+ * SIDM_FP32_SPLIT: separations, neighbour counts, kernel weights and
+ * probabilities in FP32; FP64 kicks and accumulators; a draw is re-tested
+ * in FP64 only when |P - u| < 1e-5.  Its accepted pairs may differ from the
+ * FP64 form in rare near-boundary cases; energy and momentum stay
+ * conserved to FP64 round-off. */
+enum { SIDM_FP64_PLAIN = 0, SIDM_FP32_SPLIT = 1 };
 
 typedef struct {
   int n_ngb;            /* target neighbour number N_ngb (paper: 32)                     */
@@ -76,7 +83,7 @@ typedef struct {
   double c_sidm;        /* C_SIDM of Eq. 9 (paper: 0.1)                                   */
   double box;           /* > 0: periodic cube [0, box)^3; 0: open boundaries              */
   int kernel;           /* SIDM_KERNEL_CUBIC (fiducial) or SIDM_KERNEL_TOPHAT              */
-  int precision;        /* SIDM_FP64_PLAIN                                                */
+  int precision;        /* SIDM_FP64_PLAIN or SIDM_FP32_SPLIT                              */
   double fixed_h;       /* > 0: every active particle uses this h (no bisection); 0: adaptive */
   int64_t n_max;        /* capacity in particles (0: sized by the first sidm_set_particles) */
   int64_t pair_capacity;/* accepted-pair buffer (0: 2 n_max + 4096)                        */

@@ -379,11 +379,13 @@ int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
     L += launch_forest(c->so, F, s);
     mark(3);
     L += launch_search(c->so, F, n, c->act_list, c->cfg.box, c->cfg.n_ngb, c->cfg.ngb_tol,
-                       c->cfg.fixed_h, c->h_user, c->nb_list, c->nb_count, c->nb_stride,
+                       c->cfg.fixed_h, c->cfg.precision == SIDM_FP32_SPLIT, c->h_user,
+                       c->nb_list, c->nb_count, c->nb_stride,
                        c->dstats, c->work, c->sms, s);
     mark(4);
     PairArgs pa;
     pa.kernel = c->cfg.kernel;
+    pa.split = c->cfg.precision == SIDM_FP32_SPLIT;
     pa.c_sidm = c->cfg.c_sidm;
     pa.box = c->cfg.box;
     pa.pair_cap = c->pair_cap;
@@ -454,7 +456,8 @@ int sidm_create(const sidm_config* cfg, sidm_ctx** out) {
   if (cfg->n_ngb < 1 || cfg->ngb_tol < 0 || cfg->ngb_tol >= cfg->n_ngb ||
       cfg->n_ngb + cfg->ngb_tol + 2 > 256 || !(cfg->c_sidm > 0.0) || !(cfg->box >= 0.0) ||
       !std::isfinite(cfg->box) || (cfg->kernel != SIDM_KERNEL_CUBIC && cfg->kernel != SIDM_KERNEL_TOPHAT) ||
-      cfg->precision != SIDM_FP64_PLAIN || !(cfg->fixed_h >= 0.0) || cfg->n_max < 0 ||
+      (cfg->precision != SIDM_FP64_PLAIN && cfg->precision != SIDM_FP32_SPLIT) ||
+      !(cfg->fixed_h >= 0.0) || cfg->n_max < 0 ||
       cfg->pair_capacity < 0)
     return SIDM_ERR_INVALID_ARG;
   sidm_ctx* c = new (std::nothrow) sidm_ctx();

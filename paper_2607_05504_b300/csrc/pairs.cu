@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
         const uint32_t idj = so.id[j];
         const bool actj = so.act[j] != 0;
         // separation interval
-        const float r = sqrtf(sep2f(fi, fj, boxf));
+        const float r2f = sep2f(fi, fj, boxf);
+        const float r = sqrtf(r2f);
         const float e = eq + ABS * r;
         const float rlo = fmaxf(r * (1.0f - REL) - e, 0.0f);
         const float rhi = r * (1.0f + REL) + e;
@@ -175,13 +176,22 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
         const float dv = 4.0f * U * (3.0f * (vmax_i + vmax_j) + vr) + 4.0f * U * vr;
         const float vl = fmaxf(vr - dv, 0.0f), vu = vr + dv;
         g_bounds(kind, s0f, wf, vl, vu, &glo, &ghi);
-        // does j see i?  (j active and r^2 < h_j^2, decided exactly)
+        if (P.split) {
+          const float g = vr * sigma_f(kind, s0f, wf, vr);
+          glo = ghi = g;
+        }
+        // does j see i?  (j active and r^2 < h_j^2: decided exactly, or in
+        // FP32 by the split form, as its neighbour lists are)
         bool sees = false;
         float2 hbj = make_float2(0.f, 0.f);
         if (actj) {
           hbj = so.hb[j];
-          if (rhi < hbj.x) sees = true;
-          else if (rlo < hbj.y) {
+          if (P.split) {
+            const float hjf = (float)so.h[j];
+            sees = r2f < hjf * hjf;
+          } else if (rhi < hbj.x) {
+            sees = true;
+          } else if (rlo < hbj.y) {
             const double hj = so.h[j];
             sees = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half) < hj * hj;
           }
@@ -215,7 +225,22 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
           const U4 w = philox10(k0, k1, step, 0u, a, b);
           const double u = unit53(w.x, w.y);
           double pp = (double)pc;
-          if (tiny || u < (double)pu) {
+          // plain form: FP64 whenever u is under the FP32 upper bound;
+          // split form: FP64 re-test only when |P - u| < 1e-5
+          const bool need64 = P.split ? (fabs((double)pc - u) < 1e-5) : (tiny || u < (double)pu);
+          if (P.split && !need64) {
+            if (pc >= 1.0f) ++pge1;
+            if (u < pp) {
+              acc = true;
+              rec.ord = ((unsigned long long)w.z << 32) | (unsigned long long)w.w;
+              rec.a = a;
+              rec.b = b;
+              const int32_t oj = so.orig[j];
+              rec.ia = i_is_a ? oi : oj;
+              rec.ib = i_is_a ? oj : oi;
+            }
+          }
+          if (need64) {
             // exact FP64 probability, in the oracle's operation order
             const double r2 = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half);
             const double ddx = vxi - so.vx[j], ddy = vyi - so.vy[j], ddz = vzi - so.vz[j];
@@ -299,7 +324,7 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
       double mine = 0.0;
 #pragma unroll
       for (int r = 0; r < MAXR; ++r)
-        if (jr[r] >= 0 && ghi[r] >= mlo) mine = fmax(mine, exact_g(jr[r]));
+        if (jr[r] >= 0 && ghi[r] >= mlo) mine = fmax(mine, P.split ? (double)glo[r] : exact_g(jr[r]));
       vs_max = warp_maxd(mine);
     } else {
       // direct walk with radius h_i (list incomplete): exact membership
@@ -313,11 +338,16 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
           const float r = sqrtf(sep2f(fi, so.f[j], boxf));
           const float e = eq + ABS * r;
           const float rlo = fmaxf(r * (1.0f - REL) - e, 0.0f);
-          if (rlo < hbi.y) in = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half) < hhi;
+          if (P.split) {
+            const float hf = (float)hi;
+            in = r * r < hf * hf;
+          } else if (rlo < hbi.y) {
+            in = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half) < hhi;
+          }
         }
         float gl, gh;
         visit(j, in, &gl, &gh);
-        if (in) mine = fmax(mine, exact_g(j));
+        if (in) mine = fmax(mine, P.split ? (double)gl : exact_g(j));
       });
       if (!ok) status |= ST_ERR_STACK;
       vs_max = warp_maxd(mine);

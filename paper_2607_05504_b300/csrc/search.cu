@@ -51,6 +51,7 @@ struct SearchArgs {
   double box;
   int n_ngb, tol;
   double fixed_h;
+  int split;             // 1: FP32 counts and lists, no FP64 re-tests
   double* h_user;
   int32_t* nb_list;     // [n_act][nb_stride]
   int32_t* nb_count;    // [n_act]: count, or -1 (walk the tree)
@@ -261,8 +262,19 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
       return sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half);
     };
     // #{r^2 < h h} over the list (exact); requires h <= T (1 + 2^-22)
+    // FP32-split form: the counts compare FP32 r^2 with the FP32 h^2 directly
+    auto thresholds = [&](double hv, float hl, float hu, float* in2, float* out2) {
+      if (A.split) {
+        const float hf = (float)hv;
+        *in2 = *out2 = hf * hf;
+      } else {
+        *in2 = thr_in2(hl, eq);
+        *out2 = thr_out2(hu, eq);
+      }
+    };
     auto count_below = [&](double hv, float hl, float hu) {
-      const float in2 = thr_in2(hl, eq), out2 = thr_out2(hu, eq);
+      float in2, out2;
+      thresholds(hv, hl, hu, &in2, &out2);
       int c = 0;
       bool amb = false;
       for (int k = lane; k < len; k += 32) {
@@ -313,7 +325,8 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
     int cnt = -1;
     const bool list_covers = complete && (!window_bound || !(hl > T));
     if (list_covers) {
-      const float in2 = thr_in2(hl, eq), out2 = thr_out2(hu, eq);
+      float in2, out2;
+      thresholds(h, hl, hu, &in2, &out2);
       const double hh = h * h;
       cnt = 0;
       for (int k0 = 0; k0 < len; k0 += 32) {
@@ -353,11 +366,11 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
 }  // namespace
 
 int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
-                  double box, int n_ngb, int tol, double fixed_h, double* h_user,
+                  double box, int n_ngb, int tol, double fixed_h, int split, double* h_user,
                   int32_t* nb_list, int32_t* nb_count, int nb_stride, DevStats* st, int* work,
                   int sms, cudaStream_t s) {
   if (n <= 0) return 0;
-  SearchArgs a{so, f, n, act_list, box, n_ngb, tol, fixed_h, h_user,
+  SearchArgs a{so, f, n, act_list, box, n_ngb, tol, fixed_h, split, h_user,
                nb_list, nb_count, nb_stride, st, work};
   int64_t blocks = (int64_t)sms * 12;
   const int64_t need = (n + SW - 1) / SW;

@@ -213,13 +213,14 @@ int tree_levels_for(int64_t n, int64_t count[MAX_LEVELS]);
 
 // search.cu
 int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
-                  double box, int n_ngb, int tol, double fixed_h, double* h_user,
+                  double box, int n_ngb, int tol, double fixed_h, int split, double* h_user,
                   int32_t* nb_list, int32_t* nb_count, int nb_stride, DevStats* st, int* work,
                   int sms, cudaStream_t s);
 
 // pairs.cu
 struct PairArgs {
   int kernel;
+  int split;          // 1: FP32 decisions, FP64 re-test only when |P - u| < 1e-5
   double c_sidm;
   double box;
   int64_t pair_cap;

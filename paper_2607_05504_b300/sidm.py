@@ -20,6 +20,7 @@ from . import build as _build
 
 HOST, DEVICE = 0, 1
 KERNEL_CUBIC, KERNEL_TOPHAT = 0, 1
+FP64_PLAIN, FP32_SPLIT = 0, 1
 SIGMA_CONST, SIGMA_YUKAWA = 0, 1
 
 OK = 0
@@ -266,7 +267,8 @@ class Context:
     work; outputs are numpy arrays unless device tensors are passed in."""
 
     def __init__(self, n_ngb=32, ngb_tol=5, c_sidm=0.1, box=0.0, kernel=KERNEL_CUBIC,
-                 fixed_h=0.0, n_max=0, pair_capacity=0, stream=None, device=-1, profile=False):
+                 fixed_h=0.0, n_max=0, pair_capacity=0, stream=None, device=-1, profile=False,
+                 precision=FP64_PLAIN):
         cfg = sidm_default_config()
         cfg.n_ngb, cfg.ngb_tol, cfg.c_sidm, cfg.box = int(n_ngb), int(ngb_tol), float(c_sidm), float(box)
         cfg.kernel, cfg.fixed_h, cfg.n_max = int(kernel), float(fixed_h), int(n_max)
@@ -274,6 +276,7 @@ class Context:
         cfg.stream = stream
         cfg.device = int(device)
         cfg.profile = int(bool(profile))
+        cfg.precision = int(precision)
         self.cfg = cfg
         self.handle = sidm_create(cfg)
         self.n = 0
