@@ -192,6 +192,8 @@ int ensure_capacity(sidm_ctx* c, int64_t n) {
   CK(dalloc(c, &rb.touched, 2 * pc));
   CK(dalloc(c, &rb.pending, pc));
   CK(dalloc(c, &rb.flags, pc));
+  CK(dalloc(c, &rb.pos_a, pc));
+  CK(dalloc(c, &rb.pos_b, pc));
   CK(dalloc(c, &c->cons_partial, 4 * conserved_blocks()));
   CK(dalloc(c, &c->cons, 8));
   CK(cudaMemsetAsync(rb.mult, 0, want * sizeof(int32_t), c->stream));
@@ -379,7 +381,8 @@ int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
     L += launch_forest(c->so, F, s);
     mark(3);
     L += launch_search(c->so, F, n, c->act_list, c->cfg.box, c->cfg.n_ngb, c->cfg.ngb_tol,
-                       c->cfg.fixed_h, c->cfg.precision == SIDM_FP32_SPLIT, c->h_user,
+                       c->cfg.fixed_h, c->cfg.kernel, c->cfg.precision == SIDM_FP32_SPLIT,
+                       c->h_user,
                        c->nb_list, c->nb_count, c->nb_stride,
                        c->dstats, c->work, c->sms, s);
     mark(4);

@@ -14,10 +14,11 @@
 //
 // Exactness with little FP64: P_pair is first bounded from above in FP32
 // from the FP32 copies of positions, velocities, masses, dt and h (every
-// factor rounded or widened upwards, then a relative margin).  Only when
-// u lies below that bound (about the acceptance probability) is P_pair
-// evaluated in FP64 in the oracle's operation order, and the draw decided on
-// that value.  The owner test r^2 < h_j^2 and the maximum of Eq. 9 likewise
+// factor rounded or widened upwards, then a relative margin), and u from
+// below by its top 24 bits.  Only when that lower bound of u lies below the
+// bound of P_pair (about the acceptance probability) is P_pair evaluated in
+// FP64 in the oracle's operation order, and the draw decided on that value.
+// The FP64 state of the query is read only on these rare paths.  The owner test r^2 < h_j^2 and the maximum of Eq. 9 likewise
 // use FP32 intervals and fall back to FP64 only where an interval straddles
 // the decision.  All results equal those of a pure FP64 evaluation.
 #include "traverse.cuh"
@@ -101,20 +102,227 @@ __device__ __forceinline__ void g_bounds(int kind, float s0, float w, float vl, 
   }
 }
 
-__global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
-  __shared__ int s_stack[PW][SEARCH_STACK];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t lt = (1u << lane) - 1u;
-  int* stack = s_stack[warp];
+// What one warp knows about its query particle i.
+struct Query {
+  int64_t s;            // key-order index
+  uint32_t idi;
+  int32_t oi;           // user-order index
+  float4 fi, vmi, hbi;  // FP32 position + dt, velocity + mass, h bounds
+  float eq, vmax_i;
+  uint32_t k0, k1, step;
+  int kind;
+  float s0f, wf;
+};
+
+__device__ __forceinline__ Query load_query(const Sorted& so, const Forest& f, int64_t s,
+                                            float boxf) {
+  Query Q;
+  Q.s = s;
+  const Halo& H = f.halos[so.halo[s]];
+  Q.k0 = (uint32_t)H.seed;
+  Q.k1 = (uint32_t)(H.seed >> 32);
+  Q.step = H.step;
+  Q.kind = H.sigma_kind;
+  Q.s0f = __double2float_ru(H.sigma0);
+  Q.wf = (float)H.w;
+  Q.idi = so.id[s];
+  Q.oi = so.orig[s];
+  Q.fi = so.f[s];
+  Q.vmi = so.vm[s];
+  Q.hbi = so.hb[s];
+  Q.eq = ABS * (fmaxf(fmaxf(fabsf(Q.fi.x), fabsf(Q.fi.y)), fabsf(Q.fi.z)) + boxf);
+  Q.vmax_i = fmaxf(fmaxf(fabsf(Q.vmi.x), fabsf(Q.vmi.y)), fabsf(Q.vmi.z));
+  return Q;
+}
+
+// Everything about one neighbour j of the query (valid lanes only); the
+// accepted pair is appended by the whole warp.  Returns bounds of
+// g = v sigma/m(v) in glo/ghi and adds the pair's probability (FP32
+// estimate, or the exact value where it was computed) to *psum.
+__device__ __forceinline__ void visit(const PairKArgs& A, const Query& Q, int64_t j, bool valid,
+                                      float* glo_out, float* ghi_out, float* psum,
+                                      unsigned long long* cand, unsigned long long* pge1,
+                                      uint32_t* status) {
   const Sorted& so = A.so;
   const PairArgs& P = A.a;
-  const int64_t n_act = (int64_t)A.st->n_active;
-  const double box = P.box, half = 0.5 * P.box;
-  const float boxf = (float)P.box;
   const int kern = P.kernel;
-  const float knorm_up = __double2float_ru(kern == SIDM_KERNEL_TOPHAT
-                                               ? 3.0 / (4.0 * 3.141592653589793)
-                                               : 8.0 / 3.141592653589793);
+  const int lane = threadIdx.x & 31;
+  const float boxf = (float)P.box;
+  bool acc = false;
+  PairRec rec;
+  float glo = 0.0f, ghi = 0.0f;
+  if (valid) {
+    const float4 fj = so.f[j];
+    const float4 vmj = so.vm[j];
+    const uint32_t idj = so.id[j];
+    const bool actj = so.act[j] != 0;
+    const float4 hbj = so.hb[j];  // meaningful when j is active
+    // separation interval
+    const float r2f = sep2f(Q.fi, fj, boxf);
+    const float r = sqrtf(r2f);
+    const float e = Q.eq + ABS * r;
+    const float rlo = fmaxf(r * (1.0f - REL) - e, 0.0f);
+    const float rhi = r * (1.0f + REL) + e;
+    // relative speed interval
+    const float dvx = Q.vmi.x - vmj.x, dvy = Q.vmi.y - vmj.y, dvz = Q.vmi.z - vmj.z;
+    const float vr = sqrtf(dvx * dvx + dvy * dvy + dvz * dvz);
+    const float vmax_j = fmaxf(fmaxf(fabsf(vmj.x), fabsf(vmj.y)), fabsf(vmj.z));
+    const float dv = 4.0f * U * (3.0f * (Q.vmax_i + vmax_j) + vr) + 4.0f * U * vr;
+    const float vl = fmaxf(vr - dv, 0.0f), vu = vr + dv;
+    g_bounds(Q.kind, Q.s0f, Q.wf, vl, vu, &glo, &ghi);
+    const float gest = vr * sigma_f(Q.kind, Q.s0f, Q.wf, vr);
+    if (P.split) glo = ghi = gest;
+    // does j see i?  (j active and r^2 < h_j^2: decided exactly, or in FP32
+    // by the split form, as its neighbour lists are)
+    bool sees = false;
+    if (actj) {
+      if (P.split) {
+        const float hjf = (float)so.h[j];
+        sees = r2f < hjf * hjf;
+      } else if (rhi < hbj.x) {
+        sees = true;
+      } else if (rlo < hbj.y) {
+        const double hj = so.h[j];
+        sees = sep2(so.x[Q.s], so.y[Q.s], so.z[Q.s], so.x[j], so.y[j], so.z[j], P.box,
+                    0.5 * P.box) < hj * hj;
+      }
+    }
+    if (!(sees && idj < Q.idi)) {
+      // FP32 upper bound of P_pair.  The bound holds only while no product
+      // of the chain leaves the normal FP32 range; below 2^-100 the FP64
+      // path decides.
+      const float fi_up = shape_f(kern, __fmul_rd(rlo, Q.hbi.z)) * (1.0f + SLACK) + REL;
+      const float t1 = 0.5f * vmj.w, t2 = t1 * ghi, t3 = t2 * Q.hbi.w, t4 = t3 * fi_up;
+      float pu = t4 * Q.fi.w;
+      bool tiny = !(fminf(fminf(t1, t2), fminf(fminf(t3, t4), pu)) >= FLT_TINY);
+      float pc = 0.5f * vmj.w * gest * Q.hbi.w * shape_f(kern, r * Q.hbi.z) * Q.fi.w;
+      if (sees) {
+        const float fj_up = shape_f(kern, __fmul_rd(rlo, hbj.z)) * (1.0f + SLACK) + REL;
+        const float s1 = 0.5f * Q.vmi.w, s2 = s1 * ghi, s3 = s2 * hbj.w, s4 = s3 * fj_up;
+        const float puj = s4 * fj.w;
+        tiny = tiny || !(fminf(fminf(s1, s2), fminf(fminf(s3, s4), puj)) >= FLT_TINY);
+        pu += puj;
+        pc += 0.5f * Q.vmi.w * gest * hbj.w * shape_f(kern, r * hbj.z) * fj.w;
+      }
+      pu *= (1.0f + SLACK);
+      const bool i_is_a = Q.idi < idj;
+      const uint32_t a = i_is_a ? Q.idi : idj, b = i_is_a ? idj : Q.idi;
+      const U4 w = philox10(Q.k0, Q.k1, Q.step, 0u, a, b);
+      bool need64;
+      if (P.split) {
+        // split form: FP64 re-test only when |P - u| < 1e-5
+        const double u = unit53(w.x, w.y);
+        need64 = fabs((double)pc - u) < 1e-5;
+        if (!need64) {
+          if (pc >= 1.0f) ++*pge1;
+          acc = u < (double)pc;
+        }
+      } else {
+        // u >= (top 24 bits of u) exactly; at or above the bound of P_pair
+        // the draw is surely rejected
+        const float u_lo = __uint2float_rz(w.x >> 8) * U;
+        need64 = tiny || u_lo < pu;
+      }
+      if (need64) {
+        // exact FP64 probability, in the oracle's operation order
+        const int64_t s = Q.s;
+        const double box = P.box, half = 0.5 * P.box;
+        const double r2 = sep2(so.x[s], so.y[s], so.z[s], so.x[j], so.y[j], so.z[j], box, half);
+        const double ddx = so.vx[s] - so.vx[j], ddy = so.vy[s] - so.vy[j],
+                     ddz = so.vz[s] - so.vz[j];
+        const double vrel = sqrt((ddx * ddx + ddy * ddy) + ddz * ddz);
+        const Halo& H = A.f.halos[so.halo[s]];
+        const double sg = sigma_over_m(Q.kind, H.sigma0, H.w, vrel);
+        const double mj = so.m[j], hi = so.h[s];
+        const double qq = sqrt(r2) / hi;
+        const double p_i = ((((0.5 * mj) * sg) * vrel) * (kernel_norm(kern, hi) *
+                                                          kernel_shape(kern, qq))) * so.dt[s];
+        double p_j = 0.0;
+        if (sees) {
+          const double hj = so.h[j];
+          const double qj = sqrt(r2) / hj;
+          p_j = ((((0.5 * so.m[s]) * sg) * vrel) * (kernel_norm(kern, hj) *
+                                                     kernel_shape(kern, qj))) * so.dt[j];
+        }
+        const double pp = i_is_a ? (p_i + p_j) : (p_j + p_i);
+        if (pp >= 1.0) ++*pge1;
+        acc = unit53(w.x, w.y) < pp;
+        pc = (float)pp;
+      }
+      if (acc) {
+        rec.ord = ((unsigned long long)w.z << 32) | (unsigned long long)w.w;
+        rec.a = a;
+        rec.b = b;
+        const int32_t oj = so.orig[j];
+        rec.ia = i_is_a ? Q.oi : oj;
+        rec.ib = i_is_a ? oj : Q.oi;
+      }
+      ++*cand;
+      *psum += pc;
+    }
+  }
+  const uint32_t m = __ballot_sync(0xffffffffu, acc);
+  if (m) {
+    unsigned long long base = 0;
+    const int leader = __ffs(m) - 1;
+    if (lane == leader) base = atomicAdd(&A.st->n_acc, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (acc) {
+      const unsigned long long at = base + __popc(m & ((1u << lane) - 1u));
+      if (at < (unsigned long long)P.pair_cap) A.pairs[at] = rec;
+      else *status |= ST_ERR_PAIR_OVERFLOW;
+    }
+  }
+  *glo_out = glo;
+  *ghi_out = ghi;
+}
+
+// exact g = |v_i - v_j| sigma/m(|v_i - v_j|) in FP64
+__device__ __forceinline__ double exact_g(const PairKArgs& A, const Query& Q, int64_t j) {
+  const Sorted& so = A.so;
+  const int64_t s = Q.s;
+  const double ddx = so.vx[s] - so.vx[j], ddy = so.vy[s] - so.vy[j], ddz = so.vz[s] - so.vz[j];
+  const double vrel = sqrt((ddx * ddx + ddy * ddy) + ddz * ddz);
+  const Halo& H = A.f.halos[so.halo[s]];
+  return vrel * sigma_over_m(Q.kind, H.sigma0, H.w, vrel);
+}
+
+// Eq. 9: dt_lim,i = 2 C_SIDM / (m_i W(0, h_i) (v sigma/m)_max,i), written by lane 0
+__device__ __forceinline__ void write_limit(const PairKArgs& A, const Query& Q, double vs_max) {
+  if ((threadIdx.x & 31) == 0) {
+    const Sorted& so = A.so;
+    const double den = (so.m[Q.s] * kernel_norm(A.a.kernel, so.h[Q.s])) * vs_max;
+    A.dtlim_user[Q.oi] = vs_max > 0.0 ? (A.a.c_sidm * 2.0) / den : INFINITY;
+  }
+}
+
+__device__ __forceinline__ void flush_counters(const PairKArgs& A, unsigned long long cand,
+                                               unsigned long long pge1, double sum_p,
+                                               uint32_t status) {
+  for (int o = 16; o > 0; o >>= 1) {
+    cand += __shfl_xor_sync(0xffffffffu, cand, o);
+    pge1 += __shfl_xor_sync(0xffffffffu, pge1, o);
+  }
+  sum_p = warp_sumd(sum_p);
+  status = __reduce_or_sync(0xffffffffu, status);
+  if ((threadIdx.x & 31) == 0) {
+    if (cand) atomicAdd(&A.st->n_cand, cand);
+    if (pge1) {
+      atomicAdd(&A.st->n_pge1, pge1);
+      status |= ST_P_GE_1;
+    }
+    if (sum_p != 0.0) atomicAdd(&A.st->sum_p, sum_p);
+    if (status) atomicOr(&A.st->status, status);
+  }
+}
+
+// Queries with a complete neighbour list (the usual case).
+__global__ void __launch_bounds__(PT, 5) pairs_kernel(PairKArgs A) {
+  __shared__ float s_ghi[PW][MAXR * WARP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* ghi_row = s_ghi[warp];
+  const int64_t n_act = (int64_t)A.st->n_active;
+  const float boxf = (float)A.a.box;
   unsigned long long cand = 0, pge1 = 0;
   double sum_p = 0.0;
   uint32_t status = 0;
@@ -128,250 +336,93 @@ __global__ void __launch_bounds__(PT) pairs_kernel(PairKArgs A) {
     }
     if (q >= n_act) break;
     const int64_t qi = q++;
-    const int64_t s = A.act_list[qi];
-    // the query's halo: its particles, cross-section model, random key and step
-    const Halo& H = A.f.halos[so.halo[s]];
-    const int64_t hs = H.start, hn = H.n;
-    const uint32_t k0 = (uint32_t)H.seed, k1 = (uint32_t)(H.seed >> 32);
-    const uint32_t step = H.step;
-    const int kind = H.sigma_kind;
-    const double sigma0 = H.sigma0, wv = H.w;
-    const float s0f = __double2float_ru(sigma0);
-    const float wf = (float)wv;
-    const double xi = so.x[s], yi = so.y[s], zi = so.z[s];
-    const double vxi = so.vx[s], vyi = so.vy[s], vzi = so.vz[s];
-    const double mi = so.m[s], hi = so.h[s], dti = so.dt[s];
-    const uint32_t idi = so.id[s];
-    const int32_t oi = so.orig[s];
-    const float4 fi = so.f[s];
-    const float4 vmi = so.vm[s];
-    const float2 hbi = so.hb[s];
-    const double hhi = hi * hi;
-    const double wni = kernel_norm(kern, hi);
-    const float wni_up = __double2float_ru(wni);
-    const float eq = ABS * (fmaxf(fmaxf(fabsf(fi.x), fabsf(fi.y)), fabsf(fi.z)) + boxf);
-    const float vmax_i = fmaxf(fmaxf(fabsf(vmi.x), fabsf(vmi.y)), fabsf(vmi.z));
-
-    // Everything about one neighbour j (valid lanes only); the accepted pair
-    // is appended by the whole warp.  Returns bounds of g = v sigma/m(v).
-    auto visit = [&](int64_t j, bool valid, float* glo_out, float* ghi_out) {
-      bool acc = false;
-      PairRec rec;
-      float glo = 0.0f, ghi = 0.0f;
-      if (valid) {
-        const float4 fj = so.f[j];
-        const float4 vmj = so.vm[j];
-        const uint32_t idj = so.id[j];
-        const bool actj = so.act[j] != 0;
-        // separation interval
-        const float r2f = sep2f(fi, fj, boxf);
-        const float r = sqrtf(r2f);
-        const float e = eq + ABS * r;
-        const float rlo = fmaxf(r * (1.0f - REL) - e, 0.0f);
-        const float rhi = r * (1.0f + REL) + e;
-        // relative speed interval
-        const float dvx = vmi.x - vmj.x, dvy = vmi.y - vmj.y, dvz = vmi.z - vmj.z;
-        const float vr = sqrtf(dvx * dvx + dvy * dvy + dvz * dvz);
-        const float vmax_j = fmaxf(fmaxf(fabsf(vmj.x), fabsf(vmj.y)), fabsf(vmj.z));
-        const float dv = 4.0f * U * (3.0f * (vmax_i + vmax_j) + vr) + 4.0f * U * vr;
-        const float vl = fmaxf(vr - dv, 0.0f), vu = vr + dv;
-        g_bounds(kind, s0f, wf, vl, vu, &glo, &ghi);
-        if (P.split) {
-          const float g = vr * sigma_f(kind, s0f, wf, vr);
-          glo = ghi = g;
-        }
-        // does j see i?  (j active and r^2 < h_j^2: decided exactly, or in
-        // FP32 by the split form, as its neighbour lists are)
-        bool sees = false;
-        float2 hbj = make_float2(0.f, 0.f);
-        if (actj) {
-          hbj = so.hb[j];
-          if (P.split) {
-            const float hjf = (float)so.h[j];
-            sees = r2f < hjf * hjf;
-          } else if (rhi < hbj.x) {
-            sees = true;
-          } else if (rlo < hbj.y) {
-            const double hj = so.h[j];
-            sees = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half) < hj * hj;
-          }
-        }
-        if (!(sees && idj < idi)) {
-          // FP32 upper bound of P_pair.  The bound holds only while no product
-          // leaves the normal FP32 range; below 2^-100 the FP64 path decides.
-          const float qi_lo = rlo / hbi.y;
-          const float fi_up = shape_f(kern, qi_lo) * (1.0f + SLACK) + REL;
-          const float t1 = 0.5f * vmj.w, t2 = t1 * ghi, t3 = t2 * wni_up, t4 = t3 * fi_up;
-          float pu = t4 * fi.w;
-          bool tiny = !(fminf(fminf(t1, t2), fminf(fminf(t3, t4), pu)) >= FLT_TINY);
-          float pc = 0.5f * vmj.w * (vr * sigma_f(kind, s0f, wf, vr)) * wni_up *
-                     shape_f(kern, r / hbi.y) * fi.w;
-          if (sees) {
-            const float hl = hbj.x;
-            const float wnj_up = knorm_up / (hl * hl * hl) * (1.0f + SLACK);
-            const float qj_lo = rlo / hbj.y;
-            const float fj_up = shape_f(kern, qj_lo) * (1.0f + SLACK) + REL;
-            const float s1 = 0.5f * vmi.w, s2 = s1 * ghi, s3 = s2 * wnj_up, s4 = s3 * fj_up;
-            const float puj = s4 * fj.w;
-            tiny = tiny || !(fminf(fminf(fminf(s1, s2), fminf(s3, s4)),
-                                   fminf(puj, hl * hl * hl)) >= FLT_TINY);
-            pu += puj;
-            pc += 0.5f * vmi.w * (vr * sigma_f(kind, s0f, wf, vr)) * wnj_up *
-                  shape_f(kern, r / hbj.y) * fj.w;
-          }
-          pu *= (1.0f + SLACK);
-          const bool i_is_a = idi < idj;
-          const uint32_t a = i_is_a ? idi : idj, b = i_is_a ? idj : idi;
-          const U4 w = philox10(k0, k1, step, 0u, a, b);
-          const double u = unit53(w.x, w.y);
-          double pp = (double)pc;
-          // plain form: FP64 whenever u is under the FP32 upper bound;
-          // split form: FP64 re-test only when |P - u| < 1e-5
-          const bool need64 = P.split ? (fabs((double)pc - u) < 1e-5) : (tiny || u < (double)pu);
-          if (P.split && !need64) {
-            if (pc >= 1.0f) ++pge1;
-            if (u < pp) {
-              acc = true;
-              rec.ord = ((unsigned long long)w.z << 32) | (unsigned long long)w.w;
-              rec.a = a;
-              rec.b = b;
-              const int32_t oj = so.orig[j];
-              rec.ia = i_is_a ? oi : oj;
-              rec.ib = i_is_a ? oj : oi;
-            }
-          }
-          if (need64) {
-            // exact FP64 probability, in the oracle's operation order
-            const double r2 = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half);
-            const double ddx = vxi - so.vx[j], ddy = vyi - so.vy[j], ddz = vzi - so.vz[j];
-            const double vrel = sqrt((ddx * ddx + ddy * ddy) + ddz * ddz);
-            const double sg = sigma_over_m(kind, sigma0, wv, vrel);
-            const double mj = so.m[j];
-            const double qq = sqrt(r2) / hi;
-            const double p_i = ((((0.5 * mj) * sg) * vrel) * (wni * kernel_shape(kern, qq))) * dti;
-            double p_j = 0.0;
-            if (sees) {
-              const double hj = so.h[j];
-              const double qj = sqrt(r2) / hj;
-              p_j = ((((0.5 * mi) * sg) * vrel) * (kernel_norm(kern, hj) * kernel_shape(kern, qj))) *
-                    so.dt[j];
-            }
-            pp = i_is_a ? (p_i + p_j) : (p_j + p_i);
-            if (pp >= 1.0) ++pge1;
-            if (u < pp) {
-              acc = true;
-              rec.ord = ((unsigned long long)w.z << 32) | (unsigned long long)w.w;
-              rec.a = a;
-              rec.b = b;
-              const int32_t oj = so.orig[j];
-              rec.ia = i_is_a ? oi : oj;
-              rec.ib = i_is_a ? oj : oi;
-            }
-          }
-          ++cand;
-          sum_p += pp;
-        }
-      }
-      const uint32_t m = __ballot_sync(0xffffffffu, acc);
-      if (m) {
-        unsigned long long base = 0;
-        const int leader = __ffs(m) - 1;
-        if (lane == leader) base = atomicAdd(&A.st->n_acc, (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (acc) {
-          const unsigned long long at = base + __popc(m & lt);
-          if (at < (unsigned long long)P.pair_cap) A.pairs[at] = rec;
-          else status |= ST_ERR_PAIR_OVERFLOW;
-        }
-      }
-      *glo_out = glo;
-      *ghi_out = ghi;
-    };
-
-    // exact g = |v_i - v_j| sigma/m(|v_i - v_j|) in FP64
-    auto exact_g = [&](int64_t j) {
-      const double ddx = vxi - so.vx[j], ddy = vyi - so.vy[j], ddz = vzi - so.vz[j];
-      const double vrel = sqrt((ddx * ddx + ddy * ddy) + ddz * ddz);
-      return vrel * sigma_over_m(kind, sigma0, wv, vrel);
-    };
-
-    double vs_max = 0.0;
     const int cnt = A.nb_count[qi];
-    if (cnt >= 0) {
-      const int32_t* row = A.nb_list + qi * (int64_t)A.nb_stride;
-      const int nr = (cnt + 31) >> 5;
-      float glo[MAXR], ghi[MAXR];
-      int32_t jr[MAXR];
-#pragma unroll
-      for (int r = 0; r < MAXR; ++r) {
-        glo[r] = 0.0f;
-        ghi[r] = -1.0f;
-        jr[r] = -1;
-        if (r < nr) {
-          const int k = r * 32 + lane;
-          const bool valid = k < cnt;
-          const int32_t j = valid ? row[k] : -1;
-          jr[r] = j;
-          visit(j, valid, &glo[r], &ghi[r]);
-          if (!valid) ghi[r] = -1.0f;
+    if (cnt < 0) continue;  // left to the tree-walk kernel
+    const Query Q = load_query(A.so, A.f, A.act_list[qi], boxf);
+    const int32_t* row = A.nb_list + qi * (int64_t)A.nb_stride;
+    const int nr = (cnt + 31) >> 5;
+    float mlo = 0.0f, psum = 0.0f;
+    for (int r = 0; r < nr; ++r) {
+      const int k = r * 32 + lane;
+      const bool valid = k < cnt;
+      const int32_t j = valid ? row[k] : -1;
+      float gl, gh;
+      visit(A, Q, j, valid, &gl, &gh, &psum, &cand, &pge1, &status);
+      mlo = fmaxf(mlo, gl);
+      ghi_row[k] = valid ? gh : -1.0f;
+    }
+    sum_p += (double)psum;
+    // exact maximum of g: only j whose upper bound reaches the largest lower bound
+    mlo = warp_maxf(mlo);
+    __syncwarp();
+    double mine = 0.0;
+    if (A.a.split) {
+      mine = (double)mlo;
+    } else {
+      for (int r = 0; r < nr; ++r) {
+        const int k = r * 32 + lane;
+        if (k < cnt && ghi_row[k] >= mlo) mine = fmax(mine, exact_g(A, Q, row[k]));
+      }
+    }
+    write_limit(A, Q, warp_maxd(mine));
+    __syncwarp();
+  }
+  flush_counters(A, cand, pge1, sum_p, status);
+}
+
+// Queries whose neighbour list was not complete: walk the tree with radius
+// h_i and decide membership exactly.
+__global__ void __launch_bounds__(PT) pairs_walk_kernel(PairKArgs A) {
+  __shared__ int s_stack[PW][SEARCH_STACK];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int* stack = s_stack[warp];
+  const Sorted& so = A.so;
+  const int64_t n_act = (int64_t)A.st->n_active;
+  const double box = A.a.box, half = 0.5 * A.a.box;
+  const float boxf = (float)A.a.box;
+  unsigned long long cand = 0, pge1 = 0;
+  double sum_p = 0.0;
+  uint32_t status = 0;
+  const int64_t w0 = (int64_t)blockIdx.x * PW + warp, ws = (int64_t)gridDim.x * PW;
+  for (int64_t qi = w0; qi < n_act; qi += ws) {
+    if (A.nb_count[qi] >= 0) continue;
+    const Query Q = load_query(so, A.f, A.act_list[qi], boxf);
+    const int64_t s = Q.s;
+    const Halo& H = A.f.halos[so.halo[s]];
+    const int64_t hs = H.start;
+    const double xi = so.x[s], yi = so.y[s], zi = so.z[s], hi = so.h[s];
+    const double hhi = hi * hi;
+    const float rad = (__double2float_ru(hi) + 2.0f * Q.eq) * (1.0f + 4.0f * REL);
+    double mine = 0.0;
+    float psum = 0.0f;
+    const int sl = (int)(s - hs);
+    auto leaf = [&](int k, bool valid, const float4& pj) {
+      const int64_t j = hs + k;
+      bool in = false;
+      if (valid && k != sl) {
+        const float r = sqrtf(sep2f(Q.fi, pj, boxf));
+        const float e = Q.eq + ABS * r;
+        const float rlo = fmaxf(r * (1.0f - REL) - e, 0.0f);
+        if (A.a.split) {
+          const float hf = (float)hi;
+          in = r * r < hf * hf;
+        } else if (rlo < Q.hbi.y) {
+          in = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half) < hhi;
         }
       }
-      // exact maximum of g: only j whose upper bound reaches the largest lower bound
-      float mlo = 0.0f;
-#pragma unroll
-      for (int r = 0; r < MAXR; ++r) mlo = fmaxf(mlo, glo[r]);
-      mlo = warp_maxf(mlo);
-      double mine = 0.0;
-#pragma unroll
-      for (int r = 0; r < MAXR; ++r)
-        if (jr[r] >= 0 && ghi[r] >= mlo) mine = fmax(mine, P.split ? (double)glo[r] : exact_g(jr[r]));
-      vs_max = warp_maxd(mine);
-    } else {
-      // direct walk with radius h_i (list incomplete): exact membership
-      const float rad = (__double2float_ru(hi) + 2.0f * eq) * (1.0f + 4.0f * REL);
-      double mine = 0.0;
-      const bool ok = traverse(A.f, H, fi, rad * rad, boxf, stack, [&](int leaf) {
-        const int64_t jl = (int64_t)leaf * LEAF + lane;
-        const int64_t j = hs + jl;
-        bool in = false;
-        if (jl < hn && j != s) {
-          const float r = sqrtf(sep2f(fi, so.f[j], boxf));
-          const float e = eq + ABS * r;
-          const float rlo = fmaxf(r * (1.0f - REL) - e, 0.0f);
-          if (P.split) {
-            const float hf = (float)hi;
-            in = r * r < hf * hf;
-          } else if (rlo < hbi.y) {
-            in = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half) < hhi;
-          }
-        }
-        float gl, gh;
-        visit(j, in, &gl, &gh);
-        if (in) mine = fmax(mine, P.split ? (double)gl : exact_g(j));
-      });
-      if (!ok) status |= ST_ERR_STACK;
-      vs_max = warp_maxd(mine);
-    }
-    if (lane == 0) {
-      const double den = (mi * wni) * vs_max;
-      A.dtlim_user[oi] = vs_max > 0.0 ? (P.c_sidm * 2.0) / den : INFINITY;
-    }
+      float gl, gh;
+      visit(A, Q, j, in, &gl, &gh, &psum, &cand, &pge1, &status);
+      if (in) mine = fmax(mine, A.a.split ? (double)gl : exact_g(A, Q, j));
+    };
+    const bool ok = A.a.box > 0.0
+        ? traverse<true>(A.f, H, so.f + hs, Q.fi, rad * rad, boxf, stack, leaf)
+        : traverse<false>(A.f, H, so.f + hs, Q.fi, rad * rad, boxf, stack, leaf);
+    if (!ok) status |= ST_ERR_STACK;
+    sum_p += (double)psum;
+    write_limit(A, Q, warp_maxd(mine));
+    __syncwarp();
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    cand += __shfl_xor_sync(0xffffffffu, cand, o);
-    pge1 += __shfl_xor_sync(0xffffffffu, pge1, o);
-  }
-  sum_p = warp_sumd(sum_p);
-  status = __reduce_or_sync(0xffffffffu, status);
-  if (lane == 0) {
-    if (cand) atomicAdd(&A.st->n_cand, cand);
-    if (pge1) {
-      atomicAdd(&A.st->n_pge1, pge1);
-      status |= ST_P_GE_1;
-    }
-    if (sum_p != 0.0) atomicAdd(&A.st->sum_p, sum_p);
-    if (status) atomicOr(&A.st->status, status);
-  }
+  flush_counters(A, cand, pge1, sum_p, status);
 }
 
 }  // namespace
@@ -386,7 +437,8 @@ int launch_pairs(const Sorted& so, const Forest& f, int64_t n, const int32_t* ac
   const int64_t need = (n + PW - 1) / PW;
   if (blocks > need) blocks = need;
   pairs_kernel<<<(unsigned)blocks, PT, 0, s>>>(k);
-  return 1;
+  pairs_walk_kernel<<<(unsigned)sms, PT, 0, s>>>(k);
+  return 2;
 }
 
 }  // namespace sidm

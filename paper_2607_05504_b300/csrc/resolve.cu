@@ -180,11 +180,22 @@ __device__ __forceinline__ void st_release(int32_t* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// The kick of a pending pair, with the velocities read and written through
-// L2 (other SMs apply the neighbouring kicks).
-__device__ void kick_l2(const PairRec& r, double* vel, const double* mass, uint32_t k0,
-                        uint32_t k1, uint32_t step, unsigned* dirfail) {
-  double e0 = 0.0, e1 = 0.0, e2 = 1.0;
+__device__ __forceinline__ int ld_relaxed(const int32_t* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void fence_acq_rel() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+// Isotropic direction of pair r (Marsaglia, Philox streams 1, 2, ...); it
+// depends only on the pair's key, so it is drawn before the pair's turn.
+__device__ __forceinline__ void pair_direction(const PairRec& r, uint32_t k0, uint32_t k1,
+                                               uint32_t step, double* e, unsigned* dirfail) {
+  e[0] = 0.0;
+  e[1] = 0.0;
+  e[2] = 1.0;
   bool found = false;
   for (uint32_t t = 0; t < DIRECTION_TRIES && !found; ++t) {
     const U4 w = philox10(k0, k1, step, 1u + t, r.a, r.b);
@@ -193,16 +204,21 @@ __device__ void kick_l2(const PairRec& r, double* vel, const double* mass, uint3
     const double s = x1 * x1 + x2 * x2;
     if (s > 0.0 && s < 1.0) {
       const double k = 2.0 * sqrt(1.0 - s);
-      e0 = x1 * k;
-      e1 = x2 * k;
-      e2 = 1.0 - 2.0 * s;
+      e[0] = x1 * k;
+      e[1] = x2 * k;
+      e[2] = 1.0 - 2.0 * s;
       found = true;
     }
   }
   if (!found) atomicAdd(dirfail, 1u);
+}
+
+// The kick of a pending pair with direction e, the velocities read and
+// written through L2 (other SMs apply the neighbouring kicks).
+__device__ __forceinline__ void kick_l2(const PairRec& r, double* vel, double ma, double mb,
+                                        const double* e) {
   double* va = vel + 3 * (int64_t)r.ia;
   double* vb = vel + 3 * (int64_t)r.ib;
-  const double ma = mass[r.ia], mb = mass[r.ib];
   const double M = ma + mb;
   const double ax = __ldcg(va), ay = __ldcg(va + 1), az = __ldcg(va + 2);
   const double bx = __ldcg(vb), by = __ldcg(vb + 1), bz = __ldcg(vb + 2);
@@ -212,12 +228,12 @@ __device__ void kick_l2(const PairRec& r, double* vel, const double* mass, uint3
   const double dx = ax - bx, dy = ay - by, dz = az - bz;
   const double g = sqrt((dx * dx + dy * dy) + dz * dz);
   const double fa = (mb * g) / M, fb = (ma * g) / M;
-  __stcg(va, cx + fa * e0);
-  __stcg(va + 1, cy + fa * e1);
-  __stcg(va + 2, cz + fa * e2);
-  __stcg(vb, cx - fb * e0);
-  __stcg(vb + 1, cy - fb * e1);
-  __stcg(vb + 2, cz - fb * e2);
+  __stcg(va, cx + fa * e[0]);
+  __stcg(va + 1, cy + fa * e[1]);
+  __stcg(va + 2, cz + fa * e[2]);
+  __stcg(vb, cx - fb * e[0]);
+  __stcg(vb + 1, cy - fb * e[1]);
+  __stcg(vb + 2, cz - fb * e[2]);
 }
 
 __global__ void __launch_bounds__(GT) count_kernel(const PairRec* __restrict__ pairs, int64_t cap,
@@ -329,6 +345,13 @@ __global__ void __launch_bounds__(GT) segsort_kernel(const PairRec* __restrict__
       }
       sg[j + 1] = x;
     }
+    // position of each pair in this particle's order: its turn comes when the
+    // particle's cursor reaches it
+    for (int i = 0; i < len; ++i) {
+      const int32_t p = sg[i];
+      if (pairs[p].ia == e) b.pos_a[p] = i;
+      else b.pos_b[p] = i;
+    }
   }
 }
 
@@ -346,22 +369,57 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
     const int64_t np = (int64_t)st->n_pending;
     const int64_t gsize = (int64_t)gridDim.x * GT;
     const int64_t t0 = blockIdx.x * (int64_t)GT + threadIdx.x;
+    // the thread's first pair, prepared (masses, direction) before its turn;
+    // a turn is two relaxed cursor loads, then an acquire fence
+    bool first = t0 < np;
+    PairRec r0{};
+    int pa0 = 0, pb0 = 0;
+    double ma0 = 0.0, mb0 = 0.0, e0[3];
+    if (first) {
+      const int32_t p = b.pending[t0];
+      r0 = pairs[p];
+      pa0 = b.pos_a[p];
+      pb0 = b.pos_b[p];
+      ma0 = mass[r0.ia];
+      mb0 = mass[r0.ib];
+      const Halo& H = halos[halo_of[r0.ia]];
+      pair_direction(r0, (uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, e0, &s_dirfail);
+    }
     int pass = 0;
-    bool left = t0 < np;
+    bool left = first;
     for (; left && pass < DATAFLOW_MAX_PASSES; ++pass) {
       left = false;
-      for (int64_t k = t0; k < np; k += gsize) {
+      if (first) {
+        const int ca = ld_relaxed(&b.cursor[r0.ia]);
+        const int cb = ld_relaxed(&b.cursor[r0.ib]);
+        if (ca == pa0 && cb == pb0) {
+          fence_acq_rel();
+          kick_l2(r0, vel, ma0, mb0, e0);
+          fence_acq_rel();
+          st_release(&b.cursor[r0.ia], pa0 + 1);
+          st_release(&b.cursor[r0.ib], pb0 + 1);
+          first = false;
+        } else {
+          left = true;
+        }
+      }
+      // further pairs of this thread (more pending pairs than threads)
+      for (int64_t k = t0 + gsize; k < np; k += gsize) {
         const int32_t p = b.pending[k];
         if (b.flags[p]) continue;
         const PairRec r = pairs[p];
-        const int ca = ld_acquire(&b.cursor[r.ia]);
-        const int cb = ld_acquire(&b.cursor[r.ib]);
-        if (b.seg[b.seg_off[r.ia] + ca] == p && b.seg[b.seg_off[r.ib] + cb] == p) {
+        const int pa = b.pos_a[p], pb = b.pos_b[p];
+        const int ca = ld_relaxed(&b.cursor[r.ia]);
+        const int cb = ld_relaxed(&b.cursor[r.ib]);
+        if (ca == pa && cb == pb) {
+          fence_acq_rel();
           const Halo& H = halos[halo_of[r.ia]];
-          kick_l2(r, vel, mass, (uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, &s_dirfail);
-          __threadfence();
-          st_release(&b.cursor[r.ia], ca + 1);
-          st_release(&b.cursor[r.ib], cb + 1);
+          double e[3];
+          pair_direction(r, (uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, e, &s_dirfail);
+          kick_l2(r, vel, mass[r.ia], mass[r.ib], e);
+          fence_acq_rel();
+          st_release(&b.cursor[r.ia], pa + 1);
+          st_release(&b.cursor[r.ib], pb + 1);
           b.flags[p] = 1;
         } else {
           left = true;

@@ -51,6 +51,7 @@ struct SearchArgs {
   double box;
   int n_ngb, tol;
   double fixed_h;
+  int kernel;            // SIDM_KERNEL_*: normalisation bound stored with h
   int split;             // 1: FP32 counts and lists, no FP64 re-tests
   double* h_user;
   int32_t* nb_list;     // [n_act][nb_stride]
@@ -108,7 +109,8 @@ __device__ __forceinline__ double half_of(double h) {
   return (ef > 1 && ef < 2047) ? __longlong_as_double(b - (1ll << 52)) : 0.5 * h;
 }
 
-__global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
+template <bool PERIODIC>
+__global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
   __shared__ float s_r2[SW][SEARCH_CAP];
   __shared__ int32_t s_j[SW][SEARCH_CAP];
   __shared__ int s_stack[SW][SEARCH_STACK];
@@ -138,6 +140,8 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
     const int64_t s = A.act_list[qi];
     const Halo& H = A.f.halos[so.halo[s]];
     const int64_t hs = H.start, hn = H.n;   // the query's halo: [hs, hs + hn)
+    const float4* hpos = so.f + hs;         // its FP32 positions
+    const int sl = (int)(s - hs);           // the query's halo-local index
     const float4 fi = so.f[s];
     const float eq = ABS * (fmaxf(fmaxf(fabsf(fi.x), fabsf(fi.y)), fabsf(fi.z)) + boxf);
     double h;
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
         wv[k] = INFINITY;
         const int64_t j = w0 + k * 32 + lane;
         if (j < w0 + W && j != s) {
-          wv[k] = sep2f(fi, so.f[j], boxf);
+          wv[k] = sep2f<PERIODIC>(fi, so.f[j], boxf);
           vmin = fminf(vmin, wv[k]);
           vmax = fmaxf(vmax, wv[k]);
         }
@@ -193,13 +197,12 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
       const float g2 = T < INFINITY ? thr_out2(T * (1.0f + REL), eq) : INFINITY;
       const float rad = (T + 2.0f * eq) * (1.0f + 4.0f * REL);
       const float rad2 = rad < INFINITY ? rad * rad : INFINITY;
-      const bool ok = traverse(A.f, H, fi, rad2, boxf, stack, [&](int leaf) {
-        const int64_t jl = (int64_t)leaf * LEAF + lane;
-        const int64_t j = hs + jl;
+      const bool ok = traverse<PERIODIC>(A.f, H, hpos, fi, rad2, boxf, stack,
+                                         [&](int k, bool valid, const float4& pj) {
         float s2 = 0.0f;
         bool keep = false;
-        if (jl < hn && j != s) {
-          s2 = sep2f(fi, so.f[j], boxf);
+        if (valid && k != sl) {
+          s2 = sep2f<PERIODIC>(fi, pj, boxf);
           keep = s2 < g2;
         }
         const uint32_t m = __ballot_sync(0xffffffffu, keep);
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
           const int at = len + __popc(m & lt);
           if (at < SEARCH_CAP) {
             lst_r2[at] = s2;
-            lst_j[at] = (int32_t)j;
+            lst_j[at] = (int32_t)(hs + k);
           }
         }
         len += __popc(m);
@@ -235,11 +238,10 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
         const float in2 = thr_in2(Tn, eq);
         const float radn = (Tn + 2.0f * eq) * (1.0f + 4.0f * REL);
         int c = 0;
-        const bool ok2 = traverse(A.f, H, fi, radn * radn, boxf, stack, [&](int leaf) {
-          const int64_t jl = (int64_t)leaf * LEAF + lane;
-          const int64_t j = hs + jl;
+        const bool ok2 = traverse<PERIODIC>(A.f, H, hpos, fi, radn * radn, boxf, stack,
+                                            [&](int k, bool valid, const float4& pj) {
           bool in = false;
-          if (jl < hn && j != s) in = sep2f(fi, so.f[j], boxf) < in2;
+          if (valid && k != sl) in = sep2f<PERIODIC>(fi, pj, boxf) < in2;
           c += __popc(__ballot_sync(0xffffffffu, in));
         });
         if (!ok2) { status |= ST_ERR_STACK; break; }
@@ -349,7 +351,12 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
     if (lane == 0) {
       A.nb_count[qi] = cnt;
       so.h[s] = h;
-      so.hb[s] = make_float2(hl, hu);
+      // bounds used by the pair kernel: 1/h from below, K/h^3 from above
+      const float knorm_up = __double2float_ru(A.kernel == SIDM_KERNEL_TOPHAT
+                                                   ? 3.0 / (4.0 * 3.141592653589793)
+                                                   : 8.0 / 3.141592653589793);
+      so.hb[s] = make_float4(hl, hu, __frcp_rd(hu),
+                             __fdiv_ru(knorm_up, __fmul_rd(__fmul_rd(hl, hl), hl)));
       A.h_user[so.orig[s]] = h;
     }
     __syncwarp();
@@ -366,16 +373,18 @@ __global__ void __launch_bounds__(ST) search_kernel(SearchArgs A) {
 }  // namespace
 
 int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
-                  double box, int n_ngb, int tol, double fixed_h, int split, double* h_user,
+                  double box, int n_ngb, int tol, double fixed_h, int kernel, int split,
+                  double* h_user,
                   int32_t* nb_list, int32_t* nb_count, int nb_stride, DevStats* st, int* work,
                   int sms, cudaStream_t s) {
   if (n <= 0) return 0;
-  SearchArgs a{so, f, n, act_list, box, n_ngb, tol, fixed_h, split, h_user,
+  SearchArgs a{so, f, n, act_list, box, n_ngb, tol, fixed_h, kernel, split, h_user,
                nb_list, nb_count, nb_stride, st, work};
-  int64_t blocks = (int64_t)sms * 12;
+  int64_t blocks = (int64_t)sms * 8;
   const int64_t need = (n + SW - 1) / SW;
   if (blocks > need) blocks = need;
-  search_kernel<<<(unsigned)blocks, ST, 0, s>>>(a);
+  if (box > 0.0) search_kernel<true><<<(unsigned)blocks, ST, 0, s>>>(a);
+  else search_kernel<false><<<(unsigned)blocks, ST, 0, s>>>(a);
   return 1;
 }
 

@@ -18,8 +18,8 @@ constexpr int WARP = 32;
 constexpr int LEAF = 32;                 // particles per tree leaf (one per lane)
 constexpr int MAX_LEVELS = 8;            // 32-ary levels: 32^8 leaves >> any n
 constexpr int BISECT_MAX_EVALS = 128;    // neighbour-count evaluations per particle
-constexpr int SEARCH_CAP = 896;          // gathered candidates per query (shared memory)
-constexpr int SEARCH_STACK = 256;        // traversal stack per warp
+constexpr int SEARCH_CAP = 768;          // gathered candidates per query (shared memory)
+constexpr int SEARCH_STACK = 256;        // traversal stack per warp (>= 31 MAX_LEVELS + 1)
 constexpr int RADIUS_MAX_ITERS = 24;     // gather-radius adjustments per query
 constexpr int RESOLVE_MAX_ROUNDS = 4096; // resolver rounds
 constexpr int DIRECTION_TRIES = 64;      // Marsaglia rejection tries
@@ -182,7 +182,8 @@ struct Sorted {               // particle state in key order
   double *dt;                 // dt_i of the particle
   float4* f;                  // FP32 position (round to nearest); w = dt_i rounded up
   float4* vm;                 // FP32 velocity (round to nearest); w = m rounded up
-  float2* hb;                 // h of active particles rounded down / up
+  float4* hb;                 // active particles: h rounded down, h rounded up, 1/h
+                              // rounded down, kernel normalisation K / h^3 rounded up
   uint32_t* id;
   uint8_t* act;
   int32_t* orig;              // user-order index
@@ -213,7 +214,8 @@ int tree_levels_for(int64_t n, int64_t count[MAX_LEVELS]);
 
 // search.cu
 int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
-                  double box, int n_ngb, int tol, double fixed_h, int split, double* h_user,
+                  double box, int n_ngb, int tol, double fixed_h, int kernel, int split,
+                  double* h_user,
                   int32_t* nb_list, int32_t* nb_count, int nb_stride, DevStats* st, int* work,
                   int sms, cudaStream_t s);
 
@@ -240,6 +242,8 @@ struct ResolveBuffers {
   int32_t* touched;   // [2 cap] particles that own a segment
   int32_t* pending;   // [cap] pairs that share a particle with another pair
   uint8_t* flags;     // [cap] applied flags
+  int32_t* pos_a;     // [cap] place of the pair in the sorted segment of its particle a
+  int32_t* pos_b;     // [cap] ... and of its particle b
 };
 int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* mass,
                    const int32_t* halo_of, const Halo* halos, const ResolveBuffers& b,

@@ -9,9 +9,10 @@
 
 namespace sidm {
 
+template <bool PERIODIC>
 __device__ __forceinline__ float axis_gap2(float lo, float hi, float q, float box) {
   float d = fmaxf(fmaxf(lo - q, q - hi), 0.f);
-  if (box > 0.f) {
+  if (PERIODIC) {
     const float q1 = q + box, q2 = q - box;
     d = fminf(d, fmaxf(fmaxf(lo - q1, q1 - hi), 0.f));
     d = fminf(d, fmaxf(fmaxf(lo - q2, q2 - hi), 0.f));
@@ -19,16 +20,18 @@ __device__ __forceinline__ float axis_gap2(float lo, float hi, float q, float bo
   return d * d;
 }
 
-__device__ __forceinline__ bool box_hits(const float4& lo, const float4& hi, float qx, float qy,
-                                         float qz, float rad2, float box) {
-  return axis_gap2(lo.x, hi.x, qx, box) + axis_gap2(lo.y, hi.y, qy, box) +
-             axis_gap2(lo.z, hi.z, qz, box) <= rad2;
+template <bool PERIODIC>
+__device__ __forceinline__ bool box_hits(const float4& lo, const float4& hi, const float4& q,
+                                         float rad2, float box) {
+  return axis_gap2<PERIODIC>(lo.x, hi.x, q.x, box) + axis_gap2<PERIODIC>(lo.y, hi.y, q.y, box) +
+             axis_gap2<PERIODIC>(lo.z, hi.z, q.z, box) <= rad2;
 }
 
 // FP32 squared separation with a minimum image taken as min(|d|, L - |d|).
+template <bool PERIODIC>
 __device__ __forceinline__ float sep2f(const float4& a, const float4& b, float box) {
   float dx = fabsf(b.x - a.x), dy = fabsf(b.y - a.y), dz = fabsf(b.z - a.z);
-  if (box > 0.f) {
+  if (PERIODIC) {
     dx = fminf(dx, box - dx);
     dy = fminf(dy, box - dy);
     dz = fminf(dz, box - dz);
@@ -36,59 +39,56 @@ __device__ __forceinline__ float sep2f(const float4& a, const float4& b, float b
   return dx * dx + dy * dy + dz * dz;
 }
 
-// Squared FP32 test radius covering radius R around a query at q: the FP32
-// copies of the coordinates are within 2^-24 |x| of the FP64 values, so a
-// particle within R in FP64 is within (R + eps)(1 + 2^-20) in FP32 with
-// eps = 2^-20 (max|q| + R + L).
-__device__ __forceinline__ float test_radius2(double R, const float4& q, float box) {
-  const float Rf = __double2float_ru(R);
-  const float qm = fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fabsf(q.z));
-  const float eps = (qm + Rf + box) * 9.5367431640625e-07f;  // 2^-20
-  const float r = (Rf + eps) * (1.0f + 9.5367431640625e-07f);
-  return r * r;
+// The same with the boundary kind known only at run time.
+__device__ __forceinline__ float sep2f(const float4& a, const float4& b, float box) {
+  return box > 0.f ? sep2f<true>(a, b, box) : sep2f<false>(a, b, box);
 }
 
-// Visits every leaf of halo H whose box meets the sphere; leaf_fn(leaf) is
-// called by the whole warp with the halo-local leaf index (particles
-// H.start + 32 leaf + lane, below H.start + H.n).  Returns false if the
-// stack overflowed (visit incomplete).
-template <class LeafFn>
-__device__ __forceinline__ bool traverse(const Forest& f, const Halo& H, const float4& q,
+// Visits every leaf of halo H whose box meets the sphere (depth first, one
+// stack entry at a time: the stack never holds more than 31 entries per
+// level plus one).  leaf_fn(k, valid, pj) is called by the whole warp for
+// each leaf reached: lane l holds the halo-local particle k = 32 leaf + l,
+// valid when k < H.n, with FP32 position pj (hpos = key-order FP32
+// positions of the halo's particles).  Returns false if the stack
+// overflowed (visit incomplete).
+template <bool PERIODIC, class LeafFn>
+__device__ __forceinline__ bool traverse(const Forest& f, const Halo& H,
+                                         const float4* __restrict__ hpos, const float4& q,
                                          float rad2, float box, int* stack, LeafFn&& leaf_fn) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  if (H.levels <= 0) return true;
+  const int levels = H.levels;
+  if (levels <= 0) return true;
+  const int hn = (int)H.n;
   int top = 1;
-  if (lane == 0) stack[0] = (H.levels - 1) << 28;
+  if (lane == 0) stack[0] = (levels - 1) << 28;
   __syncwarp();
-  bool ok = true;
   while (top > 0) {
     --top;
     const int node = stack[top];
-    __syncwarp();
-    const int level = node >> 28, idx = node & 0x0FFFFFFF;
+    __syncwarp();  // read before the children overwrite the slot
+    const int level = node >> 28;
+    const int k = ((node & 0x0FFFFFFF) << 5) + lane;
     if (level == 0) {
-      leaf_fn(idx);
+      const bool valid = k < hn;
+      float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid) pj = hpos[k];
+      leaf_fn(k, valid, pj);
     } else {
-      const int64_t child = (int64_t)idx * 32 + lane;
       bool hit = false;
-      if (child < H.node_cnt[level - 1]) {
-        const int64_t c = H.node_off[level - 1] + child;
-        hit = box_hits(f.lo[c], f.hi[c], q.x, q.y, q.z, rad2, box);
+      if (k < (int)H.node_cnt[level - 1]) {
+        const int64_t nd = H.node_off[level - 1] + k;
+        hit = box_hits<PERIODIC>(f.lo[nd], f.hi[nd], q, rad2, box);
       }
       const uint32_t m = __ballot_sync(0xffffffffu, hit);
-      const int k = __popc(m);
-      if (top + k > SEARCH_STACK) {
-        ok = false;
-        break;
-      }
-      if (hit) stack[top + __popc(m & lt)] = ((level - 1) << 28) | (int)child;
-      top += k;
+      const int cnt = __popc(m);
+      if (top + cnt > SEARCH_STACK) return false;
+      if (hit) stack[top + __popc(m & lt)] = ((level - 1) << 28) | k;
+      top += cnt;
       __syncwarp();
     }
   }
-  __syncwarp();
-  return ok;
+  return true;
 }
 
 }  // namespace sidm
