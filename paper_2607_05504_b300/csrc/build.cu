@@ -143,7 +143,47 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
   return v;
 }
 
-// Key = halo index above a Morton key with mb = (30 - halo_bits)/3 bits per
+// Index of cell (x0, x1, x2), each coordinate of `bits` bits, along a 3-D
+// Hilbert curve (Skilling, "Programming the Hilbert curve", AIP Conf. Proc.
+// 707, 2004): the coordinates are transformed in place into the curve's
+// "transposed" index, whose bits are then interleaved, axis 0 first.
+// Consecutive cells along the curve are face neighbours, so runs of
+// key-ordered particles (tree leaves, the search window) stay compact.
+__device__ __forceinline__ uint32_t hilbert_key(uint32_t x0, uint32_t x1, uint32_t x2, int bits) {
+  if (bits <= 0) return 0u;
+  const uint32_t M = 1u << (bits - 1);
+  // inverse undo: walk the bits from the top, reflecting or exchanging
+  for (uint32_t Q = M; Q > 1; Q >>= 1) {
+    const uint32_t P = Q - 1;
+    if (x0 & Q) x0 ^= P;
+    if (x1 & Q) {
+      x0 ^= P;
+    } else {
+      const uint32_t t = (x0 ^ x1) & P;
+      x0 ^= t;
+      x1 ^= t;
+    }
+    if (x2 & Q) {
+      x0 ^= P;
+    } else {
+      const uint32_t t = (x0 ^ x2) & P;
+      x0 ^= t;
+      x2 ^= t;
+    }
+  }
+  // Gray encode
+  x1 ^= x0;
+  x2 ^= x1;
+  uint32_t t = 0;
+  for (uint32_t Q = M; Q > 1; Q >>= 1)
+    if (x2 & Q) t ^= Q - 1;
+  x0 ^= t;
+  x1 ^= t;
+  x2 ^= t;
+  return (spread10(x0) << 2) | (spread10(x1) << 1) | spread10(x2);
+}
+
+// Key = halo index above a Hilbert key with mb = (30 - halo_bits)/3 bits per
 // axis.  Periodic box: 2^mb cells per axis.  Open boundaries: the offset
 // from the halo's centre is compressed radially by asinh(r/s)/asinh(R/s)
 // (s = R/1024) before 2^mb cells per axis, so that cells stay small relative
@@ -187,8 +227,7 @@ __global__ void __launch_bounds__(BT) keys_kernel(const double* __restrict__ pos
       c[a] = (uint32_t)q;
     }
   }
-  const uint32_t morton = spread10(c[0]) | (spread10(c[1]) << 1) | (spread10(c[2]) << 2);
-  keys[i] = ((uint32_t)k << (3 * mb)) | morton;
+  keys[i] = ((uint32_t)k << (3 * mb)) | hilbert_key(c[0], c[1], c[2], mb);
   vals[i] = (int32_t)i;
 }
 
