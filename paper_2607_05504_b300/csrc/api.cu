@@ -45,6 +45,10 @@ struct sidm_ctx {
   int32_t* act_list = nullptr;
   int32_t* nb_list = nullptr;   // [n][nb_stride] neighbour lists of the active particles
   int32_t* nb_count = nullptr;  // [n] list length, or -1
+  int2* deferred = nullptr;     // [pair_cap] draws for the exact FP64 pass
+  int32_t* lim_cand = nullptr;  // [n][LIM_CAND] Eq. 9 candidates of each query
+  int32_t* lim_cnt = nullptr;   // [n]
+  float* lim_g = nullptr;       // [n]
   int nb_stride = 0;
   // haloes and their trees
   std::vector<Halo> halos;      // host copy (layout + per-step parameters)
@@ -183,6 +187,10 @@ int ensure_capacity(sidm_ctx* c, int64_t n) {
   CK(dalloc(c, &c->latched, 1));
   CK(dalloc(c, &c->work, 8));
   CK(dalloc(c, &c->pairs, pc));
+  CK(dalloc(c, &c->deferred, pc));
+  CK(dalloc(c, &c->lim_cand, want * (int64_t)LIM_CAND));
+  CK(dalloc(c, &c->lim_cnt, want));
+  CK(dalloc(c, &c->lim_g, want));
   ResolveBuffers& rb = c->rb;
   CK(dalloc(c, &rb.mult, want));
   CK(dalloc(c, &rb.seg_off, want));
@@ -392,6 +400,10 @@ int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
     pa.c_sidm = c->cfg.c_sidm;
     pa.box = c->cfg.box;
     pa.pair_cap = c->pair_cap;
+    pa.deferred = c->deferred;
+    pa.lim_cand = c->lim_cand;
+    pa.lim_cnt = c->lim_cnt;
+    pa.lim_g = c->lim_g;
     L += launch_pairs(c->so, F, n, c->act_list, c->nb_list, c->nb_count, c->nb_stride, pa,
                       c->pairs, c->dtlim, c->dstats, c->work + 1, c->sms, s);
     mark(5);

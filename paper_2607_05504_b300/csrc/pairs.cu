@@ -29,6 +29,7 @@ namespace {
 
 constexpr int PW = 4;
 constexpr int PT = PW * WARP;
+constexpr int XT = 256;                            // thread-per-item passes
 constexpr int CHUNK = 4;
 constexpr int MAXR = 8;                            // neighbour rounds of 32 (stride <= 256)
 constexpr float U = 5.9604644775390625e-08f;       // 2^-24
@@ -148,8 +149,9 @@ __device__ __forceinline__ void visit(const PairKArgs& A, const Query& Q, int64_
   const int kern = P.kernel;
   const int lane = threadIdx.x & 31;
   const float boxf = (float)P.box;
-  bool acc = false;
+  bool acc = false, defer = false;
   PairRec rec;
+  int2 drec;
   float glo = 0.0f, ghi = 0.0f;
   if (valid) {
     const float4 fj = so.f[j];
@@ -208,47 +210,23 @@ __device__ __forceinline__ void visit(const PairKArgs& A, const Query& Q, int64_
       const bool i_is_a = Q.idi < idj;
       const uint32_t a = i_is_a ? Q.idi : idj, b = i_is_a ? idj : Q.idi;
       const U4 w = philox10(Q.k0, Q.k1, Q.step, 0u, a, b);
-      bool need64;
+      // u lies in [u_lo, u_lo + 2^-24): its top 24 bits, exactly
+      const float u_lo = __uint2float_rz(w.x >> 8) * U;
       if (P.split) {
-        // split form: FP64 re-test only when |P - u| < 1e-5
-        const double u = unit53(w.x, w.y);
-        need64 = fabs((double)pc - u) < 1e-5;
-        if (!need64) {
+        // split form: FP32 decision unless u may lie within 1e-5 of P
+        const float d = pc - u_lo;
+        defer = d > -1e-5f && d < 1e-5f + U;
+        if (!defer) {
           if (pc >= 1.0f) ++*pge1;
-          acc = u < (double)pc;
+          acc = d > 0.0f;
         }
       } else {
-        // u >= (top 24 bits of u) exactly; at or above the bound of P_pair
-        // the draw is surely rejected
-        const float u_lo = __uint2float_rz(w.x >> 8) * U;
-        need64 = tiny || u_lo < pu;
+        // at or above the bound of P_pair the draw is surely rejected
+        defer = tiny || u_lo < pu;
       }
-      if (need64) {
-        // exact FP64 probability, in the oracle's operation order
-        const int64_t s = Q.s;
-        const double box = P.box, half = 0.5 * P.box;
-        const double r2 = sep2(so.x[s], so.y[s], so.z[s], so.x[j], so.y[j], so.z[j], box, half);
-        const double ddx = so.vx[s] - so.vx[j], ddy = so.vy[s] - so.vy[j],
-                     ddz = so.vz[s] - so.vz[j];
-        const double vrel = sqrt((ddx * ddx + ddy * ddy) + ddz * ddz);
-        const Halo& H = A.f.halos[so.halo[s]];
-        const double sg = sigma_over_m(Q.kind, H.sigma0, H.w, vrel);
-        const double mj = so.m[j], hi = so.h[s];
-        const double qq = sqrt(r2) / hi;
-        const double p_i = ((((0.5 * mj) * sg) * vrel) * (kernel_norm(kern, hi) *
-                                                          kernel_shape(kern, qq))) * so.dt[s];
-        double p_j = 0.0;
-        if (sees) {
-          const double hj = so.h[j];
-          const double qj = sqrt(r2) / hj;
-          p_j = ((((0.5 * so.m[s]) * sg) * vrel) * (kernel_norm(kern, hj) *
-                                                     kernel_shape(kern, qj))) * so.dt[j];
-        }
-        const double pp = i_is_a ? (p_i + p_j) : (p_j + p_i);
-        if (pp >= 1.0) ++*pge1;
-        acc = unit53(w.x, w.y) < pp;
-        pc = (float)pp;
-      }
+      // the exact FP64 decision is left to the thread-per-pair pass
+      if (defer) drec = make_int2((int)Q.s, (int)j | (sees ? (int)0x80000000u : 0));
+      else *psum += pc;
       if (acc) {
         rec.ord = ((unsigned long long)w.z << 32) | (unsigned long long)w.w;
         rec.a = a;
@@ -258,7 +236,18 @@ __device__ __forceinline__ void visit(const PairKArgs& A, const Query& Q, int64_
         rec.ib = i_is_a ? oj : Q.oi;
       }
       ++*cand;
-      *psum += pc;
+    }
+  }
+  const uint32_t dm = __ballot_sync(0xffffffffu, defer);
+  if (dm) {
+    unsigned long long base = 0;
+    const int leader = __ffs(dm) - 1;
+    if (lane == leader) base = atomicAdd(&A.st->n_deferred, (unsigned long long)__popc(dm));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (defer) {
+      const unsigned long long at = base + __popc(dm & ((1u << lane) - 1u));
+      if (at < (unsigned long long)P.pair_cap) P.deferred[at] = drec;
+      else *status |= ST_ERR_PAIR_OVERFLOW;
     }
   }
   const uint32_t m = __ballot_sync(0xffffffffu, acc);
@@ -277,23 +266,20 @@ __device__ __forceinline__ void visit(const PairKArgs& A, const Query& Q, int64_
   *ghi_out = ghi;
 }
 
-// exact g = |v_i - v_j| sigma/m(|v_i - v_j|) in FP64
-__device__ __forceinline__ double exact_g(const PairKArgs& A, const Query& Q, int64_t j) {
+// exact g = |v_i - v_j| sigma/m(|v_i - v_j|) in FP64 (i, j in key order)
+__device__ __forceinline__ double exact_g(const PairKArgs& A, int64_t s, int64_t j) {
   const Sorted& so = A.so;
-  const int64_t s = Q.s;
   const double ddx = so.vx[s] - so.vx[j], ddy = so.vy[s] - so.vy[j], ddz = so.vz[s] - so.vz[j];
   const double vrel = sqrt((ddx * ddx + ddy * ddy) + ddz * ddz);
   const Halo& H = A.f.halos[so.halo[s]];
-  return vrel * sigma_over_m(Q.kind, H.sigma0, H.w, vrel);
+  return vrel * sigma_over_m(H.sigma_kind, H.sigma0, H.w, vrel);
 }
 
-// Eq. 9: dt_lim,i = 2 C_SIDM / (m_i W(0, h_i) (v sigma/m)_max,i), written by lane 0
-__device__ __forceinline__ void write_limit(const PairKArgs& A, const Query& Q, double vs_max) {
-  if ((threadIdx.x & 31) == 0) {
-    const Sorted& so = A.so;
-    const double den = (so.m[Q.s] * kernel_norm(A.a.kernel, so.h[Q.s])) * vs_max;
-    A.dtlim_user[Q.oi] = vs_max > 0.0 ? (A.a.c_sidm * 2.0) / den : INFINITY;
-  }
+// Eq. 9: dt_lim,i = 2 C_SIDM / (m_i W(0, h_i) (v sigma/m)_max,i)
+__device__ __forceinline__ void write_limit(const PairKArgs& A, int64_t s, double vs_max) {
+  const Sorted& so = A.so;
+  const double den = (so.m[s] * kernel_norm(A.a.kernel, so.h[s])) * vs_max;
+  A.dtlim_user[so.orig[s]] = vs_max > 0.0 ? (A.a.c_sidm * 2.0) / den : INFINITY;
 }
 
 __device__ __forceinline__ void flush_counters(const PairKArgs& A, unsigned long long cand,
@@ -317,7 +303,7 @@ __device__ __forceinline__ void flush_counters(const PairKArgs& A, unsigned long
 }
 
 // Queries with a complete neighbour list (the usual case).
-__global__ void __launch_bounds__(PT, 5) pairs_kernel(PairKArgs A) {
+__global__ void __launch_bounds__(PT, 6) pairs_kernel(PairKArgs A) {
   __shared__ float s_ghi[PW][MAXR * WARP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* ghi_row = s_ghi[warp];
@@ -352,19 +338,23 @@ __global__ void __launch_bounds__(PT, 5) pairs_kernel(PairKArgs A) {
       ghi_row[k] = valid ? gh : -1.0f;
     }
     sum_p += (double)psum;
-    // exact maximum of g: only j whose upper bound reaches the largest lower bound
+    // Eq. 9 maximum: only j whose upper bound of g reaches the largest lower
+    // bound can give it; up to LIM_CAND of them are kept for the exact pass
     mlo = warp_maxf(mlo);
     __syncwarp();
-    double mine = 0.0;
-    if (A.a.split) {
-      mine = (double)mlo;
-    } else {
-      for (int r = 0; r < nr; ++r) {
-        const int k = r * 32 + lane;
-        if (k < cnt && ghi_row[k] >= mlo) mine = fmax(mine, exact_g(A, Q, row[k]));
-      }
+    int nc = 0;
+    for (int r = 0; r < nr; ++r) {
+      const int k = r * 32 + lane;
+      const bool c = k < cnt && ghi_row[k] >= mlo;
+      const uint32_t m = __ballot_sync(0xffffffffu, c);
+      const int at = nc + __popc(m & ((1u << lane) - 1u));
+      if (c && at < LIM_CAND) A.a.lim_cand[qi * LIM_CAND + at] = row[k];
+      nc += __popc(m);
     }
-    write_limit(A, Q, warp_maxd(mine));
+    if (lane == 0) {
+      A.a.lim_cnt[qi] = nc <= LIM_CAND ? nc : -1;
+      A.a.lim_g[qi] = mlo;
+    }
     __syncwarp();
   }
   flush_counters(A, cand, pge1, sum_p, status);
@@ -412,17 +402,117 @@ __global__ void __launch_bounds__(PT) pairs_walk_kernel(PairKArgs A) {
       }
       float gl, gh;
       visit(A, Q, j, in, &gl, &gh, &psum, &cand, &pge1, &status);
-      if (in) mine = fmax(mine, A.a.split ? (double)gl : exact_g(A, Q, j));
+      if (in) mine = fmax(mine, A.a.split ? (double)gl : exact_g(A, s, j));
     };
     const bool ok = A.a.box > 0.0
         ? traverse<true>(A.f, H, so.f + hs, Q.fi, rad * rad, boxf, stack, leaf)
         : traverse<false>(A.f, H, so.f + hs, Q.fi, rad * rad, boxf, stack, leaf);
     if (!ok) status |= ST_ERR_STACK;
     sum_p += (double)psum;
-    write_limit(A, Q, warp_maxd(mine));
+    mine = warp_maxd(mine);
+    if (lane == 0) write_limit(A, s, mine);
     __syncwarp();
   }
   flush_counters(A, cand, pge1, sum_p, status);
+}
+
+// The draws the warp pass could not decide in FP32, one thread each: the
+// exact FP64 P_pair in the oracle's operation order (with P(j|i) when j
+// sees i), the draw and, if accepted, the pair record.
+__global__ void __launch_bounds__(XT) pairs_exact_kernel(PairKArgs A) {
+  const Sorted& so = A.so;
+  const PairArgs& P = A.a;
+  const int kern = P.kernel;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long nd_all = A.st->n_deferred;
+  const int64_t nd = (int64_t)(nd_all < (unsigned long long)P.pair_cap ? nd_all : P.pair_cap);
+  const double box = P.box, half = 0.5 * P.box;
+  unsigned long long pge1 = 0;
+  double sum_p = 0.0;
+  uint32_t status = 0;
+  const int64_t stride = (int64_t)gridDim.x * XT;
+  for (int64_t base = blockIdx.x * (int64_t)XT + (threadIdx.x & ~31); base < nd; base += stride) {
+    const int64_t d = base + lane;
+    bool acc = false;
+    PairRec rec;
+    if (d < nd) {
+      const int2 r = P.deferred[d];
+      const int64_t s = r.x, j = r.y & 0x7fffffff;
+      const bool sees = r.y < 0;
+      const uint32_t idi = so.id[s], idj = so.id[j];
+      const Halo& H = A.f.halos[so.halo[s]];
+      const bool i_is_a = idi < idj;
+      const uint32_t a = i_is_a ? idi : idj, b = i_is_a ? idj : idi;
+      const U4 w = philox10((uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, 0u, a, b);
+      const double r2 = sep2(so.x[s], so.y[s], so.z[s], so.x[j], so.y[j], so.z[j], box, half);
+      const double ddx = so.vx[s] - so.vx[j], ddy = so.vy[s] - so.vy[j],
+                   ddz = so.vz[s] - so.vz[j];
+      const double vrel = sqrt((ddx * ddx + ddy * ddy) + ddz * ddz);
+      const double sg = sigma_over_m(H.sigma_kind, H.sigma0, H.w, vrel);
+      const double hi = so.h[s];
+      const double qq = sqrt(r2) / hi;
+      const double p_i = ((((0.5 * so.m[j]) * sg) * vrel) * (kernel_norm(kern, hi) *
+                                                            kernel_shape(kern, qq))) * so.dt[s];
+      double p_j = 0.0;
+      if (sees) {
+        const double hj = so.h[j];
+        const double qj = sqrt(r2) / hj;
+        p_j = ((((0.5 * so.m[s]) * sg) * vrel) * (kernel_norm(kern, hj) *
+                                                   kernel_shape(kern, qj))) * so.dt[j];
+      }
+      const double pp = i_is_a ? (p_i + p_j) : (p_j + p_i);
+      if (pp >= 1.0) ++pge1;
+      sum_p += pp;
+      if (unit53(w.x, w.y) < pp) {
+        acc = true;
+        rec.ord = ((unsigned long long)w.z << 32) | (unsigned long long)w.w;
+        rec.a = a;
+        rec.b = b;
+        const int32_t oi = so.orig[s], oj = so.orig[j];
+        rec.ia = i_is_a ? oi : oj;
+        rec.ib = i_is_a ? oj : oi;
+      }
+    }
+    const uint32_t m = __ballot_sync(0xffffffffu, acc);
+    if (m) {
+      unsigned long long at0 = 0;
+      const int leader = __ffs(m) - 1;
+      if (lane == leader) at0 = atomicAdd(&A.st->n_acc, (unsigned long long)__popc(m));
+      at0 = __shfl_sync(0xffffffffu, at0, leader);
+      if (acc) {
+        const unsigned long long at = at0 + __popc(m & ((1u << lane) - 1u));
+        if (at < (unsigned long long)P.pair_cap) A.pairs[at] = rec;
+        else status |= ST_ERR_PAIR_OVERFLOW;
+      }
+    }
+  }
+  flush_counters(A, 0ull, pge1, sum_p, status);
+}
+
+// Eq. 9 limits of the queries with complete neighbour lists, one thread each:
+// the exact maximum of v sigma/m over the kept candidates (over the whole
+// list when there were more), or the FP32 maximum in the split form.
+__global__ void __launch_bounds__(XT) limits_kernel(PairKArgs A) {
+  const int64_t n_act = (int64_t)A.st->n_active;
+  const int64_t stride = (int64_t)gridDim.x * XT;
+  for (int64_t qi = blockIdx.x * (int64_t)XT + threadIdx.x; qi < n_act; qi += stride) {
+    const int cnt = A.nb_count[qi];
+    if (cnt < 0) continue;  // the tree-walk kernel wrote this limit
+    const int64_t s = A.act_list[qi];
+    double vs = 0.0;
+    if (A.a.split) {
+      vs = (double)A.a.lim_g[qi];
+    } else {
+      const int nc = A.a.lim_cnt[qi];
+      if (nc >= 0) {
+        for (int r = 0; r < nc; ++r) vs = fmax(vs, exact_g(A, s, A.a.lim_cand[qi * LIM_CAND + r]));
+      } else {
+        const int32_t* row = A.nb_list + qi * (int64_t)A.nb_stride;
+        for (int k = 0; k < cnt; ++k) vs = fmax(vs, exact_g(A, s, row[k]));
+      }
+    }
+    write_limit(A, s, vs);
+  }
 }
 
 }  // namespace
@@ -438,7 +528,11 @@ int launch_pairs(const Sorted& so, const Forest& f, int64_t n, const int32_t* ac
   if (blocks > need) blocks = need;
   pairs_kernel<<<(unsigned)blocks, PT, 0, s>>>(k);
   pairs_walk_kernel<<<(unsigned)sms, PT, 0, s>>>(k);
-  return 2;
+  pairs_exact_kernel<<<(unsigned)(sms * 4), XT, 0, s>>>(k);
+  int64_t lb = (n + XT - 1) / XT;
+  if (lb > (int64_t)sms * 8) lb = (int64_t)sms * 8;
+  limits_kernel<<<(unsigned)lb, XT, 0, s>>>(k);
+  return 4;
 }
 
 }  // namespace sidm

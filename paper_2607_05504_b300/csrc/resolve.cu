@@ -171,6 +171,12 @@ __global__ void __launch_bounds__(RT) resolve_kernel(const PairRec* __restrict__
 constexpr int GT = 256;
 constexpr int DATAFLOW_MAX_PASSES = 1 << 22;
 
+// A pair or deferred-draw buffer that overflowed makes the step invalid:
+// then nothing is applied.
+__device__ __forceinline__ bool step_overflowed(const DevStats* st, int64_t cap) {
+  return st->n_acc > (unsigned long long)cap || st->n_deferred > (unsigned long long)cap;
+}
+
 __device__ __forceinline__ int ld_acquire(const int32_t* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -239,7 +245,7 @@ __device__ __forceinline__ void kick_l2(const PairRec& r, double* vel, double ma
 __global__ void __launch_bounds__(GT) count_kernel(const PairRec* __restrict__ pairs, int64_t cap,
                                                    int32_t* mult, const DevStats* st) {
   const unsigned long long nall = st->n_acc;
-  if (nall > (unsigned long long)cap) return;
+  if (step_overflowed(st, cap)) return;
   for (int64_t p = blockIdx.x * (int64_t)GT + threadIdx.x; p < (int64_t)nall;
        p += (int64_t)gridDim.x * GT) {
     atomicAdd(&mult[pairs[p].ia], 1);
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ p
   const unsigned long long nall = st->n_acc;
   const int lane = threadIdx.x & 31;
   int mm = 0;
-  if (nall <= (unsigned long long)cap) {
+  if (!step_overflowed(st, cap)) {
     const int64_t na = (int64_t)nall;
     const int64_t stride = (int64_t)gridDim.x * GT;
     for (int64_t base = blockIdx.x * (int64_t)GT + (threadIdx.x & ~31); base < na; base += stride) {
@@ -312,7 +318,7 @@ __global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ p
 
 __global__ void __launch_bounds__(GT) fill_kernel(const PairRec* __restrict__ pairs, int64_t cap,
                                                   ResolveBuffers b, const DevStats* st) {
-  if (st->n_acc > (unsigned long long)cap) return;
+  if (step_overflowed(st, cap)) return;
   const int64_t np = (int64_t)st->n_pending;
   for (int64_t k = blockIdx.x * (int64_t)GT + threadIdx.x; k < np; k += (int64_t)gridDim.x * GT) {
     const int32_t p = b.pending[k];
@@ -330,7 +336,7 @@ __device__ __forceinline__ bool key_less_id(const PairRec* pairs, int32_t x, int
 __global__ void __launch_bounds__(GT) segsort_kernel(const PairRec* __restrict__ pairs,
                                                      int64_t cap, ResolveBuffers b,
                                                      const DevStats* st) {
-  if (st->n_acc > (unsigned long long)cap) return;
+  if (step_overflowed(st, cap)) return;
   const int64_t nt = (int64_t)st->n_touched;
   for (int64_t k = blockIdx.x * (int64_t)GT + threadIdx.x; k < nt; k += (int64_t)gridDim.x * GT) {
     const int32_t e = b.touched[k];
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
   __shared__ int s_passes;
   if (threadIdx.x == 0) { s_dirfail = 0; s_passes = 0; }
   __syncthreads();
-  if (st->n_acc <= (unsigned long long)cap) {
+  if (!step_overflowed(st, cap)) {
     const int64_t np = (int64_t)st->n_pending;
     const int64_t gsize = (int64_t)gridDim.x * GT;
     const int64_t t0 = blockIdx.x * (int64_t)GT + threadIdx.x;
@@ -442,7 +448,7 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
 __global__ void __launch_bounds__(GT) reset_kernel(const PairRec* __restrict__ pairs, int64_t cap,
                                                    ResolveBuffers b, const DevStats* st) {
   const unsigned long long nall = st->n_acc;
-  if (nall > (unsigned long long)cap) return;
+  if (step_overflowed(st, cap)) return;
   const int64_t stride = (int64_t)gridDim.x * GT;
   const int64_t t0 = blockIdx.x * (int64_t)GT + threadIdx.x;
   for (int64_t p = t0; p < (int64_t)nall; p += stride) {

@@ -68,6 +68,7 @@ struct DevStats {
   unsigned long long n_pending;   // accepted pairs that share a particle with another
   unsigned long long n_seg;       // segment slots handed out to particles of pending pairs
   unsigned long long n_touched;   // particles of pending pairs
+  unsigned long long n_deferred;  // draws left to the exact FP64 pass
   double sum_p;
   unsigned int status;
   unsigned int pad;
@@ -220,12 +221,18 @@ int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* a
                   int sms, cudaStream_t s);
 
 // pairs.cu
+constexpr int LIM_CAND = 4;   // Eq. 9 maximum: candidates kept per query
 struct PairArgs {
   int kernel;
   int split;          // 1: FP32 decisions, FP64 re-test only when |P - u| < 1e-5
   double c_sidm;
   double box;
   int64_t pair_cap;
+  // scratch of the FP64 passes that follow the warp pass
+  int2* deferred;     // [pair_cap] draws to decide exactly: (i, j | sees << 31), key order
+  int32_t* lim_cand;  // [n][LIM_CAND] neighbours that may give the Eq. 9 maximum
+  int32_t* lim_cnt;   // [n] their number, -1: more than LIM_CAND (scan the whole list)
+  float* lim_g;       // [n] largest FP32 lower bound of v sigma/m (split form: the maximum)
 };
 int launch_pairs(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
                  const int32_t* nb_list, const int32_t* nb_count, int nb_stride,
