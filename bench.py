@@ -4,7 +4,7 @@ Workload: isolated Hernquist halo, N = 2^20, N_ngb = 64 +- 5, constant
 sigma/m = 1, open boundaries, FP64, power-of-two timestep bins with ~10 % of
 the particles active per finest step (step s of a 100-step cycle uses the
 active set of finest step s).  One bench step = one complete scattering step
-(keys, sort, structure, h_SI search, pairs + draws + Eq. 9, kicks) on the
+(keys, sort, structure, h_SI search, pairs + draws + Eq. 18, kicks) on the
 step's active set.  Metric: particle updates (active particles) per second.
 
     python bench.py [--steps K] [--warmup W] [--impl ours|reference]
@@ -35,13 +35,13 @@ CYCLE = 100
 
 # Algorithmic HBM bytes of each phase, per particle (n) and per active
 # particle (a): the data the phase must read and write once (FP64 state,
-# 4-byte ids/indices, 1-byte flags).  Derivation in the design doc.
+# 4-byte ids/indices, 1-byte flags).
 PHASE_BYTES = {
     "keys": (56.0, 0.0),        # bbox read 24, keys read 24, key+index write 8
     "sort": (96.0, 0.0),        # 4 passes x (hist read 4 + scatter read 8 + write 8) + index
     "structure": (190.0, 0.0),  # gather 66 read, key-order state 97 written, leaf boxes ~27
     "search": (16.0, 56.0),     # FP32 positions once; own state 40 read, h 16 written
-    "pairs": (0.0, 92.0),       # own state 84 read, Eq. 9 limit 8 written
+    "pairs": (0.0, 92.0),       # own state 84 read, Eq. 18 limit 8 written
     "resolve": (0.0, 0.0),      # per accepted pair, reported separately
 }
 

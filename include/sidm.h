@@ -8,14 +8,14 @@
  *   - for every active particle i, the search radius h_i that encloses
  *     N_ngb +- tol other particles, active or inactive (Sec. 4.2, Sec. 4.5);
  *   - the pair probability P(i|j) = 1/2 m_j (sigma/m)(v_ij) |v_i - v_j|
- *     W(|x_j - x_i|, h_i) dt_i (Eqs. 2-4, cubic spline or top-hat W, Sec. 4.2;
+ *     W(|x_j - x_i|, h_i) dt_i (Eqs. 10, 11, 14, cubic spline or top-hat W, Sec. 4.2;
  *     constant or Yukawa-like sigma/m, Sec. 5.2);
  *   - one Philox-4x32-10 draw per unordered candidate pair against
  *     P_pair = P(i|j)[i active, j in N(i)] + P(j|i)[j active, i in N(j)];
  *   - elastic isotropic centre-of-momentum kicks (Sec. 4.1), several per
  *     particle per step, applied in ascending (ord, min id, max id) order so
  *     that each kick sees the velocities left by the earlier ones (Sec. 4.4);
- *   - the per-pair timestep limit of Eq. 9.
+ *   - the per-pair timestep limit of Eq. 18.
  *
  * Conventions shared by every entry point
  *   - Return value: SIDM_OK (0), a positive warning (the call took effect),
@@ -55,7 +55,7 @@ typedef struct sidm_ctx sidm_ctx;
 typedef enum {
   SIDM_OK = 0,
   SIDM_WARN_H_NOT_CONVERGED = 1, /* a bisection hit its evaluation cap (the last h is kept) */
-  SIDM_WARN_P_GE_1 = 2,          /* some P_pair >= 1 (accepted; dt too large for Eq. 9)    */
+  SIDM_WARN_P_GE_1 = 2,          /* some P_pair >= 1 (accepted; dt too large for Eq. 18)    */
   SIDM_WARN_DIRECTION = 4,       /* a direction draw exhausted its 64 tries (e = +z used)   */
   SIDM_ERR_INVALID_ARG = -1,
   SIDM_ERR_OOM = -2,
@@ -80,7 +80,7 @@ enum { SIDM_FP64_PLAIN = 0, SIDM_FP32_SPLIT = 1 };
 typedef struct {
   int n_ngb;            /* target neighbour number N_ngb (paper: 32)                     */
   int ngb_tol;          /* accepted band N_ngb +- ngb_tol (paper: 5)                      */
-  double c_sidm;        /* C_SIDM of Eq. 9 (paper: 0.1)                                   */
+  double c_sidm;        /* C_SIDM of Eq. 18 (paper: 0.1)                                   */
   double box;           /* > 0: periodic cube [0, box)^3; 0: open boundaries              */
   int kernel;           /* SIDM_KERNEL_CUBIC (fiducial) or SIDM_KERNEL_TOPHAT              */
   int precision;        /* SIDM_FP64_PLAIN or SIDM_FP32_SPLIT                              */
@@ -185,7 +185,7 @@ SIDM_API int sidm_sync(sidm_ctx* ctx);
  * last h of every particle (0 for particles never active). */
 SIDM_API int sidm_get_particles(sidm_ctx* ctx, double* vel_out, double* h_out, int ptr_kind);
 
-/* Copies the Eq. 9 limit of every particle from its last active step
+/* Copies the Eq. 18 limit of every particle from its last active step
  * (+inf before its first active step, and when no neighbour moves
  * relative to it). */
 SIDM_API int sidm_timestep_limits(sidm_ctx* ctx, double* dt_limit_out, int ptr_kind);
@@ -205,7 +205,7 @@ SIDM_API int sidm_set_step(sidm_ctx* ctx, uint64_t step);
  * last step of a context created with profile = 1; waits for the stream.
  * ms[k] for k < min(n, SIDM_N_PHASES): 0 keys (bounding box, start radius,
  * spatial keys), 1 sort, 2 structure (key-order copy, active list, box
- * tree), 3 search (h_SI), 4 pairs (probabilities, draws, Eq. 9),
+ * tree), 3 search (h_SI), 4 pairs (probabilities, draws, Eq. 18),
  * 5 resolve (kicks).  Returns SIDM_ERR_INVALID_ARG without profiling. */
 #define SIDM_N_PHASES 6
 SIDM_API int sidm_phase_times(sidm_ctx* ctx, float* ms, int n);

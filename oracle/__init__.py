@@ -135,7 +135,7 @@ def sigma_over_m(vrel: float, kind=0, sigma0=1.0, w=1.0) -> float:
 
 
 def directed_probability(m_j, v_i, v_j, r2, h_i, dt_i, kernel=0, kind=0, sigma0=1.0, w=1.0):
-    """P(i|j) of Eq. 3 with the rate of Eq. 2 and g_ij of Eq. 4."""
+    """P(i|j) of Eq. 11 with the rate of Eq. 10 and g_ij of Eq. 14."""
     s = make_sigma(kind, sigma0, w)
     vi = np.ascontiguousarray(v_i, np.float64)
     vj = np.ascontiguousarray(v_j, np.float64)

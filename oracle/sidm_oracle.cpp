@@ -27,13 +27,13 @@
 //   sigma_over_m           constant sigma/m, or the Yukawa-like
 //                          sigma0/m / (1 + (v/w)^2)^2 (Sec. 5.2).
 //   directed_probability   P(i|j) = 1/2 m_j (sigma/m) |v_i - v_j| W(r_ij, h_i) dt_i
-//                          (Eqs. 2, 3 with the one-sided estimator, Eq. 4).
+//                          (Eqs. 10, 11 with the one-sided estimator, Eq. 14).
 //   isotropic_direction    unit vector uniform on the sphere (Sec. 4.1),
 //                          by Marsaglia's (1972) rejection method.
 //   elastic_kick           centre-of-momentum elastic kick, eps = 1 (Sec. 4.1).
 //   step                   one scattering step for the active set, pairs drawn
 //                          once, applied in a canonical order, and the per-pair
-//                          timestep criterion (Eq. 9).
+//                          timestep criterion (Eq. 18).
 //
 // Readings of points the paper leaves open (each is one deterministic choice):
 //   * the neighbour count excludes the particle itself and uses r < h;
@@ -55,7 +55,7 @@
 //     stream 0 decides the pair, streams 1.. feed the direction rejection loop
 //     (at most 64 tries, then e = (0,0,1) and a failure is counted);
 //   * P_pair >= 1 is accepted (always) and counted;
-//   * (v sigma/m)_max of Eq. 9 is taken over N(i) with start-of-step velocities.
+//   * (v sigma/m)_max of Eq. 18 is taken over N(i) with start-of-step velocities.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -71,7 +71,7 @@ extern "C" {
 typedef struct {
   int n_ngb;        // target neighbour number N_ngb
   int ngb_tol;      // accepted band N_ngb +- ngb_tol
-  double c_sidm;    // C_SIDM of Eq. 9
+  double c_sidm;    // C_SIDM of Eq. 18
   double box;       // > 0: periodic cube side; 0: open boundaries
   int kernel;       // 0 cubic spline, 1 top-hat
   double fixed_h;   // > 0: every active particle uses this h (no bisection)
@@ -601,7 +601,7 @@ int orc_step(const orc_config* cfg, int64_t n, const double* pos, double* vel,
     elastic_kick(mass[pr.i], mass[pr.j], vel + 3 * pr.i, vel + 3 * pr.j, e);
   }
 
-  // 4. outputs for the active particles: h and the Eq. 9 limit
+  // 4. outputs for the active particles: h and the Eq. 18 limit
   for (int64_t i : act) {
     if (h_out) h_out[i] = h[i];
     if (dtlim_out) {

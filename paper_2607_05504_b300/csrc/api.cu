@@ -7,7 +7,7 @@
 //   transform per halo -> halo-prefixed spatial keys -> radix sort ->
 //   key-order copy of the state + active list -> 32-ary box tree per halo ->
 //   h_SI per active particle -> candidate pairs, probabilities and draws,
-//   Eq. 9 limits -> canonical application of the accepted kicks.
+//   Eq. 18 limits -> canonical application of the accepted kicks.
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
@@ -46,7 +46,7 @@ struct sidm_ctx {
   int32_t* nb_list = nullptr;   // [n][nb_stride] neighbour lists of the active particles
   int32_t* nb_count = nullptr;  // [n] list length, or -1
   int2* deferred = nullptr;     // [pair_cap] draws for the exact FP64 pass
-  int32_t* lim_cand = nullptr;  // [n][LIM_CAND] Eq. 9 candidates of each query
+  int32_t* lim_cand = nullptr;  // [n][LIM_CAND] Eq. 18 candidates of each query
   int32_t* lim_cnt = nullptr;   // [n]
   float* lim_g = nullptr;       // [n]
   int nb_stride = 0;
@@ -675,7 +675,7 @@ const char* sidm_error_string(int status) {
   switch (status) {
     case SIDM_OK: return "ok";
     case SIDM_WARN_H_NOT_CONVERGED: return "warning: h bisection hit its evaluation cap";
-    case SIDM_WARN_P_GE_1: return "warning: a pair probability reached 1 (timestep above the Eq. 9 limit)";
+    case SIDM_WARN_P_GE_1: return "warning: a pair probability reached 1 (timestep above the Eq. 18 limit)";
     case SIDM_WARN_DIRECTION: return "warning: a direction draw exhausted its tries";
     case SIDM_ERR_INVALID_ARG: return "invalid argument";
     case SIDM_ERR_OOM: return "out of device memory";

@@ -3,12 +3,12 @@
 // One warp per active particle i, one lane per neighbour j in N(i) (from the
 // neighbour list of the search kernel; a direct tree walk with radius h_i if
 // the list was not complete).  For each j:
-//   * (v sigma/m)(v_ij) enters the maximum of Eq. 9 (start-of-step
+//   * (v sigma/m)(v_ij) enters the maximum of Eq. 18 (start-of-step
 //     velocities);
 //   * i owns the unordered pair unless j is active, sees i (r^2 < h_j^2) and
 //     has the smaller id -- every pair is evaluated exactly once;
 //   * the owner forms P_pair = P(i|j) + [j active, i in N(j)] P(j|i) with
-//     P(i|j) = 1/2 m_j (sigma/m) |v_i - v_j| W(r, h_i) dt_i (Eqs. 2-4), and
+//     P(i|j) = 1/2 m_j (sigma/m) |v_i - v_j| W(r, h_i) dt_i (Eqs. 10, 11, 14), and
 //     draws u from Philox-4x32-10 with counter (step, 0, min id, max id);
 //     u < P_pair accepts; words 2, 3 form the order key.
 //
@@ -18,7 +18,7 @@
 // below by its top 24 bits.  Only when that lower bound of u lies below the
 // bound of P_pair (about the acceptance probability) is P_pair evaluated in
 // FP64 in the oracle's operation order, and the draw decided on that value.
-// The FP64 state of the query is read only on these rare paths.  The owner test r^2 < h_j^2 and the maximum of Eq. 9 likewise
+// The FP64 state of the query is read only on these rare paths.  The owner test r^2 < h_j^2 and the maximum of Eq. 18 likewise
 // use FP32 intervals and fall back to FP64 only where an interval straddles
 // the decision.  All results equal those of a pure FP64 evaluation.
 #include "traverse.cuh"
@@ -275,7 +275,7 @@ __device__ __forceinline__ double exact_g(const PairKArgs& A, int64_t s, int64_t
   return vrel * sigma_over_m(H.sigma_kind, H.sigma0, H.w, vrel);
 }
 
-// Eq. 9: dt_lim,i = 2 C_SIDM / (m_i W(0, h_i) (v sigma/m)_max,i)
+// Eq. 18: dt_lim,i = 2 C_SIDM / (m_i W(0, h_i) (v sigma/m)_max,i)
 __device__ __forceinline__ void write_limit(const PairKArgs& A, int64_t s, double vs_max) {
   const Sorted& so = A.so;
   const double den = (so.m[s] * kernel_norm(A.a.kernel, so.h[s])) * vs_max;
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(PT, 6) pairs_kernel(PairKArgs A) {
       ghi_row[k] = valid ? gh : -1.0f;
     }
     sum_p += (double)psum;
-    // Eq. 9 maximum: only j whose upper bound of g reaches the largest lower
+    // Eq. 18 maximum: only j whose upper bound of g reaches the largest lower
     // bound can give it; up to LIM_CAND of them are kept for the exact pass
     mlo = warp_maxf(mlo);
     __syncwarp();
@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(XT) pairs_exact_kernel(PairKArgs A) {
   flush_counters(A, 0ull, pge1, sum_p, status);
 }
 
-// Eq. 9 limits of the queries with complete neighbour lists, one thread each:
+// Eq. 18 limits of the queries with complete neighbour lists, one thread each:
 // the exact maximum of v sigma/m over the kept candidates (over the whole
 // list when there were more), or the FP32 maximum in the split form.
 __global__ void __launch_bounds__(XT) limits_kernel(PairKArgs A) {

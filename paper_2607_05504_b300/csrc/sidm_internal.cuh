@@ -221,7 +221,7 @@ int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* a
                   int sms, cudaStream_t s);
 
 // pairs.cu
-constexpr int LIM_CAND = 4;   // Eq. 9 maximum: candidates kept per query
+constexpr int LIM_CAND = 4;   // Eq. 18 maximum: candidates kept per query
 struct PairArgs {
   int kernel;
   int split;          // 1: FP32 decisions, FP64 re-test only when |P - u| < 1e-5
@@ -230,7 +230,7 @@ struct PairArgs {
   int64_t pair_cap;
   // scratch of the FP64 passes that follow the warp pass
   int2* deferred;     // [pair_cap] draws to decide exactly: (i, j | sees << 31), key order
-  int32_t* lim_cand;  // [n][LIM_CAND] neighbours that may give the Eq. 9 maximum
+  int32_t* lim_cand;  // [n][LIM_CAND] neighbours that may give the Eq. 18 maximum
   int32_t* lim_cnt;   // [n] their number, -1: more than LIM_CAND (scan the whole list)
   float* lim_g;       // [n] largest FP32 lower bound of v sigma/m (split form: the maximum)
 };

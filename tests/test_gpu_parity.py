@@ -1,7 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
 The FP64 plain form must reproduce the oracle exactly: the same h for every
-active particle, the same Eq. 9 limits, the same accepted pairs (ids and
+active particle, the same Eq. 18 limits, the same accepted pairs (ids and
 order keys) and the same velocities.  The bound stated for velocities is
 1e-12 relative; the path is built to be bit-identical, and these tests
 assert bit equality (a relative-difference report is printed on failure).

@@ -220,7 +220,7 @@ def _pair_speed_sum(va, vb, weight_fn=None):
 def test_fixed_h_expectation_all_active(orc, kind):
     """With a fixed h < L/2 and uniform positions in a periodic box the mean
     kernel weight is 1/V, so summed over unordered pairs
-    E[P_pair | v] = m s(v_ij) v_ij dt / V (two directed halves, Eqs. 2-4)."""
+    E[P_pair | v] = m s(v_ij) v_ij dt / V (two directed halves, Eqs. 10, 11, 14)."""
     n, H, dt, s0, w = 1200, 0.15, 0.02, 1.7, 1.3
     rng = np.random.default_rng(21)
     vel = rng.normal(size=(n, 3))
@@ -244,7 +244,7 @@ def test_fixed_h_expectation_all_active(orc, kind):
 def test_fixed_h_expectation_beam_on_inactive_targets(orc):
     """Only the beam is active: each beam-target pair is drawn with the
     beam's half only, P = 1/2 m_target s v dt_beam W(r, h_beam)
-    (Eqs. 2-4), so E = sum_b sum_t 1/2 m_t s v_bt dt_b / V.  Unequal masses
+    (Eqs. 10, 11, 14), so E = sum_b sum_t 1/2 m_t s v_bt dt_b / V.  Unequal masses
     and bins pin m_j (not m_i) and dt_i (not dt_j)."""
     nb, nt, H, s0 = 500, 700, 0.18, 2.0
     dt_max = 0.05
@@ -366,7 +366,7 @@ def test_permutation_invariance(orc):
 
 
 def test_timestep_limit_bounds_pair_probability(orc):
-    """Eq. 9: at dt_i equal to the limit every directed probability is at
+    """Eq. 18: at dt_i equal to the limit every directed probability is at
     most C_SIDM, and in a uniform box dt_lim rho (v sigma/m)_max is close to
     3 N_ngb C_SIDM / 16 (Sec. 4.4)."""
     n, C = 5000, 0.1
