@@ -71,10 +71,11 @@ enum { SIDM_SIGMA_CONST = 0, SIDM_SIGMA_YUKAWA = 1 };
 /* SIDM_FP64_PLAIN: every decision and value equals an FP64 evaluation in a
  * fixed operation order (FP32 is used only where it is provably decisive).
  * SIDM_FP32_SPLIT: separations, neighbour counts, kernel weights and
- * probabilities in FP32; FP64 kicks and accumulators; a draw is re-tested
- * in FP64 only when |P - u| < 1e-5.  Its accepted pairs may differ from the
- * FP64 form in rare near-boundary cases; energy and momentum stay
- * conserved to FP64 round-off. */
+ * probabilities in FP32; FP64 kicks and accumulators; a draw is decided in
+ * FP32 unless u (to its top 24 bits) lies within 1e-5 of the FP32 P, and
+ * then exactly in FP64.  Its accepted pairs may differ from the FP64 form in
+ * rare near-boundary cases; energy and momentum stay conserved to FP64
+ * round-off. */
 enum { SIDM_FP64_PLAIN = 0, SIDM_FP32_SPLIT = 1 };
 
 typedef struct {
@@ -90,6 +91,10 @@ typedef struct {
   void* stream;         /* cudaStream_t for all work; NULL: a stream owned by the context */
   int device;           /* CUDA device ordinal (-1: the current device)                   */
   int profile;          /* 1: time the phases of every step with CUDA events              */
+  int use_graph;        /* 1: capture the kernels of a step into a CUDA graph on first use
+                           and replay it while the particle count, the halo layout and the
+                           launch shapes stay the same (results are unchanged); 0: direct
+                           launches.  Ignored while `profile` is set.                      */
 } sidm_config;
 
 /* Fills `cfg` with the paper's fiducial values (N_ngb 32 +- 5, C_SIDM 0.1,
@@ -212,6 +217,40 @@ SIDM_API int sidm_phase_times(sidm_ctx* ctx, float* ms, int n);
 
 /* Kernels launched by the context so far (all of them are this library's). */
 SIDM_API int64_t sidm_kernel_launches(const sidm_ctx* ctx);
+
+/* ---- launch shapes (no counterpart in the paper) ------------------------
+ * How the step's kernels are launched.  Every choice gives bit-identical
+ * results; only the time changes.  Zero fields take the defaults. */
+typedef struct {
+  int search_window;        /* key-order window that bounds each search radius:
+                               128, 256 (default) or 512 particles                   */
+  int search_chunk;         /* queries a search warp claims at a time, 1..64 (4)      */
+  int search_blocks_per_sm; /* search blocks of 4 warps launched per SM, 1..8 (8)     */
+  int pairs_chunk;          /* queries a pair warp claims at a time, 1..64 (4)        */
+  int pairs_blocks_per_sm;  /* pair blocks of 4 warps per SM, 1..6 (6)                */
+} sidm_tuning;
+
+/* Sets / reads the launch shapes of the context.  SIDM_ERR_INVALID_ARG for a
+ * value out of range (the context keeps its shapes).  Setting them drops a
+ * captured step graph (it is captured again on the next step). */
+SIDM_API int sidm_set_tuning(sidm_ctx* ctx, const sidm_tuning* t);
+SIDM_API int sidm_get_tuning(const sidm_ctx* ctx, sidm_tuning* t);
+
+/* Times candidate launch shapes on the next step (active mask, bins and one
+ * sidm_halo_params per halo as for sidm_step_haloes; a single-halo context
+ * takes one) and keeps the fastest.  Each candidate runs `reps` (1..16)
+ * times from the same state; afterwards the velocities, h, timestep limits
+ * and the step counter are restored, so the call leaves the simulation
+ * where it was.  Coordinate search: window, then search chunk and blocks,
+ * then pair chunk and blocks.  Writes the chosen shapes to `best` (nullable).
+ * Synchronises the stream; allocates one temporary copy of the state. */
+SIDM_API int sidm_autotune(sidm_ctx* ctx, const uint8_t* active_mask, const int8_t* dt_bins,
+                           const sidm_halo_params* params, int reps, sidm_tuning* best);
+
+/* 1: the step runs as a captured CUDA graph; 0: direct launches (use_graph
+ * off, profiling, or nothing stepped yet); -1: the driver refused the
+ * capture and the context launches directly. */
+SIDM_API int sidm_graph_state(const sidm_ctx* ctx);
 
 /* ---- Kick application without any device allocation ----------------------
  * The paper has no counterpart to this entry point: it exists for callers

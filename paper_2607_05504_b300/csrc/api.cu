@@ -69,6 +69,13 @@ struct sidm_ctx {
   double* h_cons = nullptr;
   unsigned* h_latched = nullptr;
   std::vector<void*> allocs;
+  // launch shapes and the captured step
+  LaunchTuning tune{};
+  uint64_t layout_version = 1;  // bumped whenever buffers, haloes or tuning change
+  cudaGraphExec_t graph_exec = nullptr;
+  uint64_t graph_version = 0;   // layout the graph was captured for
+  int64_t graph_launches = 0;   // kernels in the graph
+  int graph_state = 0;          // 0 off, 1 captured, -1 capture refused (direct launches)
   // instrumentation
   int64_t launches = 0;
   cudaEvent_t ev[SIDM_N_PHASES + 1] = {};
@@ -112,7 +119,15 @@ cudaError_t dalloc(sidm_ctx* c, T** p, size_t count) {
   return cudaSuccess;
 }
 
+void drop_graph(sidm_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+  c->graph_version = 0;
+}
+
 void free_buffers(sidm_ctx* c) {
+  drop_graph(c);
+  ++c->layout_version;
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   c->cap = 0;
@@ -239,6 +254,7 @@ int start_exponent(int64_t n, int n_ngb) {
 // Halo layout from segment offsets (host): particle ranges, tree levels and
 // node offsets (level-major), start-radius exponents; fills halo_of.
 int layout_haloes(sidm_ctx* c, int n_halos, const int64_t* off) {
+  ++c->layout_version;
   std::vector<Halo>& H = c->halos;
   H.assign(n_halos, Halo{});
   Forest& f = c->forest;
@@ -343,34 +359,20 @@ void set_step_params(Halo& h, double dt_max, const sidm_sigma_model& s, uint64_t
 }
 
 // The kernels of one step over every halo (the halo table is set).
-int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
-             sidm_step_stats* stats) {
+// The kernels of one step, from the reset of the step counters to the
+// status latch.  They read only device buffers of the context (the ingest
+// copies and the halo table upload come before), so the sequence can be
+// captured once into a CUDA graph and replayed while the particle count,
+// the halo layout, the buffers and the launch shapes stay the same.
+int launch_core(sidm_ctx* c, bool prof, int64_t* launches) {
   const int64_t n = c->n;
   cudaStream_t s = c->stream;
-  if (n > 0) {
-    if (active_mask)
-      CK(cudaMemcpyAsync(c->act, active_mask, n, is_device_ptr(active_mask)
-                                                      ? cudaMemcpyDeviceToDevice
-                                                      : cudaMemcpyHostToDevice, s));
-    else
-      CK(cudaMemsetAsync(c->act, 1, n, s));
-    if (dt_bins)
-      CK(cudaMemcpyAsync(c->bins, dt_bins, n, is_device_ptr(dt_bins) ? cudaMemcpyDeviceToDevice
-                                                                     : cudaMemcpyHostToDevice, s));
-    else
-      CK(cudaMemsetAsync(c->bins, 0, n, s));
-  }
-  const int r0 = upload_haloes(c);
-  if (r0 != SIDM_OK) return r0;
   CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), s));
   CK(cudaMemsetAsync(c->work, 0, 8 * sizeof(int), s));
-  int64_t& L = c->launches;
-  if (stats) L += launch_conserved(c->vel, c->mass, n, c->cons_partial, c->cons, s);
-  const bool prof = c->have_events && n > 0;
+  int64_t L = 0;
   auto mark = [&](int k) {
     if (prof) cudaEventRecord(c->ev[k], s);
   };
-  c->timed_step = prof;
   const int nh = (int)c->halos.size();
   const Forest& F = c->forest;
   if (n > 0) {
@@ -392,7 +394,7 @@ int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
                        c->cfg.fixed_h, c->cfg.kernel, c->cfg.precision == SIDM_FP32_SPLIT,
                        c->h_user,
                        c->nb_list, c->nb_count, c->nb_stride,
-                       c->dstats, c->work, c->sms, s);
+                       c->dstats, c->work, c->sms, c->tune, s);
     mark(4);
     PairArgs pa;
     pa.kernel = c->cfg.kernel;
@@ -405,7 +407,7 @@ int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
     pa.lim_cnt = c->lim_cnt;
     pa.lim_g = c->lim_g;
     L += launch_pairs(c->so, F, n, c->act_list, c->nb_list, c->nb_count, c->nb_stride, pa,
-                      c->pairs, c->dtlim, c->dstats, c->work + 1, c->sms, s);
+                      c->pairs, c->dtlim, c->dstats, c->work + 1, c->sms, c->tune, s);
     mark(5);
     const int nr = launch_resolve(c->pairs, c->pair_cap, c->vel, c->mass, c->halo_of,
                                   c->d_halos, c->rb, c->dstats, c->sms, s);
@@ -415,6 +417,80 @@ int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
   }
   latch_kernel<<<1, 32, 0, s>>>(c->dstats, c->latched);
   L += 1;
+  *launches = L;
+  return SIDM_OK;
+}
+
+// Captures launch_core into a graph; a capture the driver refuses leaves the
+// context on direct launches (graph_state -1).
+void capture_core(sidm_ctx* c) {
+  drop_graph(c);
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    c->graph_state = -1;
+    return;
+  }
+  int64_t k = 0;
+  const int r = launch_core(c, false, &k);
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (r != SIDM_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    c->graph_state = -1;
+    return;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    c->graph_exec = nullptr;
+    cudaGetLastError();
+    c->graph_state = -1;
+    return;
+  }
+  c->graph_version = c->layout_version;
+  c->graph_launches = k;
+  c->graph_state = 1;
+}
+
+int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
+             sidm_step_stats* stats) {
+  const int64_t n = c->n;
+  cudaStream_t s = c->stream;
+  if (n > 0) {
+    if (active_mask)
+      CK(cudaMemcpyAsync(c->act, active_mask, n, is_device_ptr(active_mask)
+                                                      ? cudaMemcpyDeviceToDevice
+                                                      : cudaMemcpyHostToDevice, s));
+    else
+      CK(cudaMemsetAsync(c->act, 1, n, s));
+    if (dt_bins)
+      CK(cudaMemcpyAsync(c->bins, dt_bins, n, is_device_ptr(dt_bins) ? cudaMemcpyDeviceToDevice
+                                                                     : cudaMemcpyHostToDevice, s));
+    else
+      CK(cudaMemsetAsync(c->bins, 0, n, s));
+  }
+  const int r0 = upload_haloes(c);
+  if (r0 != SIDM_OK) return r0;
+  int64_t& L = c->launches;
+  if (stats) L += launch_conserved(c->vel, c->mass, n, c->cons_partial, c->cons, s);
+  const bool prof = c->have_events && n > 0;
+  c->timed_step = prof;
+  bool done = false;
+  if (c->cfg.use_graph && !prof && n > 0 && c->graph_state >= 0) {
+    if (!c->graph_exec || c->graph_version != c->layout_version) capture_core(c);
+    if (c->graph_exec) {
+      CK(cudaGraphLaunch(c->graph_exec, s));
+      L += c->graph_launches;
+      done = true;
+    }
+  }
+  if (!done) {
+    int64_t k = 0;
+    const int r = launch_core(c, prof, &k);
+    L += k;
+    if (r != SIDM_OK) return r;
+  }
   CK(cudaGetLastError());
   c->step += 1;
   if (!stats) return SIDM_OK;
@@ -606,6 +682,170 @@ int sidm_step_haloes(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_b
     set_step_params(c->halos[k], params[k].dt_max, params[k].sigma, params[k].seed,
                     params[k].step);
   return run_step(c, active_mask, dt_bins, stats);
+}
+
+namespace {
+
+bool valid_tuning(const LaunchTuning& t) {
+  return (t.search_window == 128 || t.search_window == 256 || t.search_window == 512) &&
+         t.search_chunk >= 1 && t.search_chunk <= 64 && t.search_blocks_per_sm >= 1 &&
+         t.search_blocks_per_sm <= 8 && t.pairs_chunk >= 1 && t.pairs_chunk <= 64 &&
+         t.pairs_blocks_per_sm >= 1 && t.pairs_blocks_per_sm <= 6;
+}
+
+LaunchTuning from_public(const sidm_tuning& p) {
+  LaunchTuning t;
+  if (p.search_window) t.search_window = p.search_window;
+  if (p.search_chunk) t.search_chunk = p.search_chunk;
+  if (p.search_blocks_per_sm) t.search_blocks_per_sm = p.search_blocks_per_sm;
+  if (p.pairs_chunk) t.pairs_chunk = p.pairs_chunk;
+  if (p.pairs_blocks_per_sm) t.pairs_blocks_per_sm = p.pairs_blocks_per_sm;
+  return t;
+}
+
+void to_public(const LaunchTuning& t, sidm_tuning* p) {
+  p->search_window = t.search_window;
+  p->search_chunk = t.search_chunk;
+  p->search_blocks_per_sm = t.search_blocks_per_sm;
+  p->pairs_chunk = t.pairs_chunk;
+  p->pairs_blocks_per_sm = t.pairs_blocks_per_sm;
+}
+
+// Median time (ms) of `reps` steps, each from the saved state.
+int time_candidate(sidm_ctx* c, const uint8_t* act, const int8_t* bins, int reps,
+                   const double* v0, const double* h0, const double* d0, uint64_t step0,
+                   float* ms) {
+  const int64_t n = c->n;
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  std::vector<float> t;
+  int rc = SIDM_OK;
+  for (int r = 0; r < reps && rc == SIDM_OK; ++r) {
+    if (cudaMemcpyAsync(c->vel, v0, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->h_user, h0, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->dtlim, d0, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess) {
+      rc = SIDM_ERR_CUDA;
+      break;
+    }
+    c->step = step0;
+    cudaEventRecord(a, c->stream);
+    rc = run_step(c, act, bins, nullptr);
+    cudaEventRecord(b, c->stream);
+    if (rc != SIDM_OK) break;
+    const int st = wait_and_collect(c);
+    if (st < 0) rc = st;
+    float x = 0.f;
+    cudaEventElapsedTime(&x, a, b);
+    t.push_back(x);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc != SIDM_OK) return rc;
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return SIDM_OK;
+}
+
+}  // namespace
+
+int sidm_set_tuning(sidm_ctx* c, const sidm_tuning* p) {
+  if (!c || !p) return SIDM_ERR_INVALID_ARG;
+  const LaunchTuning t = from_public(*p);
+  if (!valid_tuning(t)) return SIDM_ERR_INVALID_ARG;
+  c->tune = t;
+  ++c->layout_version;
+  return SIDM_OK;
+}
+
+int sidm_get_tuning(const sidm_ctx* c, sidm_tuning* p) {
+  if (!c || !p) return SIDM_ERR_INVALID_ARG;
+  to_public(c->tune, p);
+  return SIDM_OK;
+}
+
+int sidm_graph_state(const sidm_ctx* c) {
+  if (!c) return SIDM_ERR_INVALID_ARG;
+  if (!c->cfg.use_graph) return 0;
+  return c->graph_state;
+}
+
+int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
+                  const sidm_halo_params* params, int reps, sidm_tuning* best) {
+  if (!c || !params || reps < 1 || reps > 16) return SIDM_ERR_INVALID_ARG;
+  if (!c->loaded) return SIDM_ERR_NOT_READY;
+  for (size_t k = 0; k < c->halos.size(); ++k)
+    if (!(params[k].dt_max > 0.0) || !std::isfinite(params[k].dt_max) ||
+        !valid_sigma(params[k].sigma))
+      return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  const int64_t n = c->n;
+  if (n <= 0) {
+    if (best) to_public(c->tune, best);
+    return SIDM_OK;
+  }
+  for (size_t k = 0; k < c->halos.size(); ++k)
+    set_step_params(c->halos[k], params[k].dt_max, params[k].sigma, params[k].seed,
+                    params[k].step);
+  // the state the candidates start from, and restore at the end
+  double* save = nullptr;
+  CK(cudaMalloc(&save, 5 * n * sizeof(double)));
+  double *v0 = save, *h0 = save + 3 * n, *d0 = save + 4 * n;
+  const uint64_t step0 = c->step;
+  const int use_graph = c->cfg.use_graph;
+  c->cfg.use_graph = 0;  // candidates launch directly
+  int rc = SIDM_OK;
+  if (cudaMemcpyAsync(v0, c->vel, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(h0, c->h_user, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(d0, c->dtlim, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) !=
+          cudaSuccess)
+    rc = SIDM_ERR_CUDA;
+  LaunchTuning cur = c->tune;
+  float cur_ms = 0.f;
+  if (rc == SIDM_OK) rc = time_candidate(c, active_mask, dt_bins, reps, v0, h0, d0, step0, &cur_ms);
+  // coordinate search over the launch shapes
+  const int windows[] = {128, 256, 512};
+  const int chunks[] = {1, 2, 4, 8, 16};
+  const int sblocks[] = {4, 6, 8};
+  const int pblocks[] = {3, 4, 6};
+  auto try_field = [&](int LaunchTuning::*field, const int* vals, int nv) {
+    for (int k = 0; k < nv && rc == SIDM_OK; ++k) {
+      if (cur.*field == vals[k]) continue;
+      LaunchTuning t = cur;
+      t.*field = vals[k];
+      c->tune = t;
+      float ms = 0.f;
+      rc = time_candidate(c, active_mask, dt_bins, reps, v0, h0, d0, step0, &ms);
+      if (rc == SIDM_OK && ms < cur_ms) {
+        cur = t;
+        cur_ms = ms;
+      }
+    }
+  };
+  try_field(&LaunchTuning::search_window, windows, 3);
+  try_field(&LaunchTuning::search_chunk, chunks, 5);
+  try_field(&LaunchTuning::search_blocks_per_sm, sblocks, 3);
+  try_field(&LaunchTuning::pairs_chunk, chunks, 5);
+  try_field(&LaunchTuning::pairs_blocks_per_sm, pblocks, 3);
+  // leave the simulation where it was
+  c->tune = cur;
+  ++c->layout_version;
+  c->cfg.use_graph = use_graph;
+  cudaMemcpyAsync(c->vel, v0, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(c->h_user, h0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(c->dtlim, d0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  c->step = step0;
+  const int st = wait_and_collect(c);
+  cudaFree(save);
+  if (rc != SIDM_OK) return rc;
+  if (st < 0) return st;
+  if (best) to_public(cur, best);
+  return SIDM_OK;
 }
 
 int sidm_sync(sidm_ctx* c) {

@@ -30,7 +30,6 @@ namespace {
 constexpr int PW = 4;
 constexpr int PT = PW * WARP;
 constexpr int XT = 256;                            // thread-per-item passes
-constexpr int CHUNK = 4;
 constexpr int MAXR = 8;                            // neighbour rounds of 32 (stride <= 256)
 constexpr float U = 5.9604644775390625e-08f;       // 2^-24
 constexpr float REL = 9.5367431640625e-07f;        // 2^-20
@@ -51,6 +50,7 @@ struct PairKArgs {
   double* dtlim_user;
   DevStats* st;
   int* work;
+  int chunk;          // queries claimed per work-counter increment
 };
 
 __device__ __forceinline__ double warp_maxd(double v) {
@@ -316,9 +316,9 @@ __global__ void __launch_bounds__(PT, 6) pairs_kernel(PairKArgs A) {
   int q = 0, q_end = 0;
   for (;;) {
     if (q >= q_end) {
-      if (lane == 0) q = atomicAdd(A.work, CHUNK);
+      if (lane == 0) q = atomicAdd(A.work, A.chunk);
       q = __shfl_sync(0xffffffffu, q, 0);
-      q_end = q + CHUNK;
+      q_end = q + A.chunk;
     }
     if (q >= n_act) break;
     const int64_t qi = q++;
@@ -520,10 +520,11 @@ __global__ void __launch_bounds__(XT) limits_kernel(PairKArgs A) {
 int launch_pairs(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
                  const int32_t* nb_list, const int32_t* nb_count, int nb_stride,
                  const PairArgs& a, PairRec* pairs, double* dtlim_user, DevStats* st, int* work,
-                 int sms, cudaStream_t s) {
+                 int sms, const LaunchTuning& t, cudaStream_t s) {
   if (n <= 0) return 0;
-  PairKArgs k{so, f, n, act_list, nb_list, nb_count, nb_stride, a, pairs, dtlim_user, st, work};
-  int64_t blocks = (int64_t)sms * 8;
+  PairKArgs k{so, f, n, act_list, nb_list, nb_count, nb_stride, a, pairs, dtlim_user, st, work,
+              t.pairs_chunk};
+  int64_t blocks = (int64_t)sms * t.pairs_blocks_per_sm;
   const int64_t need = (n + PW - 1) / PW;
   if (blocks > need) blocks = need;
   pairs_kernel<<<(unsigned)blocks, PT, 0, s>>>(k);

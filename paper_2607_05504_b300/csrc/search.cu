@@ -36,8 +36,6 @@ namespace {
 
 constexpr int SW = 4;                 // warps per block
 constexpr int ST = SW * WARP;
-constexpr int NWIN = 8;               // window of 8 * 32 particles
-constexpr int CHUNK = 4;              // queries per work-counter increment
 constexpr float REL = 9.5367431640625e-07f;   // 2^-20
 constexpr float ABS = 4.76837158203125e-07f;  // 2^-21
 constexpr float CREL = REL + ABS;             // relative part of the bounds
@@ -57,6 +55,7 @@ struct SearchArgs {
   int32_t* nb_list;     // [n_act][nb_stride]
   int32_t* nb_count;    // [n_act]: count, or -1 (walk the tree)
   int nb_stride;
+  int chunk;             // queries claimed per work-counter increment
   DevStats* st;
   int* work;
 };
@@ -109,7 +108,8 @@ __device__ __forceinline__ double half_of(double h) {
   return (ef > 1 && ef < 2047) ? __longlong_as_double(b - (1ll << 52)) : 0.5 * h;
 }
 
-template <bool PERIODIC>
+// NWIN: the key-order window of the search radius is 32 NWIN particles.
+template <bool PERIODIC, int NWIN>
 __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
   __shared__ float s_r2[SW][SEARCH_CAP];
   __shared__ int32_t s_j[SW][SEARCH_CAP];
@@ -131,9 +131,9 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
   int q = 0, q_end = 0;
   for (;;) {
     if (q >= q_end) {
-      if (lane == 0) q = atomicAdd(A.work, CHUNK);
+      if (lane == 0) q = atomicAdd(A.work, A.chunk);
       q = __shfl_sync(0xffffffffu, q, 0);
-      q_end = q + CHUNK;
+      q_end = q + A.chunk;
     }
     if (q >= n_act) break;
     const int64_t qi = q++;
@@ -372,19 +372,25 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
 
 }  // namespace
 
+template <bool PERIODIC>
+void launch_search_window(const SearchArgs& a, int window, unsigned blocks, cudaStream_t s) {
+  if (window <= 128) search_kernel<PERIODIC, 4><<<blocks, ST, 0, s>>>(a);
+  else if (window <= 256) search_kernel<PERIODIC, 8><<<blocks, ST, 0, s>>>(a);
+  else search_kernel<PERIODIC, 16><<<blocks, ST, 0, s>>>(a);
+}
+
 int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
                   double box, int n_ngb, int tol, double fixed_h, int kernel, int split,
-                  double* h_user,
-                  int32_t* nb_list, int32_t* nb_count, int nb_stride, DevStats* st, int* work,
-                  int sms, cudaStream_t s) {
+                  double* h_user, int32_t* nb_list, int32_t* nb_count, int nb_stride,
+                  DevStats* st, int* work, int sms, const LaunchTuning& t, cudaStream_t s) {
   if (n <= 0) return 0;
   SearchArgs a{so, f, n, act_list, box, n_ngb, tol, fixed_h, kernel, split, h_user,
-               nb_list, nb_count, nb_stride, st, work};
-  int64_t blocks = (int64_t)sms * 8;
+               nb_list, nb_count, nb_stride, t.search_chunk, st, work};
+  int64_t blocks = (int64_t)sms * t.search_blocks_per_sm;
   const int64_t need = (n + SW - 1) / SW;
   if (blocks > need) blocks = need;
-  if (box > 0.0) search_kernel<true><<<(unsigned)blocks, ST, 0, s>>>(a);
-  else search_kernel<false><<<(unsigned)blocks, ST, 0, s>>>(a);
+  if (box > 0.0) launch_search_window<true>(a, t.search_window, (unsigned)blocks, s);
+  else launch_search_window<false>(a, t.search_window, (unsigned)blocks, s);
   return 1;
 }
 

@@ -214,11 +214,18 @@ int launch_forest(const Sorted& so, const Forest& f, cudaStream_t s);
 int tree_levels_for(int64_t n, int64_t count[MAX_LEVELS]);
 
 // search.cu
+// Launch shapes that leave every result unchanged (see sidm_tuning).
+struct LaunchTuning {
+  int search_window = 256;       // key-order window of the search radius (128, 256, 512)
+  int search_chunk = 4;          // queries per work-counter increment
+  int search_blocks_per_sm = 8;  // 4-warp blocks per SM (at most 8 are resident)
+  int pairs_chunk = 4;
+  int pairs_blocks_per_sm = 6;   // at most 6 are resident
+};
 int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
                   double box, int n_ngb, int tol, double fixed_h, int kernel, int split,
-                  double* h_user,
-                  int32_t* nb_list, int32_t* nb_count, int nb_stride, DevStats* st, int* work,
-                  int sms, cudaStream_t s);
+                  double* h_user, int32_t* nb_list, int32_t* nb_count, int nb_stride,
+                  DevStats* st, int* work, int sms, const LaunchTuning& t, cudaStream_t s);
 
 // pairs.cu
 constexpr int LIM_CAND = 4;   // Eq. 18 maximum: candidates kept per query
@@ -237,7 +244,7 @@ struct PairArgs {
 int launch_pairs(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
                  const int32_t* nb_list, const int32_t* nb_count, int nb_stride,
                  const PairArgs& a, PairRec* pairs, double* dtlim_user, DevStats* st,
-                 int* work, int sms, cudaStream_t s);
+                 int* work, int sms, const LaunchTuning& t, cudaStream_t s);
 
 // resolve.cu
 struct ResolveBuffers {

@@ -42,7 +42,17 @@ class Config(C.Structure):
     _fields_ = [("n_ngb", C.c_int), ("ngb_tol", C.c_int), ("c_sidm", C.c_double),
                 ("box", C.c_double), ("kernel", C.c_int), ("precision", C.c_int),
                 ("fixed_h", C.c_double), ("n_max", C.c_int64), ("pair_capacity", C.c_int64),
-                ("stream", C.c_void_p), ("device", C.c_int), ("profile", C.c_int)]
+                ("stream", C.c_void_p), ("device", C.c_int), ("profile", C.c_int),
+                ("use_graph", C.c_int)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("search_window", C.c_int), ("search_chunk", C.c_int),
+                ("search_blocks_per_sm", C.c_int), ("pairs_chunk", C.c_int),
+                ("pairs_blocks_per_sm", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class SigmaModel(C.Structure):
@@ -75,7 +85,8 @@ ENTRY_POINTS = ("sidm_default_config", "sidm_create", "sidm_set_particles",
                 "sidm_set_velocities", "sidm_step", "sidm_sync", "sidm_get_particles",
                 "sidm_timestep_limits", "sidm_get_pairs", "sidm_get_step", "sidm_set_step",
                 "sidm_phase_times", "sidm_kernel_launches", "sidm_error_string", "sidm_destroy",
-                "sidm_apply_pairs_noalloc", "sidm_set_haloes", "sidm_step_haloes")
+                "sidm_apply_pairs_noalloc", "sidm_set_haloes", "sidm_step_haloes",
+                "sidm_set_tuning", "sidm_get_tuning", "sidm_autotune", "sidm_graph_state")
 
 N_PHASES = 6
 PHASES = ("keys", "sort", "structure", "search", "pairs", "resolve")
@@ -124,6 +135,11 @@ def lib():
         L.sidm_apply_pairs_noalloc.argtypes = [vp, i64, vp, vp, i64, C.c_uint64, C.c_uint64, vp]
         L.sidm_set_haloes.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64)]
         L.sidm_step_haloes.argtypes = [vp, vp, vp, C.POINTER(HaloParams), C.POINTER(StepStats)]
+        L.sidm_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+        L.sidm_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
+        L.sidm_autotune.argtypes = [vp, vp, vp, C.POINTER(HaloParams), C.c_int,
+                                    C.POINTER(Tuning)]
+        L.sidm_graph_state.argtypes = [vp]
         for name in ENTRY_POINTS:
             fn = getattr(L, name)
             if name not in ("sidm_default_config", "sidm_error_string", "sidm_destroy"):
@@ -205,6 +221,28 @@ def sidm_step_haloes(ctx, active_mask, dt_bins, params, stats=None) -> int:
                   "sidm_step_haloes")
 
 
+def sidm_set_tuning(ctx, t: Tuning) -> int:
+    return _check(lib().sidm_set_tuning(ctx, C.byref(t)), "sidm_set_tuning")
+
+
+def sidm_get_tuning(ctx) -> Tuning:
+    t = Tuning()
+    _check(lib().sidm_get_tuning(ctx, C.byref(t)), "sidm_get_tuning")
+    return t
+
+
+def sidm_autotune(ctx, active_mask, dt_bins, params, reps=3) -> Tuning:
+    arr = (HaloParams * len(params))(*params)
+    t = Tuning()
+    _check(lib().sidm_autotune(ctx, _ptr(active_mask)[0], _ptr(dt_bins)[0], arr, int(reps),
+                               C.byref(t)), "sidm_autotune")
+    return t
+
+
+def sidm_graph_state(ctx) -> int:
+    return int(lib().sidm_graph_state(ctx))
+
+
 def sidm_sync(ctx) -> int:
     return _check(lib().sidm_sync(ctx), "sidm_sync")
 
@@ -268,7 +306,7 @@ class Context:
 
     def __init__(self, n_ngb=32, ngb_tol=5, c_sidm=0.1, box=0.0, kernel=KERNEL_CUBIC,
                  fixed_h=0.0, n_max=0, pair_capacity=0, stream=None, device=-1, profile=False,
-                 precision=FP64_PLAIN):
+                 precision=FP64_PLAIN, use_graph=False):
         cfg = sidm_default_config()
         cfg.n_ngb, cfg.ngb_tol, cfg.c_sidm, cfg.box = int(n_ngb), int(ngb_tol), float(c_sidm), float(box)
         cfg.kernel, cfg.fixed_h, cfg.n_max = int(kernel), float(fixed_h), int(n_max)
@@ -277,6 +315,7 @@ class Context:
         cfg.device = int(device)
         cfg.profile = int(bool(profile))
         cfg.precision = int(precision)
+        cfg.use_graph = int(bool(use_graph))
         self.cfg = cfg
         self.handle = sidm_create(cfg)
         self.n = 0
@@ -355,6 +394,29 @@ class Context:
 
     def sync(self):
         return sidm_sync(self.handle)
+
+    @property
+    def tuning(self) -> dict:
+        return sidm_get_tuning(self.handle).as_dict()
+
+    def set_tuning(self, **kw):
+        t = sidm_get_tuning(self.handle)
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        sidm_set_tuning(self.handle, t)
+
+    def autotune(self, params, active=None, bins=None, reps=3) -> dict:
+        """Times launch shapes on the next step (params: one HaloParams per
+        halo) and keeps the fastest; the simulation state is left unchanged."""
+        if isinstance(active, np.ndarray):
+            active = np.ascontiguousarray(active, np.uint8)
+        if isinstance(bins, np.ndarray):
+            bins = np.ascontiguousarray(bins, np.int8)
+        return sidm_autotune(self.handle, active, bins, params, reps).as_dict()
+
+    @property
+    def graph_state(self) -> int:
+        return sidm_graph_state(self.handle)
 
     def velocities(self):
         v = np.empty((self.n, 3))
