@@ -506,6 +506,7 @@ def main():
     pctx = sidm.Context(n_ngb=64, box=0.0, stream=stream.cuda_stream, device=local, n_max=n,
                         profile=True)
     pctx.set_particles(pos_d, vel_d, ids_d, mass=mass_d)
+    pctx.set_tuning(**tuning)          # the launch shapes of the timed steps
     phase_sum = {k: 0.0 for k in sidm.PHASES}
     n_act_sum = 0
     reps = min(args.steps, CYCLE)

@@ -212,6 +212,7 @@ int ensure_capacity(sidm_ctx* c, int64_t n) {
   CK(dalloc(c, &rb.fill, want));
   CK(dalloc(c, &rb.cursor, want));
   CK(dalloc(c, &rb.seg, 2 * pc));
+  CK(dalloc(c, &rb.seg_e, 2 * pc));
   CK(dalloc(c, &rb.touched, 2 * pc));
   CK(dalloc(c, &rb.pending, pc));
   CK(dalloc(c, &rb.flags, pc));

@@ -56,13 +56,31 @@ __global__ void bbox_init_kernel(Halo* halos, int n_halos) {
   }
 }
 
-__device__ __forceinline__ void bbox_flush(Halo* halos, int k, const double* lo, const double* hi) {
+// lo / hi: running extrema as order-preserving integers of the doubles
+// (integer min/max: exact, and off B300's slow FP64 pipe)
+constexpr unsigned long long ORD_NONE_LO = ~0ull, ORD_NONE_HI = 0ull;
+__device__ __forceinline__ void bbox_flush(Halo* halos, int k, const unsigned long long* lo,
+                                           const unsigned long long* hi) {
   for (int a = 0; a < 3; ++a) {
     if (lo[a] <= hi[a]) {
-      atomicMin(&halos[k].mm[a], dbl_to_ordered(lo[a]));
-      atomicMax(&halos[k].mm[3 + a], dbl_to_ordered(hi[a]));
+      atomicMin(&halos[k].mm[a], lo[a]);
+      atomicMax(&halos[k].mm[3 + a], hi[a]);
     }
   }
+}
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w < v ? w : v;
+  }
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
 }
 
 // Bounding box of every halo: blocks walk contiguous chunks; a thread flushes
@@ -74,7 +92,8 @@ __global__ void __launch_bounds__(BT) bbox_kernel(const double* __restrict__ pos
   const int64_t chunk_len = (int64_t)BT * BB_ITEMS;
   for (int64_t c0 = blockIdx.x * chunk_len; c0 < n; c0 += (int64_t)gridDim.x * chunk_len) {
     int cur = -1;
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    unsigned long long lo[3] = {ORD_NONE_LO, ORD_NONE_LO, ORD_NONE_LO};
+    unsigned long long hi[3] = {ORD_NONE_HI, ORD_NONE_HI, ORD_NONE_HI};
     for (int j = 0; j < BB_ITEMS; ++j) {
       const int64_t i = c0 + (int64_t)j * BT + threadIdx.x;
       if (i >= n) break;
@@ -82,20 +101,20 @@ __global__ void __launch_bounds__(BT) bbox_kernel(const double* __restrict__ pos
       if (k != cur) {
         if (cur >= 0) bbox_flush(halos, cur, lo, hi);
         cur = k;
-        for (int a = 0; a < 3; ++a) { lo[a] = INFINITY; hi[a] = -INFINITY; }
+        for (int a = 0; a < 3; ++a) { lo[a] = ORD_NONE_LO; hi[a] = ORD_NONE_HI; }
       }
       for (int a = 0; a < 3; ++a) {
-        const double x = pos[3 * i + a];
-        lo[a] = fmin(lo[a], x);
-        hi[a] = fmax(hi[a], x);
+        const unsigned long long x = dbl_to_ordered(pos[3 * i + a]);
+        lo[a] = x < lo[a] ? x : lo[a];
+        hi[a] = x > hi[a] ? x : hi[a];
       }
     }
     const int k0 = __shfl_sync(0xffffffffu, cur, 0);
     const bool same = __all_sync(0xffffffffu, cur == k0 || cur < 0) && k0 >= 0;
     if (same) {
       for (int a = 0; a < 3; ++a) {
-        lo[a] = warp_min(lo[a]);
-        hi[a] = warp_max(hi[a]);
+        lo[a] = warp_min_u64(lo[a]);
+        hi[a] = warp_max_u64(hi[a]);
       }
       if (lane == 0) bbox_flush(halos, k0, lo, hi);
     } else if (cur >= 0) {
@@ -246,13 +265,14 @@ __global__ void __launch_bounds__(BT) permute_kernel(
     so.x[s] = x;
     so.y[s] = y;
     so.z[s] = z;
-    const double dt = ldexp(halos[k].dt_max, -(int)bins[o]);
+    const double dt = scale_pow2_down(halos[k].dt_max, (int)bins[o]);
     const double vx = vel[3 * o], vy = vel[3 * o + 1], vz = vel[3 * o + 2], m = mass[o];
-    so.f[s] = make_float4((float)x, (float)y, (float)z, __double2float_ru(dt));
+    so.f[s] = make_float4(f64_to_f32_rn(x), f64_to_f32_rn(y), f64_to_f32_rn(z), f64_to_f32_ru(dt));
     so.vx[s] = vx;
     so.vy[s] = vy;
     so.vz[s] = vz;
-    so.vm[s] = make_float4((float)vx, (float)vy, (float)vz, __double2float_ru(m));
+    so.vm[s] = make_float4(f64_to_f32_rn(vx), f64_to_f32_rn(vy), f64_to_f32_rn(vz),
+                           f64_to_f32_ru(m));
     so.m[s] = m;
     so.id[s] = ids[o];
     a = act[o] != 0;
@@ -273,6 +293,17 @@ __global__ void __launch_bounds__(BT) permute_kernel(
 
 // Leaves: conservative FP32 box of up to 32 consecutive particles of a halo
 // (min rounded down, max rounded up from the FP64 coordinates).
+// Leaf boxes from the FP32 copies (round to nearest) of the positions:
+// |x - fl32(x)| <= 2^-24 |fl32(x)| for normal values, so widening the FP32
+// extrema by 2^-23 of their magnitude (plus the smallest normal, for values
+// near zero), with directed rounding, gives boxes that contain the FP64
+// positions.  No FP64 arithmetic.
+__device__ __forceinline__ float widen_down(float v) {
+  return __fsub_rd(v, __fadd_ru(__fmul_ru(fabsf(v), 1.1920928955078125e-07f), 1.17549435e-38f));
+}
+__device__ __forceinline__ float widen_up(float v) {
+  return __fadd_ru(v, __fadd_ru(__fmul_ru(fabsf(v), 1.1920928955078125e-07f), 1.17549435e-38f));
+}
 __global__ void __launch_bounds__(BT) leaf_kernel(Sorted so, Forest f) {
   const int64_t g = (blockIdx.x * (int64_t)BT + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -281,21 +312,20 @@ __global__ void __launch_bounds__(BT) leaf_kernel(Sorted so, Forest f) {
   const Halo& H = f.halos[k];
   const int64_t local = g - H.node_off[0];
   const int64_t s = H.start + local * LEAF + lane;
-  double x0 = INFINITY, y0 = INFINITY, z0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY, z1 = -INFINITY;
+  float x0 = INFINITY, y0 = INFINITY, z0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY, z1 = -INFINITY;
   if (local * LEAF + lane < H.n) {
-    x0 = x1 = so.x[s];
-    y0 = y1 = so.y[s];
-    z0 = z1 = so.z[s];
+    const float4 p = so.f[s];
+    x0 = x1 = p.x;
+    y0 = y1 = p.y;
+    z0 = z1 = p.z;
   }
-  x0 = warp_min(x0); y0 = warp_min(y0); z0 = warp_min(z0);
-  x1 = warp_max(x1); y1 = warp_max(y1); z1 = warp_max(z1);
+  x0 = warp_minf(x0); y0 = warp_minf(y0); z0 = warp_minf(z0);
+  x1 = warp_maxf(x1); y1 = warp_maxf(y1); z1 = warp_maxf(z1);
   if (lane == 0) {
-    f.lo[g] = make_float4(__double2float_rd(x0), __double2float_rd(y0), __double2float_rd(z0), 0.f);
-    f.hi[g] = make_float4(__double2float_ru(x1), __double2float_ru(y1), __double2float_ru(z1), 0.f);
+    f.lo[g] = make_float4(widen_down(x0), widen_down(y0), widen_down(z0), 0.f);
+    f.hi[g] = make_float4(widen_up(x1), widen_up(y1), widen_up(z1), 0.f);
   }
 }
-
-// Level-l nodes of all haloes: the union of up to 32 children of level l-1.
 __global__ void __launch_bounds__(BT) node_kernel(Forest f, int level, int64_t level_base) {
   const int64_t g = level_base + ((blockIdx.x * (int64_t)BT + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;

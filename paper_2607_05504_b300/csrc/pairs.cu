@@ -124,8 +124,8 @@ __device__ __forceinline__ Query load_query(const Sorted& so, const Forest& f, i
   Q.k1 = (uint32_t)(H.seed >> 32);
   Q.step = H.step;
   Q.kind = H.sigma_kind;
-  Q.s0f = __double2float_ru(H.sigma0);
-  Q.wf = (float)H.w;
+  Q.s0f = f64_to_f32_ru(H.sigma0);
+  Q.wf = f64_to_f32_rn(H.w);
   Q.idi = so.id[s];
   Q.oi = so.orig[s];
   Q.fi = so.f[s];
@@ -179,7 +179,7 @@ __device__ __forceinline__ void visit(const PairKArgs& A, const Query& Q, int64_
     bool sees = false;
     if (actj) {
       if (P.split) {
-        const float hjf = (float)so.h[j];
+        const float hjf = f64_to_f32_rn(so.h[j]);
         sees = r2f < hjf * hjf;
       } else if (rhi < hbj.x) {
         sees = true;

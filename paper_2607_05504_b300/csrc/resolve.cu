@@ -40,6 +40,28 @@ __device__ bool first_at(int64_t p, const PairRec& rp, int32_t e, const int32_t*
   return true;
 }
 
+// The elastic kick of Eqs. 12-13 (eps = 1) in the operation order
+//   v_com = ((m_a v_a) + (m_b v_b)) / M,  g = sqrt((dx dx + dy dy) + dz dz),
+//   v_a' = v_com + ((m_b g) / M) e,  v_b' = v_com - ((m_a g) / M) e,
+// with M = m_a + m_b; every operation rounds once (no contraction).
+__device__ __forceinline__ void kick_values(double ma, double mb, const double* e, double* a,
+                                            double* b) {
+  const double M = ma + mb;
+  double c[3], d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    c[k] = ((ma * a[k]) + (mb * b[k])) / M;
+    d[k] = a[k] - b[k];
+  }
+  const double g = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+  const double fa = (mb * g) / M, fb = (ma * g) / M;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    a[k] = c[k] + fa * e[k];
+    b[k] = c[k] - fb * e[k];
+  }
+}
+
 __device__ void kick(const PairRec& r, double* vel, const double* mass, uint32_t k0, uint32_t k1,
                      uint32_t step, unsigned* dirfail) {
   double e0 = 0.0, e1 = 0.0, e2 = 1.0;
@@ -61,21 +83,15 @@ __device__ void kick(const PairRec& r, double* vel, const double* mass, uint32_t
   double* va = vel + 3 * (int64_t)r.ia;
   double* vb = vel + 3 * (int64_t)r.ib;
   const double ma = mass[r.ia], mb = mass[r.ib];
-  const double M = ma + mb;
-  const double ax = va[0], ay = va[1], az = va[2];
-  const double bx = vb[0], by = vb[1], bz = vb[2];
-  const double cx = ((ma * ax) + (mb * bx)) / M;
-  const double cy = ((ma * ay) + (mb * by)) / M;
-  const double cz = ((ma * az) + (mb * bz)) / M;
-  const double dx = ax - bx, dy = ay - by, dz = az - bz;
-  const double g = sqrt((dx * dx + dy * dy) + dz * dz);
-  const double fa = (mb * g) / M, fb = (ma * g) / M;
-  va[0] = cx + fa * e0;
-  va[1] = cy + fa * e1;
-  va[2] = cz + fa * e2;
-  vb[0] = cx - fb * e0;
-  vb[1] = cy - fb * e1;
-  vb[2] = cz - fb * e2;
+  const double e[3] = {e0, e1, e2};
+  double a[3] = {va[0], va[1], va[2]}, b[3] = {vb[0], vb[1], vb[2]};
+  kick_values(ma, mb, e, a, b);
+  va[0] = a[0];
+  va[1] = a[1];
+  va[2] = a[2];
+  vb[0] = b[0];
+  vb[1] = b[1];
+  vb[2] = b[2];
 }
 
 __global__ void __launch_bounds__(RT) resolve_kernel(const PairRec* __restrict__ pairs,
@@ -177,11 +193,6 @@ __device__ __forceinline__ bool step_overflowed(const DevStats* st, int64_t cap)
   return st->n_acc > (unsigned long long)cap || st->n_deferred > (unsigned long long)cap;
 }
 
-__device__ __forceinline__ int ld_acquire(const int32_t* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 __device__ __forceinline__ void st_release(int32_t* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -225,21 +236,15 @@ __device__ __forceinline__ void kick_l2(const PairRec& r, double* vel, double ma
                                         const double* e) {
   double* va = vel + 3 * (int64_t)r.ia;
   double* vb = vel + 3 * (int64_t)r.ib;
-  const double M = ma + mb;
-  const double ax = __ldcg(va), ay = __ldcg(va + 1), az = __ldcg(va + 2);
-  const double bx = __ldcg(vb), by = __ldcg(vb + 1), bz = __ldcg(vb + 2);
-  const double cx = ((ma * ax) + (mb * bx)) / M;
-  const double cy = ((ma * ay) + (mb * by)) / M;
-  const double cz = ((ma * az) + (mb * bz)) / M;
-  const double dx = ax - bx, dy = ay - by, dz = az - bz;
-  const double g = sqrt((dx * dx + dy * dy) + dz * dz);
-  const double fa = (mb * g) / M, fb = (ma * g) / M;
-  __stcg(va, cx + fa * e[0]);
-  __stcg(va + 1, cy + fa * e[1]);
-  __stcg(va + 2, cz + fa * e[2]);
-  __stcg(vb, cx - fb * e[0]);
-  __stcg(vb + 1, cy - fb * e[1]);
-  __stcg(vb + 2, cz - fb * e[2]);
+  double a[3] = {__ldcg(va), __ldcg(va + 1), __ldcg(va + 2)};
+  double b[3] = {__ldcg(vb), __ldcg(vb + 1), __ldcg(vb + 2)};
+  kick_values(ma, mb, e, a, b);
+  __stcg(va, a[0]);
+  __stcg(va + 1, a[1]);
+  __stcg(va + 2, a[2]);
+  __stcg(vb, b[0]);
+  __stcg(vb + 1, b[1]);
+  __stcg(vb + 2, b[2]);
 }
 
 __global__ void __launch_bounds__(GT) count_kernel(const PairRec* __restrict__ pairs, int64_t cap,
@@ -253,13 +258,32 @@ __global__ void __launch_bounds__(GT) count_kernel(const PairRec* __restrict__ p
   }
 }
 
-// claim a segment for particle e (first claimant allocates mult[e] slots)
-__device__ __forceinline__ void claim_segment(int32_t e, const int32_t* mult, int32_t* seg_off,
-                                              int32_t* touched, DevStats* st) {
-  if (atomicCAS(&seg_off[e], -1, -2) == -1) {
-    const unsigned long long base = atomicAdd(&st->n_seg, (unsigned long long)mult[e]);
-    seg_off[e] = (int32_t)base;
-    touched[atomicAdd(&st->n_touched, 1ull)] = e;
+// Claims a segment for particle e (the first claimant allocates mult[e]
+// slots); called by the whole warp, `want` per lane.  The slot and touched
+// counters take one atomic per warp.
+__device__ __forceinline__ void claim_segments(bool want, int32_t e, const int32_t* mult,
+                                               int32_t* seg_off, int32_t* touched, DevStats* st) {
+  const int lane = threadIdx.x & 31;
+  const bool first = want && atomicCAS(&seg_off[e], -1, -2) == -1;
+  const int cnt = first ? mult[e] : 0;
+  int incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  const uint32_t fm = __ballot_sync(0xffffffffu, first);
+  if (!fm) return;
+  unsigned long long bs = 0, bt = 0;
+  if (lane == 0) {
+    bs = atomicAdd(&st->n_seg, (unsigned long long)total);
+    bt = atomicAdd(&st->n_touched, (unsigned long long)__popc(fm));
+  }
+  bs = __shfl_sync(0xffffffffu, bs, 0);
+  bt = __shfl_sync(0xffffffffu, bt, 0);
+  if (first) {
+    seg_off[e] = (int32_t)(bs + (unsigned long long)(incl - cnt));
+    touched[bt + __popc(fm & ((1u << lane) - 1u))] = e;
   }
 }
 
@@ -281,8 +305,9 @@ __global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ p
     for (int64_t base = blockIdx.x * (int64_t)GT + (threadIdx.x & ~31); base < na; base += stride) {
       const int64_t p = base + lane;
       bool pend = false;
+      PairRec r{};
       if (p < na) {
-        const PairRec r = pairs[p];
+        r = pairs[p];
         const int ma = b.mult[r.ia], mb = b.mult[r.ib];
         mm = max(mm, max(ma, mb));
         if (ma == 1 && mb == 1) {
@@ -291,10 +316,10 @@ __global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ p
         } else {
           pend = true;
           b.flags[p] = 0;
-          claim_segment(r.ia, b.mult, b.seg_off, b.touched, st);
-          claim_segment(r.ib, b.mult, b.seg_off, b.touched, st);
         }
       }
+      claim_segments(pend, r.ia, b.mult, b.seg_off, b.touched, st);
+      claim_segments(pend, r.ib, b.mult, b.seg_off, b.touched, st);
       const uint32_t m = __ballot_sync(0xffffffffu, pend);
       if (m) {
         unsigned long long at = 0;
@@ -323,41 +348,31 @@ __global__ void __launch_bounds__(GT) fill_kernel(const PairRec* __restrict__ pa
   for (int64_t k = blockIdx.x * (int64_t)GT + threadIdx.x; k < np; k += (int64_t)gridDim.x * GT) {
     const int32_t p = b.pending[k];
     const int32_t ea = pairs[p].ia, eb = pairs[p].ib;
-    b.seg[b.seg_off[ea] + atomicAdd(&b.fill[ea], 1)] = p;
-    b.seg[b.seg_off[eb] + atomicAdd(&b.fill[eb], 1)] = p;
+    const int32_t sa = b.seg_off[ea] + atomicAdd(&b.fill[ea], 1);
+    const int32_t sb = b.seg_off[eb] + atomicAdd(&b.fill[eb], 1);
+    b.seg[sa] = p;
+    b.seg_e[sa] = ea;
+    b.seg[sb] = p;
+    b.seg_e[sb] = eb;
   }
 }
 
-__device__ __forceinline__ bool key_less_id(const PairRec* pairs, int32_t x, int32_t y) {
-  return key_less(pairs[x], pairs[y]);
-}
-
-// insertion sort of each particle's segment by key
-__global__ void __launch_bounds__(GT) segsort_kernel(const PairRec* __restrict__ pairs,
-                                                     int64_t cap, ResolveBuffers b,
-                                                     const DevStats* st) {
+// Place of each pending pair in its particles' key order: one thread per
+// segment slot counts the pairs of the same particle with a smaller key.
+// (Keys (ord, a, b) are distinct, so the places are 0 .. mult-1.)
+__global__ void __launch_bounds__(GT) rank_kernel(const PairRec* __restrict__ pairs, int64_t cap,
+                                                  ResolveBuffers b, const DevStats* st) {
   if (step_overflowed(st, cap)) return;
-  const int64_t nt = (int64_t)st->n_touched;
-  for (int64_t k = blockIdx.x * (int64_t)GT + threadIdx.x; k < nt; k += (int64_t)gridDim.x * GT) {
-    const int32_t e = b.touched[k];
-    int32_t* sg = b.seg + b.seg_off[e];
+  const int64_t ns = (int64_t)st->n_seg;
+  for (int64_t t = blockIdx.x * (int64_t)GT + threadIdx.x; t < ns; t += (int64_t)gridDim.x * GT) {
+    const int32_t e = b.seg_e[t], p = b.seg[t];
+    const int32_t* sg = b.seg + b.seg_off[e];
     const int len = b.mult[e];
-    for (int i = 1; i < len; ++i) {
-      const int32_t x = sg[i];
-      int j = i - 1;
-      while (j >= 0 && key_less_id(pairs, x, sg[j])) {
-        sg[j + 1] = sg[j];
-        --j;
-      }
-      sg[j + 1] = x;
-    }
-    // position of each pair in this particle's order: its turn comes when the
-    // particle's cursor reaches it
-    for (int i = 0; i < len; ++i) {
-      const int32_t p = sg[i];
-      if (pairs[p].ia == e) b.pos_a[p] = i;
-      else b.pos_b[p] = i;
-    }
+    const PairRec rp = pairs[p];
+    int rank = 0;
+    for (int k = 0; k < len; ++k) rank += key_less(pairs[sg[k]], rp) ? 1 : 0;
+    if (rp.ia == e) b.pos_a[p] = rank;
+    else b.pos_b[p] = rank;
   }
 }
 
@@ -485,7 +500,7 @@ int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* 
   count_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, b.mult, st);
   split_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, vel, mass, b, halo_of, halos, st);
   fill_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, b, st);
-  segsort_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, b, st);
+  rank_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, b, st);
   // cooperative launch: every block resident, as the passes wait on each other
   ResolveBuffers bb = b;
   PairRec* pp = pairs;

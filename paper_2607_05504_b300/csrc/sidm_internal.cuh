@@ -154,6 +154,49 @@ __device__ __forceinline__ unsigned long long dbl_to_ordered(double x) {
   unsigned long long u = (unsigned long long)__double_as_longlong(x);
   return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
+// FP64 -> FP32 conversions on the bit pattern (integer pipe; B300's FP64
+// pipe is slow).  The normal FP32 range is handled here, exactly as IEEE
+// round-to-nearest-even, upward and downward rounding define it; zero,
+// subnormal, out-of-range, infinite and NaN inputs take the hardware
+// conversion.
+__device__ __forceinline__ bool f32_normal_range(unsigned long long b, unsigned int* fb,
+                                                 unsigned int* rem) {
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -126 || e > 127) return false;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  *fb = ((unsigned int)(b >> 63) << 31) | ((unsigned int)(e + 127) << 23) | (unsigned int)(m >> 29);
+  *rem = (unsigned int)(m & 0x1FFFFFFFull);  // the 29 dropped significand bits
+  return true;
+}
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  unsigned int fb, rem;
+  if (!f32_normal_range((unsigned long long)__double_as_longlong(x), &fb, &rem))
+    return __double2float_rn(x);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (fb & 1u))) ++fb;  // magnitude up
+  return __uint_as_float(fb);
+}
+__device__ __forceinline__ float f64_to_f32_ru(double x) {
+  unsigned int fb, rem;
+  if (!f32_normal_range((unsigned long long)__double_as_longlong(x), &fb, &rem))
+    return __double2float_ru(x);
+  if (rem && !(fb >> 31)) ++fb;  // positive: magnitude up; negative: truncation
+  return __uint_as_float(fb);
+}
+__device__ __forceinline__ float f64_to_f32_rd(double x) {
+  unsigned int fb, rem;
+  if (!f32_normal_range((unsigned long long)__double_as_longlong(x), &fb, &rem))
+    return __double2float_rd(x);
+  if (rem && (fb >> 31)) ++fb;  // negative: magnitude up; positive: truncation
+  return __uint_as_float(fb);
+}
+// x 2^-k exactly (k >= 0) by an exponent step while the result stays normal.
+__device__ __forceinline__ double scale_pow2_down(double x, int k) {
+  const long long b = __double_as_longlong(x);
+  const int ef = (int)((b >> 52) & 0x7FF);
+  if (ef > k && ef < 2047) return __longlong_as_double(b - ((long long)k << 52));
+  return ldexp(x, -k);
+}
+
 __host__ __device__ inline double ordered_to_dbl(unsigned long long u) {
   u = (u >> 63) ? (u & 0x7FFFFFFFFFFFFFFFull) : ~u;
   double d;
@@ -252,7 +295,8 @@ struct ResolveBuffers {
   int32_t* seg_off;   // [n] start of the particle's pair segment (-1 between steps)
   int32_t* fill;      // [n] segment fill counter (0 between steps)
   int32_t* cursor;    // [n] first unapplied entry of the segment (0 between steps)
-  int32_t* seg;       // [2 cap] pair ids, one segment per particle, sorted by key
+  int32_t* seg;       // [2 cap] pair ids, one segment per particle
+  int32_t* seg_e;     // [2 cap] the particle of each segment slot
   int32_t* touched;   // [2 cap] particles that own a segment
   int32_t* pending;   // [cap] pairs that share a particle with another pair
   uint8_t* flags;     // [cap] applied flags
