@@ -362,56 +362,70 @@ __global__ void __launch_bounds__(PT, 6) pairs_kernel(PairKArgs A) {
 
 // Queries whose neighbour list was not complete: walk the tree with radius
 // h_i and decide membership exactly.
+// One query whose neighbour list was incomplete: walk the tree with radius
+// h_i and decide membership exactly (the whole warp).
+__device__ void walk_query(const PairKArgs& A, int64_t qi, int* stack, unsigned long long* cand,
+                           unsigned long long* pge1, double* sum_p, uint32_t* status) {
+  const Sorted& so = A.so;
+  const int lane = threadIdx.x & 31;
+  const double box = A.a.box, half = 0.5 * A.a.box;
+  const float boxf = (float)A.a.box;
+  const Query Q = load_query(so, A.f, A.act_list[qi], boxf);
+  const int64_t s = Q.s;
+  const Halo& H = A.f.halos[so.halo[s]];
+  const int64_t hs = H.start;
+  const double xi = so.x[s], yi = so.y[s], zi = so.z[s], hi = so.h[s];
+  const double hhi = hi * hi;
+  const float rad = (__double2float_ru(hi) + 2.0f * Q.eq) * (1.0f + 4.0f * REL);
+  double mine = 0.0;
+  float psum = 0.0f;
+  const int sl = (int)(s - hs);
+  auto leaf = [&](int k, bool valid, const float4& pj) {
+    const int64_t j = hs + k;
+    bool in = false;
+    if (valid && k != sl) {
+      const float r = sqrtf(sep2f(Q.fi, pj, boxf));
+      const float e = Q.eq + ABS * r;
+      const float rlo = fmaxf(r * (1.0f - REL) - e, 0.0f);
+      if (A.a.split) {
+        const float hf = (float)hi;
+        in = r * r < hf * hf;
+      } else if (rlo < Q.hbi.y) {
+        in = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half) < hhi;
+      }
+    }
+    float gl, gh;
+    visit(A, Q, j, in, &gl, &gh, &psum, cand, pge1, status);
+    if (in) mine = fmax(mine, A.a.split ? (double)gl : exact_g(A, s, j));
+  };
+  const bool ok = A.a.box > 0.0
+      ? traverse<true>(A.f, H, so.f + hs, Q.fi, rad * rad, boxf, stack, leaf)
+      : traverse<false>(A.f, H, so.f + hs, Q.fi, rad * rad, boxf, stack, leaf);
+  if (!ok) *status |= ST_ERR_STACK;
+  *sum_p += (double)psum;
+  mine = warp_maxd(mine);
+  if (lane == 0) write_limit(A, s, mine);
+  __syncwarp();
+}
+
+// Queries whose neighbour list was not complete (rare): the warps scan the
+// query list 32 entries at a time.
 __global__ void __launch_bounds__(PT) pairs_walk_kernel(PairKArgs A) {
   __shared__ int s_stack[PW][SEARCH_STACK];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int* stack = s_stack[warp];
-  const Sorted& so = A.so;
   const int64_t n_act = (int64_t)A.st->n_active;
-  const double box = A.a.box, half = 0.5 * A.a.box;
-  const float boxf = (float)A.a.box;
   unsigned long long cand = 0, pge1 = 0;
   double sum_p = 0.0;
   uint32_t status = 0;
-  const int64_t w0 = (int64_t)blockIdx.x * PW + warp, ws = (int64_t)gridDim.x * PW;
-  for (int64_t qi = w0; qi < n_act; qi += ws) {
-    if (A.nb_count[qi] >= 0) continue;
-    const Query Q = load_query(so, A.f, A.act_list[qi], boxf);
-    const int64_t s = Q.s;
-    const Halo& H = A.f.halos[so.halo[s]];
-    const int64_t hs = H.start;
-    const double xi = so.x[s], yi = so.y[s], zi = so.z[s], hi = so.h[s];
-    const double hhi = hi * hi;
-    const float rad = (__double2float_ru(hi) + 2.0f * Q.eq) * (1.0f + 4.0f * REL);
-    double mine = 0.0;
-    float psum = 0.0f;
-    const int sl = (int)(s - hs);
-    auto leaf = [&](int k, bool valid, const float4& pj) {
-      const int64_t j = hs + k;
-      bool in = false;
-      if (valid && k != sl) {
-        const float r = sqrtf(sep2f(Q.fi, pj, boxf));
-        const float e = Q.eq + ABS * r;
-        const float rlo = fmaxf(r * (1.0f - REL) - e, 0.0f);
-        if (A.a.split) {
-          const float hf = (float)hi;
-          in = r * r < hf * hf;
-        } else if (rlo < Q.hbi.y) {
-          in = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half) < hhi;
-        }
-      }
-      float gl, gh;
-      visit(A, Q, j, in, &gl, &gh, &psum, &cand, &pge1, &status);
-      if (in) mine = fmax(mine, A.a.split ? (double)gl : exact_g(A, s, j));
-    };
-    const bool ok = A.a.box > 0.0
-        ? traverse<true>(A.f, H, so.f + hs, Q.fi, rad * rad, boxf, stack, leaf)
-        : traverse<false>(A.f, H, so.f + hs, Q.fi, rad * rad, boxf, stack, leaf);
-    if (!ok) status |= ST_ERR_STACK;
-    sum_p += (double)psum;
-    mine = warp_maxd(mine);
-    if (lane == 0) write_limit(A, s, mine);
-    __syncwarp();
+  const int64_t w0 = ((int64_t)blockIdx.x * PW + warp) * 32, ws = (int64_t)gridDim.x * PW * 32;
+  for (int64_t q0 = w0; q0 < n_act; q0 += ws) {
+    const bool need = q0 + lane < n_act && A.nb_count[q0 + lane] < 0;
+    uint32_t todo = __ballot_sync(0xffffffffu, need);
+    while (todo) {
+      const int64_t qi = q0 + __ffs(todo) - 1;
+      todo &= todo - 1;
+      walk_query(A, qi, s_stack[warp], &cand, &pge1, &sum_p, &status);
+    }
   }
   flush_counters(A, cand, pge1, sum_p, status);
 }

@@ -67,18 +67,25 @@ __device__ __forceinline__ int warp_sum(int v) {
 
 // FP32 squared-separation thresholds for a radius H given by its FP32
 // bounds Hlo <= H <= Hhi:  s2 < in2 -> r < H surely;  s2 >= out2 -> r >= H surely.
-// (directed rounding throughout; SQ covers the rounding of s2 itself)
+// Directed-rounding multiplies only (native; directed divisions and roots
+// are not): 1/(1 + c) > 1 - c and 1/(1 - c) < 1 + 2c bound the divisions
+// from the safe side; SQ covers the rounding of s2 itself.
+constexpr float ONE_M_CREL = 1.0f - CREL;         // exact in FP32
+constexpr float ONE_P_2CREL = 1.0f + 2.0f * CREL;  // exact in FP32
+constexpr float ULP1 = 1.1920928955078125e-07f;    // 2^-23
 __device__ __forceinline__ float thr_in2(float Hlo, float eq) {
-  const float x = __fdiv_rd(__fsub_rd(Hlo, eq), 1.0f + CREL);
+  const float x = __fmul_rd(__fsub_rd(Hlo, eq), ONE_M_CREL);
   return x > 0.0f ? __fmul_rd(__fmul_rd(x, x), 1.0f - SQ) : 0.0f;
 }
 __device__ __forceinline__ float thr_out2(float Hhi, float eq) {
-  const float x = __fdiv_ru(__fadd_ru(Hhi, eq), 1.0f - CREL);
+  const float x = __fmul_ru(__fadd_ru(Hhi, eq), ONE_P_2CREL);
   return __fmul_ru(__fmul_ru(x, x), 1.0f + SQ);
 }
 // upper bound hi(s) of the true separation for FP32 squared separation s2
+// (sqrtf rounds to nearest: within 2^-24 of the root; 2^-23 covers it)
 __device__ __forceinline__ float upper_from_s2(float s2, float eq) {
-  return __fmul_ru(__fadd_ru(__fmul_ru(__fsqrt_ru(s2), 1.0f + CREL), eq), 1.0f + SQ);
+  const float r = __fmul_ru(sqrtf(s2), 1.0f + ULP1);
+  return __fmul_ru(__fadd_ru(__fmul_ru(r, 1.0f + CREL), eq), 1.0f + SQ);
 }
 
 // FP32 bounds of a positive double by bit manipulation (exact, no FP64 ops)
@@ -86,8 +93,8 @@ __device__ __forceinline__ void float_bounds(double h, float* lo, float* hi) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(h);
   const int e = (int)((b >> 52) & 0x7FF) - 1023;
   if (e < -125 || e > 126) {
-    *lo = __double2float_rd(h);
-    *hi = __double2float_ru(h);
+    *lo = hw_f32_rd(h);
+    *hi = hw_f32_ru(h);
     return;
   }
   const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
@@ -100,12 +107,14 @@ __device__ __forceinline__ void float_bounds(double h, float* lo, float* hi) {
 __device__ __forceinline__ double twice(double h) {
   const long long b = __double_as_longlong(h);
   const int ef = (int)((b >> 52) & 0x7FF);
-  return (ef >= 1 && ef < 2046) ? __longlong_as_double(b + (1ll << 52)) : 2.0 * h;
+  if (ef >= 1 && ef < 2046) return __longlong_as_double(b + (1ll << 52));
+  return hw_mul(h, 2.0);
 }
 __device__ __forceinline__ double half_of(double h) {
   const long long b = __double_as_longlong(h);
   const int ef = (int)((b >> 52) & 0x7FF);
-  return (ef > 1 && ef < 2047) ? __longlong_as_double(b - (1ll << 52)) : 0.5 * h;
+  if (ef > 1 && ef < 2047) return __longlong_as_double(b - (1ll << 52));
+  return hw_mul(h, 0.5);
 }
 
 // NWIN: the key-order window of the search radius is 32 NWIN particles.
@@ -352,11 +361,12 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
       A.nb_count[qi] = cnt;
       so.h[s] = h;
       // bounds used by the pair kernel: 1/h from below, K/h^3 from above
-      const float knorm_up = __double2float_ru(A.kernel == SIDM_KERNEL_TOPHAT
-                                                   ? 3.0 / (4.0 * 3.141592653589793)
-                                                   : 8.0 / 3.141592653589793);
-      so.hb[s] = make_float4(hl, hu, __frcp_rd(hu),
-                             __fdiv_ru(knorm_up, __fmul_rd(__fmul_rd(hl, hl), hl)));
+      // K = 8/pi or 3/(4 pi) (the FP64 constants) rounded up to FP32
+      const float knorm_up = A.kernel == SIDM_KERNEL_TOPHAT ? 0x1.e8ec8cp-3f : 0x1.45f308p+1f;
+      // (__frcp_rn is within 2^-24 of the reciprocal; 2^-23 covers it)
+      const float h3 = __fmul_rd(__fmul_rd(hl, hl), hl);
+      so.hb[s] = make_float4(hl, hu, __fmul_rd(__frcp_rn(hu), 1.0f - ULP1),
+                             __fmul_ru(__fmul_ru(knorm_up, __frcp_rn(h3)), 1.0f + ULP1));
       A.h_user[so.orig[s]] = h;
     }
     __syncwarp();

@@ -154,6 +154,15 @@ __device__ __forceinline__ unsigned long long dbl_to_ordered(double x) {
   unsigned long long u = (unsigned long long)__double_as_longlong(x);
   return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
 }
+// Rare-path hardware operations behind a real call: written inline, the
+// compiler turns such a fallback into predicated instructions that occupy
+// B300's slow FP64 pipe on every pass, taken or not.
+static __device__ __noinline__ float hw_f32_rn(double x) { return __double2float_rn(x); }
+static __device__ __noinline__ float hw_f32_ru(double x) { return __double2float_ru(x); }
+static __device__ __noinline__ float hw_f32_rd(double x) { return __double2float_rd(x); }
+static __device__ __noinline__ double hw_ldexp(double x, int k) { return ldexp(x, k); }
+static __device__ __noinline__ double hw_mul(double x, double y) { return x * y; }
+
 // FP64 -> FP32 conversions on the bit pattern (integer pipe; B300's FP64
 // pipe is slow).  The normal FP32 range is handled here, exactly as IEEE
 // round-to-nearest-even, upward and downward rounding define it; zero,
@@ -171,21 +180,21 @@ __device__ __forceinline__ bool f32_normal_range(unsigned long long b, unsigned 
 __device__ __forceinline__ float f64_to_f32_rn(double x) {
   unsigned int fb, rem;
   if (!f32_normal_range((unsigned long long)__double_as_longlong(x), &fb, &rem))
-    return __double2float_rn(x);
+    return hw_f32_rn(x);
   if (rem > 0x10000000u || (rem == 0x10000000u && (fb & 1u))) ++fb;  // magnitude up
   return __uint_as_float(fb);
 }
 __device__ __forceinline__ float f64_to_f32_ru(double x) {
   unsigned int fb, rem;
   if (!f32_normal_range((unsigned long long)__double_as_longlong(x), &fb, &rem))
-    return __double2float_ru(x);
+    return hw_f32_ru(x);
   if (rem && !(fb >> 31)) ++fb;  // positive: magnitude up; negative: truncation
   return __uint_as_float(fb);
 }
 __device__ __forceinline__ float f64_to_f32_rd(double x) {
   unsigned int fb, rem;
   if (!f32_normal_range((unsigned long long)__double_as_longlong(x), &fb, &rem))
-    return __double2float_rd(x);
+    return hw_f32_rd(x);
   if (rem && (fb >> 31)) ++fb;  // negative: magnitude up; positive: truncation
   return __uint_as_float(fb);
 }
@@ -194,7 +203,7 @@ __device__ __forceinline__ double scale_pow2_down(double x, int k) {
   const long long b = __double_as_longlong(x);
   const int ef = (int)((b >> 52) & 0x7FF);
   if (ef > k && ef < 2047) return __longlong_as_double(b - ((long long)k << 52));
-  return ldexp(x, -k);
+  return hw_ldexp(x, -k);
 }
 
 __host__ __device__ inline double ordered_to_dbl(unsigned long long u) {
