@@ -43,7 +43,8 @@ class Config(C.Structure):
 
 
 class Sigma(C.Structure):
-    _fields_ = [("kind", C.c_int), ("sigma0", C.c_double), ("w", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("sigma0", C.c_double), ("w", C.c_double),
+                ("inelastic", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -86,7 +87,7 @@ def lib():
             L.orc_directed_probability.restype = C.c_double
             L.orc_direction.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, dp]
             L.orc_direction.restype = C.c_int
-            L.orc_kick.argtypes = [C.c_double, C.c_double, dp, dp, dp]
+            L.orc_kick.argtypes = [C.c_double, C.c_double, dp, dp, dp, C.c_double]
             L.orc_initial_h.argtypes = [C.c_double, C.c_int64, C.c_int]
             L.orc_initial_h.restype = C.c_double
             L.orc_counts.argtypes = [C.c_int64, dp, C.c_double, C.c_int, C.c_int64, i64p, dp, i64p]
@@ -105,8 +106,8 @@ def make_config(n_ngb=32, ngb_tol=5, c_sidm=0.1, box=0.0, kernel=0, fixed_h=0.0,
                   float(fixed_h), int(use_tree), int(n_threads))
 
 
-def make_sigma(kind=0, sigma0=1.0, w=1.0) -> Sigma:
-    return Sigma(int(kind), float(sigma0), float(w))
+def make_sigma(kind=0, sigma0=1.0, w=1.0, inelastic=0.0) -> Sigma:
+    return Sigma(int(kind), float(sigma0), float(w), float(inelastic))
 
 
 # ------------------------------------------------------------ primitives ---
@@ -149,12 +150,14 @@ def direction(seed: int, step: int, a: int, b: int):
     return e, bool(ok)
 
 
-def kick(mi, mj, vi, vj, e):
-    """Elastic centre-of-momentum kick, Sec. 4.1 (eps = 1)."""
+def kick(mi, mj, vi, vj, e, eps=1.0):
+    """Centre-of-momentum kick, Sec. 4.1: outgoing relative speed eps times
+    the incoming one (eps = 1: elastic)."""
     vi = np.array(vi, np.float64)
     vj = np.array(vj, np.float64)
     e = np.ascontiguousarray(e, np.float64)
-    lib().orc_kick(float(mi), float(mj), _p(vi, C.c_double), _p(vj, C.c_double), _p(e, C.c_double))
+    lib().orc_kick(float(mi), float(mj), _p(vi, C.c_double), _p(vj, C.c_double), _p(e, C.c_double),
+                   float(eps))
     return vi, vj
 
 
@@ -188,7 +191,8 @@ def h_for(pos, query, n_ngb=32, ngb_tol=5, box=0.0, use_tree=True, n_threads=0):
 
 
 def step(pos, vel, mass, ids, active, bins, dt_max, *, n_ngb=32, ngb_tol=5, c_sidm=0.1,
-         box=0.0, kernel=0, fixed_h=0.0, sigma_kind=0, sigma0=1.0, w=1.0, seed=0, step=0,
+         box=0.0, kernel=0, fixed_h=0.0, sigma_kind=0, sigma0=1.0, w=1.0, inelastic=0.0,
+         seed=0, step=0,
          use_tree=True, n_threads=0, max_pairs=None, h_init=None, dtlim_init=None):
     """One scattering step (Sec. 4); returns a dict with the new velocities,
     h and dt-limits (active particles updated, others from *_init or 0/inf),
@@ -209,7 +213,7 @@ def step(pos, vel, mass, ids, active, bins, dt_max, *, n_ngb=32, ngb_tol=5, c_si
     npairs = C.c_int64(0)
     st = Stats()
     cfg = make_config(n_ngb, ngb_tol, c_sidm, box, kernel, fixed_h, int(use_tree), n_threads)
-    sg = make_sigma(sigma_kind, sigma0, w)
+    sg = make_sigma(sigma_kind, sigma0, w, inelastic)
     rc = lib().orc_step(C.byref(cfg), n, _p(pos, C.c_double), _p(vel, C.c_double),
                         _p(mass, C.c_double), _p(ids, C.c_uint32), _p(act, C.c_uint8),
                         _p(bins, C.c_int8), float(dt_max), C.byref(sg), int(seed), int(step),

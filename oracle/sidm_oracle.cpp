@@ -30,7 +30,8 @@
 //                          (Eqs. 10, 11 with the one-sided estimator, Eq. 14).
 //   isotropic_direction    unit vector uniform on the sphere (Sec. 4.1),
 //                          by Marsaglia's (1972) rejection method.
-//   elastic_kick           centre-of-momentum elastic kick, eps = 1 (Sec. 4.1).
+//   kick                   centre-of-momentum kick with outgoing relative speed
+//                          eps |v_i - v_j| (Sec. 4.1; eps = 1: elastic).
 //   step                   one scattering step for the active set, pairs drawn
 //                          once, applied in a canonical order, and the per-pair
 //                          timestep criterion (Eq. 18).
@@ -83,6 +84,8 @@ typedef struct {
   int kind;         // 0 constant sigma/m; 1 Yukawa-like sigma0/m / (1+(v/w)^2)^2
   double sigma0;    // sigma0/m
   double w;         // velocity scale of the Yukawa-like law
+  double inelastic; // 1 - eps: the outgoing relative speed is eps times the
+                    // incoming one (Sec. 4.1); 0 = elastic, the paper's runs
 } orc_sigma;
 
 typedef struct {
@@ -373,12 +376,14 @@ int isotropic_direction(uint64_t seed, uint64_t step, uint32_t a, uint32_t b, do
   return 0;
 }
 
-// Elastic (eps = 1) kick in the centre-of-momentum frame.
-void elastic_kick(double mi, double mj, double* vi, double* vj, const double e[3]) {
+// Kick in the centre-of-momentum frame (Sec. 4.1): the pair keeps its
+// centre-of-momentum velocity and leaves along +-e with relative speed
+// eps |v_i - v_j| (eps = 1: elastic).
+void kick(double mi, double mj, double* vi, double* vj, const double e[3], double eps) {
   const double M = mi + mj;
   double vc[3];
   for (int k = 0; k < 3; ++k) vc[k] = ((mi * vi[k]) + (mj * vj[k])) / M;
-  const double g = rel_speed(vi, vj);
+  const double g = rel_speed(vi, vj) * eps;
   const double fi = (mj * g) / M, fj = (mi * g) / M;
   for (int k = 0; k < 3; ++k) {
     vi[k] = vc[k] + fi * e[k];
@@ -443,8 +448,8 @@ int orc_direction(uint64_t seed, uint64_t step, uint32_t a, uint32_t b, double e
   return isotropic_direction(seed, step, a, b, e);
 }
 
-void orc_kick(double mi, double mj, double* vi, double* vj, const double e[3]) {
-  elastic_kick(mi, mj, vi, vj, e);
+void orc_kick(double mi, double mj, double* vi, double* vj, const double e[3], double eps) {
+  kick(mi, mj, vi, vj, e, eps);
 }
 
 double orc_initial_h(double l_ext, int64_t n, int n_ngb) { return initial_h(l_ext, n, n_ngb); }
@@ -598,7 +603,7 @@ int orc_step(const orc_config* cfg, int64_t n, const double* pos, double* vel,
   for (const Pair& pr : acc) {
     double e[3];
     if (!isotropic_direction(seed, step, pr.a, pr.b, e)) ++S.n_dir_fail;
-    elastic_kick(mass[pr.i], mass[pr.j], vel + 3 * pr.i, vel + 3 * pr.j, e);
+    kick(mass[pr.i], mass[pr.j], vel + 3 * pr.i, vel + 3 * pr.j, e, 1.0 - sig->inelastic);
   }
 
   // 4. outputs for the active particles: h and the Eq. 18 limit
