@@ -44,7 +44,8 @@ class Config(C.Structure):
 
 class Sigma(C.Structure):
     _fields_ = [("kind", C.c_int), ("sigma0", C.c_double), ("w", C.c_double),
-                ("inelastic", C.c_double)]
+                ("inelastic", C.c_double), ("tab_n", C.c_int32),
+                ("tab_v", C.POINTER(C.c_double)), ("tab_s", C.POINTER(C.c_double))]
 
 
 class Stats(C.Structure):
@@ -106,8 +107,21 @@ def make_config(n_ngb=32, ngb_tol=5, c_sidm=0.1, box=0.0, kernel=0, fixed_h=0.0,
                   float(fixed_h), int(use_tree), int(n_threads))
 
 
-def make_sigma(kind=0, sigma0=1.0, w=1.0, inelastic=0.0) -> Sigma:
-    return Sigma(int(kind), float(sigma0), float(w), float(inelastic))
+_tables = []   # keeps the arrays behind Sigma.tab_v / tab_s alive
+
+
+def make_sigma(kind=0, sigma0=1.0, w=1.0, inelastic=0.0, table=None) -> Sigma:
+    """Cross-section model; kind 2 takes table = (v nodes, sigma/m values)."""
+    s = Sigma(int(kind), float(sigma0), float(w), float(inelastic), 0, None, None)
+    if table is not None:
+        tv = np.ascontiguousarray(table[0], np.float64)
+        ts = np.ascontiguousarray(table[1], np.float64)
+        _tables.append((tv, ts))
+        del _tables[:-8]
+        s.tab_n = int(tv.shape[0])
+        s.tab_v = tv.ctypes.data_as(C.POINTER(C.c_double))
+        s.tab_s = ts.ctypes.data_as(C.POINTER(C.c_double))
+    return s
 
 
 # ------------------------------------------------------------ primitives ---
@@ -130,8 +144,8 @@ def kernel_w(r: float, h: float, kernel: int = 0) -> float:
     return lib().orc_kernel_w(int(kernel), float(r), float(h))
 
 
-def sigma_over_m(vrel: float, kind=0, sigma0=1.0, w=1.0) -> float:
-    s = make_sigma(kind, sigma0, w)
+def sigma_over_m(vrel: float, kind=0, sigma0=1.0, w=1.0, table=None) -> float:
+    s = make_sigma(kind, sigma0, w, table=table)
     return lib().orc_sigma_over_m(C.byref(s), float(vrel))
 
 
@@ -192,7 +206,7 @@ def h_for(pos, query, n_ngb=32, ngb_tol=5, box=0.0, use_tree=True, n_threads=0):
 
 def step(pos, vel, mass, ids, active, bins, dt_max, *, n_ngb=32, ngb_tol=5, c_sidm=0.1,
          box=0.0, kernel=0, fixed_h=0.0, sigma_kind=0, sigma0=1.0, w=1.0, inelastic=0.0,
-         seed=0, step=0,
+         table=None, seed=0, step=0,
          use_tree=True, n_threads=0, max_pairs=None, h_init=None, dtlim_init=None):
     """One scattering step (Sec. 4); returns a dict with the new velocities,
     h and dt-limits (active particles updated, others from *_init or 0/inf),
@@ -213,7 +227,7 @@ def step(pos, vel, mass, ids, active, bins, dt_max, *, n_ngb=32, ngb_tol=5, c_si
     npairs = C.c_int64(0)
     st = Stats()
     cfg = make_config(n_ngb, ngb_tol, c_sidm, box, kernel, fixed_h, int(use_tree), n_threads)
-    sg = make_sigma(sigma_kind, sigma0, w, inelastic)
+    sg = make_sigma(sigma_kind, sigma0, w, inelastic, table)
     rc = lib().orc_step(C.byref(cfg), n, _p(pos, C.c_double), _p(vel, C.c_double),
                         _p(mass, C.c_double), _p(ids, C.c_uint32), _p(act, C.c_uint8),
                         _p(bins, C.c_int8), float(dt_max), C.byref(sg), int(seed), int(step),

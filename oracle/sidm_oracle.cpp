@@ -24,7 +24,8 @@
 //                          Sec. 4.5 "32 +- 5 neighbours").
 //   kernel_w               cubic spline W_CS(q, h) (Sec. 4.2) and top-hat
 //                          W_TH (Sec. 4.2), h = radius of compact support.
-//   sigma_over_m           constant sigma/m, or the Yukawa-like
+//   sigma_over_m           constant sigma/m, a table interpolated linearly in
+//                          log v (Sec. 4.1), or the Yukawa-like
 //                          sigma0/m / (1 + (v/w)^2)^2 (Sec. 5.2).
 //   directed_probability   P(i|j) = 1/2 m_j (sigma/m) |v_i - v_j| W(r_ij, h_i) dt_i
 //                          (Eqs. 10, 11 with the one-sided estimator, Eq. 14).
@@ -86,6 +87,10 @@ typedef struct {
   double w;         // velocity scale of the Yukawa-like law
   double inelastic; // 1 - eps: the outgoing relative speed is eps times the
                     // incoming one (Sec. 4.1); 0 = elastic, the paper's runs
+  // kind 2: tabulated sigma/m(v) (Sec. 4.1), n >= 2 nodes, v increasing
+  int32_t tab_n;
+  const double* tab_v;
+  const double* tab_s;
 } orc_sigma;
 
 typedef struct {
@@ -335,7 +340,21 @@ double kernel_shape(int kernel, double q) {
   return 2.0 * ((u * u) * u);
 }
 
+// Tabulated sigma/m(v), Sec. 4.1: linear in log v between nodes, held at
+// the end values outside the table.
+double sigma_table(const orc_sigma& s, double v) {
+  const int n = s.tab_n;
+  if (!(v > s.tab_v[0])) return s.tab_s[0];
+  if (v >= s.tab_v[n - 1]) return s.tab_s[n - 1];
+  int k = 0;
+  while (!(v < s.tab_v[k + 1])) ++k;  // v_k <= v < v_{k+1}
+  const double t = (std::log(v) - std::log(s.tab_v[k])) /
+                   (std::log(s.tab_v[k + 1]) - std::log(s.tab_v[k]));
+  return s.tab_s[k] + t * (s.tab_s[k + 1] - s.tab_s[k]);
+}
+
 double sigma_over_m(const orc_sigma& s, double vrel) {
+  if (s.kind == 2) return sigma_table(s, vrel);
   if (s.kind == 1) {
     const double t = 1.0 + (vrel * vrel) / (s.w * s.w);
     return s.sigma0 / (t * t);

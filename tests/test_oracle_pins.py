@@ -165,6 +165,62 @@ def test_inelastic_step_removes_the_predicted_energy(orc):
     assert 0.5 * pred < lost < 1.5 * pred
 
 
+def _table(n=12, seed=5):
+    rng = np.random.default_rng(seed)
+    v = np.sort(10 ** rng.uniform(-1.5, 1.5, n))
+    sg = 10 ** rng.uniform(-1, 1, n)
+    return v, sg
+
+
+def test_sigma_table_nodes_clamps_and_log_linearity(orc):
+    """Tabulated sigma/m(v) (Sec. 4.1, linear interpolation in log v): the
+    node values exactly, the end values outside the table, and along a
+    segment the value at v_k (v_{k+1}/v_k)^tau is s_k + tau (s_{k+1} - s_k)."""
+    v, sg = _table()
+    T = (v, sg)
+    for k in range(len(v)):
+        assert orc.sigma_over_m(v[k], kind=2, table=T) == sg[k]
+    assert orc.sigma_over_m(0.5 * v[0], kind=2, table=T) == sg[0]
+    assert orc.sigma_over_m(0.0, kind=2, table=T) == sg[0]
+    assert orc.sigma_over_m(2.0 * v[-1], kind=2, table=T) == sg[-1]
+    rng = np.random.default_rng(6)
+    for _ in range(500):
+        k = int(rng.integers(0, len(v) - 1))
+        tau = rng.uniform(0.0, 1.0)
+        x = v[k] * (v[k + 1] / v[k]) ** tau
+        want = sg[k] + tau * (sg[k + 1] - sg[k])
+        assert abs(orc.sigma_over_m(x, kind=2, table=T) - want) <= 1e-12 * max(sg[k], sg[k + 1])
+
+
+def test_sigma_table_sampled_from_yukawa_reproduces_it(orc):
+    """A dense log-spaced table of the Yukawa-like law reproduces it to the
+    interpolation error (second order in the node spacing)."""
+    w = 1.3
+    v = np.geomspace(1e-3, 1e3, 4001)
+    sg = np.array([orc.sigma_over_m(x, kind=1, sigma0=2.0, w=w) for x in v])
+    rng = np.random.default_rng(7)
+    for x in 10 ** rng.uniform(-2.9, 2.9, 400):
+        a = orc.sigma_over_m(x, kind=2, table=(v, sg))
+        b = orc.sigma_over_m(x, kind=1, sigma0=2.0, w=w)
+        assert abs(a - b) <= 2e-5 * 2.0
+
+
+def test_constant_table_equals_constant_cross_section(orc):
+    """A table with equal values is the constant model: a whole step gives the
+    same pairs, velocities and timestep limits bit for bit."""
+    p = I.uniform_box(3000, 1.0, 1.0, 33)
+    bins = np.zeros(p.n, np.int8)
+    T = (np.array([0.01, 0.3, 2.0, 50.0]), np.full(4, 1.7))
+    a = orc.step(p.pos, p.vel, p.mass, p.ids, None, bins, 0.1, box=1.0, sigma_kind=0, sigma0=1.7,
+                 seed=5)
+    b = orc.step(p.pos, p.vel, p.mass, p.ids, None, bins, 0.1, box=1.0, sigma_kind=2, table=T,
+                 seed=5)
+    assert a["n_pairs"] == b["n_pairs"] > 50
+    assert np.array_equal(a["pairs_ab"], b["pairs_ab"])
+    assert np.array_equal(a["vel"], b["vel"])
+    assert np.array_equal(a["dtlim"], b["dtlim"])
+
+
 def test_direction_uniform_on_sphere(orc):
     """e is uniform on the unit sphere (isotropic scattering, Sec. 4.1)."""
     es = []
