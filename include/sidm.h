@@ -67,7 +67,8 @@ typedef enum {
 
 enum { SIDM_HOST = 0, SIDM_DEVICE = 1 };
 enum { SIDM_KERNEL_CUBIC = 0, SIDM_KERNEL_TOPHAT = 1 };
-enum { SIDM_SIGMA_CONST = 0, SIDM_SIGMA_YUKAWA = 1 };
+enum { SIDM_SIGMA_CONST = 0, SIDM_SIGMA_YUKAWA = 1, SIDM_SIGMA_TABLE = 2 };
+#define SIDM_SIGMA_TABLE_MAX 256
 /* SIDM_FP64_PLAIN: every decision and value equals an FP64 evaluation in a
  * fixed operation order (FP32 is used only where it is provably decisive).
  * SIDM_FP32_SPLIT: separations, neighbour counts, kernel weights and
@@ -105,6 +106,10 @@ typedef struct {
   int kind;             /* SIDM_SIGMA_CONST or SIDM_SIGMA_YUKAWA                           */
   double sigma0;        /* sigma/m, or sigma0/m of sigma0/m / (1 + (v/w)^2)^2 (Sec. 5.2)    */
   double w;             /* velocity scale w of the Yukawa-like law                         */
+  double inelastic;     /* 1 - eps (Sec. 4.1): each scatter leaves the pair's relative speed
+                           at eps times its incoming value and keeps its centre-of-momentum
+                           velocity; 0 = elastic (the paper's runs).  Must be finite and
+                           <= 1 (eps >= 0); eps > 1 adds energy.                            */
 } sidm_sigma_model;
 
 typedef struct {
@@ -217,6 +222,20 @@ SIDM_API int sidm_phase_times(sidm_ctx* ctx, float* ms, int n);
 
 /* Kernels launched by the context so far (all of them are this library's). */
 SIDM_API int64_t sidm_kernel_launches(const sidm_ctx* ctx);
+
+/* Tabulated sigma/m(v) (Sec. 4.1: an arbitrary tabulated function of the
+ * pair's relative velocity, interpolated linearly in log v).  Host arrays of
+ * n nodes (2 <= n <= SIDM_SIGMA_TABLE_MAX): v strictly increasing and > 0,
+ * sigma/m >= 0, all finite; copied.  sigma/m(v) = sigma_0 for v <= v_0,
+ * sigma_{n-1} for v >= v_{n-1}, else sigma_k + t (sigma_{k+1} - sigma_k) with
+ * t = (ln v - ln v_k) / (ln v_{k+1} - ln v_k) on the segment v_k <= v < v_{k+1}.
+ * Used by every halo whose model has kind SIDM_SIGMA_TABLE (sigma0 and w are
+ * then ignored); a step with that kind before a table is set returns
+ * SIDM_ERR_INVALID_ARG.  The logarithm of v in the FP64 evaluation is the
+ * device's; results agree with a host evaluation to the last bits of
+ * sigma/m (draws differ only if u falls within that distance of P). */
+SIDM_API int sidm_set_sigma_table(sidm_ctx* ctx, int32_t n, const double* v,
+                                  const double* sigma_over_m);
 
 /* ---- launch shapes (no counterpart in the paper) ------------------------
  * How the step's kernels are launched.  Every choice gives bit-identical

@@ -69,6 +69,9 @@ struct sidm_ctx {
   double* h_cons = nullptr;
   unsigned* h_latched = nullptr;
   std::vector<void*> allocs;
+  // tabulated sigma/m (one device buffer, see SigmaTable)
+  SigmaTable table{};
+  void* table_mem = nullptr;
   // launch shapes and the captured step
   LaunchTuning tune{};
   uint64_t layout_version = 1;  // bumped whenever buffers, haloes or tuning change
@@ -344,7 +347,9 @@ int wait_and_collect(sidm_ctx* c) {
   return status_from_bits(*c->h_latched);
 }
 
-bool valid_sigma(const sidm_sigma_model& s) {
+bool valid_sigma(const sidm_ctx* c, const sidm_sigma_model& s) {
+  if (!std::isfinite(s.inelastic) || !(s.inelastic <= 1.0)) return false;
+  if (s.kind == SIDM_SIGMA_TABLE) return c->table.n >= 2;
   return (s.sigma0 >= 0.0) && std::isfinite(s.sigma0) &&
          (s.kind == SIDM_SIGMA_CONST || (s.kind == SIDM_SIGMA_YUKAWA && s.w > 0.0 && std::isfinite(s.w)));
 }
@@ -355,6 +360,7 @@ void set_step_params(Halo& h, double dt_max, const sidm_sigma_model& s, uint64_t
   h.sigma_kind = s.kind;
   h.sigma0 = s.sigma0;
   h.w = s.kind == SIDM_SIGMA_YUKAWA ? s.w : 1.0;
+  h.eps = 1.0 - s.inelastic;
   h.seed = seed;
   h.step = (uint32_t)step;
 }
@@ -407,6 +413,7 @@ int launch_core(sidm_ctx* c, bool prof, int64_t* launches) {
     pa.lim_cand = c->lim_cand;
     pa.lim_cnt = c->lim_cnt;
     pa.lim_g = c->lim_g;
+    pa.table = c->table;
     L += launch_pairs(c->so, F, n, c->act_list, c->nb_list, c->nb_count, c->nb_stride, pa,
                       c->pairs, c->dtlim, c->dstats, c->work + 1, c->sms, c->tune, s);
     mark(5);
@@ -663,7 +670,7 @@ int sidm_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins, do
               const sidm_sigma_model* sigma, uint64_t seed, sidm_step_stats* stats) {
   if (!c || !sigma) return SIDM_ERR_INVALID_ARG;
   if (!c->loaded) return SIDM_ERR_NOT_READY;
-  if (!(dt_max > 0.0) || !std::isfinite(dt_max) || !valid_sigma(*sigma)) return SIDM_ERR_INVALID_ARG;
+  if (!(dt_max > 0.0) || !std::isfinite(dt_max) || !valid_sigma(c, *sigma)) return SIDM_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
   for (Halo& h : c->halos) set_step_params(h, dt_max, *sigma, seed, c->step);
   return run_step(c, active_mask, dt_bins, stats);
@@ -675,7 +682,7 @@ int sidm_step_haloes(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_b
   if (!c->loaded) return SIDM_ERR_NOT_READY;
   for (size_t k = 0; k < c->halos.size(); ++k) {
     const sidm_halo_params& p = params[k];
-    if (!(p.dt_max > 0.0) || !std::isfinite(p.dt_max) || !valid_sigma(p.sigma))
+    if (!(p.dt_max > 0.0) || !std::isfinite(p.dt_max) || !valid_sigma(c, p.sigma))
       return SIDM_ERR_INVALID_ARG;
   }
   DeviceGuard g(c->device);
@@ -753,6 +760,62 @@ int time_candidate(sidm_ctx* c, const uint8_t* act, const int8_t* bins, int reps
 
 }  // namespace
 
+int sidm_set_sigma_table(sidm_ctx* c, int32_t n, const double* v, const double* sg) {
+  if (!c || !v || !sg || n < 2 || n > SIDM_SIGMA_TABLE_MAX) return SIDM_ERR_INVALID_ARG;
+  for (int k = 0; k < n; ++k) {
+    if (!std::isfinite(v[k]) || !(v[k] > 0.0) || !std::isfinite(sg[k]) || !(sg[k] >= 0.0))
+      return SIDM_ERR_INVALID_ARG;
+    // nodes must stay distinct after rounding to FP32 (the bounds of the FP32
+    // pass compare them there)
+    if (k > 0 && !(v[k] > v[k - 1] * (1.0 + 0x1p-20))) return SIDM_ERR_INVALID_ARG;
+  }
+  DeviceGuard g(c->device);
+  // layout: v, s, ln v (FP64), then v rounded down / up, s down / up (FP32)
+  std::vector<char> host(n * (3 * sizeof(double) + 4 * sizeof(float)));
+  double* hv = (double*)host.data();
+  double* hs = hv + n;
+  double* hl = hs + n;
+  float* f = (float*)(hl + n);
+  auto rd = [](double x) {
+    float y = (float)x;
+    if ((double)y > x) y = std::nextafter(y, -INFINITY);
+    return y;
+  };
+  auto ru = [](double x) {
+    float y = (float)x;
+    if ((double)y < x) y = std::nextafter(y, INFINITY);
+    return y;
+  };
+  for (int k = 0; k < n; ++k) {
+    hv[k] = v[k];
+    hs[k] = sg[k];
+    hl[k] = std::log(v[k]);
+    f[k] = rd(v[k]);
+    f[n + k] = ru(v[k]);
+    f[2 * n + k] = rd(sg[k]);
+    f[3 * n + k] = ru(sg[k]);
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->table_mem) cudaFree(c->table_mem);
+  c->table_mem = nullptr;
+  c->table = SigmaTable{};
+  void* d = nullptr;
+  CK(cudaMalloc(&d, host.size()));
+  c->table_mem = d;
+  CK(cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice));
+  SigmaTable& T = c->table;
+  T.n = n;
+  T.v = (const double*)d;
+  T.s = T.v + n;
+  T.lnv = T.s + n;
+  T.v_rd = (const float*)(T.lnv + n);
+  T.v_ru = T.v_rd + n;
+  T.s_rd = T.v_ru + n;
+  T.s_ru = T.s_rd + n;
+  ++c->layout_version;  // the captured step holds the old table address
+  return SIDM_OK;
+}
+
 int sidm_set_tuning(sidm_ctx* c, const sidm_tuning* p) {
   if (!c || !p) return SIDM_ERR_INVALID_ARG;
   const LaunchTuning t = from_public(*p);
@@ -780,7 +843,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
   if (!c->loaded) return SIDM_ERR_NOT_READY;
   for (size_t k = 0; k < c->halos.size(); ++k)
     if (!(params[k].dt_max > 0.0) || !std::isfinite(params[k].dt_max) ||
-        !valid_sigma(params[k].sigma))
+        !valid_sigma(c, params[k].sigma))
       return SIDM_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
   const int64_t n = c->n;
@@ -941,6 +1004,7 @@ void sidm_destroy(sidm_ctx* c) {
     if (c->h_stats) cudaFreeHost(c->h_stats);
     if (c->h_cons) cudaFreeHost(c->h_cons);
     if (c->h_latched) cudaFreeHost(c->h_latched);
+    if (c->table_mem) cudaFree(c->table_mem);
     for (int k = 0; k <= SIDM_N_PHASES; ++k)
       if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -75,7 +75,25 @@ __device__ __forceinline__ float shape_f(int kernel, float q) {
   return 2.0f * (u * u * u);
 }
 
-__device__ __forceinline__ float sigma_f(int kind, float s0, float w, float v) {
+// FP32 estimate of a tabulated sigma/m (statistics and the split form)
+__device__ __forceinline__ float table_f(const SigmaTable& T, float v) {
+  const int n = T.n;
+  if (!(v > T.v_rd[0])) return T.s_rd[0];
+  if (v >= T.v_rd[n - 1]) return T.s_rd[n - 1];
+  int lo = 0, hi = n - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (T.v_rd[mid] <= v) lo = mid;
+    else hi = mid;
+  }
+  const float l0 = __log2f(T.v_rd[lo]), l1 = __log2f(T.v_rd[lo + 1]);
+  const float t = fminf(fmaxf((__log2f(v) - l0) / (l1 - l0), 0.0f), 1.0f);
+  return T.s_rd[lo] + t * (T.s_rd[lo + 1] - T.s_rd[lo]);
+}
+
+__device__ __forceinline__ float sigma_f(int kind, float s0, float w, const SigmaTable& T,
+                                         float v) {
+  if (kind == SIDM_SIGMA_TABLE) return table_f(T, v);
   if (kind == SIDM_SIGMA_YUKAWA) {
     const float t = 1.0f + (v * v) / (w * w);
     return s0 / (t * t);
@@ -83,18 +101,52 @@ __device__ __forceinline__ float sigma_f(int kind, float s0, float w, float v) {
   return s0;
 }
 
+// Bounds of a tabulated sigma/m over v in [vl, vu] from node values alone:
+// nodes a..b cover every segment that may hold such a v (a: the last node
+// surely <= vl, b: the first node surely >= vu), and sigma/m on a segment
+// lies between its two node values.
+__device__ __forceinline__ void table_bounds(const SigmaTable& T, float vl, float vu, float* smin,
+                                             float* smax) {
+  const int n = T.n;
+  int a = 0, hi = n;  // a: largest k with v_ru[k] <= vl (0 if none)
+  while (hi - a > 1) {
+    const int mid = (a + hi) >> 1;
+    if (T.v_ru[mid] <= vl) a = mid;
+    else hi = mid;
+  }
+  int lo = -1, b = n - 1;  // b: smallest k with v_rd[k] >= vu (n - 1 if none)
+  while (b - lo > 1) {
+    const int mid = (lo + b) >> 1;
+    if (T.v_rd[mid] >= vu) b = mid;
+    else lo = mid;
+  }
+  if (b < a) b = a;
+  float mn = INFINITY, mx = 0.0f;
+  for (int k = a; k <= b; ++k) {
+    mn = fminf(mn, T.s_rd[k]);
+    mx = fmaxf(mx, T.s_ru[k]);
+  }
+  *smin = mn;
+  *smax = mx;
+}
+
 // g(v) = v sigma/m(v) for v in [vl, vu]: lower and upper bounds.  Constant
 // sigma: g is increasing.  Yukawa-like: g rises up to v = w / sqrt(3) and
-// falls after it.
-__device__ __forceinline__ void g_bounds(int kind, float s0, float w, float vl, float vu,
-                                         float* glo, float* ghi) {
-  if (kind == SIDM_SIGMA_YUKAWA) {
+// falls after it.  Table: v times the node-value bounds.
+__device__ __forceinline__ void g_bounds(int kind, float s0, float w, const SigmaTable& T,
+                                         float vl, float vu, float* glo, float* ghi) {
+  if (kind == SIDM_SIGMA_TABLE) {
+    float smin, smax;
+    table_bounds(T, vl, vu, &smin, &smax);
+    *ghi = __fmul_ru(__fmul_ru(vu, smax), 1.0f + SLACK);
+    *glo = __fmul_rd(__fmul_rd(vl, smin), 1.0f - SLACK);
+  } else if (kind == SIDM_SIGMA_YUKAWA) {
     const float vp = w * 0.57735026918962576f;
-    const float gl = vl * sigma_f(kind, s0, w, vl), gu = vu * sigma_f(kind, s0, w, vu);
+    const float gl = vl * sigma_f(kind, s0, w, T, vl), gu = vu * sigma_f(kind, s0, w, T, vu);
     float hi;
     if (vu <= vp * (1.0f - SLACK)) hi = gu;
     else if (vl >= vp * (1.0f + SLACK)) hi = gl;
-    else hi = vp * sigma_f(kind, s0, w, vp);
+    else hi = vp * sigma_f(kind, s0, w, T, vp);
     *ghi = fmaxf(hi, fmaxf(gl, gu)) * (1.0f + SLACK);
     *glo = fminf(gl, gu) * (1.0f - SLACK);
   } else {
@@ -171,8 +223,8 @@ __device__ __forceinline__ void visit(const PairKArgs& A, const Query& Q, int64_
     const float vmax_j = fmaxf(fmaxf(fabsf(vmj.x), fabsf(vmj.y)), fabsf(vmj.z));
     const float dv = 4.0f * U * (3.0f * (Q.vmax_i + vmax_j) + vr) + 4.0f * U * vr;
     const float vl = fmaxf(vr - dv, 0.0f), vu = vr + dv;
-    g_bounds(Q.kind, Q.s0f, Q.wf, vl, vu, &glo, &ghi);
-    const float gest = vr * sigma_f(Q.kind, Q.s0f, Q.wf, vr);
+    g_bounds(Q.kind, Q.s0f, Q.wf, P.table, vl, vu, &glo, &ghi);
+    const float gest = vr * sigma_f(Q.kind, Q.s0f, Q.wf, P.table, vr);
     if (P.split) glo = ghi = gest;
     // does j see i?  (j active and r^2 < h_j^2: decided exactly, or in FP32
     // by the split form, as its neighbour lists are)
@@ -272,7 +324,7 @@ __device__ __forceinline__ double exact_g(const PairKArgs& A, int64_t s, int64_t
   const double ddx = so.vx[s] - so.vx[j], ddy = so.vy[s] - so.vy[j], ddz = so.vz[s] - so.vz[j];
   const double vrel = sqrt((ddx * ddx + ddy * ddy) + ddz * ddz);
   const Halo& H = A.f.halos[so.halo[s]];
-  return vrel * sigma_over_m(H.sigma_kind, H.sigma0, H.w, vrel);
+  return vrel * sigma_over_m(H.sigma_kind, H.sigma0, H.w, A.a.table, vrel);
 }
 
 // Eq. 18: dt_lim,i = 2 C_SIDM / (m_i W(0, h_i) (v sigma/m)_max,i)
@@ -462,7 +514,7 @@ __global__ void __launch_bounds__(XT) pairs_exact_kernel(PairKArgs A) {
       const double ddx = so.vx[s] - so.vx[j], ddy = so.vy[s] - so.vy[j],
                    ddz = so.vz[s] - so.vz[j];
       const double vrel = sqrt((ddx * ddx + ddy * ddy) + ddz * ddz);
-      const double sg = sigma_over_m(H.sigma_kind, H.sigma0, H.w, vrel);
+      const double sg = sigma_over_m(H.sigma_kind, H.sigma0, H.w, P.table, vrel);
       const double hi = so.h[s];
       const double qq = sqrt(r2) / hi;
       const double p_i = ((((0.5 * so.m[j]) * sg) * vrel) * (kernel_norm(kern, hi) *

@@ -40,12 +40,13 @@ __device__ bool first_at(int64_t p, const PairRec& rp, int32_t e, const int32_t*
   return true;
 }
 
-// The elastic kick of Eqs. 12-13 (eps = 1) in the operation order
-//   v_com = ((m_a v_a) + (m_b v_b)) / M,  g = sqrt((dx dx + dy dy) + dz dz),
+// The kick of Eqs. 12-13 in the operation order
+//   v_com = ((m_a v_a) + (m_b v_b)) / M,  g = sqrt((dx dx + dy dy) + dz dz) eps,
 //   v_a' = v_com + ((m_b g) / M) e,  v_b' = v_com - ((m_a g) / M) e,
-// with M = m_a + m_b; every operation rounds once (no contraction).
-__device__ __forceinline__ void kick_values(double ma, double mb, const double* e, double* a,
-                                            double* b) {
+// with M = m_a + m_b and eps the outgoing / incoming relative speed (1:
+// elastic; the product with 1 is exact); every operation rounds once.
+__device__ __forceinline__ void kick_values(double ma, double mb, double eps, const double* e,
+                                            double* a, double* b) {
   const double M = ma + mb;
   double c[3], d[3];
 #pragma unroll
@@ -53,7 +54,7 @@ __device__ __forceinline__ void kick_values(double ma, double mb, const double* 
     c[k] = ((ma * a[k]) + (mb * b[k])) / M;
     d[k] = a[k] - b[k];
   }
-  const double g = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+  const double g = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) * eps;
   const double fa = (mb * g) / M, fb = (ma * g) / M;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -63,7 +64,7 @@ __device__ __forceinline__ void kick_values(double ma, double mb, const double* 
 }
 
 __device__ void kick(const PairRec& r, double* vel, const double* mass, uint32_t k0, uint32_t k1,
-                     uint32_t step, unsigned* dirfail) {
+                     uint32_t step, double eps, unsigned* dirfail) {
   double e0 = 0.0, e1 = 0.0, e2 = 1.0;
   bool found = false;
   for (uint32_t t = 0; t < DIRECTION_TRIES && !found; ++t) {
@@ -85,7 +86,7 @@ __device__ void kick(const PairRec& r, double* vel, const double* mass, uint32_t
   const double ma = mass[r.ia], mb = mass[r.ib];
   const double e[3] = {e0, e1, e2};
   double a[3] = {va[0], va[1], va[2]}, b[3] = {vb[0], vb[1], vb[2]};
-  kick_values(ma, mb, e, a, b);
+  kick_values(ma, mb, eps, e, a, b);
   va[0] = a[0];
   va[1] = a[1];
   va[2] = a[2];
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(RT) resolve_kernel(const PairRec* __restrict__
     if (!__syncthreads_or(left)) { done = true; break; }
     for (int64_t p = t; p < na; p += RT) {
       if (flags[p] == 2) {
-        kick(pairs[p], vel, mass, k0, k1, step, &s_dirfail);
+        kick(pairs[p], vel, mass, k0, k1, step, 1.0, &s_dirfail);
         flags[p] = 1;
       }
     }
@@ -233,12 +234,12 @@ __device__ __forceinline__ void pair_direction(const PairRec& r, uint32_t k0, ui
 // The kick of a pending pair with direction e, the velocities read and
 // written through L2 (other SMs apply the neighbouring kicks).
 __device__ __forceinline__ void kick_l2(const PairRec& r, double* vel, double ma, double mb,
-                                        const double* e) {
+                                        double eps, const double* e) {
   double* va = vel + 3 * (int64_t)r.ia;
   double* vb = vel + 3 * (int64_t)r.ib;
   double a[3] = {__ldcg(va), __ldcg(va + 1), __ldcg(va + 2)};
   double b[3] = {__ldcg(vb), __ldcg(vb + 1), __ldcg(vb + 2)};
-  kick_values(ma, mb, e, a, b);
+  kick_values(ma, mb, eps, e, a, b);
   __stcg(va, a[0]);
   __stcg(va + 1, a[1]);
   __stcg(va + 2, a[2]);
@@ -312,7 +313,8 @@ __global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ p
         mm = max(mm, max(ma, mb));
         if (ma == 1 && mb == 1) {
           const Halo& H = halos[halo_of[r.ia]];
-          kick(r, vel, mass, (uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, &s_dirfail);
+          kick(r, vel, mass, (uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, H.eps,
+               &s_dirfail);
         } else {
           pend = true;
           b.flags[p] = 0;
@@ -395,7 +397,7 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
     bool first = t0 < np;
     PairRec r0{};
     int pa0 = 0, pb0 = 0;
-    double ma0 = 0.0, mb0 = 0.0, e0[3];
+    double ma0 = 0.0, mb0 = 0.0, eps0 = 1.0, e0[3];
     if (first) {
       const int32_t p = b.pending[t0];
       r0 = pairs[p];
@@ -404,6 +406,7 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
       ma0 = mass[r0.ia];
       mb0 = mass[r0.ib];
       const Halo& H = halos[halo_of[r0.ia]];
+      eps0 = H.eps;
       pair_direction(r0, (uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, e0, &s_dirfail);
     }
     int pass = 0;
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
         const int cb = ld_relaxed(&b.cursor[r0.ib]);
         if (ca == pa0 && cb == pb0) {
           fence_acq_rel();
-          kick_l2(r0, vel, ma0, mb0, e0);
+          kick_l2(r0, vel, ma0, mb0, eps0, e0);
           fence_acq_rel();
           st_release(&b.cursor[r0.ia], pa0 + 1);
           st_release(&b.cursor[r0.ib], pb0 + 1);
@@ -437,7 +440,7 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
           const Halo& H = halos[halo_of[r.ia]];
           double e[3];
           pair_direction(r, (uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, e, &s_dirfail);
-          kick_l2(r, vel, mass[r.ia], mass[r.ib], e);
+          kick_l2(r, vel, mass[r.ia], mass[r.ib], H.eps, e);
           fence_acq_rel();
           st_release(&b.cursor[r.ia], pa + 1);
           st_release(&b.cursor[r.ib], pb + 1);

@@ -50,6 +50,7 @@ struct Halo {
   int32_t e0;                       // start radius h0 = l_ext 2^-e0 (8^e0 N_ngb <= 4 n)
   // per step (host)
   double dt_max, sigma0, w;
+  double eps;                       // outgoing / incoming relative speed of a scatter
   int32_t sigma_kind;
   uint32_t step;                    // Philox counter word 0
   uint64_t seed;                    // Philox key
@@ -141,7 +142,38 @@ __device__ __forceinline__ double kernel_shape(int kernel, double q) {
   return 2.0 * ((u * u) * u);
 }
 
-__device__ __forceinline__ double sigma_over_m(int kind, double s0, double w, double v) {
+// Tabulated sigma/m(v) on the device: FP64 nodes, values and logarithms of
+// the nodes (taken on the host), and FP32 copies rounded down / up for the
+// bounds of the FP32 pass.
+struct SigmaTable {
+  int32_t n;
+  const double* v;
+  const double* s;
+  const double* lnv;
+  const float* v_rd;
+  const float* v_ru;
+  const float* s_rd;
+  const float* s_ru;
+};
+
+// Linear in log v between nodes, held at the end values (Sec. 4.1).
+__device__ __forceinline__ double sigma_table(const SigmaTable& T, double v) {
+  const int n = T.n;
+  if (!(v > T.v[0])) return T.s[0];
+  if (v >= T.v[n - 1]) return T.s[n - 1];
+  int lo = 0, hi = n - 1;  // v_lo <= v < v_hi
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (T.v[mid] <= v) lo = mid;
+    else hi = mid;
+  }
+  const double t = (log(v) - T.lnv[lo]) / (T.lnv[lo + 1] - T.lnv[lo]);
+  return T.s[lo] + t * (T.s[lo + 1] - T.s[lo]);
+}
+
+__device__ __forceinline__ double sigma_over_m(int kind, double s0, double w, const SigmaTable& T,
+                                               double v) {
+  if (kind == SIDM_SIGMA_TABLE) return sigma_table(T, v);
   if (kind == SIDM_SIGMA_YUKAWA) {
     const double t = 1.0 + (v * v) / (w * w);
     return s0 / (t * t);
@@ -292,6 +324,7 @@ struct PairArgs {
   int32_t* lim_cand;  // [n][LIM_CAND] neighbours that may give the Eq. 18 maximum
   int32_t* lim_cnt;   // [n] their number, -1: more than LIM_CAND (scan the whole list)
   float* lim_g;       // [n] largest FP32 lower bound of v sigma/m (split form: the maximum)
+  SigmaTable table;   // tabulated sigma/m (kind SIDM_SIGMA_TABLE)
 };
 int launch_pairs(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
                  const int32_t* nb_list, const int32_t* nb_count, int nb_stride,

@@ -21,7 +21,8 @@ from . import build as _build
 HOST, DEVICE = 0, 1
 KERNEL_CUBIC, KERNEL_TOPHAT = 0, 1
 FP64_PLAIN, FP32_SPLIT = 0, 1
-SIGMA_CONST, SIGMA_YUKAWA = 0, 1
+SIGMA_CONST, SIGMA_YUKAWA, SIGMA_TABLE = 0, 1, 2
+SIGMA_TABLE_MAX = 256
 
 OK = 0
 WARN_H_NOT_CONVERGED, WARN_P_GE_1, WARN_DIRECTION = 1, 2, 4
@@ -56,7 +57,8 @@ class Tuning(C.Structure):
 
 
 class SigmaModel(C.Structure):
-    _fields_ = [("kind", C.c_int), ("sigma0", C.c_double), ("w", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("sigma0", C.c_double), ("w", C.c_double),
+                ("inelastic", C.c_double)]
 
 
 class HaloParams(C.Structure):
@@ -86,7 +88,8 @@ ENTRY_POINTS = ("sidm_default_config", "sidm_create", "sidm_set_particles",
                 "sidm_timestep_limits", "sidm_get_pairs", "sidm_get_step", "sidm_set_step",
                 "sidm_phase_times", "sidm_kernel_launches", "sidm_error_string", "sidm_destroy",
                 "sidm_apply_pairs_noalloc", "sidm_set_haloes", "sidm_step_haloes",
-                "sidm_set_tuning", "sidm_get_tuning", "sidm_autotune", "sidm_graph_state")
+                "sidm_set_tuning", "sidm_get_tuning", "sidm_autotune", "sidm_graph_state",
+                "sidm_set_sigma_table")
 
 N_PHASES = 6
 PHASES = ("keys", "sort", "structure", "search", "pairs", "resolve")
@@ -140,6 +143,7 @@ def lib():
         L.sidm_autotune.argtypes = [vp, vp, vp, C.POINTER(HaloParams), C.c_int,
                                     C.POINTER(Tuning)]
         L.sidm_graph_state.argtypes = [vp]
+        L.sidm_set_sigma_table.argtypes = [vp, C.c_int32, vp, vp]
         for name in ENTRY_POINTS:
             fn = getattr(L, name)
             if name not in ("sidm_default_config", "sidm_error_string", "sidm_destroy"):
@@ -237,6 +241,15 @@ def sidm_autotune(ctx, active_mask, dt_bins, params, reps=3) -> Tuning:
     _check(lib().sidm_autotune(ctx, _ptr(active_mask)[0], _ptr(dt_bins)[0], arr, int(reps),
                                C.byref(t)), "sidm_autotune")
     return t
+
+
+def sidm_set_sigma_table(ctx, v, sigma_over_m) -> int:
+    v = np.ascontiguousarray(v, np.float64)
+    s = np.ascontiguousarray(sigma_over_m, np.float64)
+    if v.shape != s.shape:
+        raise ValueError("table arrays differ in length")
+    return _check(lib().sidm_set_sigma_table(ctx, int(v.shape[0]), v.ctypes.data, s.ctypes.data),
+                  "sidm_set_sigma_table")
 
 
 def sidm_graph_state(ctx) -> int:
@@ -353,12 +366,12 @@ class Context:
         sidm_set_velocities(self.handle, vel)
 
     def step(self, dt_max, active=None, bins=None, sigma0=1.0, sigma_kind=SIGMA_CONST, w=1.0,
-             seed=0, stats=True):
+             seed=0, stats=True, inelastic=0.0):
         if isinstance(active, np.ndarray):
             active = np.ascontiguousarray(active, np.uint8)
         if isinstance(bins, np.ndarray):
             bins = np.ascontiguousarray(bins, np.int8)
-        sg = SigmaModel(int(sigma_kind), float(sigma0), float(w))
+        sg = SigmaModel(int(sigma_kind), float(sigma0), float(w), float(inelastic))
         st = StepStats() if stats else None
         status = sidm_step(self.handle, active, bins, dt_max, sg, seed, st)
         if st is not None:
@@ -382,7 +395,8 @@ class Context:
         hp = [p if isinstance(p, HaloParams) else
               HaloParams(float(p["dt_max"]), SigmaModel(int(p.get("sigma_kind", 0)),
                                                           float(p.get("sigma0", 1.0)),
-                                                          float(p.get("w", 1.0))),
+                                                          float(p.get("w", 1.0)),
+                                                          float(p.get("inelastic", 0.0))),
                          int(p.get("seed", 0)), int(p.get("step", 0))) for p in params]
         st = StepStats() if stats else None
         status = sidm_step_haloes(self.handle, active, bins, hp, st)
@@ -413,6 +427,11 @@ class Context:
         if isinstance(bins, np.ndarray):
             bins = np.ascontiguousarray(bins, np.int8)
         return sidm_autotune(self.handle, active, bins, params, reps).as_dict()
+
+    def set_sigma_table(self, v, sigma_over_m):
+        """Tabulated sigma/m(v) for models of kind SIGMA_TABLE (linear in log v
+        between nodes, held at the ends)."""
+        sidm_set_sigma_table(self.handle, v, sigma_over_m)
 
     @property
     def graph_state(self) -> int:

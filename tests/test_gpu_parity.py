@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 
 def _gpu_step(ctx, p, act, bins, dt_max, **kw):
     st = ctx.step(dt_max, act, bins, sigma0=kw.get("sigma0", 1.0),
-                  sigma_kind=kw.get("sigma_kind", 0), w=kw.get("w", 1.0), seed=kw.get("seed", 0))
+                  sigma_kind=kw.get("sigma_kind", 0), w=kw.get("w", 1.0), seed=kw.get("seed", 0),
+                  inelastic=kw.get("inelastic", 0.0))
     v, h = ctx.velocities()
     return {"vel": v, "h": h, "dtlim": ctx.timestep_limits(), "pairs": ctx.pairs(), "stats": st}
 
@@ -51,7 +52,7 @@ def _compare(g, o, act, what=""):
 
 def run_pair(p, act, bins, dt_max, *, n_ngb=32, ngb_tol=5, kernel=0, fixed_h=0.0, steps=1,
              seed=0, sigma_kind=0, sigma0=1.0, w=1.0, c_sidm=0.1, device_inputs=False,
-             pair_capacity=0):
+             pair_capacity=0, inelastic=0.0):
     ctx = sidm.Context(n_ngb=n_ngb, ngb_tol=ngb_tol, c_sidm=c_sidm, box=p.box, kernel=kernel,
                        fixed_h=fixed_h, pair_capacity=pair_capacity)
     if device_inputs:
@@ -68,9 +69,10 @@ def run_pair(p, act, bins, dt_max, *, n_ngb=32, ngb_tol=5, kernel=0, fixed_h=0.0
         a = act(k) if callable(act) else act
         o = oracle.step(p.pos, vel, p.mass, p.ids, a, bins, dt_max, n_ngb=n_ngb, ngb_tol=ngb_tol,
                         c_sidm=c_sidm, box=p.box, kernel=kernel, fixed_h=fixed_h,
-                        sigma_kind=sigma_kind, sigma0=sigma0, w=w, seed=seed, step=k,
-                        h_init=h, dtlim_init=dl)
-        g = _gpu_step(ctx, p, a, bins, dt_max, sigma_kind=sigma_kind, sigma0=sigma0, w=w, seed=seed)
+                        sigma_kind=sigma_kind, sigma0=sigma0, w=w, inelastic=inelastic,
+                        seed=seed, step=k, h_init=h, dtlim_init=dl)
+        g = _gpu_step(ctx, p, a, bins, dt_max, sigma_kind=sigma_kind, sigma0=sigma0, w=w, seed=seed,
+                      inelastic=inelastic)
         _compare(g, o, a, f"step {k}")
         vel, h, dl = o["vel"], o["h"], o["dtlim"]
         # outputs of inactive particles keep their previous values
@@ -83,6 +85,18 @@ def test_box_small_all_active():
     p = I.uniform_box(4096, 1.0, 1.0, 3)
     g, o = run_pair(p, None, np.zeros(p.n, np.int8), 0.05)
     assert o["n_pairs"] > 50
+
+
+@pytest.mark.parametrize("inelastic", [0.5, 1.0])
+def test_inelastic_scatters_match_the_oracle(inelastic):
+    """eps = 1 - inelastic < 1 (Sec. 4.1): same pairs, bit-identical velocities
+    over several steps (eps = 0: the pair leaves at its centre-of-momentum
+    velocity)."""
+    p = I.uniform_box(5000, 1.0, 1.0, 17, ids="random")
+    bins = np.zeros(p.n, np.int8)
+    g, o = run_pair(p, None, bins, 0.15, steps=3, seed=4, inelastic=inelastic)
+    assert o["n_pairs"] > 100
+    assert g["stats"]["e_after"] < g["stats"]["e_before"]
 
 
 def test_box_32cubed_workload():
@@ -228,3 +242,56 @@ def test_hernquist_2pow20_full_size(hernquist_full, s):
                     step=s)
     g = _gpu_step(ctx, p, act, bins, w["dt_max"], seed=w["seed"])
     _compare(g, o, act, f"hernquist step {s}")
+
+
+def test_tabulated_cross_section_matches_the_oracle():
+    """Tabulated sigma/m(v), linear in log v (Sec. 4.1), on a halo with
+    partial activity: h, accepted pairs and velocities equal the oracle's;
+    the Eq. 18 limits agree to the last bits (the device and the host take
+    their own logarithm of v)."""
+    p = I.hernquist_halo(20000, 8, ids="random")
+    rng = np.random.default_rng(9)
+    tv = np.sort(10 ** rng.uniform(-2.0, 1.0, 16))
+    ts = 10 ** rng.uniform(-1.0, 1.0, 16)
+    bins = rng.integers(0, 4, p.n).astype(np.int8)
+    ctx = sidm.Context(n_ngb=32, box=0.0)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    ctx.set_sigma_table(tv, ts)
+    vel, h, dl = p.vel.copy(), np.zeros(p.n), np.full(p.n, np.inf)
+    total = 0
+    for k in range(3):
+        act = I.active_at_step(bins, k)
+        o = oracle.step(p.pos, vel, p.mass, p.ids, act, bins, 2.0, n_ngb=32, sigma_kind=2,
+                        table=(tv, ts), seed=12, step=k, h_init=h, dtlim_init=dl)
+        st = ctx.step(2.0, act, bins, sigma_kind=sidm.SIGMA_TABLE, seed=12)
+        gv, gh = ctx.velocities()
+        ab, ords = ctx.pairs()
+        assert np.array_equal(gh, o["h"])
+        assert np.array_equal(ab, o["pairs_ab"][: o["n_pairs"]])
+        assert np.array_equal(ords, o["pairs_ord"][: o["n_pairs"]])
+        assert np.array_equal(gv, o["vel"])
+        gl = ctx.timestep_limits()
+        fin = np.isfinite(o["dtlim"])
+        assert np.array_equal(np.isfinite(gl), fin)
+        assert np.allclose(gl[fin], o["dtlim"][fin], rtol=1e-14, atol=0)
+        assert st["n_accepted"] == o["n_pairs"]
+        total += o["n_pairs"]
+        vel, h, dl = o["vel"], o["h"], o["dtlim"]
+    assert total > 200
+    ctx.close()
+
+
+def test_sigma_table_validation():
+    ctx = sidm.Context()
+    p = I.uniform_box(500, 1.0, 1.0, 1)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    with pytest.raises(sidm.SidmError):      # no table yet
+        ctx.step(0.1, sigma_kind=sidm.SIGMA_TABLE)
+    for v, s in (([1.0], [1.0]), ([1.0, 1.0], [1.0, 2.0]), ([2.0, 1.0], [1.0, 1.0]),
+                 ([0.0, 1.0], [1.0, 1.0]), ([1.0, 2.0], [1.0, -1.0]),
+                 ([1.0, 1.0 + 1e-9], [1.0, 1.0])):
+        with pytest.raises(sidm.SidmError):
+            ctx.set_sigma_table(np.array(v), np.array(s))
+    ctx.set_sigma_table(np.array([0.5, 2.0]), np.array([1.0, 3.0]))
+    ctx.step(0.1, sigma_kind=sidm.SIGMA_TABLE, stats=False)
+    ctx.close()

@@ -75,3 +75,60 @@ def test_mono_speed_box_relaxes_to_maxwell_boltzmann(sigma_kind):
     # (the Yukawa-like law scatters the fast tail ~100x less, so it relaxes
     # more slowly; the paper compares that case with a kinetic solver)
     assert d_end < d_one / 3.0
+
+
+@pytest.mark.parametrize("c_sidm", [0.1, 1.0, 5.0])
+def test_timestep_from_the_criterion_alone(c_sidm):
+    """The paper's C_SIDM scan of this test (Sec. 5.2): no external maximum
+    timestep, so the Eq. 18 limits alone set dt (here one global
+    power-of-two step, the finest any particle needs).  With N_ngb = 32 the
+    criterion's step is about 3.9 C_SIDM collision times, so C_SIDM = 5
+    takes steps of 16 collision times; a pair scatters at most once per step,
+    so such steps scatter less than their length suggests, and the run takes
+    at least three of them.  The speeds end at the MB spread (and, for
+    C_SIDM <= 1, pass a KS test against MB), with energy and momentum
+    conserved to round-off."""
+    n, v0, L = 10000, 1.0, 1.0
+    p = I.mono_speed_box(n, L, v0, seed=7)
+    tau = math.sqrt(3.0 * math.pi) / (4.0 * v0 * 1.0 * 1.0)
+    dt_max = 64.0 * tau
+    ctx = sidm.Context(n_ngb=32, box=L, c_sidm=c_sidm, pair_capacity=60 * n)
+    pos, vel = p.pos.copy(), p.vel.copy()
+    ctx.set_particles(pos, vel, p.ids, mass=p.mass)
+    e0 = 0.5 * (p.mass * (vel ** 2).sum(1)).sum()
+    p0 = (p.mass[:, None] * vel).sum(0)
+    b = 12                               # bootstrap step (dt = dt_max / 4096) gives the limits
+    t, steps, p_ge_1 = 0.0, 0, 0
+    while t < 8.0 * tau or steps < 4:   # the bootstrap step and at least 3 more
+        dt = math.ldexp(dt_max, -b)
+        st = ctx.step(dt_max, None, np.full(n, b, np.int8), seed=13, stats=True)
+        p_ge_1 += st["n_p_ge_1"]
+        vel, _ = ctx.velocities()
+        lim = ctx.timestep_limits()          # Eq. 18, from this step's velocities
+        pos = np.mod(pos + vel * dt, L)
+        pos[pos >= L] = 0.0
+        ctx.set_particles(pos, vel, p.ids, mass=p.mass)
+        steps += 1
+        ctx.step_counter = steps
+        t += dt
+        # next step: the finest bin b with dt_max 2^-b below every limit
+        assert np.all(np.isfinite(lim)) and lim.min() > 0.0
+        need = np.ceil(np.log2(dt_max / lim.min()))
+        b = int(max(0, need if math.ldexp(dt_max, -int(need)) < lim.min() else need + 1))
+    ctx.close()
+    e1 = 0.5 * (p.mass * (vel ** 2).sum(1)).sum()
+    p1 = (p.mass[:, None] * vel).sum(0)
+    assert abs(e1 - e0) <= 1e-11 * e0
+    assert np.max(np.abs(p1 - p0)) <= 1e-13 * (p.mass[:, None] * np.abs(vel)).sum()
+    sp = np.linalg.norm(vel, axis=1)
+    ks = stats.kstest(sp, lambda x: np.array(_mb_cdf(np.atleast_1d(x), v0)))
+    # MB with <v^2> = v0^2 has var|v| = v0^2 (1 - 8 / (3 pi)); the mono-speed start has 0
+    var_mb = v0 ** 2 * (1.0 - 8.0 / (3.0 * math.pi))
+    assert abs(np.var(sp) / var_mb - 1.0) < 0.05, (c_sidm, steps, np.var(sp) / var_mb)
+    assert ks.statistic < 0.05, (c_sidm, steps, ks)
+    if c_sidm <= 1.0:
+        # up to a step of about 4 collision times the speeds pass as MB
+        assert ks.pvalue > 1e-3, (c_sidm, steps, ks)
+    # the criterion's step is about 3.9 C_SIDM collision times (Sec. 4.4 with
+    # N_ngb = 32 and the mono-speed v_max = 2 v0), rounded down to a power of two
+    assert steps <= int(8.0 / (0.1 * c_sidm)) + 4
