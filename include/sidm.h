@@ -96,6 +96,13 @@ typedef struct {
                            and replay it while the particle count, the halo layout and the
                            launch shapes stay the same (results are unchanged); 0: direct
                            launches.  Ignored while `profile` is set.                      */
+  int rebuild_every;    /* k > 1: the spatial keys are recomputed and sorted only every k
+                           steps (and after any change of particle count or halo layout);
+                           the steps in between keep that key order and refit the tree's
+                           boxes to the current positions (the paper rebuilds its tree only
+                           at domain decompositions, Sec. 4.3).  Results are unchanged; the
+                           search slows as particles drift from their key order.  0 or 1:
+                           every step (the default).                                        */
 } sidm_config;
 
 /* Fills `cfg` with the paper's fiducial values (N_ngb 32 +- 5, C_SIDM 0.1,

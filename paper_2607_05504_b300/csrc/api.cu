@@ -75,10 +75,14 @@ struct sidm_ctx {
   // launch shapes and the captured step
   LaunchTuning tune{};
   uint64_t layout_version = 1;  // bumped whenever buffers, haloes or tuning change
-  cudaGraphExec_t graph_exec = nullptr;
-  uint64_t graph_version = 0;   // layout the graph was captured for
-  int64_t graph_launches = 0;   // kernels in the graph
+  // captured steps: [0] refit only, [1] full rebuild (keys + sort)
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  uint64_t graph_version[2] = {0, 0};  // layout each graph was captured for
+  int64_t graph_launches[2] = {0, 0};  // kernels in each graph
   int graph_state = 0;          // 0 off, 1 captured, -1 capture refused (direct launches)
+  // key order kept between full rebuilds
+  uint64_t order_version = 0;   // layout of the last full rebuild
+  int64_t since_rebuild = 0;    // steps since it
   // instrumentation
   int64_t launches = 0;
   cudaEvent_t ev[SIDM_N_PHASES + 1] = {};
@@ -123,9 +127,11 @@ cudaError_t dalloc(sidm_ctx* c, T** p, size_t count) {
 }
 
 void drop_graph(sidm_ctx* c) {
-  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-  c->graph_exec = nullptr;
-  c->graph_version = 0;
+  for (int k = 0; k < 2; ++k) {
+    if (c->graph_exec[k]) cudaGraphExecDestroy(c->graph_exec[k]);
+    c->graph_exec[k] = nullptr;
+    c->graph_version[k] = 0;
+  }
 }
 
 void free_buffers(sidm_ctx* c) {
@@ -258,7 +264,11 @@ int start_exponent(int64_t n, int n_ngb) {
 // Halo layout from segment offsets (host): particle ranges, tree levels and
 // node offsets (level-major), start-radius exponents; fills halo_of.
 int layout_haloes(sidm_ctx* c, int n_halos, const int64_t* off) {
-  ++c->layout_version;
+  // a new layout (particle ranges) invalidates the key order and the captured steps
+  bool same = (int)c->halos.size() == n_halos;
+  for (int k = 0; same && k < n_halos; ++k)
+    same = c->halos[k].start == off[k] && c->halos[k].n == off[k + 1] - off[k];
+  if (!same) ++c->layout_version;
   std::vector<Halo>& H = c->halos;
   H.assign(n_halos, Halo{});
   Forest& f = c->forest;
@@ -371,7 +381,7 @@ void set_step_params(Halo& h, double dt_max, const sidm_sigma_model& s, uint64_t
 // copies and the halo table upload come before), so the sequence can be
 // captured once into a CUDA graph and replayed while the particle count,
 // the halo layout, the buffers and the launch shapes stay the same.
-int launch_core(sidm_ctx* c, bool prof, int64_t* launches) {
+int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches) {
   const int64_t n = c->n;
   cudaStream_t s = c->stream;
   CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), s));
@@ -386,12 +396,15 @@ int launch_core(sidm_ctx* c, bool prof, int64_t* launches) {
     mark(0);
     L += launch_bbox(c->pos, c->halo_of, n, c->d_halos, nh, s);
     L += launch_params(c->d_halos, nh, c->cfg.box, s);
-    L += launch_keys(c->pos, c->halo_of, n, c->d_halos, F.halo_bits, c->cfg.box, c->keys,
-                     c->vals, s);
+    if (rebuild)
+      L += launch_keys(c->pos, c->halo_of, n, c->d_halos, F.halo_bits, c->cfg.box, c->keys,
+                       c->vals, s);
     mark(1);
-    const int mb = (30 - F.halo_bits) / 3;
-    L += radix_sort_pairs(c->keys, c->vals, c->keys_alt, c->vals_alt, n, F.halo_bits + 3 * mb,
-                          c->sort_tmp, s);
+    if (rebuild) {
+      const int mb = (30 - F.halo_bits) / 3;
+      L += radix_sort_pairs(c->keys, c->vals, c->keys_alt, c->vals_alt, n,
+                            F.halo_bits + 3 * mb, c->sort_tmp, s);
+    }
     mark(2);
     L += launch_permute(c->vals, n, c->pos, c->vel, c->mass, c->ids, c->halo_of, c->act,
                         c->bins, c->d_halos, c->so, c->act_list, c->dstats, s);
@@ -431,8 +444,9 @@ int launch_core(sidm_ctx* c, bool prof, int64_t* launches) {
 
 // Captures launch_core into a graph; a capture the driver refuses leaves the
 // context on direct launches (graph_state -1).
-void capture_core(sidm_ctx* c) {
-  drop_graph(c);
+void capture_core(sidm_ctx* c, int rebuild) {
+  if (c->graph_exec[rebuild]) cudaGraphExecDestroy(c->graph_exec[rebuild]);
+  c->graph_exec[rebuild] = nullptr;
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
@@ -440,7 +454,7 @@ void capture_core(sidm_ctx* c) {
     return;
   }
   int64_t k = 0;
-  const int r = launch_core(c, false, &k);
+  const int r = launch_core(c, false, rebuild != 0, &k);
   const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   if (r != SIDM_OK || e != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
@@ -448,16 +462,16 @@ void capture_core(sidm_ctx* c) {
     c->graph_state = -1;
     return;
   }
-  const cudaError_t ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
+  const cudaError_t ei = cudaGraphInstantiate(&c->graph_exec[rebuild], g, 0);
   cudaGraphDestroy(g);
   if (ei != cudaSuccess) {
-    c->graph_exec = nullptr;
+    c->graph_exec[rebuild] = nullptr;
     cudaGetLastError();
     c->graph_state = -1;
     return;
   }
-  c->graph_version = c->layout_version;
-  c->graph_launches = k;
+  c->graph_version[rebuild] = c->layout_version;
+  c->graph_launches[rebuild] = k;
   c->graph_state = 1;
 }
 
@@ -484,20 +498,30 @@ int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
   if (stats) L += launch_conserved(c->vel, c->mass, n, c->cons_partial, c->cons, s);
   const bool prof = c->have_events && n > 0;
   c->timed_step = prof;
+  // full rebuild (keys + sort) or a refit in the key order of the last one
+  const int rebuild = (c->cfg.rebuild_every <= 1 || c->order_version != c->layout_version ||
+                       c->since_rebuild >= c->cfg.rebuild_every) ? 1 : 0;
   bool done = false;
   if (c->cfg.use_graph && !prof && n > 0 && c->graph_state >= 0) {
-    if (!c->graph_exec || c->graph_version != c->layout_version) capture_core(c);
-    if (c->graph_exec) {
-      CK(cudaGraphLaunch(c->graph_exec, s));
-      L += c->graph_launches;
+    if (!c->graph_exec[rebuild] || c->graph_version[rebuild] != c->layout_version)
+      capture_core(c, rebuild);
+    if (c->graph_exec[rebuild]) {
+      CK(cudaGraphLaunch(c->graph_exec[rebuild], s));
+      L += c->graph_launches[rebuild];
       done = true;
     }
   }
   if (!done) {
     int64_t k = 0;
-    const int r = launch_core(c, prof, &k);
+    const int r = launch_core(c, prof, rebuild != 0, &k);
     L += k;
     if (r != SIDM_OK) return r;
+  }
+  if (rebuild) {
+    c->order_version = c->layout_version;
+    c->since_rebuild = 1;
+  } else {
+    ++c->since_rebuild;
   }
   CK(cudaGetLastError());
   c->step += 1;
@@ -557,7 +581,7 @@ int sidm_create(const sidm_config* cfg, sidm_ctx** out) {
       !std::isfinite(cfg->box) || (cfg->kernel != SIDM_KERNEL_CUBIC && cfg->kernel != SIDM_KERNEL_TOPHAT) ||
       (cfg->precision != SIDM_FP64_PLAIN && cfg->precision != SIDM_FP32_SPLIT) ||
       !(cfg->fixed_h >= 0.0) || cfg->n_max < 0 ||
-      cfg->pair_capacity < 0)
+      cfg->pair_capacity < 0 || cfg->rebuild_every < 0)
     return SIDM_ERR_INVALID_ARG;
   sidm_ctx* c = new (std::nothrow) sidm_ctx();
   if (!c) return SIDM_ERR_OOM;
@@ -859,8 +883,11 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
   CK(cudaMalloc(&save, 5 * n * sizeof(double)));
   double *v0 = save, *h0 = save + 3 * n, *d0 = save + 4 * n;
   const uint64_t step0 = c->step;
-  const int use_graph = c->cfg.use_graph;
-  c->cfg.use_graph = 0;  // candidates launch directly
+  const int64_t since0 = c->since_rebuild;
+  const uint64_t order0 = c->order_version;
+  const int use_graph = c->cfg.use_graph, rebuild_every = c->cfg.rebuild_every;
+  c->cfg.use_graph = 0;      // candidates launch directly
+  c->cfg.rebuild_every = 0;  // and rebuild fully, like the steps they stand for
   int rc = SIDM_OK;
   if (cudaMemcpyAsync(v0, c->vel, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) !=
           cudaSuccess ||
@@ -900,10 +927,13 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
   c->tune = cur;
   ++c->layout_version;
   c->cfg.use_graph = use_graph;
+  c->cfg.rebuild_every = rebuild_every;
   cudaMemcpyAsync(c->vel, v0, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   cudaMemcpyAsync(c->h_user, h0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   cudaMemcpyAsync(c->dtlim, d0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   c->step = step0;
+  c->since_rebuild = since0;
+  c->order_version = order0;
   const int st = wait_and_collect(c);
   cudaFree(save);
   if (rc != SIDM_OK) return rc;
