@@ -228,20 +228,26 @@ def hernquist_full():
     return I.hernquist_2pow20()
 
 
-@pytest.mark.parametrize("s", [1, 2])
+@pytest.mark.parametrize("s", [0, 1, 4])
 def test_hernquist_2pow20_full_size(hernquist_full, s):
     """The halo workload at full size (N = 2^20, N_ngb = 64, open boundaries,
-    power-of-two bins) in the configuration the benchmark times."""
+    power-of-two bins) in the configuration the benchmark times: a captured
+    step graph with autotuned launch shapes.  Step 0 of the bin cycle has
+    every particle active (~2e5 accepted pairs, the longest kick chains)."""
     w = hernquist_full
     p, bins = w["particles"], w["bins"]
     act = I.active_at_step(bins, s)
-    ctx = sidm.Context(n_ngb=64, box=0.0)
+    ctx = sidm.Context(n_ngb=64, box=0.0, use_graph=True)
     ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
     ctx.step_counter = s
+    ctx.autotune([sidm.HaloParams(w["dt_max"], sidm.SigmaModel(0, 1.0, 1.0), w["seed"], s)],
+                 I.active_at_step(bins, 1), bins, reps=1)
     o = oracle.step(p.pos, p.vel, p.mass, p.ids, act, bins, w["dt_max"], n_ngb=64, seed=w["seed"],
                     step=s)
     g = _gpu_step(ctx, p, act, bins, w["dt_max"], seed=w["seed"])
+    assert ctx.graph_state == 1
     _compare(g, o, act, f"hernquist step {s}")
+    ctx.close()
 
 
 def test_tabulated_cross_section_matches_the_oracle():
