@@ -36,10 +36,14 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_tables = []   # keeps the arrays behind table pointers (Config, Sigma) alive
+
+
 class Config(C.Structure):
     _fields_ = [("n_ngb", C.c_int), ("ngb_tol", C.c_int), ("c_sidm", C.c_double),
                 ("box", C.c_double), ("kernel", C.c_int), ("fixed_h", C.c_double),
-                ("use_tree", C.c_int), ("n_threads", C.c_int)]
+                ("use_tree", C.c_int), ("n_threads", C.c_int), ("estimator", C.c_int),
+                ("ov_na", C.c_int), ("ov_ns", C.c_int), ("ov_table", C.POINTER(C.c_double))]
 
 
 class Sigma(C.Structure):
@@ -83,6 +87,12 @@ def lib():
             L.orc_kernel_w.restype = C.c_double
             L.orc_sigma_over_m.argtypes = [C.POINTER(Sigma), C.c_double]
             L.orc_sigma_over_m.restype = C.c_double
+            L.orc_overlap_quadrature.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int]
+            L.orc_overlap_quadrature.restype = C.c_double
+            L.orc_overlap_table.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp]
+            L.orc_overlap_table.restype = None
+            L.orc_overlap_g.argtypes = [C.POINTER(Config), C.c_double, C.c_double, C.c_double]
+            L.orc_overlap_g.restype = C.c_double
             L.orc_directed_probability.argtypes = [C.c_int, C.POINTER(Sigma), C.c_double, dp, dp,
                                                    C.c_double, C.c_double, C.c_double]
             L.orc_directed_probability.restype = C.c_double
@@ -102,12 +112,21 @@ def lib():
 
 
 def make_config(n_ngb=32, ngb_tol=5, c_sidm=0.1, box=0.0, kernel=0, fixed_h=0.0,
-                use_tree=1, n_threads=0) -> Config:
-    return Config(int(n_ngb), int(ngb_tol), float(c_sidm), float(box), int(kernel),
-                  float(fixed_h), int(use_tree), int(n_threads))
+                use_tree=1, n_threads=0, overlap_table=None) -> Config:
+    """overlap_table: None (one-sided estimator, Eq. 14) or a (na+1, ns+1) array
+    of ghat on a = k / (2 na), s = l / ns (kernel-overlap estimator, Eq. 15)."""
+    cfg = Config(int(n_ngb), int(ngb_tol), float(c_sidm), float(box), int(kernel),
+                 float(fixed_h), int(use_tree), int(n_threads), 0, 0, 0, None)
+    if overlap_table is not None:
+        t = np.ascontiguousarray(overlap_table, np.float64)
+        _tables.append((t,))
+        del _tables[:-8]
+        cfg.estimator = 1
+        cfg.ov_na, cfg.ov_ns = t.shape[0] - 1, t.shape[1] - 1
+        cfg.ov_table = t.ctypes.data_as(C.POINTER(C.c_double))
+    return cfg
 
 
-_tables = []   # keeps the arrays behind Sigma.tab_v / tab_s alive
 
 
 def make_sigma(kind=0, sigma0=1.0, w=1.0, inelastic=0.0, table=None) -> Sigma:
@@ -158,6 +177,24 @@ def directed_probability(m_j, v_i, v_j, r2, h_i, dt_i, kernel=0, kind=0, sigma0=
                                           _p(vj, C.c_double), float(r2), float(h_i), float(dt_i))
 
 
+def overlap_quadrature(a: float, s: float, kernel=0, panels=24) -> float:
+    """ghat(a, s) of the kernel-overlap estimator (Eq. 15) by quadrature."""
+    return lib().orc_overlap_quadrature(int(kernel), float(a), float(s), int(panels))
+
+
+def overlap_table(na=32, ns=128, kernel=0, panels=24) -> np.ndarray:
+    """Table of ghat on a = k / (2 na), s = l / ns (Appendix A)."""
+    out = np.zeros((na + 1, ns + 1))
+    lib().orc_overlap_table(int(kernel), int(na), int(ns), int(panels), _p(out, C.c_double))
+    return out
+
+
+def overlap_g(table, h_i, h_j, r2) -> float:
+    """g_ij from the table: ghat(min(h)/H, r/H) / H^3, H = h_i + h_j."""
+    cfg = make_config(overlap_table=table)
+    return lib().orc_overlap_g(C.byref(cfg), float(h_i), float(h_j), float(r2))
+
+
 def direction(seed: int, step: int, a: int, b: int):
     e = np.zeros(3)
     ok = lib().orc_direction(seed, step, a, b, _p(e, C.c_double))
@@ -206,7 +243,7 @@ def h_for(pos, query, n_ngb=32, ngb_tol=5, box=0.0, use_tree=True, n_threads=0):
 
 def step(pos, vel, mass, ids, active, bins, dt_max, *, n_ngb=32, ngb_tol=5, c_sidm=0.1,
          box=0.0, kernel=0, fixed_h=0.0, sigma_kind=0, sigma0=1.0, w=1.0, inelastic=0.0,
-         table=None, seed=0, step=0,
+         table=None, overlap_table=None, seed=0, step=0,
          use_tree=True, n_threads=0, max_pairs=None, h_init=None, dtlim_init=None):
     """One scattering step (Sec. 4); returns a dict with the new velocities,
     h and dt-limits (active particles updated, others from *_init or 0/inf),
@@ -226,7 +263,8 @@ def step(pos, vel, mass, ids, active, bins, dt_max, *, n_ngb=32, ngb_tol=5, c_si
     pp = np.zeros(cap, np.float64)
     npairs = C.c_int64(0)
     st = Stats()
-    cfg = make_config(n_ngb, ngb_tol, c_sidm, box, kernel, fixed_h, int(use_tree), n_threads)
+    cfg = make_config(n_ngb, ngb_tol, c_sidm, box, kernel, fixed_h, int(use_tree), n_threads,
+                      overlap_table)
     sg = make_sigma(sigma_kind, sigma0, w, inelastic, table)
     rc = lib().orc_step(C.byref(cfg), n, _p(pos, C.c_double), _p(vel, C.c_double),
                         _p(mass, C.c_double), _p(ids, C.c_uint32), _p(act, C.c_uint8),

@@ -79,6 +79,13 @@ typedef struct {
   double fixed_h;   // > 0: every active particle uses this h (no bisection)
   int use_tree;     // 1: k-d tree neighbour search; 0: brute force O(N^2)
   int n_threads;    // OpenMP threads for the per-particle phases (0 = default)
+  // estimator of g_ij: 0 one-sided W(r_ij, h_i) (Eq. 14); 1 kernel overlap
+  // (Eq. 15, Appendix A) from the table ghat(a, s), a = min(h_i, h_j) / H,
+  // s = r_ij / H, H = h_i + h_j: (ov_na + 1) x (ov_ns + 1) values on
+  // a = k / (2 ov_na), s = l / ov_ns, row-major in a
+  int estimator;
+  int ov_na, ov_ns;
+  const double* ov_table;
 } orc_config;
 
 typedef struct {
@@ -371,6 +378,93 @@ double directed_probability(int kernel, const orc_sigma& sig, double m_j, double
   return ((((0.5 * m_j) * s) * vrel) * W) * dt_i;
 }
 
+// ---- kernel-overlap estimator (Eq. 15, Appendix A) ----------------------
+// ghat(a, s) = int W(|y|, a) W(|y - s z|, 1 - a) d^3y: the overlap of the
+// kernels of two particles a distance s apart, in units of H = h_i + h_j
+// (g_ij = ghat / H^3).  Composite Gauss-Legendre in cylindrical coordinates
+// (z along the separation) over the lens where both kernels are non-zero.
+double overlap_quadrature(int kernel, double a, double s, int panels) {
+  const double b = 1.0 - a;
+  if (a <= 0.0) return kernel_norm(kernel, 1.0) * kernel_shape(kernel, s < 1.0 ? s : 1.0) *
+                       (s < 1.0 ? 1.0 : 0.0);
+  if (!(s < a + b)) return 0.0;
+  static const double gx[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290,
+                               -0.1834346424956498, 0.1834346424956498, 0.5255324099163290,
+                               0.7966664774136267, 0.9602898564975363};
+  static const double gw[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873,
+                               0.3626837833783620, 0.3626837833783620, 0.3137066458778873,
+                               0.2223810344533745, 0.1012285362903763};
+  auto w = [&](double r, double h) {
+    const double q = r / h;
+    return q < 1.0 ? kernel_norm(kernel, h) * kernel_shape(kernel, q) : 0.0;
+  };
+  const double z0 = std::max(-a, s - b), z1 = std::min(a, s + b);
+  // the lens's radial limit switches from one sphere to the other on the
+  // plane where the spheres meet: integrate either side of it separately
+  double zc = s > 0.0 ? (a * a - b * b + s * s) / (2.0 * s) : z1;
+  if (!(zc > z0 && zc < z1)) zc = z1;
+  double total = 0.0;
+  for (int pz = 0; pz < 2 * panels; ++pz) {
+    const bool first = pz < panels;
+    const double lo = first ? z0 : zc, hi = first ? zc : z1;
+    if (!(hi > lo)) continue;
+    const int k = first ? pz : pz - panels;
+    const double za = lo + (hi - lo) * k / panels, zb = lo + (hi - lo) * (k + 1) / panels;
+    for (int iz = 0; iz < 8; ++iz) {
+      const double z = 0.5 * (za + zb) + 0.5 * (zb - za) * gx[iz];
+      const double wz = 0.5 * (zb - za) * gw[iz];
+      const double ra2 = a * a - z * z, rb2 = b * b - (z - s) * (z - s);
+      if (ra2 <= 0.0 || rb2 <= 0.0) continue;
+      const double rmax = std::sqrt(std::min(ra2, rb2));
+      double inner = 0.0;
+      for (int pr = 0; pr < panels; ++pr) {
+        const double ra = rmax * pr / panels, rb = rmax * (pr + 1) / panels;
+        for (int ir = 0; ir < 8; ++ir) {
+          const double rho = 0.5 * (ra + rb) + 0.5 * (rb - ra) * gx[ir];
+          const double wr = 0.5 * (rb - ra) * gw[ir];
+          inner += wr * 2.0 * M_PI * rho * w(std::sqrt(rho * rho + z * z), a) *
+                   w(std::sqrt(rho * rho + (z - s) * (z - s)), b);
+        }
+      }
+      total += wz * inner;
+    }
+  }
+  return total;
+}
+
+// Bilinear interpolation of the table (a in [0, 1/2], s in [0, 1)).
+double overlap_hat(const double* T, int na, int ns, double a, double s) {
+  if (!(s < 1.0)) return 0.0;
+  const double fa = a * (2.0 * (double)na);
+  int ia = (int)fa;
+  if (ia > na - 1) ia = na - 1;
+  const double ta = fa - (double)ia;
+  const double fs = s * (double)ns;
+  int is = (int)fs;
+  if (is > ns - 1) is = ns - 1;
+  const double ts = fs - (double)is;
+  const double* r0 = T + (int64_t)ia * (ns + 1);
+  const double* r1 = r0 + (ns + 1);
+  const double g0 = (1.0 - ts) * r0[is] + ts * r0[is + 1];
+  const double g1 = (1.0 - ts) * r1[is] + ts * r1[is + 1];
+  return (1.0 - ta) * g0 + ta * g1;
+}
+
+// g_ij = ghat(min(h_i, h_j) / H, r_ij / H) / H^3, H = h_i + h_j (symmetric in i, j)
+double overlap_g(const orc_config& cfg, double hi, double hj, double r2) {
+  const double H = hi + hj;
+  const double a = std::min(hi, hj) / H;
+  const double s = std::sqrt(r2) / H;
+  return overlap_hat(cfg.ov_table, cfg.ov_na, cfg.ov_ns, a, s) / ((H * H) * H);
+}
+
+// P(i|j) with the overlap factor in place of W(r_ij, h_i)
+double overlap_probability(const orc_sigma& sig, double m_j, double vrel, double g,
+                           double dt_i) {
+  const double s = sigma_over_m(sig, vrel);
+  return ((((0.5 * m_j) * s) * vrel) * g) * dt_i;
+}
+
 double rel_speed(const double* vi, const double* vj) {
   const double dx = vi[0] - vj[0], dy = vi[1] - vj[1], dz = vi[2] - vj[2];
   return std::sqrt((dx * dx + dy * dy) + dz * dz);
@@ -456,6 +550,23 @@ double orc_kernel_w(int kernel, double r, double h) {
 }
 
 double orc_sigma_over_m(const orc_sigma* s, double vrel) { return sigma_over_m(*s, vrel); }
+
+double orc_overlap_quadrature(int kernel, double a, double s, int panels) {
+  return overlap_quadrature(kernel, a, s, panels);
+}
+
+// The table of the overlap estimator: ghat(k / (2 na), l / ns), row-major in a.
+void orc_overlap_table(int kernel, int na, int ns, int panels, double* out) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int k = 0; k <= na; ++k)
+    for (int l = 0; l <= ns; ++l)
+      out[(int64_t)k * (ns + 1) + l] =
+          overlap_quadrature(kernel, 0.5 * (double)k / (double)na, (double)l / (double)ns, panels);
+}
+
+double orc_overlap_g(const orc_config* cfg, double hi, double hj, double r2) {
+  return overlap_g(*cfg, hi, hj, r2);
+}
 
 double orc_directed_probability(int kernel, const orc_sigma* sig, double m_j,
                                 const double* vi, const double* vj, double r2,
@@ -548,14 +659,20 @@ int orc_step(const orc_config* cfg, int64_t n, const double* pos, double* vel,
   }
   const double h0 = initial_h(l_ext, n, cfg->n_ngb);
 
-  // 1. smoothing lengths of the active particles
+  // 1. smoothing lengths of the active particles (of every particle for the
+  // overlap estimator, whose neighbours are those with r_ij < h_i + h_j)
+  const bool overlap = cfg->estimator == 1;
   std::vector<double> h(n, 0.0);
   std::vector<char> is_act(n, 0);
   for (int64_t i : act) is_act[i] = 1;
+  std::vector<int64_t> all;
+  if (overlap)
+    for (int64_t i = 0; i < n; ++i) all.push_back(i);
+  const std::vector<int64_t>& hset = overlap ? all : act;
   int64_t nonconv = 0;
 #pragma omp parallel for schedule(dynamic, 32) num_threads(nthr) reduction(+ : nonconv)
-  for (int64_t t = 0; t < (int64_t)act.size(); ++t) {
-    const int64_t i = act[t];
+  for (int64_t t = 0; t < (int64_t)hset.size(); ++t) {
+    const int64_t i = hset[t];
     if (cfg->fixed_h > 0.0) { h[i] = cfg->fixed_h; continue; }
     int nc = 0; int64_t cnt = 0;
     h[i] = bisect_h(s, i, h0, cfg->n_ngb, cfg->ngb_tol, &nc, &cnt);
@@ -564,6 +681,9 @@ int orc_step(const orc_config* cfg, int64_t n, const double* pos, double* vel,
   S.n_h_nonconv = nonconv;
 
   auto dt_of = [&](int64_t i) { return std::ldexp(dt_max, -(int)bins[i]); };
+  double h_max = 0.0;
+  if (overlap)
+    for (int64_t i = 0; i < n; ++i) h_max = std::max(h_max, h[i]);
 
   // 2. candidate pairs, drawn once each, and (v sigma/m)_max per active particle
   std::vector<std::vector<Pair>> acc_t(nthr);
@@ -575,14 +695,26 @@ int orc_step(const orc_config* cfg, int64_t n, const double* pos, double* vel,
     const int64_t i = act[t];
     const int tid = omp_get_thread_num();
     double vs = 0.0;
-    s.within(i, h[i], [&](int64_t j, double r2) {
+    s.within(i, overlap ? h[i] + h_max : h[i], [&](int64_t j, double r2) {
+      if (overlap) {
+        const double H = h[i] + h[j];
+        if (!(r2 < H * H)) return;               // not overlapping
+      }
       const double vrel = rel_speed(vel + 3 * i, vel + 3 * j);
       vs = std::max(vs, vrel * sigma_over_m(*sig, vrel));
-      const bool j_sees_i = is_act[j] && (r2 < h[j] * h[j]);
+      // j sees i: j active and i in its neighbour set (symmetric for the overlap)
+      const bool j_sees_i = is_act[j] && (overlap || r2 < h[j] * h[j]);
       if (j_sees_i && ids[j] < ids[i]) return;   // j owns the pair
       ++n_cand;
-      const double p_i = directed_probability(cfg->kernel, *sig, mass[j], vrel, r2, h[i], dt_of(i));
-      const double p_j = j_sees_i ? directed_probability(cfg->kernel, *sig, mass[i], vrel, r2, h[j], dt_of(j)) : 0.0;
+      double p_i, p_j = 0.0;
+      if (overlap) {
+        const double g = overlap_g(*cfg, h[i], h[j], r2);
+        p_i = overlap_probability(*sig, mass[j], vrel, g, dt_of(i));
+        if (j_sees_i) p_j = overlap_probability(*sig, mass[i], vrel, g, dt_of(j));
+      } else {
+        p_i = directed_probability(cfg->kernel, *sig, mass[j], vrel, r2, h[i], dt_of(i));
+        if (j_sees_i) p_j = directed_probability(cfg->kernel, *sig, mass[i], vrel, r2, h[j], dt_of(j));
+      }
       const bool i_is_a = ids[i] < ids[j];
       const double p_pair = i_is_a ? (p_i + p_j) : (p_j + p_i);
       if (p_pair >= 1.0) ++n_pge1;
@@ -625,7 +757,10 @@ int orc_step(const orc_config* cfg, int64_t n, const double* pos, double* vel,
     kick(mass[pr.i], mass[pr.j], vel + 3 * pr.i, vel + 3 * pr.j, e, 1.0 - sig->inelastic);
   }
 
-  // 4. outputs for the active particles: h and the Eq. 18 limit
+  // 4. outputs for the active particles: h and the Eq. 18 limit (h of every
+  // particle for the overlap estimator)
+  if (overlap && h_out)
+    for (int64_t i = 0; i < n; ++i) h_out[i] = h[i];
   for (int64_t i : act) {
     if (h_out) h_out[i] = h[i];
     if (dtlim_out) {

@@ -350,6 +350,92 @@ def test_fixed_h_expectation_all_active(orc, kind):
     assert abs(sums.mean() / expect - 1) < 0.03
 
 
+@pytest.fixture(scope="module")
+def ov_table(orc):
+    return orc.overlap_table(32, 128)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_overlap_normalisation_and_symmetry(orc, kernel):
+    """The overlap of two normalised kernels integrates to one over all
+    separations (int ghat 4 pi s^2 ds = 1, Eq. 15), and is symmetric under
+    exchanging the two particles (a <-> 1 - a)."""
+    from scipy import integrate
+    for a in (0.02, 0.2, 0.5):
+        v, _ = integrate.quad(lambda x: orc.overlap_quadrature(a, x, kernel) * 4 * math.pi * x * x,
+                              0.0, 1.0, limit=400, points=[abs(1 - 2 * a), 0.5])
+        assert abs(v - 1.0) < 1e-6, (a, v)
+    for a in (0.1, 0.3, 0.45):
+        for x in (0.0, 0.2, 0.55, 0.8):
+            g1, g2 = orc.overlap_quadrature(a, x, kernel), orc.overlap_quadrature(1 - a, x, kernel)
+            assert abs(g1 - g2) <= 1e-9 * max(g1, 1e-300)
+
+
+def test_overlap_top_hat_is_the_lens_volume(orc):
+    """Two top-hat kernels overlap by the volume of the lens of their spheres
+    divided by both sphere volumes (a closed form)."""
+    def lens(d, r1, r2):
+        if d <= abs(r1 - r2):
+            return 4.0 / 3.0 * math.pi * min(r1, r2) ** 3
+        if d >= r1 + r2:
+            return 0.0
+        return (math.pi * (r1 + r2 - d) ** 2 *
+                (d * d + 2 * d * (r1 + r2) - 3 * (r1 - r2) ** 2) / (12 * d))
+    for a in (0.1, 0.25, 0.5):
+        va, vb = 4.0 / 3.0 * math.pi * a ** 3, 4.0 / 3.0 * math.pi * (1 - a) ** 3
+        for x in (0.05, 0.3, 0.6, 0.9):
+            want = lens(x, a, 1 - a) / (va * vb)
+            assert abs(orc.overlap_quadrature(a, x, 1) - want) <= 1e-10 * want, (a, x)
+
+
+def test_overlap_of_a_point_is_the_kernel(orc):
+    """As h_i -> 0 the kernel of i becomes a point: ghat(a, s) tends to the
+    partner's kernel W(s, 1 - a), with an error of second order in a (the
+    kernel's first moment vanishes)."""
+    for x in (0.0, 0.2, 0.4, 0.7, 0.9):
+        for a in (1e-3, 1e-4):
+            w = orc.kernel_w(x, 1.0 - a, 0)
+            g = orc.overlap_quadrature(a, x)
+            assert abs(g - w) <= 50 * a * a * w + 1e-12, (x, a, g, w)
+
+
+def test_overlap_g_symmetric_and_table_interpolated(orc, ov_table):
+    """g_ij from the table equals g_ji bit for bit, vanishes for r >= h_i + h_j,
+    scales as H^-3, and matches the quadrature to the interpolation error."""
+    rng = np.random.default_rng(40)
+    for _ in range(300):
+        hi, hj = rng.uniform(0.05, 2.0, 2)
+        H = hi + hj
+        r = rng.uniform(0.0, 1.0) * H
+        g1 = orc.overlap_g(ov_table, hi, hj, r * r)
+        assert g1 == orc.overlap_g(ov_table, hj, hi, r * r)
+        q = orc.overlap_quadrature(min(hi, hj) / H, r / H) / H ** 3
+        assert abs(g1 - q) <= 2e-3 * orc.overlap_quadrature(min(hi, hj) / H, 0.0) / H ** 3
+    assert orc.overlap_g(ov_table, 0.3, 0.5, 0.8 ** 2) == 0.0
+
+
+def test_overlap_fixed_h_expectation(orc, ov_table):
+    """With a fixed h every pair closer than 2h overlaps, and a uniform partner
+    position averages g_ij to 1/V (the overlap integrates to one), so the
+    expected summed P_pair is that of the one-sided estimator."""
+    n, H, dt = 1200, 0.12, 0.02
+    rng = np.random.default_rng(22)
+    vel = rng.normal(size=(n, 3))
+    m = 0.8 / n
+    expect = m * _pair_speed_sum(vel, vel, lambda d: 1.0) / 2.0 * dt
+    sums = []
+    for seed in range(16):
+        pos = np.random.default_rng(300 + seed).random((n, 3))
+        r = orc.step(pos, vel, np.full(n, m), np.arange(n, dtype=np.uint32), None,
+                     np.zeros(n, np.int8), dt, fixed_h=H, box=1.0, overlap_table=ov_table,
+                     seed=seed)
+        sums.append(r["stats"]["sum_p"])
+    sums = np.array(sums)
+    se = sums.std(ddof=1) / math.sqrt(len(sums))
+    assert abs(sums.mean() - expect) < 5 * se + 1e-3 * expect
+    assert abs(sums.mean() / expect - 1) < 0.03
+
+
 def test_fixed_h_expectation_beam_on_inactive_targets(orc):
     """Only the beam is active: each beam-target pair is drawn with the
     beam's half only, P = 1/2 m_target s v dt_beam W(r, h_beam)
