@@ -78,6 +78,7 @@ enum { SIDM_SIGMA_CONST = 0, SIDM_SIGMA_YUKAWA = 1, SIDM_SIGMA_TABLE = 2 };
  * rare near-boundary cases; energy and momentum stay conserved to FP64
  * round-off. */
 enum { SIDM_FP64_PLAIN = 0, SIDM_FP32_SPLIT = 1 };
+enum { SIDM_ESTIMATOR_ONE_SIDED = 0, SIDM_ESTIMATOR_OVERLAP = 1 };
 
 typedef struct {
   int n_ngb;            /* target neighbour number N_ngb (paper: 32)                     */
@@ -96,6 +97,11 @@ typedef struct {
                            and replay it while the particle count, the halo layout and the
                            launch shapes stay the same (results are unchanged); 0: direct
                            launches.  Ignored while `profile` is set.                      */
+  int estimator;        /* g_ij of the pair rate: SIDM_ESTIMATOR_ONE_SIDED, W(r_ij, h_i)
+                           (Eq. 14, the paper's fiducial choice), or SIDM_ESTIMATOR_OVERLAP,
+                           the overlap of both kernels (Eq. 15, Appendix A; needs
+                           sidm_set_overlap_table; h is then found for every particle, and
+                           the neighbours of i are all j with r_ij < h_i + h_j)           */
   int rebuild_every;    /* k > 1: the spatial keys are recomputed and sorted only every k
                            steps (and after any change of particle count or halo layout);
                            the steps in between keep that key order and refit the tree's
@@ -243,6 +249,22 @@ SIDM_API int64_t sidm_kernel_launches(const sidm_ctx* ctx);
  * sigma/m (draws differ only if u falls within that distance of P). */
 SIDM_API int sidm_set_sigma_table(sidm_ctx* ctx, int32_t n, const double* v,
                                   const double* sigma_over_m);
+
+/* Table of the kernel-overlap estimator (Eq. 15, Appendix A): ghat(a, s) =
+ * int W(|y|, a) W(|y - s z|, 1 - a) d^3y on a = k / (2 na), k = 0..na, and
+ * s = l / ns, l = 0..ns, as (na + 1) x (ns + 1) host doubles, row-major in a
+ * (copied).  A pair uses g_ij = ghat(min(h_i, h_j)/H, r_ij/H) / H^3 with
+ * H = h_i + h_j, ghat interpolated bilinearly (0 for s >= 1).  1 <= na <= 4096,
+ * 1 <= ns <= 65536, values finite and >= 0.  Required before a step of a
+ * context with estimator SIDM_ESTIMATOR_OVERLAP (else SIDM_ERR_NOT_READY). */
+SIDM_API int sidm_set_overlap_table(sidm_ctx* ctx, int32_t na, int32_t ns, const double* table);
+
+/* Computes that table for kernel SIDM_KERNEL_CUBIC or SIDM_KERNEL_TOPHAT into
+ * `out` ((na + 1) x (ns + 1) host doubles): spherical shells around one
+ * particle, the angular integral of the other kernel in closed form, the
+ * radial integral by Gauss-Legendre between the kernels' breakpoints (about
+ * 1e-12 relative).  Host only; no context needed. */
+SIDM_API int sidm_overlap_table(int kernel, int32_t na, int32_t ns, double* out);
 
 /* ---- launch shapes (no counterpart in the paper) ------------------------
  * How the step's kernels are launched.  Every choice gives bit-identical

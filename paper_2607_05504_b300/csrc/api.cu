@@ -72,6 +72,9 @@ struct sidm_ctx {
   // tabulated sigma/m (one device buffer, see SigmaTable)
   SigmaTable table{};
   void* table_mem = nullptr;
+  // table of the kernel-overlap estimator
+  OverlapTable ov{};
+  void* ov_mem = nullptr;
   // launch shapes and the captured step
   LaunchTuning tune{};
   uint64_t layout_version = 1;  // bumped whenever buffers, haloes or tuning change
@@ -414,7 +417,9 @@ int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches) {
                        c->cfg.fixed_h, c->cfg.kernel, c->cfg.precision == SIDM_FP32_SPLIT,
                        c->h_user,
                        c->nb_list, c->nb_count, c->nb_stride,
-                       c->dstats, c->work, c->sms, c->tune, s);
+                       c->dstats, c->work, c->sms, c->tune,
+                       c->cfg.estimator == SIDM_ESTIMATOR_OVERLAP, s);
+    if (c->cfg.estimator == SIDM_ESTIMATOR_OVERLAP) L += launch_hmax(c->so, F, s);
     mark(4);
     PairArgs pa;
     pa.kernel = c->cfg.kernel;
@@ -427,6 +432,7 @@ int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches) {
     pa.lim_cnt = c->lim_cnt;
     pa.lim_g = c->lim_g;
     pa.table = c->table;
+    pa.ov = c->cfg.estimator == SIDM_ESTIMATOR_OVERLAP ? c->ov : OverlapTable{};
     L += launch_pairs(c->so, F, n, c->act_list, c->nb_list, c->nb_count, c->nb_stride, pa,
                       c->pairs, c->dtlim, c->dstats, c->work + 1, c->sms, c->tune, s);
     mark(5);
@@ -477,6 +483,7 @@ void capture_core(sidm_ctx* c, int rebuild) {
 
 int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
              sidm_step_stats* stats) {
+  if (c->cfg.estimator == SIDM_ESTIMATOR_OVERLAP && c->ov.na <= 0) return SIDM_ERR_NOT_READY;
   const int64_t n = c->n;
   cudaStream_t s = c->stream;
   if (n > 0) {
@@ -581,7 +588,8 @@ int sidm_create(const sidm_config* cfg, sidm_ctx** out) {
       !std::isfinite(cfg->box) || (cfg->kernel != SIDM_KERNEL_CUBIC && cfg->kernel != SIDM_KERNEL_TOPHAT) ||
       (cfg->precision != SIDM_FP64_PLAIN && cfg->precision != SIDM_FP32_SPLIT) ||
       !(cfg->fixed_h >= 0.0) || cfg->n_max < 0 ||
-      cfg->pair_capacity < 0 || cfg->rebuild_every < 0)
+      cfg->pair_capacity < 0 || cfg->rebuild_every < 0 ||
+      (cfg->estimator != SIDM_ESTIMATOR_ONE_SIDED && cfg->estimator != SIDM_ESTIMATOR_OVERLAP))
     return SIDM_ERR_INVALID_ARG;
   sidm_ctx* c = new (std::nothrow) sidm_ctx();
   if (!c) return SIDM_ERR_OOM;
@@ -783,6 +791,117 @@ int time_candidate(sidm_ctx* c, const uint8_t* act, const int8_t* bins, int reps
 }
 
 }  // namespace
+
+namespace {
+
+// ---- table of the kernel-overlap estimator (host) --------------------------
+// ghat(a, s) = int_0^a 2 pi r^2 W(r, a) I(r) dr, where I(r) is the integral
+// of W(., b), b = 1 - a, over the sphere of radius r around a point at
+// distance s: with rho^2 = r^2 + s^2 - 2 r s mu it is
+// (K / (b r s)) [F(min(r + s, b) / b) - F(min(|r - s|, b) / b)], F(t) the
+// antiderivative of t f(t) of the kernel shape f (W = K f(r / h) / h^3).
+// Between the kinks of f the integrand is a polynomial in r, so an 8-point
+// Gauss-Legendre rule per piece is exact up to rounding.
+double ov_shape(int kernel, double q) {
+  if (!(q < 1.0)) return 0.0;
+  if (kernel == SIDM_KERNEL_TOPHAT) return 1.0;
+  if (q <= 0.5) return 1.0 - 6.0 * q * q + 6.0 * q * q * q;
+  const double u = 1.0 - q;
+  return 2.0 * u * u * u;
+}
+double ov_norm(int kernel) {
+  return kernel == SIDM_KERNEL_TOPHAT ? 3.0 / (4.0 * M_PI) : 8.0 / M_PI;
+}
+double ov_F(int kernel, double t) {
+  if (!(t > 0.0)) return 0.0;
+  if (t > 1.0) t = 1.0;
+  if (kernel == SIDM_KERNEL_TOPHAT) return 0.5 * t * t;
+  if (t <= 0.5) return 0.5 * t * t - 1.5 * t * t * t * t + 1.2 * t * t * t * t * t;
+  auto G = [](double x) {
+    const double u = 1.0 - x;
+    return -0.5 * u * u * u * u + 0.4 * u * u * u * u * u;
+  };
+  return 0.06875 + G(t) - G(0.5);  // 0.06875 = F(1/2)
+}
+double ov_ghat(int kernel, double a, double s) {
+  const double b = 1.0 - a, K = ov_norm(kernel);
+  if (!(s < 1.0)) return 0.0;
+  if (a <= 0.0) return K * ov_shape(kernel, s);
+  auto I = [&](double r) {
+    if (s <= 0.0) return 2.0 * K * ov_shape(kernel, r / b) / (b * b * b);
+    return K / (b * r * s) *
+           (ov_F(kernel, std::min(r + s, b) / b) - ov_F(kernel, std::fabs(r - s) / b));
+  };
+  double cut[12];
+  int nc = 0;
+  cut[nc++] = 0.0;
+  const double cand[9] = {0.5 * a, s, 0.5 * b - s, b - s, s - 0.5 * b, s - b, s + 0.5 * b, s + b,
+                          a};
+  for (double x : cand)
+    if (x > 0.0 && x <= a) cut[nc++] = x;
+  std::sort(cut, cut + nc);
+  static const double gx[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290,
+                               -0.1834346424956498, 0.1834346424956498, 0.5255324099163290,
+                               0.7966664774136267, 0.9602898564975363};
+  static const double gw[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873,
+                               0.3626837833783620, 0.3626837833783620, 0.3137066458778873,
+                               0.2223810344533745, 0.1012285362903763};
+  double total = 0.0;
+  for (int k = 0; k + 1 < nc; ++k) {
+    const double lo = cut[k], hi = cut[k + 1];
+    if (!(hi > lo)) continue;
+    for (int q = 0; q < 8; ++q) {
+      const double r = 0.5 * (lo + hi) + 0.5 * (hi - lo) * gx[q];
+      const double wa = K * ov_shape(kernel, r / a) / (a * a * a);
+      total += 0.5 * (hi - lo) * gw[q] * 2.0 * M_PI * r * r * wa * I(r);
+    }
+  }
+  return total;
+}
+
+}  // namespace
+
+int sidm_overlap_table(int kernel, int32_t na, int32_t ns, double* out) {
+  if (!out || na < 1 || na > 4096 || ns < 1 || ns > 65536 ||
+      (kernel != SIDM_KERNEL_CUBIC && kernel != SIDM_KERNEL_TOPHAT))
+    return SIDM_ERR_INVALID_ARG;
+  for (int k = 0; k <= na; ++k)
+    for (int l = 0; l <= ns; ++l)
+      out[(int64_t)k * (ns + 1) + l] =
+          ov_ghat(kernel, 0.5 * (double)k / (double)na, (double)l / (double)ns);
+  return SIDM_OK;
+}
+
+int sidm_set_overlap_table(sidm_ctx* c, int32_t na, int32_t ns, const double* t) {
+  if (!c || !t || na < 1 || na > 4096 || ns < 1 || ns > 65536) return SIDM_ERR_INVALID_ARG;
+  const int64_t m = (int64_t)(na + 1) * (ns + 1);
+  for (int64_t k = 0; k < m; ++k)
+    if (!std::isfinite(t[k]) || !(t[k] >= 0.0)) return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  std::vector<char> host(m * (sizeof(double) + sizeof(float)));
+  double* hg = (double*)host.data();
+  float* hf = (float*)(hg + m);
+  for (int64_t k = 0; k < m; ++k) {
+    hg[k] = t[k];
+    float y = (float)t[k];
+    if ((double)y < t[k]) y = std::nextafter(y, INFINITY);
+    hf[k] = y;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->ov_mem) cudaFree(c->ov_mem);
+  c->ov_mem = nullptr;
+  c->ov = OverlapTable{};
+  void* d = nullptr;
+  CK(cudaMalloc(&d, host.size()));
+  c->ov_mem = d;
+  CK(cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice));
+  c->ov.na = na;
+  c->ov.ns = ns;
+  c->ov.g = (const double*)d;
+  c->ov.g_ru = (const float*)((const double*)d + m);
+  ++c->layout_version;  // the captured step holds the old table address
+  return SIDM_OK;
+}
 
 int sidm_set_sigma_table(sidm_ctx* c, int32_t n, const double* v, const double* sg) {
   if (!c || !v || !sg || n < 2 || n > SIDM_SIGMA_TABLE_MAX) return SIDM_ERR_INVALID_ARG;
@@ -1035,6 +1154,7 @@ void sidm_destroy(sidm_ctx* c) {
     if (c->h_cons) cudaFreeHost(c->h_cons);
     if (c->h_latched) cudaFreeHost(c->h_latched);
     if (c->table_mem) cudaFree(c->table_mem);
+    if (c->ov_mem) cudaFree(c->ov_mem);
     for (int k = 0; k <= SIDM_N_PHASES; ++k)
       if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

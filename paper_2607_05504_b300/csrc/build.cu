@@ -368,6 +368,49 @@ int launch_params(Halo* halos, int n_halos, double box, cudaStream_t s) {
   return 1;
 }
 
+// Largest h (rounded up, from the search) under every node, stored in the w
+// of the node's upper corner: the overlap walk widens its radius by it.
+__global__ void __launch_bounds__(BT) hmax_leaf_kernel(Sorted so, Forest f) {
+  const int64_t g = (blockIdx.x * (int64_t)BT + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (g >= f.level_nodes[0]) return;
+  const int k = find_halo_level(f.halos, f.n_halos, 0, g);
+  const Halo& H = f.halos[k];
+  const int64_t local = g - H.node_off[0];
+  float m = 0.0f;
+  if (local * LEAF + lane < H.n) m = so.hb[H.start + local * LEAF + lane].y;
+  m = warp_maxf(m);
+  if (lane == 0) f.hi[g].w = m;
+}
+__global__ void __launch_bounds__(BT) hmax_node_kernel(Forest f, int level, int64_t level_base) {
+  const int64_t g = level_base + ((blockIdx.x * (int64_t)BT + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (g >= level_base + f.level_nodes[level]) return;
+  const int k = find_halo_level(f.halos, f.n_halos, level, g);
+  const Halo& H = f.halos[k];
+  const int64_t c = (g - H.node_off[level]) * 32 + lane;
+  float m = 0.0f;
+  if (c < H.node_cnt[level - 1]) m = f.hi[H.node_off[level - 1] + c].w;
+  m = warp_maxf(m);
+  if (lane == 0) f.hi[g].w = m;
+}
+
+int launch_hmax(const Sorted& so, const Forest& f, cudaStream_t s) {
+  if (f.level_nodes[0] <= 0) return 0;
+  int launches = 0;
+  hmax_leaf_kernel<<<blocks_for(f.level_nodes[0] * 32), BT, 0, s>>>(so, f);
+  ++launches;
+  int64_t base = f.level_nodes[0];
+  for (int l = 1; l < f.max_levels; ++l) {
+    if (f.level_nodes[l] > 0) {
+      hmax_node_kernel<<<blocks_for(f.level_nodes[l] * 32), BT, 0, s>>>(f, l, base);
+      ++launches;
+    }
+    base += f.level_nodes[l];
+  }
+  return launches;
+}
+
 int launch_keys(const double* pos, const int32_t* halo_of, int64_t n, const Halo* halos,
                 int halo_bits, double box, uint32_t* keys, int32_t* vals, cudaStream_t s) {
   if (n <= 0) return 0;

@@ -155,6 +155,51 @@ __device__ __forceinline__ void g_bounds(int kind, float s0, float w, const Sigm
   }
 }
 
+// Bounds of g_ij for the overlap estimator from the FP32 bounds of h_i,
+// h_j and r_ij: a = min(h)/H and s = r/H lie in intervals; the exact value
+// interpolates four table nodes of a cell those intervals reach (one cell
+// of margin covers the FP64 rounding of a and s), so it is at most their
+// largest rounded-up value, over H^3 from below.  gest: an FP32 estimate
+// (statistics and the split form).
+constexpr float ULP1 = 1.1920928955078125e-07f;  // 2^-23
+__device__ __forceinline__ void overlap_bounds(const OverlapTable& T, float4 hbi, float4 hbj,
+                                               float rlo, float rhi, float r, float* gup,
+                                               float* gest) {
+  const float Hlo = __fadd_rd(hbi.x, hbj.x), Hhi = __fadd_ru(hbi.y, hbj.y);
+  const float ilo = __fmul_rd(__frcp_rn(Hhi), 1.0f - ULP1);  // <= 1/H
+  const float ihi = __fmul_ru(__frcp_rn(Hlo), 1.0f + ULP1);  // >= 1/H
+  const float alo = __fmul_rd(fminf(hbi.x, hbj.x), ilo), ahi = __fmul_ru(fminf(hbi.y, hbj.y), ihi);
+  const float slo = __fmul_rd(rlo, ilo), shi = __fmul_ru(rhi, ihi);
+  const int na = T.na, ns = T.ns;
+  const float fa2 = 2.0f * (float)na, fs1 = (float)ns;
+  int a0 = (int)fminf(__fmul_rd(alo, fa2), (float)na) - 1;
+  int a1 = (int)fminf(__fmul_ru(ahi, fa2), (float)na) + 1;
+  int s0 = (int)fminf(__fmul_rd(slo, fs1), (float)ns) - 1;
+  int s1 = (int)fminf(__fmul_ru(shi, fs1), (float)ns) + 1;
+  a0 = max(a0, 0);
+  a1 = min(a1, na - 1);
+  s0 = max(s0, 0);
+  s1 = min(s1, ns - 1);
+  float gmax = 0.0f;
+  for (int ia = a0; ia <= a1 + 1; ++ia)
+    for (int is = s0; is <= s1 + 1; ++is) gmax = fmaxf(gmax, T.g_ru[ia * (ns + 1) + is]);
+  *gup = __fmul_ru(gmax, __fmul_ru(__fmul_ru(ihi, ihi), ihi));
+  // estimate at the midpoint
+  const float H = 0.5f * (Hlo + Hhi);
+  const float a = fminf(0.5f * (hbi.x + hbi.y), 0.5f * (hbj.x + hbj.y)) / H, sv = r / H;
+  float est = 0.0f;
+  if (sv < 1.0f) {
+    const float fa = a * fa2, fs = sv * fs1;
+    const int ia = min((int)fa, na - 1), is = min((int)fs, ns - 1);
+    const float ta = fa - (float)ia, ts = fs - (float)is;
+    const float* r0 = T.g_ru + ia * (ns + 1);
+    const float* r1 = r0 + (ns + 1);
+    est = (1.0f - ta) * ((1.0f - ts) * r0[is] + ts * r0[is + 1]) +
+          ta * ((1.0f - ts) * r1[is] + ts * r1[is + 1]);
+  }
+  *gest = est / (H * H * H);
+}
+
 // What one warp knows about its query particle i.
 struct Query {
   int64_t s;            // key-order index
@@ -229,7 +274,9 @@ __device__ __forceinline__ void visit(const PairKArgs& A, const Query& Q, int64_
     // does j see i?  (j active and r^2 < h_j^2: decided exactly, or in FP32
     // by the split form, as its neighbour lists are)
     bool sees = false;
-    if (actj) {
+    if (P.ov.na > 0) {
+      sees = actj;  // overlap membership r < h_i + h_j is symmetric
+    } else if (actj) {
       if (P.split) {
         const float hjf = f64_to_f32_rn(so.h[j]);
         sees = r2f < hjf * hjf;
@@ -245,11 +292,28 @@ __device__ __forceinline__ void visit(const PairKArgs& A, const Query& Q, int64_
       // FP32 upper bound of P_pair.  The bound holds only while no product
       // of the chain leaves the normal FP32 range; below 2^-100 the FP64
       // path decides.
+      float pu, pc;
+      bool tiny;
+      if (P.ov.na > 0) {
+        // kernel overlap: the same g_ij bounds both directed terms
+        float gup, gov;
+        overlap_bounds(P.ov, Q.hbi, hbj, rlo, rhi, r, &gup, &gov);
+        const float t1 = 0.5f * vmj.w, t2 = t1 * ghi, t3 = t2 * gup;
+        pu = t3 * Q.fi.w;
+        tiny = !(fminf(fminf(t1, t2), fminf(t3, pu)) >= FLT_TINY);
+        pc = 0.5f * vmj.w * gest * gov * Q.fi.w;
+        if (sees) {
+          const float s1 = 0.5f * Q.vmi.w, s2 = s1 * ghi, s3 = s2 * gup, puj = s3 * fj.w;
+          tiny = tiny || !(fminf(fminf(s1, s2), fminf(s3, puj)) >= FLT_TINY);
+          pu += puj;
+          pc += 0.5f * Q.vmi.w * gest * gov * fj.w;
+        }
+      } else {
       const float fi_up = shape_f(kern, __fmul_rd(rlo, Q.hbi.z)) * (1.0f + SLACK) + REL;
       const float t1 = 0.5f * vmj.w, t2 = t1 * ghi, t3 = t2 * Q.hbi.w, t4 = t3 * fi_up;
-      float pu = t4 * Q.fi.w;
-      bool tiny = !(fminf(fminf(t1, t2), fminf(fminf(t3, t4), pu)) >= FLT_TINY);
-      float pc = 0.5f * vmj.w * gest * Q.hbi.w * shape_f(kern, r * Q.hbi.z) * Q.fi.w;
+      pu = t4 * Q.fi.w;
+      tiny = !(fminf(fminf(t1, t2), fminf(fminf(t3, t4), pu)) >= FLT_TINY);
+      pc = 0.5f * vmj.w * gest * Q.hbi.w * shape_f(kern, r * Q.hbi.z) * Q.fi.w;
       if (sees) {
         const float fj_up = shape_f(kern, __fmul_rd(rlo, hbj.z)) * (1.0f + SLACK) + REL;
         const float s1 = 0.5f * Q.vmi.w, s2 = s1 * ghi, s3 = s2 * hbj.w, s4 = s3 * fj_up;
@@ -257,6 +321,7 @@ __device__ __forceinline__ void visit(const PairKArgs& A, const Query& Q, int64_
         tiny = tiny || !(fminf(fminf(s1, s2), fminf(fminf(s3, s4), puj)) >= FLT_TINY);
         pu += puj;
         pc += 0.5f * Q.vmi.w * gest * hbj.w * shape_f(kern, r * hbj.z) * fj.w;
+      }
       }
       pu *= (1.0f + SLACK);
       const bool i_is_a = Q.idi < idj;
@@ -357,6 +422,7 @@ __device__ __forceinline__ void flush_counters(const PairKArgs& A, unsigned long
 // Queries with a complete neighbour list (the usual case).
 __global__ void __launch_bounds__(PT, 6) pairs_kernel(PairKArgs A) {
   __shared__ float s_ghi[PW][MAXR * WARP];
+  if (A.a.ov.na > 0) return;  // the overlap estimator's queries all walk the tree
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* ghi_row = s_ghi[warp];
   const int64_t n_act = (int64_t)A.st->n_active;
@@ -428,7 +494,8 @@ __device__ void walk_query(const PairKArgs& A, int64_t qi, int* stack, unsigned 
   const int64_t hs = H.start;
   const double xi = so.x[s], yi = so.y[s], zi = so.z[s], hi = so.h[s];
   const double hhi = hi * hi;
-  const float rad = (__double2float_ru(hi) + 2.0f * Q.eq) * (1.0f + 4.0f * REL);
+  const bool ov = A.a.ov.na > 0;
+  const float rad = (f64_to_f32_ru(hi) + 2.0f * Q.eq) * (1.0f + 4.0f * REL);
   double mine = 0.0;
   float psum = 0.0f;
   const int sl = (int)(s - hs);
@@ -439,7 +506,17 @@ __device__ void walk_query(const PairKArgs& A, int64_t qi, int* stack, unsigned 
       const float r = sqrtf(sep2f(Q.fi, pj, boxf));
       const float e = Q.eq + ABS * r;
       const float rlo = fmaxf(r * (1.0f - REL) - e, 0.0f);
-      if (A.a.split) {
+      if (ov) {
+        // overlap neighbours: r_ij < h_i + h_j, decided exactly near the edge
+        const float4 hbj = so.hb[j];
+        const float rhi = r * (1.0f + REL) + e;
+        if (rhi < __fadd_rd(Q.hbi.x, hbj.x)) {
+          in = true;
+        } else if (rlo < __fadd_ru(Q.hbi.y, hbj.y)) {
+          const double H = hi + so.h[j];
+          in = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half) < H * H;
+        }
+      } else if (A.a.split) {
         const float hf = (float)hi;
         in = r * r < hf * hf;
       } else if (rlo < Q.hbi.y) {
@@ -450,9 +527,15 @@ __device__ void walk_query(const PairKArgs& A, int64_t qi, int* stack, unsigned 
     visit(A, Q, j, in, &gl, &gh, &psum, cand, pge1, status);
     if (in) mine = fmax(mine, A.a.split ? (double)gl : exact_g(A, s, j));
   };
-  const bool ok = A.a.box > 0.0
-      ? traverse<true>(A.f, H, so.f + hs, Q.fi, rad * rad, boxf, stack, leaf)
-      : traverse<false>(A.f, H, so.f + hs, Q.fi, rad * rad, boxf, stack, leaf);
+  bool ok;
+  if (ov)  // the radius at each node is widened by the node's largest h
+    ok = A.a.box > 0.0
+        ? traverse<true, true>(A.f, H, so.f + hs, Q.fi, 0.0f, boxf, stack, leaf, rad)
+        : traverse<false, true>(A.f, H, so.f + hs, Q.fi, 0.0f, boxf, stack, leaf, rad);
+  else
+    ok = A.a.box > 0.0
+        ? traverse<true>(A.f, H, so.f + hs, Q.fi, rad * rad, boxf, stack, leaf)
+        : traverse<false>(A.f, H, so.f + hs, Q.fi, rad * rad, boxf, stack, leaf);
   if (!ok) *status |= ST_ERR_STACK;
   *sum_p += (double)psum;
   mine = warp_maxd(mine);
@@ -471,7 +554,8 @@ __global__ void __launch_bounds__(PT) pairs_walk_kernel(PairKArgs A) {
   uint32_t status = 0;
   const int64_t w0 = ((int64_t)blockIdx.x * PW + warp) * 32, ws = (int64_t)gridDim.x * PW * 32;
   for (int64_t q0 = w0; q0 < n_act; q0 += ws) {
-    const bool need = q0 + lane < n_act && A.nb_count[q0 + lane] < 0;
+    // every query walks for the overlap estimator (its neighbours need h_j)
+    const bool need = q0 + lane < n_act && (A.a.ov.na > 0 || A.nb_count[q0 + lane] < 0);
     uint32_t todo = __ballot_sync(0xffffffffu, need);
     while (todo) {
       const int64_t qi = q0 + __ffs(todo) - 1;
@@ -516,15 +600,22 @@ __global__ void __launch_bounds__(XT) pairs_exact_kernel(PairKArgs A) {
       const double vrel = sqrt((ddx * ddx + ddy * ddy) + ddz * ddz);
       const double sg = sigma_over_m(H.sigma_kind, H.sigma0, H.w, P.table, vrel);
       const double hi = so.h[s];
-      const double qq = sqrt(r2) / hi;
-      const double p_i = ((((0.5 * so.m[j]) * sg) * vrel) * (kernel_norm(kern, hi) *
-                                                            kernel_shape(kern, qq))) * so.dt[s];
-      double p_j = 0.0;
-      if (sees) {
-        const double hj = so.h[j];
-        const double qj = sqrt(r2) / hj;
-        p_j = ((((0.5 * so.m[s]) * sg) * vrel) * (kernel_norm(kern, hj) *
-                                                   kernel_shape(kern, qj))) * so.dt[j];
+      double p_i, p_j = 0.0;
+      if (P.ov.na > 0) {
+        // kernel overlap (Eq. 15): the same g_ij for both directed terms
+        const double g = overlap_g(P.ov, hi, so.h[j], r2);
+        p_i = ((((0.5 * so.m[j]) * sg) * vrel) * g) * so.dt[s];
+        if (sees) p_j = ((((0.5 * so.m[s]) * sg) * vrel) * g) * so.dt[j];
+      } else {
+        const double qq = sqrt(r2) / hi;
+        p_i = ((((0.5 * so.m[j]) * sg) * vrel) * (kernel_norm(kern, hi) *
+                                                   kernel_shape(kern, qq))) * so.dt[s];
+        if (sees) {
+          const double hj = so.h[j];
+          const double qj = sqrt(r2) / hj;
+          p_j = ((((0.5 * so.m[s]) * sg) * vrel) * (kernel_norm(kern, hj) *
+                                                     kernel_shape(kern, qj))) * so.dt[j];
+        }
       }
       const double pp = i_is_a ? (p_i + p_j) : (p_j + p_i);
       if (pp >= 1.0) ++pge1;
@@ -559,6 +650,7 @@ __global__ void __launch_bounds__(XT) pairs_exact_kernel(PairKArgs A) {
 // the exact maximum of v sigma/m over the kept candidates (over the whole
 // list when there were more), or the FP32 maximum in the split form.
 __global__ void __launch_bounds__(XT) limits_kernel(PairKArgs A) {
+  if (A.a.ov.na > 0) return;  // the tree walks wrote every limit
   const int64_t n_act = (int64_t)A.st->n_active;
   const int64_t stride = (int64_t)gridDim.x * XT;
   for (int64_t qi = blockIdx.x * (int64_t)XT + threadIdx.x; qi < n_act; qi += stride) {

@@ -56,6 +56,7 @@ struct SearchArgs {
   int32_t* nb_count;    // [n_act]: count, or -1 (walk the tree)
   int nb_stride;
   int chunk;             // queries claimed per work-counter increment
+  int all;               // 1: every particle is a query (overlap estimator), s = query index
   DevStats* st;
   int* work;
 };
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
   int32_t* lst_j = s_j[warp];
   int* stack = s_stack[warp];
   const Sorted& so = A.so;
-  const int64_t n_act = (int64_t)A.st->n_active;
+  const int64_t n_act = A.all ? A.n : (int64_t)A.st->n_active;
   const double box = A.box, half = 0.5 * A.box;
   const float boxf = (float)A.box;
   const int K = A.n_ngb + A.tol + 1;
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
     }
     if (q >= n_act) break;
     const int64_t qi = q++;
-    const int64_t s = A.act_list[qi];
+    const int64_t s = A.all ? qi : (int64_t)A.act_list[qi];
     const Halo& H = A.f.halos[so.halo[s]];
     const int64_t hs = H.start, hn = H.n;   // the query's halo: [hs, hs + hn)
     const float4* hpos = so.f + hs;         // its FP32 positions
@@ -392,10 +393,11 @@ void launch_search_window(const SearchArgs& a, int window, unsigned blocks, cuda
 int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
                   double box, int n_ngb, int tol, double fixed_h, int kernel, int split,
                   double* h_user, int32_t* nb_list, int32_t* nb_count, int nb_stride,
-                  DevStats* st, int* work, int sms, const LaunchTuning& t, cudaStream_t s) {
+                  DevStats* st, int* work, int sms, const LaunchTuning& t, int all,
+                  cudaStream_t s) {
   if (n <= 0) return 0;
   SearchArgs a{so, f, n, act_list, box, n_ngb, tol, fixed_h, kernel, split, h_user,
-               nb_list, nb_count, nb_stride, t.search_chunk, st, work};
+               nb_list, nb_count, nb_stride, t.search_chunk, all, st, work};
   int64_t blocks = (int64_t)sms * t.search_blocks_per_sm;
   const int64_t need = (n + SW - 1) / SW;
   if (blocks > need) blocks = need;

@@ -171,6 +171,43 @@ __device__ __forceinline__ double sigma_table(const SigmaTable& T, double v) {
   return T.s[lo] + t * (T.s[lo + 1] - T.s[lo]);
 }
 
+// Kernel-overlap estimator (Eq. 15, Appendix A): ghat on a = k / (2 na),
+// s = l / ns, row-major in a; the FP32 copy is rounded up.  na = 0: the
+// one-sided estimator (Eq. 14).
+struct OverlapTable {
+  int32_t na, ns;
+  const double* g;
+  const float* g_ru;
+};
+
+// Bilinear interpolation of ghat (a in [0, 1/2], s in [0, 1)).
+__device__ __forceinline__ double overlap_hat(const OverlapTable& T, double a, double s) {
+  if (!(s < 1.0)) return 0.0;
+  const int na = T.na, ns = T.ns;
+  const double fa = a * (2.0 * (double)na);
+  int ia = (int)fa;
+  if (ia > na - 1) ia = na - 1;
+  const double ta = fa - (double)ia;
+  const double fs = s * (double)ns;
+  int is = (int)fs;
+  if (is > ns - 1) is = ns - 1;
+  const double ts = fs - (double)is;
+  const double* r0 = T.g + (int64_t)ia * (ns + 1);
+  const double* r1 = r0 + (ns + 1);
+  const double g0 = (1.0 - ts) * r0[is] + ts * r0[is + 1];
+  const double g1 = (1.0 - ts) * r1[is] + ts * r1[is + 1];
+  return (1.0 - ta) * g0 + ta * g1;
+}
+
+// g_ij = ghat(min(h_i, h_j) / H, r_ij / H) / H^3, H = h_i + h_j (symmetric)
+__device__ __forceinline__ double overlap_g(const OverlapTable& T, double hi, double hj,
+                                            double r2) {
+  const double H = hi + hj;
+  const double a = fmin(hi, hj) / H;
+  const double s = sqrt(r2) / H;
+  return overlap_hat(T, a, s) / ((H * H) * H);
+}
+
 __device__ __forceinline__ double sigma_over_m(int kind, double s0, double w, const SigmaTable& T,
                                                double v) {
   if (kind == SIDM_SIGMA_TABLE) return sigma_table(T, v);
@@ -309,7 +346,10 @@ struct LaunchTuning {
 int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
                   double box, int n_ngb, int tol, double fixed_h, int kernel, int split,
                   double* h_user, int32_t* nb_list, int32_t* nb_count, int nb_stride,
-                  DevStats* st, int* work, int sms, const LaunchTuning& t, cudaStream_t s);
+                  DevStats* st, int* work, int sms, const LaunchTuning& t, int all,
+                  cudaStream_t s);
+// largest h (rounded up) of each tree node, in the w of its upper corner
+int launch_hmax(const Sorted& so, const Forest& f, cudaStream_t s);
 
 // pairs.cu
 constexpr int LIM_CAND = 4;   // Eq. 18 maximum: candidates kept per query
@@ -325,6 +365,7 @@ struct PairArgs {
   int32_t* lim_cnt;   // [n] their number, -1: more than LIM_CAND (scan the whole list)
   float* lim_g;       // [n] largest FP32 lower bound of v sigma/m (split form: the maximum)
   SigmaTable table;   // tabulated sigma/m (kind SIDM_SIGMA_TABLE)
+  OverlapTable ov;    // kernel-overlap estimator (ov.na > 0)
 };
 int launch_pairs(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
                  const int32_t* nb_list, const int32_t* nb_count, int nb_stride,

@@ -51,10 +51,14 @@ __device__ __forceinline__ float sep2f(const float4& a, const float4& b, float b
 // valid when k < H.n, with FP32 position pj (hpos = key-order FP32
 // positions of the halo's particles).  Returns false if the stack
 // overflowed (visit incomplete).
-template <bool PERIODIC, class LeafFn>
+// HMAX: the radius at a node is widened by the node's largest h (the w of
+// its upper corner), the overlap walk's h_i + h_j bound; `rad` is then the
+// query's own radius and rad2 is ignored.
+template <bool PERIODIC, bool HMAX = false, class LeafFn>
 __device__ __forceinline__ bool traverse(const Forest& f, const Halo& H,
                                          const float4* __restrict__ hpos, const float4& q,
-                                         float rad2, float box, int* stack, LeafFn&& leaf_fn) {
+                                         float rad2, float box, int* stack, LeafFn&& leaf_fn,
+                                         float rad = 0.0f) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   const int levels = H.levels;
@@ -78,7 +82,13 @@ __device__ __forceinline__ bool traverse(const Forest& f, const Halo& H,
       bool hit = false;
       if (k < (int)H.node_cnt[level - 1]) {
         const int64_t nd = H.node_off[level - 1] + k;
-        hit = box_hits<PERIODIC>(f.lo[nd], f.hi[nd], q, rad2, box);
+        const float4 lo = f.lo[nd], hi = f.hi[nd];
+        float r2 = rad2;
+        if (HMAX) {
+          const float rr = __fmul_ru(__fadd_ru(rad, hi.w), 1.0f + 3.814697265625e-06f);
+          r2 = __fmul_ru(rr, rr);
+        }
+        hit = box_hits<PERIODIC>(lo, hi, q, r2, box);
       }
       const uint32_t m = __ballot_sync(0xffffffffu, hit);
       const int cnt = __popc(m);

@@ -21,6 +21,7 @@ from . import build as _build
 HOST, DEVICE = 0, 1
 KERNEL_CUBIC, KERNEL_TOPHAT = 0, 1
 FP64_PLAIN, FP32_SPLIT = 0, 1
+ESTIMATOR_ONE_SIDED, ESTIMATOR_OVERLAP = 0, 1
 SIGMA_CONST, SIGMA_YUKAWA, SIGMA_TABLE = 0, 1, 2
 SIGMA_TABLE_MAX = 256
 
@@ -44,7 +45,7 @@ class Config(C.Structure):
                 ("box", C.c_double), ("kernel", C.c_int), ("precision", C.c_int),
                 ("fixed_h", C.c_double), ("n_max", C.c_int64), ("pair_capacity", C.c_int64),
                 ("stream", C.c_void_p), ("device", C.c_int), ("profile", C.c_int),
-                ("use_graph", C.c_int), ("rebuild_every", C.c_int)]
+                ("use_graph", C.c_int), ("estimator", C.c_int), ("rebuild_every", C.c_int)]
 
 
 class Tuning(C.Structure):
@@ -89,7 +90,7 @@ ENTRY_POINTS = ("sidm_default_config", "sidm_create", "sidm_set_particles",
                 "sidm_phase_times", "sidm_kernel_launches", "sidm_error_string", "sidm_destroy",
                 "sidm_apply_pairs_noalloc", "sidm_set_haloes", "sidm_step_haloes",
                 "sidm_set_tuning", "sidm_get_tuning", "sidm_autotune", "sidm_graph_state",
-                "sidm_set_sigma_table")
+                "sidm_set_sigma_table", "sidm_set_overlap_table", "sidm_overlap_table")
 
 N_PHASES = 6
 PHASES = ("keys", "sort", "structure", "search", "pairs", "resolve")
@@ -144,6 +145,8 @@ def lib():
                                     C.POINTER(Tuning)]
         L.sidm_graph_state.argtypes = [vp]
         L.sidm_set_sigma_table.argtypes = [vp, C.c_int32, vp, vp]
+        L.sidm_set_overlap_table.argtypes = [vp, C.c_int32, C.c_int32, vp]
+        L.sidm_overlap_table.argtypes = [C.c_int, C.c_int32, C.c_int32, vp]
         for name in ENTRY_POINTS:
             fn = getattr(L, name)
             if name not in ("sidm_default_config", "sidm_error_string", "sidm_destroy"):
@@ -252,6 +255,22 @@ def sidm_set_sigma_table(ctx, v, sigma_over_m) -> int:
                   "sidm_set_sigma_table")
 
 
+def sidm_set_overlap_table(ctx, table) -> int:
+    t = np.ascontiguousarray(table, np.float64)
+    if t.ndim != 2:
+        raise ValueError("overlap table must be (na + 1) x (ns + 1)")
+    return _check(lib().sidm_set_overlap_table(ctx, t.shape[0] - 1, t.shape[1] - 1, t.ctypes.data),
+                  "sidm_set_overlap_table")
+
+
+def sidm_overlap_table(kernel=KERNEL_CUBIC, na=32, ns=128) -> np.ndarray:
+    """The kernel-overlap table ghat on a = k / (2 na), s = l / ns (host)."""
+    out = np.zeros((na + 1, ns + 1))
+    _check(lib().sidm_overlap_table(int(kernel), int(na), int(ns), out.ctypes.data),
+           "sidm_overlap_table")
+    return out
+
+
 def sidm_graph_state(ctx) -> int:
     return int(lib().sidm_graph_state(ctx))
 
@@ -319,7 +338,8 @@ class Context:
 
     def __init__(self, n_ngb=32, ngb_tol=5, c_sidm=0.1, box=0.0, kernel=KERNEL_CUBIC,
                  fixed_h=0.0, n_max=0, pair_capacity=0, stream=None, device=-1, profile=False,
-                 precision=FP64_PLAIN, use_graph=False, rebuild_every=0):
+                 precision=FP64_PLAIN, use_graph=False, rebuild_every=0,
+                 estimator=ESTIMATOR_ONE_SIDED):
         cfg = sidm_default_config()
         cfg.n_ngb, cfg.ngb_tol, cfg.c_sidm, cfg.box = int(n_ngb), int(ngb_tol), float(c_sidm), float(box)
         cfg.kernel, cfg.fixed_h, cfg.n_max = int(kernel), float(fixed_h), int(n_max)
@@ -330,6 +350,7 @@ class Context:
         cfg.precision = int(precision)
         cfg.use_graph = int(bool(use_graph))
         cfg.rebuild_every = int(rebuild_every)
+        cfg.estimator = int(estimator)
         self.cfg = cfg
         self.handle = sidm_create(cfg)
         self.n = 0
@@ -428,6 +449,10 @@ class Context:
         if isinstance(bins, np.ndarray):
             bins = np.ascontiguousarray(bins, np.int8)
         return sidm_autotune(self.handle, active, bins, params, reps).as_dict()
+
+    def set_overlap_table(self, table):
+        """ghat table of the kernel-overlap estimator ((na + 1) x (ns + 1))."""
+        sidm_set_overlap_table(self.handle, table)
 
     def set_sigma_table(self, v, sigma_over_m):
         """Tabulated sigma/m(v) for models of kind SIGMA_TABLE (linear in log v

@@ -52,9 +52,12 @@ def _compare(g, o, act, what=""):
 
 def run_pair(p, act, bins, dt_max, *, n_ngb=32, ngb_tol=5, kernel=0, fixed_h=0.0, steps=1,
              seed=0, sigma_kind=0, sigma0=1.0, w=1.0, c_sidm=0.1, device_inputs=False,
-             pair_capacity=0, inelastic=0.0):
+             pair_capacity=0, inelastic=0.0, overlap_table=None):
     ctx = sidm.Context(n_ngb=n_ngb, ngb_tol=ngb_tol, c_sidm=c_sidm, box=p.box, kernel=kernel,
-                       fixed_h=fixed_h, pair_capacity=pair_capacity)
+                       fixed_h=fixed_h, pair_capacity=pair_capacity,
+                       estimator=int(overlap_table is not None))
+    if overlap_table is not None:
+        ctx.set_overlap_table(overlap_table)
     if device_inputs:
         import torch
         ctx.set_particles(torch.from_numpy(p.pos).cuda(), torch.from_numpy(p.vel).cuda(),
@@ -70,7 +73,7 @@ def run_pair(p, act, bins, dt_max, *, n_ngb=32, ngb_tol=5, kernel=0, fixed_h=0.0
         o = oracle.step(p.pos, vel, p.mass, p.ids, a, bins, dt_max, n_ngb=n_ngb, ngb_tol=ngb_tol,
                         c_sidm=c_sidm, box=p.box, kernel=kernel, fixed_h=fixed_h,
                         sigma_kind=sigma_kind, sigma0=sigma0, w=w, inelastic=inelastic,
-                        seed=seed, step=k, h_init=h, dtlim_init=dl)
+                        overlap_table=overlap_table, seed=seed, step=k, h_init=h, dtlim_init=dl)
         g = _gpu_step(ctx, p, a, bins, dt_max, sigma_kind=sigma_kind, sigma0=sigma0, w=w, seed=seed,
                       inelastic=inelastic)
         _compare(g, o, a, f"step {k}")
@@ -300,4 +303,50 @@ def test_sigma_table_validation():
             ctx.set_sigma_table(np.array(v), np.array(s))
     ctx.set_sigma_table(np.array([0.5, 2.0]), np.array([1.0, 3.0]))
     ctx.step(0.1, sigma_kind=sidm.SIGMA_TABLE, stats=False)
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def ov_tables():
+    return {k: oracle.overlap_table(32, 128, kernel=k) for k in (0, 1)}
+
+
+def test_overlap_estimator_box_all_active(ov_tables):
+    """Kernel-overlap estimator (Eq. 15, Appendix A) in a periodic box: h of
+    every particle, pairs (r_ij < h_i + h_j) and velocities equal the
+    oracle's over several steps."""
+    p = I.uniform_box(5000, 1.0, 1.0, 41, ids="random")
+    g, o = run_pair(p, None, np.zeros(p.n, np.int8), 0.05, steps=3, seed=6,
+                    overlap_table=ov_tables[0])
+    assert o["n_pairs"] > 100
+
+
+def test_overlap_estimator_halo_partial_activity(ov_tables):
+    """Inactive neighbours enter with their own h (found for every particle);
+    unequal masses, random ids, power-of-two bins."""
+    p = I.hernquist_halo(15000, 42, ids="random")
+    rng = np.random.default_rng(43)
+    p.mass[:] = p.mass * rng.uniform(0.5, 2.0, p.n)
+    bins = rng.integers(0, 4, p.n).astype(np.int8)
+    g, o = run_pair(p, lambda k: I.active_at_step(bins, k), bins, 2.0, n_ngb=32, steps=3,
+                    seed=7, overlap_table=ov_tables[0])
+    assert o["n_pairs"] > 30
+
+
+def test_overlap_estimator_fixed_h_tophat(ov_tables):
+    p = I.uniform_box(3000, 1.0, 1.0, 44)
+    g, o = run_pair(p, None, np.zeros(p.n, np.int8), 0.05, fixed_h=0.08, kernel=1,
+                    overlap_table=ov_tables[1])
+    assert o["n_pairs"] > 50
+
+
+def test_overlap_estimator_needs_its_table():
+    p = I.uniform_box(500, 1.0, 1.0, 45)
+    ctx = sidm.Context(box=1.0, estimator=sidm.ESTIMATOR_OVERLAP)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    with pytest.raises(sidm.SidmError) as e:
+        ctx.step(0.1)
+    assert e.value.status == sidm.ERR_NOT_READY
+    ctx.set_overlap_table(sidm.sidm_overlap_table(0, 8, 32))
+    ctx.step(0.1, stats=False)
     ctx.close()
