@@ -323,6 +323,21 @@ __device__ __forceinline__ void visit(const PairKArgs& A, const Query& Q, int64_
         pc += 0.5f * Q.vmi.w * gest * hbj.w * shape_f(kern, r * hbj.z) * fj.w;
       }
       }
+      if (pu == 0.0f) {
+        // A zero bound is an underflow unless P_pair is exactly zero: no
+        // cross section, zero masses in every term, or two bit-equal
+        // velocities (g(0) = 0, e.g. targets at rest).  Exact zeros are
+        // rejected for any u >= 0 and need no FP64 pass.
+        bool exact_zero = (Q.kind != SIDM_SIGMA_TABLE && Q.s0f == 0.0f) ||
+                          (vmj.w == 0.0f && (!sees || Q.vmi.w == 0.0f));
+        if (!exact_zero && vr == 0.0f) {
+          const unsigned long long* bx = (const unsigned long long*)so.vx;
+          const unsigned long long* by = (const unsigned long long*)so.vy;
+          const unsigned long long* bz = (const unsigned long long*)so.vz;
+          exact_zero = bx[Q.s] == bx[j] && by[Q.s] == by[j] && bz[Q.s] == bz[j];
+        }
+        tiny = !exact_zero;
+      }
       pu *= (1.0f + SLACK);
       const bool i_is_a = Q.idi < idj;
       const uint32_t a = i_is_a ? Q.idi : idj, b = i_is_a ? idj : Q.idi;

@@ -88,6 +88,27 @@ def mono_speed_box(n: int, box: float = 1.0, v0: float = 1.0, seed: int = 0,
                      {"kind": "mono", "v0": v0, "rho": mt / box ** 3})
 
 
+def lattice_beam(n_side: int, n_beam: int, box: float = 1.0, v0: float = 1.0,
+                 seed: int = 0) -> Particles:
+    """Beam-through-lattice set-up (Sec. 5.1): n_side^3 targets at rest on a
+    cubic lattice of total mass box^3 (density 1), and n_beam particles of the
+    same mass at uniform random positions, all moving with velocity
+    (v0, 0, 0).  The targets come first."""
+    rng = np.random.default_rng(seed)
+    g = (np.arange(n_side) + 0.5) * (box / n_side)
+    gx, gy, gz = np.meshgrid(g, g, g, indexing="ij")
+    tgt = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], axis=1)
+    beam = rng.random((n_beam, 3)) * box
+    beam[beam >= box] = 0.0
+    pos = np.concatenate([tgt, beam])
+    vel = np.zeros_like(pos)
+    vel[tgt.shape[0]:, 0] = v0
+    n = pos.shape[0]
+    m = box ** 3 / tgt.shape[0]
+    return Particles(pos, vel, np.full(n, m), _ids(rng, n, "random"), float(box),
+                     {"kind": "lattice_beam", "n_target": tgt.shape[0], "v0": v0, "rho": 1.0})
+
+
 # ---------------------------------------------------------------- haloes ---
 
 def _isotropic(rng: np.random.Generator, r: np.ndarray) -> np.ndarray:

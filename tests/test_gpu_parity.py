@@ -184,6 +184,31 @@ def test_full_pair_buffer_is_reported_and_nothing_is_kicked():
     ctx.close()
 
 
+def test_pairs_at_zero_relative_speed_match_the_oracle():
+    """Half the particles at rest and 500 pairs of bit-equal moving velocities:
+    g(0) = 0 makes P_pair exactly zero for those pairs.  They are rejected
+    without the exact FP64 pass; deferring them all would overflow this pair
+    buffer, which holds about ten steps' worth of accepted pairs."""
+    p = I.uniform_box(6000, 1.0, 1.0, 14, ids="random")
+    h = p.n // 2
+    p.vel[:h] = 0.0
+    p.vel[h:h + 500] = p.vel[h + 500:h + 1000]
+    g, o = run_pair(p, None, np.zeros(p.n, np.int8), 0.1, steps=3, seed=2, pair_capacity=p.n)
+    assert o["n_pairs"] > 50
+
+
+@pytest.mark.parametrize("sigma_kind", [0, 1])
+def test_zero_cross_section_scatters_nothing(sigma_kind):
+    """sigma0 = 0: every P_pair is exactly zero, nothing is deferred (a
+    five-entry buffer suffices) and the Eq. 18 limits are infinite."""
+    p = I.uniform_box(3000, 1.0, 1.0, 15)
+    g, o = run_pair(p, None, np.zeros(p.n, np.int8), 0.5, sigma_kind=sigma_kind, sigma0=0.0,
+                    pair_capacity=5)
+    assert o["n_pairs"] == 0 and g["stats"]["n_accepted"] == 0
+    assert np.array_equal(g["vel"], p.vel)
+    assert np.all(np.isinf(g["dtlim"]))
+
+
 def test_device_inputs_match_host_inputs():
     import torch
     p = I.uniform_box(5000, 1.0, 1.0, 9)
