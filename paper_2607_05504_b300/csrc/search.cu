@@ -40,6 +40,9 @@ constexpr float REL = 9.5367431640625e-07f;   // 2^-20
 constexpr float ABS = 4.76837158203125e-07f;  // 2^-21
 constexpr float CREL = REL + ABS;             // relative part of the bounds
 constexpr float SQ = 4.76837158203125e-07f;   // 2^-21: slack on squared thresholds
+#ifndef SEARCH_LEAF_BATCH
+#define SEARCH_LEAF_BATCH 4                    // leaves per L2 round trip in the gather walk
+#endif
 
 struct SearchArgs {
   Sorted so;
@@ -207,8 +210,8 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
       const float g2 = T < INFINITY ? thr_out2(T * (1.0f + REL), eq) : INFINITY;
       const float rad = (T + 2.0f * eq) * (1.0f + 4.0f * REL);
       const float rad2 = rad < INFINITY ? rad * rad : INFINITY;
-      const bool ok = traverse<PERIODIC>(A.f, H, hpos, fi, rad2, boxf, stack,
-                                         [&](int k, bool valid, const float4& pj) {
+      const bool ok = traverse<PERIODIC, false, SEARCH_LEAF_BATCH>(
+          A.f, H, hpos, fi, rad2, boxf, stack, [&](int k, bool valid, const float4& pj) {
         float s2 = 0.0f;
         bool keep = false;
         if (valid && k != sl) {
@@ -248,8 +251,8 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
         const float in2 = thr_in2(Tn, eq);
         const float radn = (Tn + 2.0f * eq) * (1.0f + 4.0f * REL);
         int c = 0;
-        const bool ok2 = traverse<PERIODIC>(A.f, H, hpos, fi, radn * radn, boxf, stack,
-                                            [&](int k, bool valid, const float4& pj) {
+        const bool ok2 = traverse<PERIODIC, false, SEARCH_LEAF_BATCH>(
+            A.f, H, hpos, fi, radn * radn, boxf, stack, [&](int k, bool valid, const float4& pj) {
           bool in = false;
           if (valid && k != sl) in = sep2f<PERIODIC>(fi, pj, boxf) < in2;
           c += __popc(__ballot_sync(0xffffffffu, in));

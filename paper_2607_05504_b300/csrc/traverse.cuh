@@ -44,9 +44,9 @@ __device__ __forceinline__ float sep2f(const float4& a, const float4& b, float b
   return box > 0.f ? sep2f<true>(a, b, box) : sep2f<false>(a, b, box);
 }
 
-// Visits every leaf of halo H whose box meets the sphere (depth first, one
-// stack entry at a time: the stack never holds more than 31 entries per
-// level plus one).  leaf_fn(k, valid, pj) is called by the whole warp for
+// Visits every leaf of halo H whose box meets the sphere (depth first over
+// the internal nodes, one stack entry at a time: the stack never holds more
+// than 31 entries per level plus one).  leaf_fn(k, valid, pj) is called by the whole warp for
 // each leaf reached: lane l holds the halo-local particle k = 32 leaf + l,
 // valid when k < H.n, with FP32 position pj (hpos = key-order FP32
 // positions of the halo's particles).  Returns false if the stack
@@ -54,7 +54,11 @@ __device__ __forceinline__ float sep2f(const float4& a, const float4& b, float b
 // HMAX: the radius at a node is widened by the node's largest h (the w of
 // its upper corner), the overlap walk's h_i + h_j bound; `rad` is then the
 // query's own radius and rad2 is ignored.
-template <bool PERIODIC, bool HMAX = false, class LeafFn>
+// LB > 0: the leaves under a node are visited as soon as their boxes are
+// tested, LB at a time, with their particle loads issued together (one L2
+// round trip per LB leaves; leaf_fn is replicated LB times).  LB = 0: hit
+// leaves go on the stack like the other nodes (smallest code).
+template <bool PERIODIC, bool HMAX = false, int LB = 0, class LeafFn>
 __device__ __forceinline__ bool traverse(const Forest& f, const Halo& H,
                                          const float4* __restrict__ hpos, const float4& q,
                                          float rad2, float box, int* stack, LeafFn&& leaf_fn,
@@ -91,11 +95,35 @@ __device__ __forceinline__ bool traverse(const Forest& f, const Halo& H,
         hit = box_hits<PERIODIC>(lo, hi, q, r2, box);
       }
       const uint32_t m = __ballot_sync(0xffffffffu, hit);
-      const int cnt = __popc(m);
-      if (top + cnt > SEARCH_STACK) return false;
-      if (hit) stack[top + __popc(m & lt)] = ((level - 1) << 28) | k;
-      top += cnt;
-      __syncwarp();
+      if (LB > 0 && level == 1) {
+        // the children are leaves: visit the hit ones now, LB at a time
+        const int lbase = (node & 0x0FFFFFFF) << 5;
+        uint32_t mm = m;
+        while (mm) {
+          constexpr int NB = LB > 0 ? LB : 1;
+          int kk[NB];
+          bool on[NB], valid[NB];
+          float4 pj[NB];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            on[b] = mm != 0u;                       // warp-uniform
+            const int c = on[b] ? __ffs(mm) - 1 : 0;
+            mm &= mm - 1u;
+            kk[b] = ((lbase + c) << 5) + lane;
+            valid[b] = on[b] && kk[b] < hn;
+            pj[b] = valid[b] ? hpos[kk[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int b = 0; b < NB; ++b)
+            if (on[b]) leaf_fn(kk[b], valid[b], pj[b]);
+        }
+      } else {
+        const int cnt = __popc(m);
+        if (top + cnt > SEARCH_STACK) return false;
+        if (hit) stack[top + __popc(m & lt)] = ((level - 1) << 28) | k;
+        top += cnt;
+        __syncwarp();
+      }
     }
   }
   return true;
