@@ -178,7 +178,9 @@ __global__ void __launch_bounds__(RT) resolve_kernel(const PairRec* __restrict__
 // 4. dataflow: a pending pair is ready when it sits at the cursor of both of
 //    its particles, i.e. when every earlier pair of both particles has been
 //    applied.  Ready pairs are applied and advance the two cursors (release
-//    store after the kick; acquire load before reading velocities), so every
+//    pattern after the kick: one fence.acq_rel, then relaxed stores; the
+//    cursors are polled with acquire loads, which order the velocity reads
+//    after the earlier kicks without a fence), so every
 //    particle meets its pairs in key order -- the sequential result.  The
 //    grid is launched cooperatively (all blocks resident); the globally first
 //    unapplied pair is always ready, so the passes make progress.  A bounded
@@ -194,13 +196,13 @@ __device__ __forceinline__ bool step_overflowed(const DevStats* st, int64_t cap)
   return st->n_acc > (unsigned long long)cap || st->n_deferred > (unsigned long long)cap;
 }
 
-__device__ __forceinline__ void st_release(int32_t* p, int v) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_relaxed(int32_t* p, int v) {
+  asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ int ld_relaxed(const int32_t* p) {
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
   int v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ void fence_acq_rel() {
@@ -393,7 +395,7 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
     const int64_t gsize = (int64_t)gridDim.x * GT;
     const int64_t t0 = blockIdx.x * (int64_t)GT + threadIdx.x;
     // the thread's first pair, prepared (masses, direction) before its turn;
-    // a turn is two relaxed cursor loads, then an acquire fence
+    // a turn is two acquire loads of the cursors
     bool first = t0 < np;
     PairRec r0{};
     int pa0 = 0, pb0 = 0;
@@ -414,14 +416,13 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
     for (; left && pass < DATAFLOW_MAX_PASSES; ++pass) {
       left = false;
       if (first) {
-        const int ca = ld_relaxed(&b.cursor[r0.ia]);
-        const int cb = ld_relaxed(&b.cursor[r0.ib]);
+        const int ca = ld_acquire(&b.cursor[r0.ia]);
+        const int cb = ld_acquire(&b.cursor[r0.ib]);
         if (ca == pa0 && cb == pb0) {
-          fence_acq_rel();
           kick_l2(r0, vel, ma0, mb0, eps0, e0);
-          fence_acq_rel();
-          st_release(&b.cursor[r0.ia], pa0 + 1);
-          st_release(&b.cursor[r0.ib], pb0 + 1);
+          fence_acq_rel();   // release: one fence covers both cursor stores
+          st_relaxed(&b.cursor[r0.ia], pa0 + 1);
+          st_relaxed(&b.cursor[r0.ib], pb0 + 1);
           first = false;
         } else {
           left = true;
@@ -433,17 +434,16 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
         if (b.flags[p]) continue;
         const PairRec r = pairs[p];
         const int pa = b.pos_a[p], pb = b.pos_b[p];
-        const int ca = ld_relaxed(&b.cursor[r.ia]);
-        const int cb = ld_relaxed(&b.cursor[r.ib]);
+        const int ca = ld_acquire(&b.cursor[r.ia]);
+        const int cb = ld_acquire(&b.cursor[r.ib]);
         if (ca == pa && cb == pb) {
-          fence_acq_rel();
           const Halo& H = halos[halo_of[r.ia]];
           double e[3];
           pair_direction(r, (uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, e, &s_dirfail);
           kick_l2(r, vel, mass[r.ia], mass[r.ib], H.eps, e);
           fence_acq_rel();
-          st_release(&b.cursor[r.ia], pa + 1);
-          st_release(&b.cursor[r.ib], pb + 1);
+          st_relaxed(&b.cursor[r.ia], pa + 1);
+          st_relaxed(&b.cursor[r.ib], pb + 1);
           b.flags[p] = 1;
         } else {
           left = true;
