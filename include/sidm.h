@@ -146,7 +146,8 @@ typedef struct {
  * kernel or precision; SIDM_ERR_CUDA if the device cannot be used. */
 SIDM_API int sidm_create(const sidm_config* cfg, sidm_ctx** out);
 
-/* Loads n particles (replaces any previous set).  pos, vel: n x 3; mass:
+/* Loads n particles, 0 <= n < 2^30 (replaces any previous set; larger n:
+ * SIDM_ERR_INVALID_ARG).  pos, vel: n x 3; mass:
  * n values, or NULL to give every particle `mass_scalar`; ids: n unique
  * uint32 (they key the random draws, Philox counter words 2-3).  With a
  * periodic box every coordinate must lie in [0, box).  The buffers grow if

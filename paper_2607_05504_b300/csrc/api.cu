@@ -405,8 +405,10 @@ int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches) {
     mark(1);
     if (rebuild) {
       const int mb = (30 - F.halo_bits) / 3;
-      L += radix_sort_pairs(c->keys, c->vals, c->keys_alt, c->vals_alt, n,
-                            F.halo_bits + 3 * mb, c->sort_tmp, s);
+      const int sl = radix_sort_pairs(c->keys, c->vals, c->keys_alt, c->vals_alt, n,
+                                      F.halo_bits + 3 * mb, c->sort_tmp, &c->dstats->status, s);
+      if (sl < 0) return SIDM_ERR_CUDA;
+      L += sl;
     }
     mark(2);
     L += launch_permute(c->vals, n, c->pos, c->vel, c->mass, c->ids, c->halo_of, c->act,
@@ -640,7 +642,7 @@ int64_t sidm_kernel_launches(const sidm_ctx* c) { return c ? c->launches : -1; }
 
 int sidm_set_particles(sidm_ctx* c, int64_t n, const double* pos, const double* vel,
                        const double* mass, double mass_scalar, const uint32_t* ids, int ptr_kind) {
-  if (!c || n < 0 || n > (int64_t)1 << 31 || (n > 0 && (!pos || !vel || !ids)) ||
+  if (!c || n < 0 || n >= (int64_t)1 << 30 || (n > 0 && (!pos || !vel || !ids)) ||
       (ptr_kind != SIDM_HOST && ptr_kind != SIDM_DEVICE) || (!mass && !(mass_scalar > 0.0)))
     return SIDM_ERR_INVALID_ARG;
   DeviceGuard g(c->device);

@@ -251,7 +251,11 @@ __global__ void __launch_bounds__(BT) permute_kernel(
   const int64_t s = blockIdx.x * (int64_t)BT + threadIdx.x;
   bool a = false;
   if (s < n) {
-    const int64_t o = perm[s];
+    int64_t o = perm[s];
+    if (o < 0 || o >= n) {   // only after a failed sort (the step is then invalid)
+      atomicOr(&st->status, (unsigned)ST_ERR_SORT);
+      o = s;
+    }
     const int k = halo_of[o];
     const double x = pos[3 * o], y = pos[3 * o + 1], z = pos[3 * o + 2];
     so.x[s] = x;

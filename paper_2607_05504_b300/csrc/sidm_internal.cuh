@@ -34,6 +34,7 @@ enum : uint32_t {
   ST_ERR_RADIUS = 1u << 10,       // gather radius adjustment did not settle
   ST_ERR_PAIR_OVERFLOW = 1u << 11,// accepted-pair buffer full
   ST_ERR_ROUNDS = 1u << 12,       // resolver did not finish within its round cap
+  ST_ERR_SORT = 1u << 13,         // key sort: a look-back wait gave up (order not valid)
   ST_ERR_MASK = 0xFF00u
 };
 
@@ -316,10 +317,7 @@ struct Sorted {               // particle state in key order
 // sort.cu
 size_t radix_sort_temp_bytes(int64_t n);
 int radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_alt, int32_t* vals_alt,
-                      int64_t n, int key_bits, void* temp, cudaStream_t s);
-int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
-                        cudaStream_t s);
-size_t exclusive_scan_temp_bytes(int64_t n);
+                     int64_t n, int key_bits, void* temp, unsigned* status, cudaStream_t s);
 
 // build.cu
 int launch_bbox(const double* pos, const int32_t* halo_of, int64_t n, Halo* halos,

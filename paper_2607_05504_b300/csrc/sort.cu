@@ -1,199 +1,227 @@
-// Least-significant-digit radix sort of (uint32 key, int32 value) pairs and a
-// device-wide exclusive scan.  The sort orders particles by their spatial key
-// so that tree leaves are compact; it is stable, hence deterministic.
+// Least-significant-digit radix sort of (uint32 key, int32 value) pairs.  The
+// sort orders particles by their spatial key so that tree leaves are compact;
+// it is stable, hence deterministic.
 //
-// Each 8-bit pass: (1) every block histograms the digit of its 4096-key tile,
-// (2) one exclusive scan over the digit-major [digit][block] table gives every
-// (digit, block) its output offset, (3) every block re-reads its tile in
-// order, ranks each key among the earlier keys of the same digit (warp
-// match + per-warp counters in shared memory) and scatters it.
+// Single-pass digit placement ("onesweep" form, Merrill & Garland's
+// decoupled look-back applied per digit):
+//   1. one kernel histograms every 8-bit digit of every pass at once (the
+//      digit counts do not depend on the order of the keys) and clears the
+//      look-back slots;
+//   2. per pass, one kernel: every block claims the next 4096-key tile in
+//      order, publishes its digit counts, adds up the counts of the earlier
+//      tiles from their published slots (stopping at the first slot that
+//      already holds an inclusive prefix) and publishes its own inclusive
+//      prefix.  Each warp ranks the keys of its own 512-key part of the
+//      tile among the earlier keys of the same digit (warp match, warp-
+//      private counters, no block barrier), so a tile needs four barriers.
+// A slot is one 32-bit word holding a 2-bit state and a 30-bit count, so a
+// reader sees the state and the count together without a fence.  Six
+// launches per sort (a memset, the histogram, four passes) instead of a
+// histogram, scan and scatter per pass.
 #include "sidm_internal.cuh"
 
 namespace sidm {
 
 namespace {
 
-constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
-constexpr int RS_RADIX = 256;
-constexpr int RS_WARPS = RS_THREADS / WARP;
+constexpr int OS_THREADS = 256;
+constexpr int OS_ITEMS = 16;
+constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
+constexpr int RADIX = 256;
+constexpr int OS_WARPS = OS_THREADS / WARP;
+constexpr int MAX_PASSES = 4;
+constexpr uint32_t SLOT_AGG = 1u << 30;    // the tile's own count
+constexpr uint32_t SLOT_PRE = 2u << 30;    // the count of this and every earlier tile
+constexpr uint32_t SLOT_STATE = 3u << 30;
+constexpr uint32_t SLOT_VALUE = (1u << 30) - 1u;
+constexpr int LOOKBACK_MAX_SPINS = 1 << 20;
+constexpr int LOOKBACK_BATCH = 8;            // earlier slots loaded per round trip
+// temp layout (32-bit words): digit counts [MAX_PASSES][RADIX], tile
+// counters [MAX_PASSES] (padded to 64 words), then the slots
+// [passes][tiles][RADIX]
+constexpr int HEAD_WORDS = MAX_PASSES * RADIX + 64;
 
-constexpr int SC_THREADS = 1024;
-constexpr int SC_ITEMS = 4;
-constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
-
-__global__ void __launch_bounds__(RS_THREADS) rs_hist_kernel(const uint32_t* __restrict__ keys,
-                                                             int64_t n, int shift,
-                                                             uint32_t* __restrict__ hist,
-                                                             int nblocks) {
-  __shared__ uint32_t h[RS_RADIX];
-  h[threadIdx.x] = 0;
-  __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-  for (int r = 0; r < RS_ITEMS; ++r) {
-    const int64_t i = base + (int64_t)r * RS_THREADS + threadIdx.x;
-    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
-  }
-  __syncthreads();
-  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+__device__ __forceinline__ void st_relaxed_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
-__global__ void __launch_bounds__(RS_THREADS) rs_scatter_kernel(
-    const uint32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
-    uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int64_t n, int shift,
-    const uint32_t* __restrict__ offs, int nblocks) {
-  __shared__ uint32_t s_run[RS_RADIX];
-  __shared__ uint32_t s_cnt[RS_WARPS][RS_RADIX];
-  __shared__ uint32_t s_base[RS_WARPS][RS_RADIX];
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  s_run[t] = offs[(int64_t)t * nblocks + blockIdx.x];
-  for (int w = 0; w < RS_WARPS; ++w) s_cnt[w][t] = 0;
-  __syncthreads();
-  const uint32_t lt = (1u << lane) - 1u;
-  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
-  for (int r = 0; r < RS_ITEMS; ++r) {
-    const int64_t i = base + (int64_t)r * RS_THREADS + t;
-    const bool valid = i < n;
-    uint32_t key = 0, d = RS_RADIX;
-    int32_t val = 0;
-    if (valid) {
-      key = keys_in[i];
-      val = vals_in[i];
-      d = (key >> shift) & 255u;
-    }
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const uint32_t rank = __popc(peers & lt);
-    if (valid && rank == 0) s_cnt[warp][d] = __popc(peers);
-    __syncthreads();
-    {
-      uint32_t run = s_run[t];
-      for (int w = 0; w < RS_WARPS; ++w) {
-        const uint32_t c = s_cnt[w][t];
-        s_base[w][t] = run;
-        run += c;
-        s_cnt[w][t] = 0;
-      }
-      s_run[t] = run;
-    }
-    __syncthreads();
-    if (valid) {
-      const uint32_t pos = s_base[warp][d] + rank;
-      keys_out[pos] = key;
-      vals_out[pos] = val;
-    }
-  }
-}
-
-// Block-wide exclusive scan of SC_TILE items; returns the tile total.
-__device__ uint32_t block_scan_tile(uint32_t (&v)[SC_ITEMS], uint32_t* s_warp) {
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  uint32_t sum = 0;
+__global__ void __launch_bounds__(OS_THREADS) os_hist_kernel(const uint32_t* __restrict__ keys,
+                                                             int64_t n, int passes,
+                                                             uint32_t* __restrict__ counts,
+                                                             uint32_t* __restrict__ slots,
+                                                             int tiles) {
+  __shared__ uint32_t h[MAX_PASSES][RADIX];
+  const int t = threadIdx.x;
 #pragma unroll
-  for (int k = 0; k < SC_ITEMS; ++k) { const uint32_t x = v[k]; v[k] = sum; sum += x; }
-  uint32_t inc = sum;
+  for (int p = 0; p < MAX_PASSES; ++p) h[p][t] = 0;
+  for (int p = 0; p < passes; ++p)
+    slots[((int64_t)p * tiles + blockIdx.x) * RADIX + t] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * OS_TILE;
+  for (int r = 0; r < OS_ITEMS; ++r) {
+    const int64_t i = base + (int64_t)r * OS_THREADS + t;
+    if (i < n) {
+      const uint32_t k = keys[i];
+      for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 255u], 1u);
+    }
+  }
+  __syncthreads();
+  for (int p = 0; p < passes; ++p)
+    if (h[p][t]) atomicAdd(&counts[p * RADIX + t], h[p][t]);
+}
+
+__global__ void __launch_bounds__(OS_THREADS) os_pass_kernel(
+    const uint32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
+    uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int64_t n, int pass,
+    const uint32_t* __restrict__ counts, uint32_t* tile_ctr, uint32_t* slots, unsigned* status) {
+  __shared__ uint32_t s_tile;
+  __shared__ uint32_t s_cnt[OS_WARPS][RADIX];   // per warp: keys of each digit, then their start
+  __shared__ uint32_t s_wsum[OS_WARPS];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int shift = 8 * pass;
+  if (t == 0) s_tile = atomicAdd(&tile_ctr[pass], 1u);
+#pragma unroll
+  for (int w = 0; w < OS_WARPS; ++w) s_cnt[w][t] = 0;
+  __syncthreads();
+  const int64_t tile = s_tile;
+  // warp w holds keys [w 512, (w + 1) 512) of the tile, 32 per round in order
+  const int64_t base = tile * OS_TILE + (int64_t)warp * (OS_ITEMS * WARP);
+
+  // 1. rank every key among the earlier keys of its digit in the warp's
+  //    sub-tile (warp-private counters, no block barrier)
+  uint32_t key[OS_ITEMS], rank[OS_ITEMS];
+  int32_t val[OS_ITEMS];
+  const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < OS_ITEMS; ++r) {
+    const int64_t i = base + (int64_t)r * WARP + lane;
+    const bool valid = i < n;
+    key[r] = valid ? keys_in[i] : 0u;
+    val[r] = valid ? vals_in[i] : 0;
+    const uint32_t d = valid ? (key[r] >> shift) & 255u : (uint32_t)RADIX;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const int leader = __ffs(peers) - 1;
+    uint32_t before = 0;
+    if (valid && lane == leader) {
+      before = s_cnt[warp][d];
+      s_cnt[warp][d] = before + __popc(peers);
+    }
+    rank[r] = __shfl_sync(0xffffffffu, before, leader) + __popc(peers & lt);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // 2. the tile's count of digit t; publish it, then look back over the
+  //    earlier tiles
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int w = 0; w < OS_WARPS; ++w) cnt += s_cnt[w][t];
+  uint32_t* my = slots + tile * RADIX + t;
+  st_relaxed_u32(my, (tile == 0 ? SLOT_PRE : SLOT_AGG) | cnt);
+  uint32_t excl = 0;
+  if (tile > 0) {
+    // slots j, j-1, ... are loaded LOOKBACK_BATCH at a time and consumed in
+    // order until an inclusive prefix; a slot not yet published is
+    // reloaded (the earlier tile's block is resident and publishes before
+    // it waits on anything; the wait is bounded nonetheless)
+    int64_t j = tile - 1;
+    int spins = 0;
+    bool done = false;
+    while (!done) {
+      uint32_t v[LOOKBACK_BATCH];
+#pragma unroll
+      for (int k = 0; k < LOOKBACK_BATCH; ++k)
+        v[k] = j - k >= 0 ? ld_relaxed_u32(slots + (j - k) * RADIX + t) : 0u;
+      bool stall = false;
+#pragma unroll
+      for (int k = 0; k < LOOKBACK_BATCH; ++k) {
+        if (done || stall) continue;
+        const uint32_t state = v[k] & SLOT_STATE;
+        if (state == 0u) { stall = true; continue; }
+        excl += v[k] & SLOT_VALUE;
+        if (state == SLOT_PRE || j == 0) done = true;
+        else --j;
+      }
+      if (stall && ++spins > LOOKBACK_MAX_SPINS) {
+        atomicOr(status, (unsigned)ST_ERR_SORT);
+        break;
+      }
+    }
+    st_relaxed_u32(my, SLOT_PRE | (excl + cnt));
+  }
+
+  // 3. start of digit t in the output (keys of smaller digits, then the
+  //    earlier tiles' keys of digit t), then of each warp's run of it
+  const uint32_t g = counts[pass * RADIX + t];
+  uint32_t inc = g;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
     if (lane >= o) inc += y;
   }
-  if (lane == 31) s_warp[warp] = inc;
+  if (lane == 31) s_wsum[warp] = inc;
   __syncthreads();
-  if (warp == 0) {
-    uint32_t w = (lane < SC_THREADS / 32) ? s_warp[lane] : 0u;
-    uint32_t wi = w;
+  uint32_t run = inc - g + excl;
+  for (int w = 0; w < warp; ++w) run += s_wsum[w];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-      if (lane >= o) wi += y;
-    }
-    s_warp[lane] = wi - w;         // exclusive prefix of warp totals
-    if (lane == 31) s_warp[32] = wi;
+  for (int w = 0; w < OS_WARPS; ++w) {
+    const uint32_t c = s_cnt[w][t];
+    s_cnt[w][t] = run;
+    run += c;
   }
   __syncthreads();
-  const uint32_t off = s_warp[warp] + (inc - sum);
-#pragma unroll
-  for (int k = 0; k < SC_ITEMS; ++k) v[k] += off;
-  const uint32_t total = s_warp[32];
-  __syncthreads();
-  return total;
-}
 
-__global__ void __launch_bounds__(SC_THREADS) scan_tiles_kernel(const uint32_t* in, uint32_t* out,
-                                                               int64_t n, uint32_t* sums) {
-  __shared__ uint32_t s_warp[33];
-  const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
-  uint32_t v[SC_ITEMS];
+  // 4. scatter (stable: warp, then round, then lane is the input order)
 #pragma unroll
-  for (int k = 0; k < SC_ITEMS; ++k) v[k] = (base + k < n) ? in[base + k] : 0u;
-  const uint32_t total = block_scan_tile(v, s_warp);
-#pragma unroll
-  for (int k = 0; k < SC_ITEMS; ++k)
-    if (base + k < n) out[base + k] = v[k];
-  if (threadIdx.x == 0 && sums) sums[blockIdx.x] = total;
-}
-
-__global__ void __launch_bounds__(SC_THREADS) scan_add_kernel(uint32_t* out, int64_t n,
-                                                             const uint32_t* sums) {
-  const uint32_t add = sums[blockIdx.x];
-  const int64_t base = (int64_t)blockIdx.x * SC_TILE;
-  for (int k = threadIdx.x; k < SC_TILE; k += SC_THREADS)
-    if (base + k < n) out[base + k] += add;
+  for (int r = 0; r < OS_ITEMS; ++r) {
+    const int64_t i = base + (int64_t)r * WARP + lane;
+    if (i < n) {
+      const uint32_t pos = s_cnt[warp][(key[r] >> shift) & 255u] + rank[r];
+      keys_out[pos] = key[r];
+      vals_out[pos] = val[r];
+    }
+  }
 }
 
 }  // namespace
 
-size_t exclusive_scan_temp_bytes(int64_t n) {
-  const int64_t tiles = (n + SC_TILE - 1) / SC_TILE;
-  return (size_t)(tiles + 1) * sizeof(uint32_t);
-}
-
-// Exclusive scan of n uint32 (in may equal out); n <= SC_TILE^2 (16.7 M).
-int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* tmp,
-                       cudaStream_t s) {
-  if (n <= 0) return 0;
-  const int64_t tiles = (n + SC_TILE - 1) / SC_TILE;
-  if (tiles == 1) {
-    scan_tiles_kernel<<<1, SC_THREADS, 0, s>>>(in, out, n, nullptr);
-    return 1;
-  }
-  scan_tiles_kernel<<<(unsigned)tiles, SC_THREADS, 0, s>>>(in, out, n, tmp);
-  scan_tiles_kernel<<<1, SC_THREADS, 0, s>>>(tmp, tmp, tiles, nullptr);
-  scan_add_kernel<<<(unsigned)tiles, SC_THREADS, 0, s>>>(out, n, tmp);
-  return 3;
-}
-
 size_t radix_sort_temp_bytes(int64_t n) {
-  const int64_t nblocks = (n + RS_TILE - 1) / RS_TILE;
-  const int64_t entries = nblocks * RS_RADIX;
-  return (size_t)entries * sizeof(uint32_t) + exclusive_scan_temp_bytes(entries) + 256;
+  const int64_t tiles = (n + OS_TILE - 1) / OS_TILE;
+  return (size_t)(HEAD_WORDS + (int64_t)MAX_PASSES * tiles * RADIX) * sizeof(uint32_t);
 }
 
 // Sorts (keys, vals) by the low `key_bits` bits of the keys; the result is
-// left in (keys, vals).  keys_alt / vals_alt are scratch of n entries.
+// left in (keys, vals).  keys_alt / vals_alt are scratch of n entries;
+// n < 2^30.  A look-back that gives up sets ST_ERR_SORT in *status (the
+// order is then not valid; every index written stays below n).
 int radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_alt, int32_t* vals_alt,
-                     int64_t n, int key_bits, void* temp, cudaStream_t s) {
+                     int64_t n, int key_bits, void* temp, unsigned* status, cudaStream_t s) {
   if (n <= 1) return 0;
-  int launches = 0;
-  const int nblocks = (int)((n + RS_TILE - 1) / RS_TILE);
-  const int64_t entries = (int64_t)nblocks * RS_RADIX;
-  uint32_t* hist = (uint32_t*)temp;
-  uint32_t* scan_tmp = hist + entries;
+  const int tiles = (int)((n + OS_TILE - 1) / OS_TILE);
   int passes = (key_bits + 7) / 8;
   if (passes & 1) ++passes;  // even number of passes: the result lands back in keys/vals
+  if (passes > MAX_PASSES) passes = MAX_PASSES;
+  uint32_t* counts = (uint32_t*)temp;
+  uint32_t* tile_ctr = counts + MAX_PASSES * RADIX;
+  uint32_t* slots = counts + HEAD_WORDS;
+  if (cudaMemsetAsync(counts, 0, HEAD_WORDS * sizeof(uint32_t), s) != cudaSuccess) return -1;
+  os_hist_kernel<<<tiles, OS_THREADS, 0, s>>>(keys, n, passes, counts, slots, tiles);
   uint32_t* kin = keys;
   int32_t* vin = vals;
   uint32_t* kout = keys_alt;
   int32_t* vout = vals_alt;
   for (int p = 0; p < passes; ++p) {
-    const int shift = 8 * p;
-    rs_hist_kernel<<<nblocks, RS_THREADS, 0, s>>>(kin, n, shift, hist, nblocks);
-    launches += 2 + exclusive_scan_u32(hist, hist, entries, scan_tmp, s);
-    rs_scatter_kernel<<<nblocks, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, hist, nblocks);
+    os_pass_kernel<<<tiles, OS_THREADS, 0, s>>>(kin, vin, kout, vout, n, p, counts, tile_ctr,
+                                                slots + (int64_t)p * tiles * RADIX, status);
     uint32_t* tk = kin; kin = kout; kout = tk;
     int32_t* tv = vin; vin = vout; vout = tv;
   }
-  return launches;
+  return 1 + passes;
 }
 
 }  // namespace sidm
