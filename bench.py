@@ -491,7 +491,12 @@ def main():
         torch.cuda.synchronize()
     launches = ctx.kernel_launches - l0
     ctx_graph_state = ctx.graph_state
-    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = sum(step_ms)
+    srt = sorted(range(len(step_ms)), key=lambda i: step_ms[i])
+    step_dist = {"median": step_ms[srt[len(srt) // 2]], "max": step_ms[srt[-1]],
+                 "slowest": [[(args.warmup + i) % CYCLE, round(step_ms[i], 3)] for i in srt[-3:]],
+                 "note": "finest step index in the cycle: the all-active step 0 is the slowest"}
     if dist:
         import torch.distributed as D
         tt = torch.tensor([t_ms, float(upd)], dtype=torch.float64, device=dev)
@@ -602,7 +607,7 @@ def main():
                            "l2": "flushed between timed steps (256 MB write)"},
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(),
-                "launch": {"graph": ctx_graph_state, "tuning": tuning},
+                "launch": {"graph": ctx_graph_state, "tuning": tuning}, "step_ms": step_dist,
                 "tree_reuse": reuse}
         print(json.dumps(line), flush=True)
     if dist:
