@@ -40,6 +40,12 @@ constexpr float REL = 9.5367431640625e-07f;   // 2^-20
 constexpr float ABS = 4.76837158203125e-07f;  // 2^-21
 constexpr float CREL = REL + ABS;             // relative part of the bounds
 constexpr float SQ = 4.76837158203125e-07f;   // 2^-21: slack on squared thresholds
+// The gather walk visits leaves without stacking them, so its stack holds at
+// most 31 entries for each internal level below the root except the lowest,
+// plus one: 31 * 4 + 1 = 125 for the 6 levels of n < 2^30.  128 entries keep
+// a block's shared memory at 26 KB, so that 8 blocks fit on an SM (228 KB,
+// 1 KB reserved per block).
+constexpr int WALK_STACK = 128;
 #ifndef SEARCH_LEAF_BATCH
 #define SEARCH_LEAF_BATCH 4                    // leaves per L2 round trip in the gather walk
 #endif
@@ -126,7 +132,7 @@ template <bool PERIODIC, int NWIN>
 __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
   __shared__ float s_r2[SW][SEARCH_CAP];
   __shared__ int32_t s_j[SW][SEARCH_CAP];
-  __shared__ int s_stack[SW][SEARCH_STACK];
+  __shared__ int s_stack[SW][WALK_STACK];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
   float* lst_r2 = s_r2[warp];
@@ -210,7 +216,7 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
       const float g2 = T < INFINITY ? thr_out2(T * (1.0f + REL), eq) : INFINITY;
       const float rad = (T + 2.0f * eq) * (1.0f + 4.0f * REL);
       const float rad2 = rad < INFINITY ? rad * rad : INFINITY;
-      const bool ok = traverse<PERIODIC, false, SEARCH_LEAF_BATCH>(
+      const bool ok = traverse<PERIODIC, false, SEARCH_LEAF_BATCH, WALK_STACK>(
           A.f, H, hpos, fi, rad2, boxf, stack, [&](int k, bool valid, const float4& pj) {
         float s2 = 0.0f;
         bool keep = false;
@@ -251,7 +257,7 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
         const float in2 = thr_in2(Tn, eq);
         const float radn = (Tn + 2.0f * eq) * (1.0f + 4.0f * REL);
         int c = 0;
-        const bool ok2 = traverse<PERIODIC, false, SEARCH_LEAF_BATCH>(
+        const bool ok2 = traverse<PERIODIC, false, SEARCH_LEAF_BATCH, WALK_STACK>(
             A.f, H, hpos, fi, radn * radn, boxf, stack, [&](int k, bool valid, const float4& pj) {
           bool in = false;
           if (valid && k != sl) in = sep2f<PERIODIC>(fi, pj, boxf) < in2;

@@ -58,7 +58,9 @@ __device__ __forceinline__ float sep2f(const float4& a, const float4& b, float b
 // tested, LB at a time, with their particle loads issued together (one L2
 // round trip per LB leaves; leaf_fn is replicated LB times).  LB = 0: hit
 // leaves go on the stack like the other nodes (smallest code).
-template <bool PERIODIC, bool HMAX = false, int LB = 0, class LeafFn>
+// CAP: stack entries; the walk reports an overflow (returns false) rather
+// than exceed it.
+template <bool PERIODIC, bool HMAX = false, int LB = 0, int CAP = SEARCH_STACK, class LeafFn>
 __device__ __forceinline__ bool traverse(const Forest& f, const Halo& H,
                                          const float4* __restrict__ hpos, const float4& q,
                                          float rad2, float box, int* stack, LeafFn&& leaf_fn,
@@ -119,7 +121,7 @@ __device__ __forceinline__ bool traverse(const Forest& f, const Halo& H,
         }
       } else {
         const int cnt = __popc(m);
-        if (top + cnt > SEARCH_STACK) return false;
+        if (top + cnt > CAP) return false;
         if (hit) stack[top + __popc(m & lt)] = ((level - 1) << 28) | k;
         top += cnt;
         __syncwarp();
