@@ -38,7 +38,7 @@ CYCLE = 100
 # 4-byte ids/indices, 1-byte flags).
 PHASE_BYTES = {
     "keys": (56.0, 0.0),        # bbox read 24, keys read 24, key+index write 8
-    "sort": (96.0, 0.0),        # 4 passes x (hist read 4 + scatter read 8 + write 8) + index
+    "sort": (68.0, 0.0),        # one histogram read 4 + 4 passes x (read 8 + write 8)
     "structure": (190.0, 0.0),  # gather 66 read, key-order state 97 written, leaf boxes ~27
     "search": (16.0, 56.0),     # FP32 positions once; own state 40 read, h 16 written
     "pairs": (0.0, 92.0),       # own state 84 read, Eq. 18 limit 8 written
