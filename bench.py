@@ -46,6 +46,10 @@ PHASE_BYTES = {
 }
 
 
+SEARCH_DRAM_BYTES = 6.547712e6 + 1.033472e6   # dram read + write of the captured launch
+SEARCH_DRAM_QUERIES = 51520
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -558,8 +562,15 @@ def main():
     bytes_per_step = per_n * n + per_a * (n_act_sum / reps)
     avg_ms = phase_sum[dom] / reps
     achieved = bytes_per_step / (avg_ms * 1e-3) / 1e9
+    # DRAM bytes of the search kernel from one ncu capture of the current
+    # kernel (7.58 MB on a launch of 51,520 queries of this workload),
+    # scaled to this run's mean queries per step
+    traffic = (SEARCH_DRAM_BYTES * (n_act_sum / reps) / SEARCH_DRAM_QUERIES
+               if dom == "search" else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "kernel": dom,
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "traffic_note": "bytes per launch, scaled by queries from a 51,520-query capture",
+                "kernel": dom,
                 "peak_kind": peak_kind,
                 "phase_ms_per_step": {k: v / reps for k, v in phase_sum.items()},
                 "phase_share": {k: v / sum(phase_sum.values()) for k, v in phase_sum.items()}}
