@@ -156,8 +156,23 @@ SIDM_API int sidm_set_particles(sidm_ctx* ctx, int64_t n, const double* pos, con
                        const double* mass, double mass_scalar, const uint32_t* ids,
                        int ptr_kind);
 
-/* Replaces the velocities only (n must equal the loaded count). */
+/* Replaces the velocities only (n x 3, the loaded count).  The copy runs on
+ * a stream of the context's own, after the work already queued on
+ * config.stream that uses the velocities, so that it overlaps the first part
+ * of the next step (keys, sort, tree and search read positions only); every
+ * later call that uses the velocities is ordered after it.  The source
+ * buffer must stay unchanged until the copy is done: after the next
+ * sidm_step, sidm_get_particles or sidm_sync has returned on the host
+ * (sidm_step returns before it is done). */
 SIDM_API int sidm_set_velocities(sidm_ctx* ctx, const double* vel, int ptr_kind);
+
+/* Replaces the positions only (n x 3, the loaded count), as between two
+ * scattering steps of a simulation whose particles drift (Fig. 1: the step
+ * reads the current positions).  Masses, ids, h, the dt limits and the halo
+ * layout are kept.  With a periodic box every coordinate must lie in
+ * [0, box); the check waits for the stream and returns
+ * SIDM_ERR_INVALID_ARG (positions are then already replaced). */
+SIDM_API int sidm_set_positions(sidm_ctx* ctx, const double* pos, int ptr_kind);
 
 /* One scattering step (the whole path above).
  *   active_mask: n bytes, nonzero = active; NULL = all particles active.

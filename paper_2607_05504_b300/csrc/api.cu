@@ -78,11 +78,19 @@ struct sidm_ctx {
   // launch shapes and the captured step
   LaunchTuning tune{};
   uint64_t layout_version = 1;  // bumped whenever buffers, haloes or tuning change
-  // captured steps: [0] refit only, [1] full rebuild (keys + sort)
-  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  // captured steps: [0] refit only, [1] full rebuild (keys + sort); each in
+  // two parts, [.][0] up to the search and [.][1] from the key-order
+  // velocities on, so that a velocity upload can run beside the first part
+  cudaGraphExec_t graph_exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   uint64_t graph_version[2] = {0, 0};  // layout each graph was captured for
-  int64_t graph_launches[2] = {0, 0};  // kernels in each graph
+  int64_t graph_launches[2] = {0, 0};  // kernels in each graph (both parts)
   int graph_state = 0;          // 0 off, 1 captured, -1 capture refused (direct launches)
+  // velocity uploads on a side stream: they overlap the first part of the
+  // next step; every use of the velocities waits for them (join_velocities)
+  cudaStream_t vstream = nullptr;
+  cudaEvent_t ev_vfree = nullptr;   // the stream's earlier work on the velocities
+  cudaEvent_t ev_vdone = nullptr;   // the upload
+  bool vel_pending = false;
   // key order kept between full rebuilds
   uint64_t order_version = 0;   // layout of the last full rebuild
   int64_t since_rebuild = 0;    // steps since it
@@ -131,10 +139,19 @@ cudaError_t dalloc(sidm_ctx* c, T** p, size_t count) {
 
 void drop_graph(sidm_ctx* c) {
   for (int k = 0; k < 2; ++k) {
-    if (c->graph_exec[k]) cudaGraphExecDestroy(c->graph_exec[k]);
-    c->graph_exec[k] = nullptr;
+    for (int part = 0; part < 2; ++part) {
+      if (c->graph_exec[k][part]) cudaGraphExecDestroy(c->graph_exec[k][part]);
+      c->graph_exec[k][part] = nullptr;
+    }
     c->graph_version[k] = 0;
   }
+}
+
+// Orders the context's stream after a pending velocity upload.
+cudaError_t join_velocities(sidm_ctx* c) {
+  if (!c->vel_pending) return cudaSuccess;
+  c->vel_pending = false;
+  return cudaStreamWaitEvent(c->stream, c->ev_vdone, 0);
 }
 
 void free_buffers(sidm_ctx* c) {
@@ -384,18 +401,22 @@ void set_step_params(Halo& h, double dt_max, const sidm_sigma_model& s, uint64_t
 // copies and the halo table upload come before), so the sequence can be
 // captured once into a CUDA graph and replayed while the particle count,
 // the halo layout, the buffers and the launch shapes stay the same.
-int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches) {
+// part 0: from the counter reset to the search (positions only); part 1:
+// from the key-order velocities to the status latch.
+int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches, int part) {
   const int64_t n = c->n;
   cudaStream_t s = c->stream;
-  CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), s));
-  CK(cudaMemsetAsync(c->work, 0, 8 * sizeof(int), s));
   int64_t L = 0;
+  if (part == 0) {
+    CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), s));
+    CK(cudaMemsetAsync(c->work, 0, 8 * sizeof(int), s));
+  }
   auto mark = [&](int k) {
     if (prof) cudaEventRecord(c->ev[k], s);
   };
   const int nh = (int)c->halos.size();
   const Forest& F = c->forest;
-  if (n > 0) {
+  if (n > 0 && part == 0) {
     mark(0);
     L += launch_bbox(c->pos, c->halo_of, n, c->d_halos, nh, s);
     L += launch_params(c->d_halos, nh, c->cfg.box, s);
@@ -411,7 +432,7 @@ int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches) {
       L += sl;
     }
     mark(2);
-    L += launch_permute(c->vals, n, c->pos, c->vel, c->mass, c->ids, c->halo_of, c->act,
+    L += launch_permute(c->vals, n, c->pos, c->mass, c->ids, c->halo_of, c->act,
                         c->bins, c->d_halos, c->so, c->act_list, c->dstats, s);
     L += launch_forest(c->so, F, s);
     mark(3);
@@ -423,6 +444,9 @@ int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches) {
                        c->cfg.estimator == SIDM_ESTIMATOR_OVERLAP, s);
     if (c->cfg.estimator == SIDM_ESTIMATOR_OVERLAP) L += launch_hmax(c->so, F, s);
     mark(4);
+  }
+  if (n > 0 && part == 1) {
+    L += launch_permute_vel(n, c->vel, c->so, s);
     PairArgs pa;
     pa.kernel = c->cfg.kernel;
     pa.split = c->cfg.precision == SIDM_FP32_SPLIT;
@@ -444,8 +468,10 @@ int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches) {
     L += nr;
     mark(6);
   }
-  latch_kernel<<<1, 32, 0, s>>>(c->dstats, c->latched);
-  L += 1;
+  if (part == 1) {
+    latch_kernel<<<1, 32, 0, s>>>(c->dstats, c->latched);
+    L += 1;
+  }
   *launches = L;
   return SIDM_OK;
 }
@@ -453,33 +479,41 @@ int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches) {
 // Captures launch_core into a graph; a capture the driver refuses leaves the
 // context on direct launches (graph_state -1).
 void capture_core(sidm_ctx* c, int rebuild) {
-  if (c->graph_exec[rebuild]) cudaGraphExecDestroy(c->graph_exec[rebuild]);
-  c->graph_exec[rebuild] = nullptr;
-  cudaGraph_t g = nullptr;
-  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-    cudaGetLastError();
-    c->graph_state = -1;
-    return;
+  int64_t total = 0;
+  for (int part = 0; part < 2; ++part) {
+    cudaGraphExec_t& x = c->graph_exec[rebuild][part];
+    if (x) cudaGraphExecDestroy(x);
+    x = nullptr;
   }
-  int64_t k = 0;
-  const int r = launch_core(c, false, rebuild != 0, &k);
-  const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-  if (r != SIDM_OK || e != cudaSuccess || !g) {
-    if (g) cudaGraphDestroy(g);
-    cudaGetLastError();
-    c->graph_state = -1;
-    return;
-  }
-  const cudaError_t ei = cudaGraphInstantiate(&c->graph_exec[rebuild], g, 0);
-  cudaGraphDestroy(g);
-  if (ei != cudaSuccess) {
-    c->graph_exec[rebuild] = nullptr;
-    cudaGetLastError();
-    c->graph_state = -1;
-    return;
+  for (int part = 0; part < 2; ++part) {
+    cudaGraphExec_t& x = c->graph_exec[rebuild][part];
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      c->graph_state = -1;
+      return;
+    }
+    int64_t k = 0;
+    const int r = launch_core(c, false, rebuild != 0, &k, part);
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (r != SIDM_OK || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      c->graph_state = -1;
+      return;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      x = nullptr;
+      cudaGetLastError();
+      c->graph_state = -1;
+      return;
+    }
+    total += k;
   }
   c->graph_version[rebuild] = c->layout_version;
-  c->graph_launches[rebuild] = k;
+  c->graph_launches[rebuild] = total;
   c->graph_state = 1;
 }
 
@@ -504,7 +538,10 @@ int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
   const int r0 = upload_haloes(c);
   if (r0 != SIDM_OK) return r0;
   int64_t& L = c->launches;
-  if (stats) L += launch_conserved(c->vel, c->mass, n, c->cons_partial, c->cons, s);
+  if (stats) {
+    CK(join_velocities(c));
+    L += launch_conserved(c->vel, c->mass, n, c->cons_partial, c->cons, s);
+  }
   const bool prof = c->have_events && n > 0;
   c->timed_step = prof;
   // full rebuild (keys + sort) or a refit in the key order of the last one
@@ -512,19 +549,25 @@ int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
                        c->since_rebuild >= c->cfg.rebuild_every) ? 1 : 0;
   bool done = false;
   if (c->cfg.use_graph && !prof && n > 0 && c->graph_state >= 0) {
-    if (!c->graph_exec[rebuild] || c->graph_version[rebuild] != c->layout_version)
+    if (!c->graph_exec[rebuild][0] || !c->graph_exec[rebuild][1] ||
+        c->graph_version[rebuild] != c->layout_version)
       capture_core(c, rebuild);
-    if (c->graph_exec[rebuild]) {
-      CK(cudaGraphLaunch(c->graph_exec[rebuild], s));
+    if (c->graph_exec[rebuild][0] && c->graph_exec[rebuild][1]) {
+      CK(cudaGraphLaunch(c->graph_exec[rebuild][0], s));
+      CK(join_velocities(c));
+      CK(cudaGraphLaunch(c->graph_exec[rebuild][1], s));
       L += c->graph_launches[rebuild];
       done = true;
     }
   }
   if (!done) {
-    int64_t k = 0;
-    const int r = launch_core(c, prof, rebuild != 0, &k);
-    L += k;
-    if (r != SIDM_OK) return r;
+    for (int part = 0; part < 2; ++part) {
+      if (part == 1) CK(join_velocities(c));
+      int64_t k = 0;
+      const int r = launch_core(c, prof, rebuild != 0, &k, part);
+      L += k;
+      if (r != SIDM_OK) return r;
+    }
   }
   if (rebuild) {
     c->order_version = c->layout_version;
@@ -611,6 +654,12 @@ int sidm_create(const sidm_config* cfg, sidm_ctx** out) {
     }
     c->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&c->vstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_vfree, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_vdone, cudaEventDisableTiming) != cudaSuccess) {
+    sidm_destroy(c);
+    return SIDM_ERR_CUDA;
+  }
   if (cudaMallocHost(&c->h_stats, sizeof(DevStats)) != cudaSuccess ||
       cudaMallocHost(&c->h_cons, 8 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&c->h_latched, sizeof(unsigned)) != cudaSuccess) {
@@ -640,12 +689,34 @@ int sidm_phase_times(sidm_ctx* c, float* ms, int n) {
 
 int64_t sidm_kernel_launches(const sidm_ctx* c) { return c ? c->launches : -1; }
 
+// Periodic box: checks that every loaded coordinate lies in [0, box) (one
+// bounding-box pass over all haloes together; waits for the stream).
+int check_in_box(sidm_ctx* c) {
+  const int64_t n = c->n;
+  const int nh = (int)c->halos.size();
+  int r = upload_haloes(c);
+  if (r != SIDM_OK) return r;
+  launch_bbox(c->pos, c->halo_of, n, c->d_halos, nh, c->stream);
+  std::vector<unsigned long long> hm(6 * (size_t)nh);
+  for (int k = 0; k < nh; ++k)
+    CK(cudaMemcpyAsync(hm.data() + 6 * k, (const char*)(c->d_halos + k) + offsetof(Halo, mm),
+                       6 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < nh; ++k)
+    for (int a = 0; a < 3; ++a) {
+      const double lo = ordered_to_dbl(hm[6 * k + a]), hi = ordered_to_dbl(hm[6 * k + 3 + a]);
+      if (c->halos[k].n > 0 && (!(lo >= 0.0) || !(hi < c->cfg.box))) return SIDM_ERR_INVALID_ARG;
+    }
+  return SIDM_OK;
+}
+
 int sidm_set_particles(sidm_ctx* c, int64_t n, const double* pos, const double* vel,
                        const double* mass, double mass_scalar, const uint32_t* ids, int ptr_kind) {
   if (!c || n < 0 || n >= (int64_t)1 << 30 || (n > 0 && (!pos || !vel || !ids)) ||
       (ptr_kind != SIDM_HOST && ptr_kind != SIDM_DEVICE) || (!mass && !(mass_scalar > 0.0)))
     return SIDM_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
+  CK(join_velocities(c));
   int r = ensure_capacity(c, n);
   if (r != SIDM_OK) return r;
   const cudaMemcpyKind k = copy_kind_in(ptr_kind);
@@ -662,22 +733,16 @@ int sidm_set_particles(sidm_ctx* c, int64_t n, const double* pos, const double* 
   const int64_t off[2] = {0, n};
   r = layout_haloes(c, 1, off);
   if (r != SIDM_OK) return r;
+  c->n = n;
   // periodic box: every coordinate in [0, box)
   if (c->cfg.box > 0.0 && n > 0) {
-    r = upload_haloes(c);
-    if (r != SIDM_OK) return r;
-    launch_bbox(c->pos, c->halo_of, n, c->d_halos, 1, c->stream);
-    unsigned long long hm[6];
-    CK(cudaMemcpyAsync(hm, (const char*)c->d_halos + offsetof(Halo, mm), sizeof(hm),
-                       cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    for (int a = 0; a < 3; ++a) {
-      const double lo = ordered_to_dbl(hm[a]), hi = ordered_to_dbl(hm[3 + a]);
-      if (!(lo >= 0.0) || !(hi < c->cfg.box)) return SIDM_ERR_INVALID_ARG;
+    r = check_in_box(c);
+    if (r != SIDM_OK) {
+      c->n = 0;
+      return r;
     }
   }
   CK(cudaGetLastError());
-  c->n = n;
   c->loaded = true;
   return SIDM_OK;
 }
@@ -688,15 +753,34 @@ int sidm_set_haloes(sidm_ctx* c, int32_t n_halos, const int64_t* offsets) {
   for (int k = 0; k < n_halos; ++k)
     if (offsets[k + 1] < offsets[k]) return SIDM_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
+  CK(join_velocities(c));
   return layout_haloes(c, n_halos, offsets);
+}
+
+int sidm_set_positions(sidm_ctx* c, const double* pos, int ptr_kind) {
+  if (!c || !c->loaded || !pos || (ptr_kind != SIDM_HOST && ptr_kind != SIDM_DEVICE))
+    return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  const int64_t n = c->n;
+  if (n > 0)
+    CK(cudaMemcpyAsync(c->pos, pos, 3 * n * sizeof(double), copy_kind_in(ptr_kind), c->stream));
+  if (c->cfg.box > 0.0 && n > 0) return check_in_box(c);
+  return SIDM_OK;
 }
 
 int sidm_set_velocities(sidm_ctx* c, const double* vel, int ptr_kind) {
   if (!c || !c->loaded || !vel || (ptr_kind != SIDM_HOST && ptr_kind != SIDM_DEVICE))
     return SIDM_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
-  if (c->n > 0)
-    CK(cudaMemcpyAsync(c->vel, vel, 3 * c->n * sizeof(double), copy_kind_in(ptr_kind), c->stream));
+  if (c->n > 0) {
+    // after the stream's earlier work on the velocities, beside its next work
+    CK(cudaEventRecord(c->ev_vfree, c->stream));
+    CK(cudaStreamWaitEvent(c->vstream, c->ev_vfree, 0));
+    CK(cudaMemcpyAsync(c->vel, vel, 3 * c->n * sizeof(double), copy_kind_in(ptr_kind),
+                       c->vstream));
+    CK(cudaEventRecord(c->ev_vdone, c->vstream));
+    c->vel_pending = true;
+  }
   return SIDM_OK;
 }
 
@@ -991,6 +1075,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
         !valid_sigma(c, params[k].sigma))
       return SIDM_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
+  CK(join_velocities(c));
   const int64_t n = c->n;
   if (n <= 0) {
     if (best) to_public(c->tune, best);
@@ -1066,6 +1151,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
 int sidm_sync(sidm_ctx* c) {
   if (!c) return SIDM_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
+  CK(join_velocities(c));
   return wait_and_collect(c);
 }
 
@@ -1073,6 +1159,7 @@ int sidm_get_particles(sidm_ctx* c, double* vel_out, double* h_out, int ptr_kind
   if (!c || !c->loaded || (!vel_out && !h_out) || (ptr_kind != SIDM_HOST && ptr_kind != SIDM_DEVICE))
     return SIDM_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
+  CK(join_velocities(c));
   const cudaMemcpyKind k = copy_kind_out(ptr_kind);
   if (c->n > 0) {
     if (vel_out) CK(cudaMemcpyAsync(vel_out, c->vel, 3 * c->n * sizeof(double), k, c->stream));
@@ -1150,6 +1237,7 @@ void sidm_destroy(sidm_ctx* c) {
   if (!c) return;
   {
     DeviceGuard g(c->device);
+    if (c->vstream) cudaStreamSynchronize(c->vstream);
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_buffers(c);
     if (c->h_stats) cudaFreeHost(c->h_stats);
@@ -1160,6 +1248,9 @@ void sidm_destroy(sidm_ctx* c) {
     for (int k = 0; k <= SIDM_N_PHASES; ++k)
       if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->vstream) cudaStreamDestroy(c->vstream);
+    if (c->ev_vfree) cudaEventDestroy(c->ev_vfree);
+    if (c->ev_vdone) cudaEventDestroy(c->ev_vdone);
   }
   delete c;
 }

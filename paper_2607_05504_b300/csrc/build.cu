@@ -242,9 +242,11 @@ __global__ void __launch_bounds__(BT) keys_kernel(const double* __restrict__ pos
   vals[i] = (int32_t)i;
 }
 
+// Key-order copy of everything but the velocities (which the search does not
+// read: they are copied by permute_vel_kernel just before the pair kernels).
 __global__ void __launch_bounds__(BT) permute_kernel(
     const int32_t* __restrict__ perm, int64_t n, const double* __restrict__ pos,
-    const double* __restrict__ vel, const double* __restrict__ mass,
+    const double* __restrict__ mass,
     const uint32_t* __restrict__ ids, const int32_t* __restrict__ halo_of,
     const uint8_t* __restrict__ act, const int8_t* __restrict__ bins,
     const Halo* __restrict__ halos, Sorted so, int32_t* __restrict__ act_list, DevStats* st) {
@@ -262,13 +264,8 @@ __global__ void __launch_bounds__(BT) permute_kernel(
     so.y[s] = y;
     so.z[s] = z;
     const double dt = scale_pow2_down(halos[k].dt_max, (int)bins[o]);
-    const double vx = vel[3 * o], vy = vel[3 * o + 1], vz = vel[3 * o + 2], m = mass[o];
+    const double m = mass[o];
     so.f[s] = make_float4(f64_to_f32_rn(x), f64_to_f32_rn(y), f64_to_f32_rn(z), f64_to_f32_ru(dt));
-    so.vx[s] = vx;
-    so.vy[s] = vy;
-    so.vz[s] = vz;
-    so.vm[s] = make_float4(f64_to_f32_rn(vx), f64_to_f32_rn(vy), f64_to_f32_rn(vz),
-                           f64_to_f32_ru(m));
     so.m[s] = m;
     so.id[s] = ids[o];
     a = act[o] != 0;
@@ -407,6 +404,21 @@ int launch_hmax(const Sorted& so, const Forest& f, cudaStream_t s) {
   return launches;
 }
 
+// Key-order velocities: FP64 copies and the FP32 copy with the mass rounded up.
+__global__ void __launch_bounds__(BT) permute_vel_kernel(int64_t n,
+                                                         const double* __restrict__ vel,
+                                                         Sorted so) {
+  const int64_t s = blockIdx.x * (int64_t)BT + threadIdx.x;
+  if (s >= n) return;
+  const int64_t o = so.orig[s];   // range-checked by permute_kernel
+  const double vx = vel[3 * o], vy = vel[3 * o + 1], vz = vel[3 * o + 2];
+  so.vx[s] = vx;
+  so.vy[s] = vy;
+  so.vz[s] = vz;
+  so.vm[s] = make_float4(f64_to_f32_rn(vx), f64_to_f32_rn(vy), f64_to_f32_rn(vz),
+                         f64_to_f32_ru(so.m[s]));
+}
+
 int launch_keys(const double* pos, const int32_t* halo_of, int64_t n, const Halo* halos,
                 int halo_bits, double box, uint32_t* keys, int32_t* vals, cudaStream_t s) {
   if (n <= 0) return 0;
@@ -414,12 +426,18 @@ int launch_keys(const double* pos, const int32_t* halo_of, int64_t n, const Halo
   return 1;
 }
 
-int launch_permute(const int32_t* perm, int64_t n, const double* pos, const double* vel,
+int launch_permute_vel(int64_t n, const double* vel, const Sorted& so, cudaStream_t s) {
+  if (n <= 0) return 0;
+  permute_vel_kernel<<<blocks_for(n), BT, 0, s>>>(n, vel, so);
+  return 1;
+}
+
+int launch_permute(const int32_t* perm, int64_t n, const double* pos,
                    const double* mass, const uint32_t* ids, const int32_t* halo_of,
                    const uint8_t* act, const int8_t* bins, const Halo* halos, Sorted so,
                    int32_t* act_list, DevStats* st, cudaStream_t s) {
   if (n <= 0) return 0;
-  permute_kernel<<<blocks_for(n), BT, 0, s>>>(perm, n, pos, vel, mass, ids, halo_of, act, bins,
+  permute_kernel<<<blocks_for(n), BT, 0, s>>>(perm, n, pos, mass, ids, halo_of, act, bins,
                                               halos, so, act_list, st);
   return 1;
 }

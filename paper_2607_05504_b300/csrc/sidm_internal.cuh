@@ -325,10 +325,11 @@ int launch_bbox(const double* pos, const int32_t* halo_of, int64_t n, Halo* halo
 int launch_params(Halo* halos, int n_halos, double box, cudaStream_t s);
 int launch_keys(const double* pos, const int32_t* halo_of, int64_t n, const Halo* halos,
                 int halo_bits, double box, uint32_t* keys, int32_t* vals, cudaStream_t s);
-int launch_permute(const int32_t* perm, int64_t n, const double* pos, const double* vel,
+int launch_permute(const int32_t* perm, int64_t n, const double* pos,
                    const double* mass, const uint32_t* ids, const int32_t* halo_of,
                    const uint8_t* act, const int8_t* bins, const Halo* halos, Sorted so,
                    int32_t* act_list, DevStats* st, cudaStream_t s);
+int launch_permute_vel(int64_t n, const double* vel, const Sorted& so, cudaStream_t s);
 int launch_forest(const Sorted& so, const Forest& f, cudaStream_t s);
 int tree_levels_for(int64_t n, int64_t count[MAX_LEVELS]);
 

@@ -85,7 +85,7 @@ class StepStats(C.Structure):
 
 # names of every entry point declared in include/sidm.h
 ENTRY_POINTS = ("sidm_default_config", "sidm_create", "sidm_set_particles",
-                "sidm_set_velocities", "sidm_step", "sidm_sync", "sidm_get_particles",
+                "sidm_set_velocities", "sidm_set_positions", "sidm_step", "sidm_sync", "sidm_get_particles",
                 "sidm_timestep_limits", "sidm_get_pairs", "sidm_get_step", "sidm_set_step",
                 "sidm_phase_times", "sidm_kernel_launches", "sidm_error_string", "sidm_destroy",
                 "sidm_apply_pairs_noalloc", "sidm_set_haloes", "sidm_step_haloes",
@@ -122,6 +122,7 @@ def lib():
         L.sidm_create.argtypes = [C.POINTER(Config), C.POINTER(vp)]
         L.sidm_set_particles.argtypes = [vp, i64, vp, vp, vp, dp, vp, C.c_int]
         L.sidm_set_velocities.argtypes = [vp, vp, C.c_int]
+        L.sidm_set_positions.argtypes = [vp, vp, C.c_int]
         L.sidm_step.argtypes = [vp, vp, vp, dp, C.POINTER(SigmaModel), C.c_uint64,
                                 C.POINTER(StepStats)]
         L.sidm_sync.argtypes = [vp]
@@ -206,6 +207,11 @@ def sidm_set_particles(ctx, pos, vel, mass, mass_scalar, ids) -> int:
 def sidm_set_velocities(ctx, vel) -> int:
     p, kind = _ptr(vel)
     return _check(lib().sidm_set_velocities(ctx, p, kind), "sidm_set_velocities")
+
+
+def sidm_set_positions(ctx, pos) -> int:
+    p, kind = _ptr(pos)
+    return _check(lib().sidm_set_positions(ctx, p, kind), "sidm_set_positions")
 
 
 def sidm_step(ctx, active_mask, dt_bins, dt_max, sigma: SigmaModel, seed, stats=None) -> int:
@@ -386,6 +392,13 @@ class Context:
         if isinstance(vel, np.ndarray):
             vel = np.ascontiguousarray(vel, np.float64)
         sidm_set_velocities(self.handle, vel)
+
+    def set_positions(self, pos):
+        """New positions of the loaded particles (masses, ids, h and limits kept)."""
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, np.float64)
+            self._keep = (pos,) + tuple(self._keep[1:])
+        sidm_set_positions(self.handle, pos)
 
     def step(self, dt_max, active=None, bins=None, sigma0=1.0, sigma_kind=SIGMA_CONST, w=1.0,
              seed=0, stats=True, inelastic=0.0):
