@@ -224,6 +224,28 @@ SIDM_API int sidm_sync(sidm_ctx* ctx);
  * last h of every particle (0 for particles never active). */
 SIDM_API int sidm_get_particles(sidm_ctx* ctx, double* vel_out, double* h_out, int ptr_kind);
 
+/* The particles whose velocities the last step (sidm_step or
+ * sidm_step_haloes) changed: the two particles of every accepted pair, each
+ * once, in no fixed order.  idx_out[k] is a user-order index, vel_out[3k ..
+ * 3k+2] its velocity now.  At most cap entries are written; *n_out is the
+ * full count (at most twice the accepted pairs, and at most n).  Waits for
+ * the stream.  A host code that keeps its own copy of the velocities moves
+ * far fewer bytes this way than with sidm_get_particles, since a step kicks
+ * a small fraction of the particles (Sec. 4.1: each particle scatters with
+ * probability ~ its rate times dt).  Before the first step, and after
+ * sidm_set_particles or sidm_autotune, *n_out = 0. */
+SIDM_API int sidm_get_changed(sidm_ctx* ctx, int32_t* idx_out, double* vel_out, int64_t cap,
+                              int64_t* n_out, int ptr_kind);
+
+/* Brings a host copy of the velocities up to date after a step: vel_inout
+ * (host memory, n x 3) holds the velocities before the last step; the
+ * velocities the step changed are written into it, and nothing else is
+ * touched.  Only the changed particles cross the bus (as with
+ * sidm_get_changed, into pinned staging of the context's own, allocated on
+ * the first call), then a host loop scatters them.  Waits for the stream;
+ * returns the latched status of the last step. */
+SIDM_API int sidm_update_velocities(sidm_ctx* ctx, double* vel_inout);
+
 /* Copies the Eq. 18 limit of every particle from its last active step
  * (+inf before its first active step, and when no neighbour moves
  * relative to it). */

@@ -91,6 +91,17 @@ struct sidm_ctx {
   cudaEvent_t ev_vfree = nullptr;   // the stream's earlier work on the velocities
   cudaEvent_t ev_vdone = nullptr;   // the upload
   bool vel_pending = false;
+  // particles changed by the last step (sidm_get_changed)
+  uint32_t* chg_stamps = nullptr;   // [n] number of the call that listed the particle
+  int32_t* chg_idx = nullptr;       // [n]
+  double* chg_vel = nullptr;        // [3 n]
+  unsigned long long* chg_count = nullptr;
+  unsigned long long* h_chg_count = nullptr;   // pinned
+  uint32_t chg_call = 0;
+  int32_t* h_chg_idx = nullptr;     // pinned staging of sidm_update_velocities
+  double* h_chg_vel = nullptr;
+  int64_t h_chg_cap = 0;
+  bool stepped = false;             // a step ran since the particles were loaded
   // key order kept between full rebuilds
   uint64_t order_version = 0;   // layout of the last full rebuild
   int64_t since_rebuild = 0;    // steps since it
@@ -249,6 +260,11 @@ int ensure_capacity(sidm_ctx* c, int64_t n) {
   CK(dalloc(c, &rb.pos_b, pc));
   CK(dalloc(c, &c->cons_partial, 4 * conserved_blocks()));
   CK(dalloc(c, &c->cons, 8));
+  CK(dalloc(c, &c->chg_stamps, want));
+  CK(dalloc(c, &c->chg_idx, want));
+  CK(dalloc(c, &c->chg_vel, 3 * want));
+  CK(dalloc(c, &c->chg_count, 1));
+  CK(cudaMemsetAsync(c->chg_stamps, 0, want * sizeof(uint32_t), c->stream));
   CK(cudaMemsetAsync(rb.mult, 0, want * sizeof(int32_t), c->stream));
   CK(cudaMemsetAsync(rb.seg_off, 0xFF, want * sizeof(int32_t), c->stream));
   CK(cudaMemsetAsync(rb.fill, 0, want * sizeof(int32_t), c->stream));
@@ -577,6 +593,7 @@ int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
   }
   CK(cudaGetLastError());
   c->step += 1;
+  c->stepped = true;
   if (!stats) return SIDM_OK;
   L += launch_conserved(c->vel, c->mass, n, c->cons_partial, c->cons + 4, s);
   CK(cudaMemcpyAsync(c->h_stats, c->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, s));
@@ -662,7 +679,8 @@ int sidm_create(const sidm_config* cfg, sidm_ctx** out) {
   }
   if (cudaMallocHost(&c->h_stats, sizeof(DevStats)) != cudaSuccess ||
       cudaMallocHost(&c->h_cons, 8 * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&c->h_latched, sizeof(unsigned)) != cudaSuccess) {
+      cudaMallocHost(&c->h_latched, sizeof(unsigned)) != cudaSuccess ||
+      cudaMallocHost(&c->h_chg_count, sizeof(unsigned long long)) != cudaSuccess) {
     sidm_destroy(c);
     return SIDM_ERR_OOM;
   }
@@ -730,6 +748,7 @@ int sidm_set_particles(sidm_ctx* c, int64_t n, const double* pos, const double* 
     fill(c->dtlim, n, INFINITY, c->stream);
   }
   c->loaded = false;
+  c->stepped = false;
   const int64_t off[2] = {0, n};
   r = layout_haloes(c, 1, off);
   if (r != SIDM_OK) return r;
@@ -1140,6 +1159,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
   c->step = step0;
   c->since_rebuild = since0;
   c->order_version = order0;
+  c->stepped = false;   // the pair buffer holds a trial step's pairs
   const int st = wait_and_collect(c);
   cudaFree(save);
   if (rc != SIDM_OK) return rc;
@@ -1166,6 +1186,63 @@ int sidm_get_particles(sidm_ctx* c, double* vel_out, double* h_out, int ptr_kind
     if (h_out) CK(cudaMemcpyAsync(h_out, c->h_user, c->n * sizeof(double), k, c->stream));
   }
   return wait_and_collect(c);
+}
+
+int sidm_get_changed(sidm_ctx* c, int32_t* idx_out, double* vel_out, int64_t cap,
+                     int64_t* n_out, int ptr_kind) {
+  if (!c || !n_out || cap < 0 || (cap > 0 && (!idx_out || !vel_out)) ||
+      (ptr_kind != SIDM_HOST && ptr_kind != SIDM_DEVICE))
+    return SIDM_ERR_INVALID_ARG;
+  *n_out = 0;
+  if (!c->loaded || c->n <= 0 || !c->stepped) return SIDM_OK;
+  DeviceGuard g(c->device);
+  CK(join_velocities(c));
+  cudaStream_t s = c->stream;
+  if (++c->chg_call == 0) c->chg_call = 1;   // stamps start at 0
+  CK(cudaMemsetAsync(c->chg_count, 0, sizeof(unsigned long long), s));
+  c->launches += launch_changed(c->pairs, c->pair_cap, c->dstats, c->chg_call, c->chg_stamps,
+                                c->vel, c->chg_idx, c->chg_vel, c->chg_count, c->sms, s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->h_chg_count, c->chg_count, sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int64_t cnt = (int64_t)*c->h_chg_count;
+  const int64_t m = std::min(cnt, cap);
+  if (m > 0) {
+    const cudaMemcpyKind k = copy_kind_out(ptr_kind);
+    CK(cudaMemcpyAsync(idx_out, c->chg_idx, m * sizeof(int32_t), k, s));
+    CK(cudaMemcpyAsync(vel_out, c->chg_vel, 3 * m * sizeof(double), k, s));
+  }
+  *n_out = cnt;
+  return wait_and_collect(c);
+}
+
+int sidm_update_velocities(sidm_ctx* c, double* vel_inout) {
+  if (!c || !vel_inout) return SIDM_ERR_INVALID_ARG;
+  if (!c->loaded || c->n <= 0 || !c->stepped) return SIDM_OK;
+  DeviceGuard g(c->device);
+  const int64_t n = c->n;
+  if (c->h_chg_cap < n) {
+    if (c->h_chg_idx) cudaFreeHost(c->h_chg_idx);
+    if (c->h_chg_vel) cudaFreeHost(c->h_chg_vel);
+    c->h_chg_idx = nullptr;
+    c->h_chg_vel = nullptr;
+    c->h_chg_cap = 0;
+    CK(cudaMallocHost(&c->h_chg_idx, n * sizeof(int32_t)));
+    CK(cudaMallocHost(&c->h_chg_vel, 3 * n * sizeof(double)));
+    c->h_chg_cap = n;
+  }
+  int64_t cnt = 0;
+  const int r = sidm_get_changed(c, c->h_chg_idx, c->h_chg_vel, n, &cnt, SIDM_HOST);
+  if (r < 0) return r;
+  for (int64_t k = 0; k < cnt; ++k) {
+    double* d = vel_inout + 3 * (int64_t)c->h_chg_idx[k];
+    const double* v = c->h_chg_vel + 3 * k;
+    d[0] = v[0];
+    d[1] = v[1];
+    d[2] = v[2];
+  }
+  return r;
 }
 
 int sidm_timestep_limits(sidm_ctx* c, double* out, int ptr_kind) {
@@ -1243,6 +1320,9 @@ void sidm_destroy(sidm_ctx* c) {
     if (c->h_stats) cudaFreeHost(c->h_stats);
     if (c->h_cons) cudaFreeHost(c->h_cons);
     if (c->h_latched) cudaFreeHost(c->h_latched);
+    if (c->h_chg_count) cudaFreeHost(c->h_chg_count);
+    if (c->h_chg_idx) cudaFreeHost(c->h_chg_idx);
+    if (c->h_chg_vel) cudaFreeHost(c->h_chg_vel);
     if (c->table_mem) cudaFree(c->table_mem);
     if (c->ov_mem) cudaFree(c->ov_mem);
     for (int k = 0; k <= SIDM_N_PHASES; ++k)

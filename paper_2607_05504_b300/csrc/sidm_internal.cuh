@@ -397,5 +397,8 @@ void launch_resolve_with_scratch(const PairRec* pairs, int64_t pair_cap, double*
 int launch_conserved(const double* vel, const double* mass, int64_t n, double* partial,
                       double* out4, cudaStream_t s);
 int conserved_blocks();
+int launch_changed(const PairRec* pairs, int64_t cap, const DevStats* st, uint32_t stamp,
+                   uint32_t* stamps, const double* vel, int32_t* idx_out, double* vel_out,
+                   unsigned long long* count, int sms, cudaStream_t s);
 
 }  // namespace sidm

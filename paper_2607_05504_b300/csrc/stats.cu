@@ -62,4 +62,56 @@ int launch_conserved(const double* vel, const double* mass, int64_t n, double* p
   return 2;
 }
 
+// Particles whose velocities the last step changed: the two particles of
+// every accepted pair, each listed once (the first pair to reach it claims
+// it by stamping it with the call's number), with their current velocities.
+// Nothing changed if the step overflowed its pair buffers.
+__global__ void __launch_bounds__(CT) changed_kernel(const PairRec* __restrict__ pairs,
+                                                     int64_t cap, const DevStats* st,
+                                                     uint32_t stamp, uint32_t* stamps,
+                                                     const double* __restrict__ vel,
+                                                     int32_t* idx_out, double* vel_out,
+                                                     unsigned long long* count) {
+  const unsigned long long na = st->n_acc;
+  if (na > (unsigned long long)cap || st->n_deferred > (unsigned long long)cap) return;
+  const int lane = threadIdx.x & 31;
+  // whole warps step through the pairs, so that each list append takes one
+  // atomic per warp
+  for (int64_t base = blockIdx.x * (int64_t)CT + (threadIdx.x & ~31); base < (int64_t)na;
+       base += (int64_t)gridDim.x * CT) {
+    const int64_t p = base + lane;
+    const bool valid = p < (int64_t)na;
+    int32_t e2[2] = {0, 0};
+    if (valid) {
+      e2[0] = pairs[p].ia;
+      e2[1] = pairs[p].ib;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int32_t e = e2[q];
+      const bool first = valid && atomicExch(&stamps[e], stamp) != stamp;
+      const uint32_t m = __ballot_sync(0xffffffffu, first);
+      if (!m) continue;
+      unsigned long long at = 0;
+      if (lane == 0) at = atomicAdd(count, (unsigned long long)__popc(m));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (first) {
+        const unsigned long long k = at + __popc(m & ((1u << lane) - 1u));
+        idx_out[k] = e;
+        vel_out[3 * k] = vel[3 * (int64_t)e];
+        vel_out[3 * k + 1] = vel[3 * (int64_t)e + 1];
+        vel_out[3 * k + 2] = vel[3 * (int64_t)e + 2];
+      }
+    }
+  }
+}
+
+int launch_changed(const PairRec* pairs, int64_t cap, const DevStats* st, uint32_t stamp,
+                   uint32_t* stamps, const double* vel, int32_t* idx_out, double* vel_out,
+                   unsigned long long* count, int sms, cudaStream_t s) {
+  changed_kernel<<<(unsigned)(sms * 4), CT, 0, s>>>(pairs, cap, st, stamp, stamps, vel, idx_out,
+                                                    vel_out, count);
+  return 1;
+}
+
 }  // namespace sidm

@@ -85,7 +85,7 @@ class StepStats(C.Structure):
 
 # names of every entry point declared in include/sidm.h
 ENTRY_POINTS = ("sidm_default_config", "sidm_create", "sidm_set_particles",
-                "sidm_set_velocities", "sidm_set_positions", "sidm_step", "sidm_sync", "sidm_get_particles",
+                "sidm_set_velocities", "sidm_set_positions", "sidm_get_changed", "sidm_update_velocities", "sidm_step", "sidm_sync", "sidm_get_particles",
                 "sidm_timestep_limits", "sidm_get_pairs", "sidm_get_step", "sidm_set_step",
                 "sidm_phase_times", "sidm_kernel_launches", "sidm_error_string", "sidm_destroy",
                 "sidm_apply_pairs_noalloc", "sidm_set_haloes", "sidm_step_haloes",
@@ -123,6 +123,8 @@ def lib():
         L.sidm_set_particles.argtypes = [vp, i64, vp, vp, vp, dp, vp, C.c_int]
         L.sidm_set_velocities.argtypes = [vp, vp, C.c_int]
         L.sidm_set_positions.argtypes = [vp, vp, C.c_int]
+        L.sidm_get_changed.argtypes = [vp, vp, vp, i64, C.POINTER(i64), C.c_int]
+        L.sidm_update_velocities.argtypes = [vp, vp]
         L.sidm_step.argtypes = [vp, vp, vp, dp, C.POINTER(SigmaModel), C.c_uint64,
                                 C.POINTER(StepStats)]
         L.sidm_sync.argtypes = [vp]
@@ -288,6 +290,26 @@ def sidm_sync(ctx) -> int:
 def sidm_get_particles(ctx, vel_out, h_out=None) -> int:
     p, kind = _ptr(vel_out)
     return _check(lib().sidm_get_particles(ctx, p, _ptr(h_out)[0], kind), "sidm_get_particles")
+
+
+def sidm_get_changed(ctx, idx_out, vel_out) -> int:
+    """Fills idx_out (int32) and vel_out (k x 3) with the particles the last
+    step changed, up to their length; returns the full count."""
+    p, kind = _ptr(idx_out)
+    n = C.c_int64(0)
+    _check(lib().sidm_get_changed(ctx, p, _ptr(vel_out)[0], int(idx_out.shape[0]),
+                                  C.byref(n), kind), "sidm_get_changed")
+    return int(n.value)
+
+
+def sidm_update_velocities(ctx, vel_inout) -> int:
+    """Writes the velocities the last step changed into the host array
+    vel_inout (n x 3, float64, C-contiguous) in place."""
+    if not (isinstance(vel_inout, np.ndarray) and vel_inout.dtype == np.float64 and
+            vel_inout.flags.c_contiguous):
+        raise SidmError(ERR_INVALID_ARG, "sidm_update_velocities: host float64 C-contiguous array")
+    return _check(lib().sidm_update_velocities(ctx, vel_inout.ctypes.data_as(C.c_void_p)),
+                  "sidm_update_velocities")
 
 
 def sidm_timestep_limits(ctx, out) -> int:
@@ -475,6 +497,13 @@ class Context:
     @property
     def graph_state(self) -> int:
         return sidm_graph_state(self.handle)
+
+    def changed(self):
+        """(indices, velocities) of the particles the last step changed."""
+        idx = np.empty(self.n, np.int32)
+        vel = np.empty((self.n, 3))
+        k = sidm_get_changed(self.handle, idx, vel)
+        return idx[:k].copy(), vel[:k].copy()
 
     def velocities(self):
         v = np.empty((self.n, 3))

@@ -1,0 +1,76 @@
+"""sidm_get_changed: the particles whose velocities the last step changed,
+each once, with their new velocities.  A host copy of the velocities kept
+up to date from these deltas alone must equal the full read-back."""
+import numpy as np
+import pytest
+
+from paper_2607_05504_b300 import inputs as I
+from paper_2607_05504_b300 import sidm
+
+pytestmark = pytest.mark.gpu
+
+
+def test_changed_set_is_the_particles_of_the_accepted_pairs():
+    p = I.hernquist_halo(20000, 41, ids="random")
+    bins = np.random.default_rng(42).integers(0, 3, p.n).astype(np.int8)
+    where = {int(i): k for k, i in enumerate(p.ids)}
+    ctx = sidm.Context(n_ngb=32, use_graph=True)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    idx, v = ctx.changed()
+    assert idx.size == 0                       # no step yet
+    host = p.vel.copy()
+    total = 0
+    for k in range(6):
+        before = ctx.velocities()[0]
+        ctx.step(2.0, I.active_at_step(bins, k), bins, seed=43, stats=False)
+        after = ctx.velocities()[0]
+        idx, v = ctx.changed()
+        assert np.unique(idx).size == idx.size
+        ab, _ = ctx.pairs()
+        kicked = {where[int(i)] for i in ab.ravel()}
+        assert set(idx.tolist()) == kicked, k
+        assert np.array_equal(v, after[idx])
+        moved = np.nonzero(np.any(after != before, axis=1))[0]
+        assert set(moved.tolist()) <= kicked
+        host[idx] = v
+        assert np.array_equal(host, after), k
+        total += idx.size
+    assert total > 500
+    # a new particle set starts with nothing changed
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    assert ctx.changed()[0].size == 0
+    ctx.close()
+
+
+def test_short_output_gets_the_full_count():
+    p = I.uniform_box(4000, 1.0, 1.0, 44)
+    ctx = sidm.Context(box=1.0)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    ctx.step(0.2, None, np.zeros(p.n, np.int8), seed=45, stats=False)
+    full_idx, full_v = ctx.changed()
+    assert full_idx.size > 10
+    idx = np.full(5, -1, np.int32)
+    vel = np.zeros((5, 3))
+    n = sidm.sidm_get_changed(ctx.handle, idx, vel)
+    assert n == full_idx.size
+    assert set(idx.tolist()) <= set(full_idx.tolist())
+    after = ctx.velocities()[0]
+    assert np.array_equal(vel, after[idx])
+    ctx.close()
+
+
+def test_update_velocities_keeps_a_host_copy_current():
+    p = I.hernquist_halo(15000, 46, ids="random")
+    bins = np.random.default_rng(47).integers(0, 3, p.n).astype(np.int8)
+    ctx = sidm.Context(n_ngb=32, use_graph=True)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    host = p.vel.copy()
+    sidm.sidm_update_velocities(ctx.handle, host)       # no step yet: untouched
+    assert np.array_equal(host, p.vel)
+    for k in range(5):
+        ctx.step(2.0, I.active_at_step(bins, k), bins, seed=48, stats=False)
+        sidm.sidm_update_velocities(ctx.handle, host)
+        assert np.array_equal(host, ctx.velocities()[0]), k
+    with pytest.raises(sidm.SidmError):
+        sidm.sidm_update_velocities(ctx.handle, host.astype(np.float32))
+    ctx.close()
