@@ -283,9 +283,7 @@ __device__ __forceinline__ void visit(const PairKArgs& A, const Query& Q, int64_
       } else if (rhi < hbj.x) {
         sees = true;
       } else if (rlo < hbj.y) {
-        const double hj = so.h[j];
-        sees = sep2(so.x[Q.s], so.y[Q.s], so.z[Q.s], so.x[j], so.y[j], so.z[j], P.box,
-                    0.5 * P.box) < hj * hj;
+        sees = hw_within(so.x, so.y, so.z, Q.s, j, P.box, so.h[j]);
       }
     }
     if (!(sees && idj < Q.idi)) {
@@ -501,14 +499,13 @@ __device__ void walk_query(const PairKArgs& A, int64_t qi, int* stack, unsigned 
                            unsigned long long* pge1, double* sum_p, uint32_t* status) {
   const Sorted& so = A.so;
   const int lane = threadIdx.x & 31;
-  const double box = A.a.box, half = 0.5 * A.a.box;
+  const double box = A.a.box;
   const float boxf = (float)A.a.box;
   const Query Q = load_query(so, A.f, A.act_list[qi], boxf);
   const int64_t s = Q.s;
   const Halo& H = A.f.halos[so.halo[s]];
   const int64_t hs = H.start;
-  const double xi = so.x[s], yi = so.y[s], zi = so.z[s], hi = so.h[s];
-  const double hhi = hi * hi;
+  const double hi = so.h[s];
   const bool ov = A.a.ov.na > 0;
   const float rad = (f64_to_f32_ru(hi) + 2.0f * Q.eq) * (1.0f + 4.0f * REL);
   double mine = 0.0;
@@ -528,14 +525,13 @@ __device__ void walk_query(const PairKArgs& A, int64_t qi, int* stack, unsigned 
         if (rhi < __fadd_rd(Q.hbi.x, hbj.x)) {
           in = true;
         } else if (rlo < __fadd_ru(Q.hbi.y, hbj.y)) {
-          const double H = hi + so.h[j];
-          in = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half) < H * H;
+          in = hw_within_sum(so.x, so.y, so.z, s, j, box, hi, so.h[j]);
         }
       } else if (A.a.split) {
         const float hf = (float)hi;
         in = r * r < hf * hf;
       } else if (rlo < Q.hbi.y) {
-        in = sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half) < hhi;
+        in = hw_within(so.x, so.y, so.z, s, j, box, hi);
       }
     }
     float gl, gh;

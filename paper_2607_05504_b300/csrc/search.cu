@@ -348,7 +348,6 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
     if (list_covers) {
       float in2, out2;
       thresholds(h, hl, hu, &in2, &out2);
-      const double hh = h * h;
       cnt = 0;
       for (int k0 = 0; k0 < len; k0 += 32) {
         const int k = k0 + lane;
@@ -356,7 +355,7 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
         if (k < len) {
           const float v = lst_r2[k];
           if (v < in2) in = true;
-          else if (v < out2) in = exact_r2(k) < hh;
+          else if (v < out2) in = hw_within(so.x, so.y, so.z, s, lst_j[k], box, h);
         }
         const uint32_t m = __ballot_sync(0xffffffffu, in);
         if (in) {

@@ -127,6 +127,21 @@ __device__ __forceinline__ double sep2(double xi, double yi, double zi, double x
   return (dx * dx + dy * dy) + dz * dz;
 }
 
+// Exact boundary tests r_ij^2 < h^2 (h = h_j, or h_i + h_j for the overlap
+// estimator), in the fixed order of sep2.  They decide the rare pairs inside
+// the FP32 rounding band; as real calls, their FP64 instructions stay off the
+// common path (an inline FP64 branch is predicated and paid on every pass).
+static __device__ __noinline__ bool hw_within(const double* x, const double* y, const double* z,
+                                              int64_t i, int64_t j, double box, double h) {
+  return sep2(x[i], y[i], z[i], x[j], y[j], z[j], box, 0.5 * box) < h * h;
+}
+static __device__ __noinline__ bool hw_within_sum(const double* x, const double* y,
+                                                  const double* z, int64_t i, int64_t j,
+                                                  double box, double hi, double hj) {
+  const double H = hi + hj;
+  return sep2(x[i], y[i], z[i], x[j], y[j], z[j], box, 0.5 * box) < H * H;
+}
+
 // Kernel normalisation K / h^3 with K = 8/pi (cubic spline) or 3/(4 pi) (top-hat).
 __device__ __forceinline__ double kernel_norm(int kernel, double h) {
   const double k = kernel == SIDM_KERNEL_TOPHAT ? 3.0 / (4.0 * 3.141592653589793)
