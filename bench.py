@@ -477,7 +477,7 @@ def main():
     # launch shapes: timed on the first timed step's active set (the state is restored)
     s_tune = args.warmup % CYCLE
     tuning = ctx.autotune([sidm.HaloParams(w["dt_max"], sg, 0, ctx.step_counter)],
-                          masks_d[s_tune], bins_d, reps=2)
+                          masks_d[s_tune], bins_d, reps=3)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]

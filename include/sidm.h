@@ -309,8 +309,8 @@ SIDM_API int sidm_overlap_table(int kernel, int32_t na, int32_t ns, double* out)
  * results; only the time changes.  Zero fields take the defaults. */
 typedef struct {
   int search_window;        /* key-order window that bounds each search radius:
-                               128, 256 (default) or 512 particles                   */
-  int search_chunk;         /* queries a search warp claims at a time, 1..64 (4)      */
+                               128, 256 or 512 (default) particles                   */
+  int search_chunk;         /* queries a search warp claims at a time, 1..64 (1)      */
   int search_blocks_per_sm; /* search blocks of 4 warps launched per SM, 1..8 (8)     */
   int pairs_chunk;          /* queries a pair warp claims at a time, 1..64 (4)        */
   int pairs_blocks_per_sm;  /* pair blocks of 4 warps per SM, 1..6 (6)                */
@@ -325,7 +325,9 @@ SIDM_API int sidm_get_tuning(const sidm_ctx* ctx, sidm_tuning* t);
 /* Times candidate launch shapes on the next step (active mask, bins and one
  * sidm_halo_params per halo as for sidm_step_haloes; a single-halo context
  * takes one) and keeps the fastest.  Each candidate runs `reps` (1..16)
- * times from the same state; afterwards the velocities, h, timestep limits
+ * times from the same state and counts with its fastest run; a shape
+ * replaces the current one only if it is at least 2 % faster.  Afterwards
+ * the velocities, h, timestep limits
  * and the step counter are restored, so the call leaves the simulation
  * where it was.  Coordinate search: window, then search chunk and blocks,
  * then pair chunk and blocks.  Writes the chosen shapes to `best` (nullable).

@@ -47,7 +47,7 @@ constexpr float SQ = 4.76837158203125e-07f;   // 2^-21: slack on squared thresho
 // 1 KB reserved per block).
 constexpr int WALK_STACK = 128;
 #ifndef SEARCH_LEAF_BATCH
-#define SEARCH_LEAF_BATCH 4                    // leaves per L2 round trip in the gather walk
+#define SEARCH_LEAF_BATCH 2                    // leaves per L2 round trip in the gather walk
 #endif
 
 struct SearchArgs {
@@ -217,22 +217,29 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
       const float rad = (T + 2.0f * eq) * (1.0f + 4.0f * REL);
       const float rad2 = rad < INFINITY ? rad * rad : INFINITY;
       const bool ok = traverse<PERIODIC, false, SEARCH_LEAF_BATCH, WALK_STACK>(
-          A.f, H, hpos, fi, rad2, boxf, stack, [&](int k, bool valid, const float4& pj) {
-        float s2 = 0.0f;
-        bool keep = false;
-        if (valid && k != sl) {
-          s2 = sep2f<PERIODIC>(fi, pj, boxf);
-          keep = s2 < g2;
+          A.f, H, hpos, fi, rad2, boxf, stack,
+          [&](const int* kk, const bool* valid, const float4* pj, const bool* on) {
+        // every slot's separation first (independent work), then the appends
+        float s2[SEARCH_LEAF_BATCH];
+        bool keep[SEARCH_LEAF_BATCH];
+#pragma unroll
+        for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
+          s2[b] = sep2f<PERIODIC>(fi, pj[b], boxf);
+          keep[b] = valid[b] && kk[b] != sl && s2[b] < g2;
         }
-        const uint32_t m = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-          const int at = len + __popc(m & lt);
-          if (at < SEARCH_CAP) {
-            lst_r2[at] = s2;
-            lst_j[at] = (int32_t)(hs + k);
+#pragma unroll
+        for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
+          if (!on[b]) break;
+          const uint32_t m = __ballot_sync(0xffffffffu, keep[b]);
+          if (keep[b]) {
+            const int at = len + __popc(m & lt);
+            if (at < SEARCH_CAP) {
+              lst_r2[at] = s2[b];
+              lst_j[at] = (int32_t)(hs + kk[b]);
+            }
           }
+          len += __popc(m);
         }
-        len += __popc(m);
       });
       __syncwarp();
       if (!ok) { status |= ST_ERR_STACK; complete = false; break; }
@@ -258,10 +265,13 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
         const float radn = (Tn + 2.0f * eq) * (1.0f + 4.0f * REL);
         int c = 0;
         const bool ok2 = traverse<PERIODIC, false, SEARCH_LEAF_BATCH, WALK_STACK>(
-            A.f, H, hpos, fi, radn * radn, boxf, stack, [&](int k, bool valid, const float4& pj) {
-          bool in = false;
-          if (valid && k != sl) in = sep2f<PERIODIC>(fi, pj, boxf) < in2;
-          c += __popc(__ballot_sync(0xffffffffu, in));
+            A.f, H, hpos, fi, radn * radn, boxf, stack,
+            [&](const int* kk, const bool* valid, const float4* pj, const bool* on) {
+#pragma unroll
+          for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
+            const bool in = valid[b] && kk[b] != sl && sep2f<PERIODIC>(fi, pj[b], boxf) < in2;
+            c += __popc(__ballot_sync(0xffffffffu, in));   // invalid slots add 0
+          }
         });
         if (!ok2) { status |= ST_ERR_STACK; break; }
         if (c >= K) { verified = true; break; }

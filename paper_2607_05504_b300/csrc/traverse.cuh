@@ -58,8 +58,11 @@ __device__ __forceinline__ float sep2f(const float4& a, const float4& b, float b
 // query's own radius and rad2 is ignored.
 // LB > 0: the leaves under a node are visited as soon as their boxes are
 // tested, LB at a time, with their particle loads issued together (one L2
-// round trip per LB leaves; leaf_fn is replicated LB times).  LB = 0: hit
-// leaves go on the stack like the other nodes (smallest code).
+// round trip per LB leaves); leaf_fn then takes the batch as arrays,
+// leaf_fn(k[LB], valid[LB], pj[LB], on[LB]) with on[b] warp-uniform (batch
+// slot b holds a leaf), so that it can compute every slot before its
+// ballots.  LB = 0: hit leaves go on the stack like the other nodes and
+// leaf_fn(k, valid, pj) sees one leaf (smallest code).
 // CAP: stack entries; the walk reports an overflow (returns false) rather
 // than exceed it.
 template <bool PERIODIC, bool HMAX = false, int LB = 0, int CAP = SEARCH_STACK, class LeafFn>
@@ -85,7 +88,21 @@ __device__ __forceinline__ bool traverse(const Forest& f, const Halo& H,
       const bool valid = k < hn;
       float4 pj = make_float4(0.f, 0.f, 0.f, 0.f);
       if (valid) pj = hpos[k];
-      leaf_fn(k, valid, pj);
+      if constexpr (LB > 0) {
+        int kk[LB];
+        bool vv[LB], on[LB];
+        float4 pp[LB];
+#pragma unroll
+        for (int b = 0; b < LB; ++b) {
+          kk[b] = k;
+          vv[b] = b == 0 && valid;
+          on[b] = b == 0;
+          pp[b] = pj;
+        }
+        leaf_fn(kk, vv, pp, on);
+      } else {
+        leaf_fn(k, valid, pj);
+      }
     } else {
       bool hit = false;
       if (k < (int)H.node_cnt[level - 1]) {
@@ -99,29 +116,31 @@ __device__ __forceinline__ bool traverse(const Forest& f, const Halo& H,
         hit = box_hits<PERIODIC>(lo, hi, q, r2, box);
       }
       const uint32_t m = __ballot_sync(0xffffffffu, hit);
-      if (LB > 0 && level == 1) {
-        // the children are leaves: visit the hit ones now, LB at a time
-        const int lbase = (node & 0x0FFFFFFF) << 5;
-        uint32_t mm = m;
-        while (mm) {
-          constexpr int NB = LB > 0 ? LB : 1;
-          int kk[NB];
-          bool on[NB], valid[NB];
-          float4 pj[NB];
+      bool visited = false;
+      if constexpr (LB > 0) {
+        if (level == 1) {
+          // the children are leaves: visit the hit ones now, LB at a time
+          const int lbase = (node & 0x0FFFFFFF) << 5;
+          uint32_t mm = m;
+          while (mm) {
+            int kk[LB];
+            bool on[LB], valid[LB];
+            float4 pj[LB];
 #pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            on[b] = mm != 0u;                       // warp-uniform
-            const int c = on[b] ? __ffs(mm) - 1 : 0;
-            mm &= mm - 1u;
-            kk[b] = ((lbase + c) << 5) + lane;
-            valid[b] = on[b] && kk[b] < hn;
-            pj[b] = valid[b] ? hpos[kk[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int b = 0; b < LB; ++b) {
+              on[b] = mm != 0u;                       // warp-uniform
+              const int c = on[b] ? __ffs(mm) - 1 : 0;
+              mm &= mm - 1u;
+              kk[b] = ((lbase + c) << 5) + lane;
+              valid[b] = on[b] && kk[b] < hn;
+              pj[b] = valid[b] ? hpos[kk[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            leaf_fn(kk, valid, pj, on);
           }
-#pragma unroll
-          for (int b = 0; b < NB; ++b)
-            if (on[b]) leaf_fn(kk[b], valid[b], pj[b]);
+          visited = true;
         }
-      } else {
+      }
+      if (!visited) {
         const int cnt = __popc(m);
         if (top + cnt > CAP) return false;
         if (hit) stack[top + __popc(m & lt)] = ((level - 1) << 28) | k;
