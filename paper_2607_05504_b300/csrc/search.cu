@@ -46,6 +46,9 @@ constexpr float SQ = 4.76837158203125e-07f;   // 2^-21: slack on squared thresho
 // a block's shared memory at 26 KB, so that 8 blocks fit on an SM (228 KB,
 // 1 KB reserved per block).
 constexpr int WALK_STACK = 128;
+#ifndef LIST_REGS
+#define LIST_REGS 8                            // candidates per lane held in registers
+#endif
 #ifndef SEARCH_LEAF_BATCH
 #define SEARCH_LEAF_BATCH 2                    // leaves per L2 round trip in the gather walk
 #endif
@@ -71,8 +74,7 @@ struct SearchArgs {
 };
 
 __device__ __forceinline__ int warp_sum(int v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  return __reduce_add_sync(0xffffffffu, v);   // one warp reduction instruction (sm_80+)
 }
 
 // FP32 squared-separation thresholds for a radius H given by its FP32
@@ -303,15 +305,31 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
         *out2 = thr_out2(hu, eq);
       }
     };
+    // a short list (the usual case) is held in registers for the bisection
+    const bool in_regs = len <= LIST_REGS * 32;
+    float rv[LIST_REGS];
+#pragma unroll
+    for (int i = 0; i < LIST_REGS; ++i) {
+      const int k = lane + 32 * i;
+      rv[i] = (in_regs && k < len) ? lst_r2[k] : INFINITY;
+    }
     auto count_below = [&](double hv, float hl, float hu) {
       float in2, out2;
       thresholds(hv, hl, hu, &in2, &out2);
       int c = 0;
       bool amb = false;
-      for (int k = lane; k < len; k += 32) {
-        const float v = lst_r2[k];
-        c += v < in2 ? 1 : 0;
-        amb |= (v >= in2) && (v < out2);
+      if (in_regs) {
+#pragma unroll
+        for (int i = 0; i < LIST_REGS; ++i) {
+          c += rv[i] < in2 ? 1 : 0;
+          amb |= (rv[i] >= in2) && (rv[i] < out2);
+        }
+      } else {
+        for (int k = lane; k < len; k += 32) {
+          const float v = lst_r2[k];
+          c += v < in2 ? 1 : 0;
+          amb |= (v >= in2) && (v < out2);
+        }
       }
       if (__any_sync(0xffffffffu, amb)) {
         const double hh = hv * hv;
