@@ -46,7 +46,7 @@ PHASE_BYTES = {
 }
 
 
-SEARCH_DRAM_BYTES = 6.521600e6 + 1.012992e6   # dram read + write of the captured launch
+SEARCH_DRAM_BYTES = 6.539008e6 + 1.027584e6   # dram read + write of the captured launch
 SEARCH_DRAM_QUERIES = 51520
 
 
@@ -563,7 +563,7 @@ def main():
     avg_ms = phase_sum[dom] / reps
     achieved = bytes_per_step / (avg_ms * 1e-3) / 1e9
     # DRAM bytes of the search kernel from one ncu capture of the current
-    # kernel (7.53 MB on a launch of 51,520 queries of this workload),
+    # kernel (7.57 MB on a launch of 51,520 queries of this workload),
     # scaled to this run's mean queries per step
     traffic = (SEARCH_DRAM_BYTES * (n_act_sum / reps) / SEARCH_DRAM_QUERIES
                if dom == "search" else None)
