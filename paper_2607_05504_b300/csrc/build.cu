@@ -76,11 +76,16 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 }
 
 // Bounding box of every halo: blocks walk contiguous chunks; a thread flushes
-// its running box when the halo changes, warps combine at chunk ends.
+// its running box when the halo changes, warps combine at chunk ends, and
+// the warps of a block combine in shared memory, so that a chunk inside one
+// halo costs one flush (atomics on the same six words serialise).
 __global__ void __launch_bounds__(BT) bbox_kernel(const double* __restrict__ pos,
                                                   const int32_t* __restrict__ halo_of, int64_t n,
                                                   Halo* halos) {
-  const int lane = threadIdx.x & 31;
+  constexpr int NW = BT / 32;
+  __shared__ unsigned long long s_lo[NW][3], s_hi[NW][3];
+  __shared__ int s_k[NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t chunk_len = (int64_t)BT * BB_ITEMS;
   for (int64_t c0 = blockIdx.x * chunk_len; c0 < n; c0 += (int64_t)gridDim.x * chunk_len) {
     int cur = -1;
@@ -108,10 +113,38 @@ __global__ void __launch_bounds__(BT) bbox_kernel(const double* __restrict__ pos
         lo[a] = warp_min_u64(lo[a]);
         hi[a] = warp_max_u64(hi[a]);
       }
-      if (lane == 0) bbox_flush(halos, k0, lo, hi);
     } else if (cur >= 0) {
-      bbox_flush(halos, cur, lo, hi);
+      bbox_flush(halos, cur, lo, hi);   // a warp across a halo boundary (rare)
     }
+    if (lane == 0) {
+      s_k[warp] = same ? k0 : -1;
+      for (int a = 0; a < 3; ++a) {
+        s_lo[warp][a] = lo[a];
+        s_hi[warp][a] = hi[a];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // runs of warps in the same halo, one flush per run
+      int kk = -1;
+      unsigned long long alo[3], ahi[3];
+      for (int w = 0; w < NW; ++w) {
+        const int kw = s_k[w];
+        if (kw < 0) continue;
+        if (kw != kk) {
+          if (kk >= 0) bbox_flush(halos, kk, alo, ahi);
+          kk = kw;
+          for (int a = 0; a < 3; ++a) { alo[a] = s_lo[w][a]; ahi[a] = s_hi[w][a]; }
+        } else {
+          for (int a = 0; a < 3; ++a) {
+            alo[a] = s_lo[w][a] < alo[a] ? s_lo[w][a] : alo[a];
+            ahi[a] = s_hi[w][a] > ahi[a] ? s_hi[w][a] : ahi[a];
+          }
+        }
+      }
+      if (kk >= 0) bbox_flush(halos, kk, alo, ahi);
+    }
+    __syncthreads();   // the next chunk reuses the shared arrays
   }
 }
 
