@@ -11,9 +11,10 @@
 //      order, publishes its digit counts, adds up the counts of the earlier
 //      tiles from their published slots (stopping at the first slot that
 //      already holds an inclusive prefix) and publishes its own inclusive
-//      prefix.  Each warp ranks the keys of its own 512-key part of the
-//      tile among the earlier keys of the same digit (warp match, warp-
-//      private counters, no block barrier), so a tile needs four barriers.
+//      prefix.  Each of the 16 warps ranks the keys of its own 256-key part
+//      of the tile among the earlier keys of the same digit (warp match,
+//      warp-private counters, no block barrier), so a tile needs four
+//      barriers.
 // A slot is one 32-bit word holding a 2-bit state and a 30-bit count, so a
 // reader sees the state and the count together without a fence.  Six
 // launches per sort (a memset, the histogram, four passes) instead of a
@@ -75,30 +76,37 @@ __global__ void __launch_bounds__(OS_THREADS) os_hist_kernel(const uint32_t* __r
     if (h[p][t]) atomicAdd(&counts[p * RADIX + t], h[p][t]);
 }
 
-__global__ void __launch_bounds__(OS_THREADS) os_pass_kernel(
+// A pass runs PASS_THREADS threads on each 4096-key tile: warp w ranks keys
+// [w 32 PASS_ITEMS, (w + 1) 32 PASS_ITEMS) of the tile; the per-digit work
+// (tile counts, look-back, digit starts) is done by the first RADIX threads.
+constexpr int PASS_THREADS = 512;
+constexpr int PASS_ITEMS = OS_TILE / PASS_THREADS;
+constexpr int PASS_WARPS = PASS_THREADS / WARP;
+static_assert(PASS_THREADS >= RADIX && PASS_ITEMS * PASS_THREADS == OS_TILE, "pass tiling");
+
+__global__ void __launch_bounds__(PASS_THREADS) os_pass_kernel(
     const uint32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int64_t n, int pass,
     const uint32_t* __restrict__ counts, uint32_t* tile_ctr, uint32_t* slots, unsigned* status) {
   __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_cnt[OS_WARPS][RADIX];   // per warp: keys of each digit, then their start
-  __shared__ uint32_t s_wsum[OS_WARPS];
+  __shared__ uint32_t s_cnt[PASS_WARPS][RADIX];   // per warp: keys of each digit, then their start
+  __shared__ uint32_t s_wsum[RADIX / WARP];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const bool digit_thread = t < RADIX;               // thread t owns digit t
   const int shift = 8 * pass;
   if (t == 0) s_tile = atomicAdd(&tile_ctr[pass], 1u);
-#pragma unroll
-  for (int w = 0; w < OS_WARPS; ++w) s_cnt[w][t] = 0;
+  for (int i = t; i < PASS_WARPS * RADIX; i += PASS_THREADS) (&s_cnt[0][0])[i] = 0;
   __syncthreads();
   const int64_t tile = s_tile;
-  // warp w holds keys [w 512, (w + 1) 512) of the tile, 32 per round in order
-  const int64_t base = tile * OS_TILE + (int64_t)warp * (OS_ITEMS * WARP);
+  const int64_t base = tile * OS_TILE + (int64_t)warp * (PASS_ITEMS * WARP);
 
   // 1. rank every key among the earlier keys of its digit in the warp's
-  //    sub-tile (warp-private counters, no block barrier)
-  uint32_t key[OS_ITEMS], rank[OS_ITEMS];
-  int32_t val[OS_ITEMS];
+  //    part of the tile (warp-private counters, no block barrier)
+  uint32_t key[PASS_ITEMS], rank[PASS_ITEMS];
+  int32_t val[PASS_ITEMS];
   const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-  for (int r = 0; r < OS_ITEMS; ++r) {
+  for (int r = 0; r < PASS_ITEMS; ++r) {
     const int64_t i = base + (int64_t)r * WARP + lane;
     const bool valid = i < n;
     key[r] = valid ? keys_in[i] : 0u;
@@ -118,67 +126,73 @@ __global__ void __launch_bounds__(OS_THREADS) os_pass_kernel(
 
   // 2. the tile's count of digit t; publish it, then look back over the
   //    earlier tiles
-  uint32_t cnt = 0;
+  uint32_t cnt = 0, excl = 0;
+  if (digit_thread) {
 #pragma unroll
-  for (int w = 0; w < OS_WARPS; ++w) cnt += s_cnt[w][t];
-  uint32_t* my = slots + tile * RADIX + t;
-  st_relaxed_u32(my, (tile == 0 ? SLOT_PRE : SLOT_AGG) | cnt);
-  uint32_t excl = 0;
-  if (tile > 0) {
-    // slots j, j-1, ... are loaded LOOKBACK_BATCH at a time and consumed in
-    // order until an inclusive prefix; a slot not yet published is
-    // reloaded (the earlier tile's block is resident and publishes before
-    // it waits on anything; the wait is bounded nonetheless)
-    int64_t j = tile - 1;
-    int spins = 0;
-    bool done = false;
-    while (!done) {
-      uint32_t v[LOOKBACK_BATCH];
+    for (int w = 0; w < PASS_WARPS; ++w) cnt += s_cnt[w][t];
+    uint32_t* my = slots + tile * RADIX + t;
+    st_relaxed_u32(my, (tile == 0 ? SLOT_PRE : SLOT_AGG) | cnt);
+    if (tile > 0) {
+      // slots j, j-1, ... are loaded LOOKBACK_BATCH at a time and consumed in
+      // order until an inclusive prefix; a slot not yet published is
+      // reloaded (the earlier tile's block is resident and publishes before
+      // it waits on anything; the wait is bounded nonetheless)
+      int64_t j = tile - 1;
+      int spins = 0;
+      bool done = false;
+      while (!done) {
+        uint32_t v[LOOKBACK_BATCH];
 #pragma unroll
-      for (int k = 0; k < LOOKBACK_BATCH; ++k)
-        v[k] = j - k >= 0 ? ld_relaxed_u32(slots + (j - k) * RADIX + t) : 0u;
-      bool stall = false;
+        for (int k = 0; k < LOOKBACK_BATCH; ++k)
+          v[k] = j - k >= 0 ? ld_relaxed_u32(slots + (j - k) * RADIX + t) : 0u;
+        bool stall = false;
 #pragma unroll
-      for (int k = 0; k < LOOKBACK_BATCH; ++k) {
-        if (done || stall) continue;
-        const uint32_t state = v[k] & SLOT_STATE;
-        if (state == 0u) { stall = true; continue; }
-        excl += v[k] & SLOT_VALUE;
-        if (state == SLOT_PRE || j == 0) done = true;
-        else --j;
+        for (int k = 0; k < LOOKBACK_BATCH; ++k) {
+          if (done || stall) continue;
+          const uint32_t state = v[k] & SLOT_STATE;
+          if (state == 0u) { stall = true; continue; }
+          excl += v[k] & SLOT_VALUE;
+          if (state == SLOT_PRE || j == 0) done = true;
+          else --j;
+        }
+        if (stall && ++spins > LOOKBACK_MAX_SPINS) {
+          atomicOr(status, (unsigned)ST_ERR_SORT);
+          break;
+        }
       }
-      if (stall && ++spins > LOOKBACK_MAX_SPINS) {
-        atomicOr(status, (unsigned)ST_ERR_SORT);
-        break;
-      }
+      st_relaxed_u32(my, SLOT_PRE | (excl + cnt));
     }
-    st_relaxed_u32(my, SLOT_PRE | (excl + cnt));
   }
 
   // 3. start of digit t in the output (keys of smaller digits, then the
   //    earlier tiles' keys of digit t), then of each warp's run of it
-  const uint32_t g = counts[pass * RADIX + t];
-  uint32_t inc = g;
+  uint32_t g = 0, inc = 0;
+  if (digit_thread) {
+    g = counts[pass * RADIX + t];
+    inc = g;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
   }
-  if (lane == 31) s_wsum[warp] = inc;
   __syncthreads();
-  uint32_t run = inc - g + excl;
-  for (int w = 0; w < warp; ++w) run += s_wsum[w];
+  if (digit_thread) {
+    uint32_t run = inc - g + excl;
+    for (int w = 0; w < warp; ++w) run += s_wsum[w];
 #pragma unroll
-  for (int w = 0; w < OS_WARPS; ++w) {
-    const uint32_t c = s_cnt[w][t];
-    s_cnt[w][t] = run;
-    run += c;
+    for (int w = 0; w < PASS_WARPS; ++w) {
+      const uint32_t c = s_cnt[w][t];
+      s_cnt[w][t] = run;
+      run += c;
+    }
   }
   __syncthreads();
 
   // 4. scatter (stable: warp, then round, then lane is the input order)
 #pragma unroll
-  for (int r = 0; r < OS_ITEMS; ++r) {
+  for (int r = 0; r < PASS_ITEMS; ++r) {
     const int64_t i = base + (int64_t)r * WARP + lane;
     if (i < n) {
       const uint32_t pos = s_cnt[warp][(key[r] >> shift) & 255u] + rank[r];
@@ -216,7 +230,7 @@ int radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_alt, int32_t*
   uint32_t* kout = keys_alt;
   int32_t* vout = vals_alt;
   for (int p = 0; p < passes; ++p) {
-    os_pass_kernel<<<tiles, OS_THREADS, 0, s>>>(kin, vin, kout, vout, n, p, counts, tile_ctr,
+    os_pass_kernel<<<tiles, PASS_THREADS, 0, s>>>(kin, vin, kout, vout, n, p, counts, tile_ctr,
                                                 slots + (int64_t)p * tiles * RADIX, status);
     uint32_t* tk = kin; kin = kout; kout = tk;
     int32_t* tv = vin; vin = vout; vout = tv;
