@@ -12,9 +12,9 @@
 //      tiles from their published slots (stopping at the first slot that
 //      already holds an inclusive prefix) and publishes its own inclusive
 //      prefix.  Each of the 16 warps ranks the keys of its own 256-key part
-//      of the tile among the earlier keys of the same digit (warp match,
-//      warp-private counters, no block barrier), so a tile needs four
-//      barriers.
+//      of the tile among the earlier keys of the same digit (peers found by
+//      one vote per digit bit, warp-private counters, no block barrier), so
+//      a tile needs four barriers.
 // A slot is one 32-bit word holding a 2-bit state and a 30-bit count, so a
 // reader sees the state and the count together without a fence.  Six
 // launches per sort (a memset, the histogram, four passes) instead of a
@@ -112,7 +112,15 @@ __global__ void __launch_bounds__(PASS_THREADS) os_pass_kernel(
     key[r] = valid ? keys_in[i] : 0u;
     val[r] = valid ? vals_in[i] : 0;
     const uint32_t d = valid ? (key[r] >> shift) & 255u : (uint32_t)RADIX;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    // lanes with the same digit: one vote per digit bit (and one for validity)
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+    if (!valid) peers = ~peers;
+#pragma unroll
+    for (int bit = 0; bit < 8; ++bit) {
+      const bool set = (d >> bit) & 1u;
+      const uint32_t vb = __ballot_sync(0xffffffffu, set);
+      peers &= set ? vb : ~vb;
+    }
     const int leader = __ffs(peers) - 1;
     uint32_t before = 0;
     if (valid && lane == leader) {
