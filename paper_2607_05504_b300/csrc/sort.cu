@@ -29,7 +29,6 @@ constexpr int OS_THREADS = 256;
 constexpr int OS_ITEMS = 16;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;
 constexpr int RADIX = 256;
-constexpr int OS_WARPS = OS_THREADS / WARP;
 constexpr int MAX_PASSES = 4;
 constexpr uint32_t SLOT_AGG = 1u << 30;    // the tile's own count
 constexpr uint32_t SLOT_PRE = 2u << 30;    // the count of this and every earlier tile
