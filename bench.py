@@ -58,11 +58,25 @@ def _peaks():
     return 6400.0, "fallback"
 
 
-def _workload(seed_offset=0):
+def _workload(seed_offset=0, n=1 << 20):
+    """The bench halo of one replica: rank r steps the Hernquist halo of
+    seed 1 + r (replicas only, no data-path collective)."""
     from paper_2607_05504_b300 import inputs as I
-    w = I.hernquist_2pow20(seed=1 + seed_offset)
+    w = I.hernquist_2pow20(seed=1 + seed_offset, n=n)
     masks = np.stack([I.active_at_step(w["bins"], s) for s in range(CYCLE)])
     return w, masks
+
+
+def reduce_over_ranks(t_ms, updates, device):
+    """Whole-job figures of a replicas run: the slowest rank's time and the
+    updates of all ranks (two all-reduces of host-side scalars)."""
+    import torch
+    import torch.distributed as D
+    tt = torch.tensor([t_ms, float(updates)], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    D.all_reduce(mx, op=D.ReduceOp.MAX)
+    D.all_reduce(tt, op=D.ReduceOp.SUM)
+    return float(mx[0]), float(tt[1])
 
 
 class Clocks:
@@ -502,13 +516,8 @@ def main():
                  "slowest": [[(args.warmup + i) % CYCLE, round(step_ms[i], 3)] for i in srt[-3:]],
                  "note": "finest step index in the cycle: the all-active step 0 is the slowest"}
     if dist:
-        import torch.distributed as D
-        tt = torch.tensor([t_ms, float(upd)], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        D.all_reduce(mx, op=D.ReduceOp.MAX)
-        D.all_reduce(tt, op=D.ReduceOp.SUM)
-        t_all, upd_all = float(mx[0]), float(tt[1])
-        D.barrier()
+        t_all, upd_all = reduce_over_ranks(t_ms, upd, dev)
+        dist.barrier()
     else:
         t_all, upd_all = t_ms, float(upd)
     value = upd_all / (t_all * 1e-3)
