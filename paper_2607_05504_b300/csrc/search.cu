@@ -11,7 +11,8 @@
 //      rounding of coordinates, differences, squares, sums).  Every test
 //      "surely inside / surely outside radius H" becomes one comparison of
 //      the FP32 squared separation with a threshold computed once per H.
-//   2. Radius T: from the key-order window of 256 particles around i, an
+//   2. Radius T: from the key-order window of 128-512 particles around i
+//      (a launch shape, 384 by default), an
 //      upper bound (within ~2 % above) of the K-th smallest hi,
 //      K = N_ngb + tol + 1: K particles have r <= T.
 //   3. Gather: every particle whose lower bound is <= T goes into a
@@ -423,6 +424,7 @@ template <bool PERIODIC>
 void launch_search_window(const SearchArgs& a, int window, unsigned blocks, cudaStream_t s) {
   if (window <= 128) search_kernel<PERIODIC, 4><<<blocks, ST, 0, s>>>(a);
   else if (window <= 256) search_kernel<PERIODIC, 8><<<blocks, ST, 0, s>>>(a);
+  else if (window <= 384) search_kernel<PERIODIC, 12><<<blocks, ST, 0, s>>>(a);
   else search_kernel<PERIODIC, 16><<<blocks, ST, 0, s>>>(a);
 }
 

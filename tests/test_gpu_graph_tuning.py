@@ -82,7 +82,7 @@ def test_autotune_leaves_the_state_and_results_unchanged():
     ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
     prm = [sidm.HaloParams(dt, sidm.SigmaModel(0, 1.0, 1.0), 5, 0)]
     best = ctx.autotune(prm, I.active_at_step(bins, 0), bins, reps=2)
-    assert best["search_window"] in (128, 256, 512)
+    assert best["search_window"] in (128, 256, 384, 512)
     assert ctx.tuning == best
     assert ctx.step_counter == 0
     v, _ = ctx.velocities()
