@@ -12,7 +12,7 @@
 //      "surely inside / surely outside radius H" becomes one comparison of
 //      the FP32 squared separation with a threshold computed once per H.
 //   2. Radius T: from the key-order window of 128-512 particles around i
-//      (a launch shape, 384 by default), an
+//      (a launch shape, 512 by default), an
 //      upper bound (within ~2 % above) of the K-th smallest hi,
 //      K = N_ngb + tol + 1: K particles have r <= T.
 //   3. Gather: every particle whose lower bound is <= T goes into a

@@ -351,7 +351,7 @@ int tree_levels_for(int64_t n, int64_t count[MAX_LEVELS]);
 // search.cu
 // Launch shapes that leave every result unchanged (see sidm_tuning).
 struct LaunchTuning {
-  int search_window = 384;       // key-order window of the search radius (128, 256, 384, 512)
+  int search_window = 512;       // key-order window of the search radius (128, 256, 384, 512)
   int search_chunk = 1;          // queries per work-counter increment
   int search_blocks_per_sm = 8;  // 4-warp blocks per SM (at most 8 are resident)
   int pairs_chunk = 4;
