@@ -60,7 +60,10 @@ typedef enum {
   SIDM_ERR_INVALID_ARG = -1,
   SIDM_ERR_OOM = -2,
   SIDM_ERR_CUDA = -3,
-  SIDM_ERR_DEVICE_LIMIT = -4,    /* a bounded device loop or buffer gave up; step not valid */
+  SIDM_ERR_DEVICE_LIMIT = -4,    /* a bounded device loop or buffer gave up; step not valid:
+                                    a full pair buffer is found before any kick (velocities
+                                    untouched); after a bounded wait gave up (resolver passes,
+                                    key-sort look-back) some kicks may have been applied */
   SIDM_ERR_NOT_READY = -5,       /* sidm_step before sidm_set_particles                     */
   SIDM_ERR_TOO_LARGE = -6        /* input beyond the fixed scratch of a no-allocation call  */
 } sidm_status;
