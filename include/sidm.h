@@ -112,6 +112,10 @@ typedef struct {
                            at domain decompositions, Sec. 4.3).  Results are unchanged; the
                            search slows as particles drift from their key order.  0 or 1:
                            every step (the default).                                        */
+  int max_resolver_passes;  /* bound on the passes of the resolver's bounded wait (0: 2^22,
+                           far above any step's needs).  A step that needs more returns
+                           SIDM_ERR_DEVICE_LIMIT with some kicks applied; a small value
+                           lets a test make that wait run out on purpose.             */
 } sidm_config;
 
 /* Fills `cfg` with the paper's fiducial values (N_ngb 32 +- 5, C_SIDM 0.1,

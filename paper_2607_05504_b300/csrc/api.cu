@@ -478,7 +478,8 @@ int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches, int par
     L += launch_pairs(c->so, F, n, c->act_list, c->nb_list, c->nb_count, c->nb_stride, pa,
                       c->pairs, c->dtlim, c->dstats, c->work + 1, c->sms, c->tune, s);
     mark(5);
-    const int nr = launch_resolve(c->pairs, c->pair_cap, c->vel, c->mass, c->halo_of,
+    const int nr = launch_resolve(c->pairs, c->pair_cap, c->cfg.max_resolver_passes, c->vel,
+                                  c->mass, c->halo_of,
                                   c->d_halos, c->rb, c->dstats, c->sms, s);
     if (nr < 0) return SIDM_ERR_CUDA;
     L += nr;
@@ -650,7 +651,7 @@ int sidm_create(const sidm_config* cfg, sidm_ctx** out) {
       !std::isfinite(cfg->box) || (cfg->kernel != SIDM_KERNEL_CUBIC && cfg->kernel != SIDM_KERNEL_TOPHAT) ||
       (cfg->precision != SIDM_FP64_PLAIN && cfg->precision != SIDM_FP32_SPLIT) ||
       !(cfg->fixed_h >= 0.0) || cfg->n_max < 0 ||
-      cfg->pair_capacity < 0 || cfg->rebuild_every < 0 ||
+      cfg->pair_capacity < 0 || cfg->rebuild_every < 0 || cfg->max_resolver_passes < 0 ||
       (cfg->estimator != SIDM_ESTIMATOR_ONE_SIDED && cfg->estimator != SIDM_ESTIMATOR_OVERLAP))
     return SIDM_ERR_INVALID_ARG;
   sidm_ctx* c = new (std::nothrow) sidm_ctx();

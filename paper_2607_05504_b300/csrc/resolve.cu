@@ -381,7 +381,8 @@ __global__ void __launch_bounds__(GT) rank_kernel(const PairRec* __restrict__ pa
 }
 
 __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict__ pairs, int64_t cap,
-                                                      double* vel, const double* __restrict__ mass,
+                                                      int max_passes, double* vel,
+                                                      const double* __restrict__ mass,
                                                       ResolveBuffers b,
                                                       const int32_t* __restrict__ halo_of,
                                                       const Halo* __restrict__ halos,
@@ -413,7 +414,7 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
     }
     int pass = 0;
     bool left = first;
-    for (; left && pass < DATAFLOW_MAX_PASSES; ++pass) {
+    for (; left && pass < max_passes; ++pass) {
       left = false;
       if (first) {
         const int ca = ld_acquire(&b.cursor[r0.ia]);
@@ -496,9 +497,9 @@ int dataflow_grid(int sms) {
 
 }  // namespace
 
-int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* mass,
-                   const int32_t* halo_of, const Halo* halos, const ResolveBuffers& b,
-                   DevStats* st, int sms, cudaStream_t s) {
+int launch_resolve(PairRec* pairs, int64_t pair_cap, int max_passes, double* vel,
+                   const double* mass, const int32_t* halo_of, const Halo* halos,
+                   const ResolveBuffers& b, DevStats* st, int sms, cudaStream_t s) {
   const unsigned g = (unsigned)(sms * 4);
   count_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, b.mult, st);
   split_kernel<<<g, GT, 0, s>>>(pairs, pair_cap, vel, mass, b, halo_of, halos, st);
@@ -508,8 +509,9 @@ int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* 
   ResolveBuffers bb = b;
   PairRec* pp = pairs;
   int64_t cap = pair_cap;
-  void* args[] = {(void*)&pp,      (void*)&cap,   (void*)&vel, (void*)&mass,
-                  (void*)&bb,      (void*)&halo_of, (void*)&halos, (void*)&st};
+  int mp = max_passes > 0 ? max_passes : DATAFLOW_MAX_PASSES;
+  void* args[] = {(void*)&pp,   (void*)&cap,     (void*)&mp,    (void*)&vel, (void*)&mass,
+                  (void*)&bb,   (void*)&halo_of, (void*)&halos, (void*)&st};
   if (cudaLaunchCooperativeKernel((const void*)dataflow_kernel, dim3(dataflow_grid(sms)),
                                   dim3(GT), args, 0, s) != cudaSuccess)
     return -1;

@@ -400,9 +400,10 @@ struct ResolveBuffers {
   int32_t* pos_a;     // [cap] place of the pair in the sorted segment of its particle a
   int32_t* pos_b;     // [cap] ... and of its particle b
 };
-int launch_resolve(PairRec* pairs, int64_t pair_cap, double* vel, const double* mass,
-                   const int32_t* halo_of, const Halo* halos, const ResolveBuffers& b,
-                   DevStats* st, int sms, cudaStream_t s);
+// max_passes: bound on the dataflow passes (0: the built-in 2^22)
+int launch_resolve(PairRec* pairs, int64_t pair_cap, int max_passes, double* vel,
+                   const double* mass, const int32_t* halo_of, const Halo* halos,
+                   const ResolveBuffers& b, DevStats* st, int sms, cudaStream_t s);
 void launch_resolve_with_scratch(const PairRec* pairs, int64_t pair_cap, double* vel,
                                  const double* mass, int32_t* head, int32_t* next, uint8_t* flags,
                                  int32_t* mult, uint64_t seed, uint32_t step, DevStats* st,

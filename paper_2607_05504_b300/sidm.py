@@ -45,7 +45,8 @@ class Config(C.Structure):
                 ("box", C.c_double), ("kernel", C.c_int), ("precision", C.c_int),
                 ("fixed_h", C.c_double), ("n_max", C.c_int64), ("pair_capacity", C.c_int64),
                 ("stream", C.c_void_p), ("device", C.c_int), ("profile", C.c_int),
-                ("use_graph", C.c_int), ("estimator", C.c_int), ("rebuild_every", C.c_int)]
+                ("use_graph", C.c_int), ("estimator", C.c_int), ("rebuild_every", C.c_int),
+                ("max_resolver_passes", C.c_int)]
 
 
 class Tuning(C.Structure):
@@ -367,7 +368,7 @@ class Context:
     def __init__(self, n_ngb=32, ngb_tol=5, c_sidm=0.1, box=0.0, kernel=KERNEL_CUBIC,
                  fixed_h=0.0, n_max=0, pair_capacity=0, stream=None, device=-1, profile=False,
                  precision=FP64_PLAIN, use_graph=False, rebuild_every=0,
-                 estimator=ESTIMATOR_ONE_SIDED):
+                 estimator=ESTIMATOR_ONE_SIDED, max_resolver_passes=0):
         cfg = sidm_default_config()
         cfg.n_ngb, cfg.ngb_tol, cfg.c_sidm, cfg.box = int(n_ngb), int(ngb_tol), float(c_sidm), float(box)
         cfg.kernel, cfg.fixed_h, cfg.n_max = int(kernel), float(fixed_h), int(n_max)
@@ -379,6 +380,7 @@ class Context:
         cfg.use_graph = int(bool(use_graph))
         cfg.rebuild_every = int(rebuild_every)
         cfg.estimator = int(estimator)
+        cfg.max_resolver_passes = int(max_resolver_passes)
         self.cfg = cfg
         self.handle = sidm_create(cfg)
         self.n = 0
