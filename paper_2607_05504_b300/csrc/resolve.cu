@@ -40,22 +40,81 @@ __device__ bool first_at(int64_t p, const PairRec& rp, int32_t e, const int32_t*
   return true;
 }
 
+// The mass terms of a pair, fixed before its turn: M = m_a + m_b and, where
+// M lies in [2^-500, 2^500), its correctly rounded reciprocal y = 1/M.
+struct KickTerms {
+  double ma, mb, M, y, eps;
+  bool rcp;      // y is set, and divisions by M start from it
+  bool elastic;  // eps == 1: the product with eps is the identity
+};
+
+// biased binary64 exponent in [523, 1522], i.e. |v| in [2^-500, 2^500)
+// (positive only when `positive`)
+__device__ __forceinline__ bool in_rcp_range(double v, bool positive) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned e = positive ? (unsigned)(b >> 52) : (unsigned)(b >> 52) & 0x7FFu;
+  return e - 523u < 1000u;
+}
+
+__device__ __forceinline__ KickTerms kick_terms(double ma, double mb, double eps) {
+  KickTerms t;
+  t.ma = ma;
+  t.mb = mb;
+  t.M = ma + mb;
+  t.eps = eps;
+  t.rcp = in_rcp_range(t.M, true);
+  t.y = t.rcp ? 1.0 / t.M : 0.0;
+  t.elastic = eps == 1.0;
+  return t;
+}
+
+// x / M, correctly rounded, with the division replaced where it is safe.
+// From y = RN(1/M), Markstein's correction (P. Markstein, IBM J. Res. Dev.
+// 34 (1990) 111) gives q = RN(q0 + RN(x - M q0) y), q0 = RN(x y), by two
+// FMAs.  q is then checked, not trusted: the FMA remainder r = RN(x - M q)
+// is M (x/M - q) rounded once, and q is kept when |r| < M s/2, s being the
+// spacing of the doubles next to q on the side of x/M (ulp(q), or half of
+// it toward zero from a power of two).  M s/2 is M times a power of two,
+// a double, and rounding is monotone, so a kept q lies within half a
+// spacing of x/M: it is the correctly rounded quotient (a quotient of two
+// doubles is never a midpoint).  Otherwise, or when x or M lies outside
+// [2^-500, 2^500) (where a step could under- or overflow), the division.
+__device__ __forceinline__ double div_m(double x, const KickTerms& t) {
+  if (t.rcp && in_rcp_range(x, false)) {
+    const double q0 = __dmul_rn(x, t.y);
+    const double q = __fma_rn(__fma_rn(-t.M, q0, x), t.y, q0);
+    const double r = __fma_rn(-t.M, q, x);
+    const unsigned long long qb = (unsigned long long)__double_as_longlong(q);
+    const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
+    const bool toward0 = ((qb ^ rb) >> 63) != 0;               // M > 0: sign(r) = sign(x/M - q)
+    const bool pow2 = (qb & 0xFFFFFFFFFFFFFull) == 0;
+    // M s/2 = M 2^(E(q) - 53) (one less toward zero from a power of two):
+    // an exponent shift of M, in range since M q ~ x
+    const long long k = (long long)((qb >> 52) & 0x7FFu) - 1076 - ((toward0 && pow2) ? 1 : 0);
+    const unsigned long long half_gap =
+        (unsigned long long)__double_as_longlong(t.M) + ((unsigned long long)k << 52);
+    if ((rb & 0x7FFFFFFFFFFFFFFFull) < half_gap) return q;
+  }
+  return x / t.M;
+}
+
 // The kick of Eqs. 12-13 in the operation order
 //   v_com = ((m_a v_a) + (m_b v_b)) / M,  g = sqrt((dx dx + dy dy) + dz dz) eps,
 //   v_a' = v_com + ((m_b g) / M) e,  v_b' = v_com - ((m_a g) / M) e,
 // with M = m_a + m_b and eps the outgoing / incoming relative speed (1:
-// elastic; the product with 1 is exact); every operation rounds once.
-__device__ __forceinline__ void kick_values(double ma, double mb, double eps, const double* e,
-                                            double* a, double* b) {
-  const double M = ma + mb;
+// elastic; the product with 1 is exact and skipped); every operation rounds
+// once.
+__device__ __forceinline__ void kick_values(const KickTerms& t, const double* e, double* a,
+                                            double* b) {
   double c[3], d[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    c[k] = ((ma * a[k]) + (mb * b[k])) / M;
+    c[k] = div_m((t.ma * a[k]) + (t.mb * b[k]), t);
     d[k] = a[k] - b[k];
   }
-  const double g = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]) * eps;
-  const double fa = (mb * g) / M, fb = (ma * g) / M;
+  double g = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+  if (!t.elastic) g = g * t.eps;
+  const double fa = div_m(t.mb * g, t), fb = div_m(t.ma * g, t);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     a[k] = c[k] + fa * e[k];
@@ -83,10 +142,10 @@ __device__ void kick(const PairRec& r, double* vel, const double* mass, uint32_t
   if (!found) atomicAdd(dirfail, 1u);
   double* va = vel + 3 * (int64_t)r.ia;
   double* vb = vel + 3 * (int64_t)r.ib;
-  const double ma = mass[r.ia], mb = mass[r.ib];
+  const KickTerms kt = kick_terms(mass[r.ia], mass[r.ib], eps);
   const double e[3] = {e0, e1, e2};
   double a[3] = {va[0], va[1], va[2]}, b[3] = {vb[0], vb[1], vb[2]};
-  kick_values(ma, mb, eps, e, a, b);
+  kick_values(kt, e, a, b);
   va[0] = a[0];
   va[1] = a[1];
   va[2] = a[2];
@@ -235,13 +294,13 @@ __device__ __forceinline__ void pair_direction(const PairRec& r, uint32_t k0, ui
 
 // The kick of a pending pair with direction e, the velocities read and
 // written through L2 (other SMs apply the neighbouring kicks).
-__device__ __forceinline__ void kick_l2(const PairRec& r, double* vel, double ma, double mb,
-                                        double eps, const double* e) {
+__device__ __forceinline__ void kick_l2(const PairRec& r, double* vel, const KickTerms& kt,
+                                        const double* e) {
   double* va = vel + 3 * (int64_t)r.ia;
   double* vb = vel + 3 * (int64_t)r.ib;
   double a[3] = {__ldcg(va), __ldcg(va + 1), __ldcg(va + 2)};
   double b[3] = {__ldcg(vb), __ldcg(vb + 1), __ldcg(vb + 2)};
-  kick_values(ma, mb, eps, e, a, b);
+  kick_values(kt, e, a, b);
   __stcg(va, a[0]);
   __stcg(va + 1, a[1]);
   __stcg(va + 2, a[2]);
@@ -290,7 +349,7 @@ __device__ __forceinline__ void claim_segments(bool want, int32_t e, const int32
   }
 }
 
-__global__ void __launch_bounds__(GT) split_kernel(const PairRec* __restrict__ pairs, int64_t cap,
+__global__ void __launch_bounds__(GT, 4) split_kernel(const PairRec* __restrict__ pairs, int64_t cap,
                                                    double* vel, const double* __restrict__ mass,
                                                    ResolveBuffers b,
                                                    const int32_t* __restrict__ halo_of,
@@ -395,21 +454,20 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
     const int64_t np = (int64_t)st->n_pending;
     const int64_t gsize = (int64_t)gridDim.x * GT;
     const int64_t t0 = blockIdx.x * (int64_t)GT + threadIdx.x;
-    // the thread's first pair, prepared (masses, direction) before its turn;
-    // a turn is two acquire loads of the cursors
+    // the thread's first pair, prepared (mass terms, direction) before its
+    // turn; a turn is two acquire loads of the cursors
     bool first = t0 < np;
     PairRec r0{};
     int pa0 = 0, pb0 = 0;
-    double ma0 = 0.0, mb0 = 0.0, eps0 = 1.0, e0[3];
+    KickTerms kt0{};
+    double e0[3];
     if (first) {
       const int32_t p = b.pending[t0];
       r0 = pairs[p];
       pa0 = b.pos_a[p];
       pb0 = b.pos_b[p];
-      ma0 = mass[r0.ia];
-      mb0 = mass[r0.ib];
       const Halo& H = halos[halo_of[r0.ia]];
-      eps0 = H.eps;
+      kt0 = kick_terms(mass[r0.ia], mass[r0.ib], H.eps);
       pair_direction(r0, (uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, e0, &s_dirfail);
     }
     int pass = 0;
@@ -420,7 +478,7 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
         const int ca = ld_acquire(&b.cursor[r0.ia]);
         const int cb = ld_acquire(&b.cursor[r0.ib]);
         if (ca == pa0 && cb == pb0) {
-          kick_l2(r0, vel, ma0, mb0, eps0, e0);
+          kick_l2(r0, vel, kt0, e0);
           fence_acq_rel();   // release: one fence covers both cursor stores
           st_relaxed(&b.cursor[r0.ia], pa0 + 1);
           st_relaxed(&b.cursor[r0.ib], pb0 + 1);
@@ -441,7 +499,7 @@ __global__ void __launch_bounds__(GT) dataflow_kernel(const PairRec* __restrict_
           const Halo& H = halos[halo_of[r.ia]];
           double e[3];
           pair_direction(r, (uint32_t)H.seed, (uint32_t)(H.seed >> 32), H.step, e, &s_dirfail);
-          kick_l2(r, vel, mass[r.ia], mass[r.ib], H.eps, e);
+          kick_l2(r, vel, kick_terms(mass[r.ia], mass[r.ib], H.eps), e);
           fence_acq_rel();
           st_relaxed(&b.cursor[r.ia], pa + 1);
           st_relaxed(&b.cursor[r.ib], pb + 1);
