@@ -316,7 +316,9 @@ SIDM_API int sidm_overlap_table(int kernel, int32_t na, int32_t ns, double* out)
  * results; only the time changes.  Zero fields take the defaults. */
 typedef struct {
   int search_window;        /* key-order window that bounds each search radius:
-                               128, 256, 384 or 512 (default) particles              */
+                               128, 256, 384 or 512 (default) particles; a window
+                               of fewer than n_ngb + ngb_tol + 2 particles runs as
+                               256                                                   */
   int search_chunk;         /* queries a search warp claims at a time, 1..64 (1)      */
   int search_blocks_per_sm; /* search blocks of 4 warps launched per SM, 1..8 (8)     */
   int pairs_chunk;          /* queries a pair warp claims at a time, 1..64 (4)        */

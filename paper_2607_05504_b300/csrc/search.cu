@@ -12,9 +12,11 @@
 //      "surely inside / surely outside radius H" becomes one comparison of
 //      the FP32 squared separation with a threshold computed once per H.
 //   2. Radius T: from the key-order window of 128-512 particles around i
-//      (a launch shape, 512 by default), an
-//      upper bound (within ~2 % above) of the K-th smallest hi,
-//      K = N_ngb + tol + 1: K particles have r <= T.
+//      (a launch shape, 512 by default; at least K + 1 particles, so 256
+//      where 128 would be too few), an upper bound (within ~2 % above) of
+//      the K-th smallest hi, K = N_ngb + tol + 1: K particles have r <= T.
+//      A halo with at most K particles besides i has no bound: T is
+//      infinite and the whole halo (fewer than SEARCH_CAP) is gathered.
 //   3. Gather: every particle whose lower bound is <= T goes into a
 //      shared-memory list (FP32 squared separation, index).  If more than
 //      SEARCH_CAP qualify, T shrinks (count-verified) and the gather repeats.
@@ -169,15 +171,17 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
     double h;
     int len = 0;
     float T = INFINITY;  // every j with r <= T (and more) is in the list
+    // the key-order window bounds T only when it holds K particles besides i
+    const int64_t W = (int64_t)NWIN * 32 < hn ? (int64_t)NWIN * 32 : hn;
+    const bool window_bound = !(A.fixed_h > 0.0) && W - 1 >= K;
 
     if (A.fixed_h > 0.0) {
       h = A.fixed_h;
       float hl, hu;
       float_bounds(h, &hl, &hu);
       T = hu;
-    } else if (hn - 1 >= K) {
+    } else if (window_bound) {
       // ---- 2. radius T from the key-order window
-      const int64_t W = (int64_t)NWIN * 32 < hn ? (int64_t)NWIN * 32 : hn;
       int64_t w0 = s - W / 2;
       if (w0 > hs + hn - W) w0 = hs + hn - W;
       if (w0 < hs) w0 = hs;
@@ -341,7 +345,6 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
       }
       return warp_sum(c);
     };
-    const bool window_bound = !(A.fixed_h > 0.0) && (hn - 1 >= K);
     if (!(A.fixed_h > 0.0)) {
       h = H.h0;
       double blo = 0.0, bhi = 0.0;
@@ -439,8 +442,12 @@ int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* a
   int64_t blocks = (int64_t)sms * t.search_blocks_per_sm;
   const int64_t need = (n + SW - 1) / SW;
   if (blocks > need) blocks = need;
-  if (box > 0.0) launch_search_window<true>(a, t.search_window, (unsigned)blocks, s);
-  else launch_search_window<false>(a, t.search_window, (unsigned)blocks, s);
+  // the window must hold K = N_ngb + tol + 1 particles besides the query for
+  // its radius to bound the K-th neighbour (K <= 255, so 256 always does)
+  int window = t.search_window;
+  if (window - 1 < n_ngb + tol + 1 && window < 256) window = 256;
+  if (box > 0.0) launch_search_window<true>(a, window, (unsigned)blocks, s);
+  else launch_search_window<false>(a, window, (unsigned)blocks, s);
   return 1;
 }
 

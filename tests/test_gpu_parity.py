@@ -119,6 +119,26 @@ def test_halo_partial_activity_random_ids_unequal_masses():
     run_pair(p, act, bins, 0.2, n_ngb=64)
 
 
+def test_large_neighbour_number_with_the_smallest_window():
+    # K = N_ngb + tol + 1 = 206 exceeds the 127 other particles of a
+    # 128-particle window, which then cannot bound the search radius: the
+    # launch takes the 256-particle window instead, with the same results
+    p = I.hernquist_halo(20000, 7, ids="random")
+    rng = np.random.default_rng(2)
+    act = (rng.random(p.n) < 0.2).astype(np.uint8)
+    bins = np.zeros(p.n, np.int8)
+    ctx = sidm.Context(n_ngb=200, ngb_tol=5)
+    ctx.set_tuning(search_window=128)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    o = oracle.step(p.pos, p.vel, p.mass, p.ids, act, bins, 2.0, n_ngb=200, ngb_tol=5, seed=0,
+                    step=0)
+    g = _gpu_step(ctx, p, act, bins, 2.0)
+    assert ctx.tuning["search_window"] == 128
+    ctx.close()
+    _compare(g, o, act)
+    assert o["n_pairs"] > 100
+
+
 def test_yukawa_tophat_box():
     p = I.uniform_box(3000, 2.0, 1.5, 4, ids="random")
     run_pair(p, None, np.zeros(p.n, np.int8), 0.3, kernel=1, sigma_kind=1, sigma0=5.0, w=1.2)
