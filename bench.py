@@ -46,7 +46,7 @@ PHASE_BYTES = {
 }
 
 
-SEARCH_DRAM_BYTES = 6.539008e6 + 1.027584e6   # dram read + write of the captured launch
+SEARCH_DRAM_BYTES = 6.573568e6 + 1.042432e6   # dram read + write of the captured launch
 SEARCH_DRAM_QUERIES = 51520
 
 
