@@ -168,7 +168,9 @@ __global__ void params_kernel(Halo* halos, int n_halos, double box) {
   H.h0 = ldexp(l_ext, -H.e0);
   float r2 = 0.f;
   for (int a = 0; a < 3; ++a) {
-    H.centre[a] = (float)(0.5 * (lo[a] + hi[a]));
+    // open boundaries: the middle of the bounding box (key transform and
+    // origin of the FP32 copies); periodic: 0 (the copies stay absolute)
+    H.centre[a] = box > 0.0 ? 0.0f : (float)(0.5 * (lo[a] + hi[a]));
     const float d = (float)(hi[a] - lo[a]);
     r2 += d * d;
   }
@@ -298,7 +300,14 @@ __global__ void __launch_bounds__(BT) permute_kernel(
     so.z[s] = z;
     const double dt = scale_pow2_down(halos[k].dt_max, (int)bins[o]);
     const double m = mass[o];
-    so.f[s] = make_float4(f64_to_f32_rn(x), f64_to_f32_rn(y), f64_to_f32_rn(z), f64_to_f32_ru(dt));
+    // FP32 copies relative to the halo's centre c (a float, so exact in
+    // FP64): their rounding, 2^-24 (1 + 2^-28) |x - c| with the FP64
+    // difference, scales with the halo's extent instead of its distance from
+    // the origin.  Every FP32 test compares particles of one halo, and a
+    // common translation changes none of their separations.
+    const float* c = halos[k].centre;
+    so.f[s] = make_float4(f64_to_f32_rn(x - (double)c[0]), f64_to_f32_rn(y - (double)c[1]),
+                          f64_to_f32_rn(z - (double)c[2]), f64_to_f32_ru(dt));
     so.m[s] = m;
     so.id[s] = ids[o];
     a = act[o] != 0;
@@ -319,11 +328,11 @@ __global__ void __launch_bounds__(BT) permute_kernel(
 
 // Leaves: conservative FP32 box of up to 32 consecutive particles of a halo
 // (min rounded down, max rounded up from the FP64 coordinates).
-// Leaf boxes from the FP32 copies (round to nearest) of the positions:
-// |x - fl32(x)| <= 2^-24 |fl32(x)| for normal values, so widening the FP32
-// extrema by 2^-23 of their magnitude (plus the smallest normal, for values
-// near zero), with directed rounding, gives boxes that contain the FP64
-// positions.  No FP64 arithmetic.
+// Leaf boxes from the FP32 copies f of the positions relative to the
+// halo's centre, u = x - c: |u - f| <= 2^-24 (1 + 2^-28) |u|, below
+// 2^-23 |f| for normal values, so widening the FP32 extrema by 2^-23 of
+// their magnitude (plus the smallest normal, for values near zero), with
+// directed rounding, gives boxes that contain every u.  No FP64 arithmetic.
 __device__ __forceinline__ float widen_down(float v) {
   return __fsub_rd(v, __fadd_ru(__fmul_ru(fabsf(v), 1.1920928955078125e-07f), 1.17549435e-38f));
 }

@@ -4,7 +4,8 @@
 //
 // One warp per active particle i:
 //   1. Bounds.  Separations are first taken in FP32 from the FP32 copies of
-//      the positions (within 2^-24 |x| of the FP64 values), so the true
+//      the positions relative to the halo's centre c (within
+//      2^-24 (1 + 2^-28) |x - c| of x - c; |x| below for x - c), so the true
 //      separation r of a candidate with FP32 separation s lies in
 //      [lo(s), hi(s)], lo(s) = s (1 - c) - e, hi(s) = s (1 + c) + e with
 //      c = 2^-20 + 2^-21 and e = 2^-21 (max|x_i| + L) (generous over the

@@ -139,6 +139,28 @@ def test_large_neighbour_number_with_the_smallest_window():
     assert o["n_pairs"] > 100
 
 
+def test_coincident_positions_match_the_oracle():
+    # groups of 8 particles at identical positions (zero separations in the
+    # window radius, the gather and the bisection) and one clump of 121, more
+    # than N_ngb + tol, whose members can reach no admissible count
+    p = I.uniform_box(4096, 1.0, 1.0, 41, ids="random")
+    p.pos[:] = np.repeat(p.pos[::8].copy(), 8, axis=0)[:p.n]
+    p.pos[-120:] = p.pos[-121]
+    g, o = run_pair(p, None, np.zeros(p.n, np.int8), 0.02, seed=5)
+    assert o["stats"]["n_h_nonconv"] > 120 and o["n_pairs"] > 1000
+
+
+def test_halo_far_from_the_origin_matches_the_oracle():
+    # at |x| ~ 3e5 the FP32 copies resolve ~0.02, a good part of the
+    # spacing: many certified bounds are ambiguous and the exact FP64 tests
+    # decide
+    q = I.hernquist_halo(20000, 9, ids="random")
+    q.pos = q.pos + np.array([1.0e5, -2.0e5, 3.0e5])
+    act = (np.random.default_rng(3).random(q.n) < 0.3).astype(np.uint8)
+    g, o = run_pair(q, act, np.zeros(q.n, np.int8), 5.0, seed=6)
+    assert o["n_pairs"] > 300
+
+
 def test_yukawa_tophat_box():
     p = I.uniform_box(3000, 2.0, 1.5, 4, ids="random")
     run_pair(p, None, np.zeros(p.n, np.int8), 0.3, kernel=1, sigma_kind=1, sigma0=5.0, w=1.2)
