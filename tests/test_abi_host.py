@@ -43,7 +43,12 @@ def test_default_config_is_the_papers_fiducial():
 @pytest.mark.parametrize("field,value", [("n_ngb", 0), ("ngb_tol", -1), ("ngb_tol", 32),
                                          ("c_sidm", 0.0), ("box", -1.0), ("kernel", 7),
                                          ("precision", 3), ("fixed_h", -1.0), ("n_max", -5),
-                                         ("n_ngb", 300)])
+                                         ("n_ngb", 300),
+                                         # K + 1 = n_ngb + tol + 2 must stay <= 256
+                                         ("n_ngb", 250),
+                                         ("max_resolver_passes", -1), ("rebuild_every", -1),
+                                         ("pair_capacity", -1), ("estimator", 5),
+                                         ("box", float("inf")), ("fixed_h", float("nan"))])
 def test_create_rejects_invalid_config(field, value):
     c = sidm.sidm_default_config()
     setattr(c, field, value)
