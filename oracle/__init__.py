@@ -107,6 +107,9 @@ def lib():
                                    C.c_double, C.POINTER(Sigma), C.c_uint64, C.c_uint64, dp, dp,
                                    C.c_int64, u32p, u64p, dp, i64p, C.POINTER(Stats)]
             L.orc_step.restype = C.c_int
+            L.orc_apply_pairs.argtypes = [C.c_int64, C.c_int64, u64p, u32p, u32p, i64p, i64p, dp,
+                                          dp, C.c_uint64, C.c_uint64, C.c_double]
+            L.orc_apply_pairs.restype = C.c_int64
             _lib = L
     return _lib
 
@@ -276,3 +279,27 @@ def step(pos, vel, mass, ids, active, bins, dt_max, *, n_ngb=32, ngb_tol=5, c_si
     k = min(npairs.value, cap)
     return {"vel": vel, "h": h, "dtlim": dl, "pairs_ab": ab[:k].copy(), "pairs_ord": ords[:k].copy(),
             "pairs_p": pp[:k].copy(), "n_pairs": npairs.value, "stats": st.as_dict()}
+
+
+def apply_pairs(vel, mass, ords, ab, idx, seed, step, eps=1.0):
+    """Canonical application of given accepted pairs (Sec. 4.1 kick, Sec. 4.4
+    multiple scatters): ascending (ord, a, b), equal keys in the order given,
+    each kick reading the current velocities.  ab: (k, 2) ids a < b; idx:
+    (k, 2) storage indices of the a- and b-particle.  Returns the new
+    velocities and the number of exhausted direction draws."""
+    vel = np.array(vel, np.float64, order="C", copy=True)
+    mass = np.ascontiguousarray(mass, np.float64)
+    o = np.ascontiguousarray(ords, np.uint64)
+    ab = np.asarray(ab)
+    idx = np.asarray(idx)
+    a = np.ascontiguousarray(ab[:, 0], np.uint32)
+    b = np.ascontiguousarray(ab[:, 1], np.uint32)
+    ia = np.ascontiguousarray(idx[:, 0], np.int64)
+    ib = np.ascontiguousarray(idx[:, 1], np.int64)
+    r = lib().orc_apply_pairs(vel.shape[0], o.shape[0], _p(o, C.c_uint64), _p(a, C.c_uint32),
+                              _p(b, C.c_uint32), _p(ia, C.c_int64), _p(ib, C.c_int64),
+                              _p(vel, C.c_double), _p(mass, C.c_double), int(seed), int(step),
+                              float(eps))
+    if r < 0:
+        raise ValueError("oracle apply_pairs: index outside [0, n) or a pair names one particle twice")
+    return vel, int(r)

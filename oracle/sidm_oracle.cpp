@@ -534,6 +534,28 @@ struct Pair {
   double p;           // P_pair
 };
 
+// Canonical application of the accepted pairs (Sec. 4.1 kick; Sec. 4.4:
+// a particle may scatter several times in one step, each kick seeing the
+// velocities the earlier ones left).  The pairs are put in ascending
+// (ord, a, b) order -- a stable sort, so records with equal keys keep the
+// order they were given in -- and kicked one after another.  Returns the
+// number of direction draws that ran out of tries.
+int64_t apply_pairs(std::vector<Pair>& acc, double* vel, const double* mass, uint64_t seed,
+                    uint64_t step, double eps) {
+  std::stable_sort(acc.begin(), acc.end(), [](const Pair& x, const Pair& y) {
+    if (x.ord != y.ord) return x.ord < y.ord;
+    if (x.a != y.a) return x.a < y.a;
+    return x.b < y.b;
+  });
+  int64_t dir_fail = 0;
+  for (const Pair& pr : acc) {
+    double e[3];
+    if (!isotropic_direction(seed, step, pr.a, pr.b, e)) ++dir_fail;
+    kick(mass[pr.i], mass[pr.j], vel + 3 * pr.i, vel + 3 * pr.j, e, eps);
+  }
+  return dir_fail;
+}
+
 }  // namespace
 
 extern "C" {
@@ -618,6 +640,21 @@ void orc_h_for(const orc_config* cfg, int64_t n, const double* pos, int64_t nq,
     if (count_out) count_out[t] = cnt;
     if (nonconv_out) nonconv_out[t] = nc;
   }
+}
+
+// Step 7 alone: applies n_pairs given accepted pairs (ord, ids a < b,
+// storage indices ia, ib) to vel (n x 3, in place) in the canonical order,
+// elastic when eps = 1.  Returns the number of exhausted direction draws,
+// or -1 if an index lies outside [0, n) or names one particle twice.
+int64_t orc_apply_pairs(int64_t n, int64_t n_pairs, const uint64_t* ord, const uint32_t* a,
+                        const uint32_t* b, const int64_t* ia, const int64_t* ib, double* vel,
+                        const double* mass, uint64_t seed, uint64_t step, double eps) {
+  std::vector<Pair> acc((size_t)n_pairs);
+  for (int64_t k = 0; k < n_pairs; ++k) {
+    if (ia[k] < 0 || ia[k] >= n || ib[k] < 0 || ib[k] >= n || ia[k] == ib[k]) return -1;
+    acc[k] = Pair{ord[k], a[k], b[k], ia[k], ib[k], 0.0};
+  }
+  return apply_pairs(acc, vel, mass, seed, step, eps);
 }
 
 // One scattering step.  pos/vel are n x 3 row-major; vel is updated in place.
@@ -745,17 +782,8 @@ int orc_step(const orc_config* cfg, int64_t n, const double* pos, double* vel,
   // 3. canonical order and sequential application with current velocities
   std::vector<Pair> acc;
   for (auto& v : acc_t) acc.insert(acc.end(), v.begin(), v.end());
-  std::sort(acc.begin(), acc.end(), [](const Pair& x, const Pair& y) {
-    if (x.ord != y.ord) return x.ord < y.ord;
-    if (x.a != y.a) return x.a < y.a;
-    return x.b < y.b;
-  });
   S.n_accepted = (int64_t)acc.size();
-  for (const Pair& pr : acc) {
-    double e[3];
-    if (!isotropic_direction(seed, step, pr.a, pr.b, e)) ++S.n_dir_fail;
-    kick(mass[pr.i], mass[pr.j], vel + 3 * pr.i, vel + 3 * pr.j, e, 1.0 - sig->inelastic);
-  }
+  S.n_dir_fail = apply_pairs(acc, vel, mass, seed, step, 1.0 - sig->inelastic);
 
   // 4. outputs for the active particles: h and the Eq. 18 limit (h of every
   // particle for the overlap estimator)

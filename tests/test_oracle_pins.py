@@ -522,6 +522,47 @@ def test_conservation_and_multiple_scatters(orc):
     assert np.any(r["vel"] != p.vel)
 
 
+def test_pair_application_order(orc):
+    """Step 7 alone (canonical application, Sec. 4.4): the pairs act in
+    ascending (ord, a, b) order, each kick on the velocities the earlier ones
+    left, and a record given twice acts twice in a row.  The expectation is
+    composed from the separately pinned direction and kick primitives."""
+    rng = np.random.default_rng(12)
+    vel = rng.normal(size=(3, 3))
+    mass = np.array([1.0, 2.0, 0.5])
+    ab = np.array([[0, 1], [1, 2], [0, 2], [0, 1]], np.uint32)
+    ords = np.array([7, 3, 5, 7], np.uint64)     # order: (1,2), (0,2), (0,1), (0,1)
+    seed, step = 21, 4
+
+    def by_hand(order):
+        v = vel.copy()
+        for k in order:
+            a, b = int(ab[k, 0]), int(ab[k, 1])
+            e, _ = orc.direction(seed, step, a, b)
+            v[a], v[b] = orc.kick(mass[a], mass[b], v[a], v[b], e)
+        return v
+
+    got, fails = orc.apply_pairs(vel, mass, ords, ab, ab, seed, step)
+    assert fails == 0
+    assert np.array_equal(got, by_hand([1, 2, 0, 3]))
+    assert not np.array_equal(got, by_hand([0, 1, 2, 3]))
+    # input order does not matter, except among equal keys (identical here)
+    perm = [3, 2, 0, 1]
+    again, _ = orc.apply_pairs(vel, mass, ords[perm], ab[perm], ab[perm], seed, step)
+    assert np.array_equal(again, got)
+    # the whole step is this application over its accepted pairs
+    p = I.uniform_box(3000, 1.0, 1.0, 13, ids="random")
+    r = orc.step(p.pos, p.vel, p.mass, p.ids, None, np.zeros(p.n, np.int8), 0.4, box=1.0,
+                 seed=2, step=5)
+    pos_of = {int(i): k for k, i in enumerate(p.ids)}
+    idx = np.array([[pos_of[int(x)] for x in q] for q in r["pairs_ab"]], np.int64)
+    sh = rng.permutation(idx.shape[0])
+    v2, _ = orc.apply_pairs(p.vel, p.mass, r["pairs_ord"][sh], r["pairs_ab"][sh], idx[sh], 2, 5)
+    assert np.array_equal(v2, r["vel"])
+    with pytest.raises(ValueError):
+        orc.apply_pairs(vel, mass, ords[:1], ab[:1], np.array([[0, 3]]), seed, step)
+
+
 def test_scattering_angle_isotropic(orc):
     """For pairs whose members scatter once, the angle between incoming and
     outgoing relative velocity has cos(theta) uniform in [-1, 1] (Sec. 5.1)."""
