@@ -29,13 +29,17 @@ __device__ __forceinline__ bool key_less(const PairRec& x, const PairRec& y) {
   return x.b < y.b;
 }
 
-// true if no other unapplied pair at particle e precedes pair p
+// true if no other unapplied pair at particle e precedes pair p.  Records
+// with equal keys (a caller may pass the same pair twice) precede one
+// another in record order, so they are applied one after the other, in the
+// order given, and never in the same round.
 __device__ bool first_at(int64_t p, const PairRec& rp, int32_t e, const int32_t* head,
                          const int32_t* next, const PairRec* pairs, const volatile uint8_t* flags) {
   for (int32_t slot = head[e]; slot >= 0; slot = next[slot]) {
     const int64_t q = slot >> 1;
     if (q == p || (flags[q] & 1)) continue;
-    if (key_less(pairs[q], rp)) return false;
+    const PairRec rq = pairs[q];
+    if (key_less(rq, rp) || (q < p && !key_less(rp, rq))) return false;
   }
   return true;
 }
