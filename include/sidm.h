@@ -38,6 +38,7 @@
 #ifndef SIDM_H
 #define SIDM_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -116,6 +117,23 @@ typedef struct {
                            far above any step's needs).  A step that needs more returns
                            SIDM_ERR_DEVICE_LIMIT with some kicks applied; a small value
                            lets a test make that wait run out on purpose.             */
+  /* Device memory of the context (the module keeps its particle and tree
+   * arrays itself, Sec. 4.6; a host code may want them in its own pool).
+   * alloc(bytes, stream, alloc_user) returns `bytes` (a multiple of 256) of
+   * device memory of the context's device, 256-byte aligned, usable on
+   * `stream` (the context's cudaStream_t), or NULL when it cannot (the
+   * calling entry point then returns SIDM_ERR_OOM).  free(ptr, stream,
+   * alloc_user) gives back a pointer alloc returned; the library calls it only
+   * after the stream has finished all work on that memory.  Both NULL (the
+   * default): cudaMalloc / cudaFree.  Set both or neither (else sidm_create
+   * returns SIDM_ERR_INVALID_ARG).  Every device buffer of the context goes
+   * through them: the capacity-sized arrays, the tree, the sigma and
+   * overlap tables and sidm_autotune's saved state.  Pinned host staging
+   * (a few bytes, and the changed-particle staging of sidm_update_velocities)
+   * stays with cudaMallocHost. */
+  void* (*alloc)(size_t bytes, void* stream, void* alloc_user);
+  void (*free)(void* ptr, void* stream, void* alloc_user);
+  void* alloc_user;
 } sidm_config;
 
 /* Fills `cfg` with the paper's fiducial values (N_ngb 32 +- 5, C_SIDM 0.1,
@@ -181,6 +199,41 @@ SIDM_API int sidm_set_velocities(sidm_ctx* ctx, const double* vel, int ptr_kind)
  * SIDM_ERR_INVALID_ARG (positions are then already replaced). */
 SIDM_API int sidm_set_positions(sidm_ctx* ctx, const double* pos, int ptr_kind);
 
+/* ---- Sub-ranges of the loaded particles ----------------------------------
+ * A serving loop keeps many independent haloes resident in one context
+ * (each a segment, see sidm_set_haloes) and admits or retires one without
+ * touching the others.
+ *
+ * sidm_write_particles: replaces particles [offset, offset + count) with
+ * `count` new ones (layouts as sidm_set_particles; mass NULL: mass_scalar
+ * for each).  0 <= offset <= n (no gap) and offset + count <= the capacity
+ * (config.n_max, or the n of the sidm_set_particles that sized the
+ * buffers); beyond it SIDM_ERR_INVALID_ARG (the buffers never move).  Their
+ * h resets to 0 and their dt limits to +inf; every other particle, its
+ * velocity, h and limit stay as they are.  If offset + count > n the loaded
+ * count grows to offset + count and the context becomes one halo over all
+ * particles (call sidm_set_haloes next).  Needs a context loaded once by
+ * sidm_set_particles (n = 0 is allowed). */
+SIDM_API int sidm_write_particles(sidm_ctx* ctx, int64_t offset, int64_t count, const double* pos,
+                                  const double* vel, const double* mass, double mass_scalar,
+                                  const uint32_t* ids, int ptr_kind);
+
+/* Drops the particles from n on (0 <= n <= the loaded count); the context
+ * becomes one halo over the remaining ones (call sidm_set_haloes next). */
+SIDM_API int sidm_set_count(sidm_ctx* ctx, int64_t n);
+
+/* Copies the velocities (n x 3, if vel_out is non-NULL) and h (if h_out is
+ * non-NULL) of particles [offset, offset + count); waits for the stream and
+ * returns the latched status, as sidm_get_particles. */
+SIDM_API int sidm_read_particles(sidm_ctx* ctx, int64_t offset, int64_t count, double* vel_out,
+                                 double* h_out, int ptr_kind);
+
+/* Device bytes a context created with `cfg` takes for a capacity of n
+ * particles in one halo (the capacity-sized buffers and that halo's tree;
+ * not the sigma and overlap tables): what an admission policy under a
+ * memory budget needs.  No device work. */
+SIDM_API int sidm_context_bytes(const sidm_config* cfg, int64_t n, int64_t* bytes);
+
 /* One scattering step (the whole path above).
  *   active_mask: n bytes, nonzero = active; NULL = all particles active.
  *   dt_bins:     n int8 bins, dt_i = dt_max * 2^-bin_i (power-of-two
@@ -188,7 +241,7 @@ SIDM_API int sidm_set_positions(sidm_ctx* ctx, const double* pos, int ptr_kind);
  *   Either pointer may be host or device memory (detected per call).
  *   sigma:       cross-section model.
  *   seed:        Philox key; the context's step counter (starts at 0, +1 per
- *                successful call) is Philox counter word 0.
+ *                successful call), modulo 2^32, is Philox counter word 0.
  *   stats:       NULL, or receives the step statistics (waits for the step).
  * The step reads start-of-step velocities for every probability and
  * applies the accepted kicks in (ord, min id, max id) order. */
@@ -265,7 +318,8 @@ SIDM_API int sidm_get_pairs(sidm_ctx* ctx, uint32_t* ab, uint64_t* ord, int64_t 
 
 /* Step counter (resume support: the random stream is a pure function of
  * (seed, step counter, ids), so restoring the particles and the counter
- * reproduces a run bit for bit). */
+ * reproduces a run bit for bit).  The draws use the counter modulo 2^32:
+ * steps 2^32 apart share their random streams. */
 SIDM_API int sidm_get_step(const sidm_ctx* ctx, uint64_t* step);
 SIDM_API int sidm_set_step(sidm_ctx* ctx, uint64_t step);
 
@@ -373,12 +427,18 @@ SIDM_API int sidm_graph_state(const sidm_ctx* ctx);
  *   vel     n x 3 FP64 velocities, updated in place; mass: n FP64 masses;
  *   seed, step: the Philox key and the step counter of the draw;
  *   stream: cudaStream_t (NULL: the legacy default stream).
+ * Records with equal (ord, a, b) keys are applied one after the other, in
+ * the order given.  The step counter enters the random counter modulo 2^32
+ * (as in sidm_step).
  * Returns SIDM_OK (or SIDM_WARN_DIRECTION); SIDM_ERR_TOO_LARGE for
  * n > SIDM_NOALLOC_MAX_PARTICLES or n_pairs > SIDM_NOALLOC_MAX_PAIRS;
  * SIDM_ERR_INVALID_ARG for NULL pointers, negative sizes, or a pair whose
  * index lies outside [0, n) or names one particle twice (checked on the
- * device; then no velocity is changed); SIDM_ERR_CUDA on a CUDA failure.
- * The call waits for the stream before it returns.
+ * device; then no velocity is changed); SIDM_ERR_DEVICE_LIMIT when the
+ * pairs form a dependency chain longer than the 4096 rounds of the kick
+ * kernel (for instance one particle in more than 4096 pairs): the kicks of
+ * the completed rounds are then already in vel; SIDM_ERR_CUDA on a CUDA
+ * failure.  The call waits for the stream before it returns.
  *
  * Set-up: the first call on each device looks up the device address of the
  * scratch array (with that device current); make that first call before

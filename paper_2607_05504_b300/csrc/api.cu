@@ -105,6 +105,9 @@ struct sidm_ctx {
   // key order kept between full rebuilds
   uint64_t order_version = 0;   // layout of the last full rebuild
   int64_t since_rebuild = 0;    // steps since it
+  // sizing only (sidm_context_bytes): dalloc counts bytes and allocates nothing
+  bool dry_run = false;
+  int64_t dry_bytes = 0;
   // instrumentation
   int64_t launches = 0;
   cudaEvent_t ev[SIDM_N_PHASES + 1] = {};
@@ -138,10 +141,34 @@ struct DeviceGuard {
   }
 };
 
+// Device memory of the context: the caller's allocator when the config
+// names one (e.g. a caching allocator of the host framework), else
+// cudaMalloc.  Sizes are rounded up to 256 bytes.
+cudaError_t raw_alloc(sidm_ctx* c, void** p, size_t bytes) {
+  bytes = (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+  if (c->cfg.alloc) {
+    *p = c->cfg.alloc(bytes, (void*)c->stream, c->cfg.alloc_user);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+void raw_free(sidm_ctx* c, void* p) {
+  if (!p) return;
+  if (c->cfg.free) c->cfg.free(p, (void*)c->stream, c->cfg.alloc_user);
+  else cudaFree(p);
+}
+
 template <class T>
 cudaError_t dalloc(sidm_ctx* c, T** p, size_t count) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (c->dry_run) {
+    c->dry_bytes += (int64_t)((bytes + 255) & ~(size_t)255);
+    *p = nullptr;
+    return cudaSuccess;
+  }
   void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+  cudaError_t e = raw_alloc(c, &q, bytes);
   if (e != cudaSuccess) return e;
   c->allocs.push_back(q);
   *p = (T*)q;
@@ -168,7 +195,7 @@ cudaError_t join_velocities(sidm_ctx* c) {
 void free_buffers(sidm_ctx* c) {
   drop_graph(c);
   ++c->layout_version;
-  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->allocs) raw_free(c, p);
   c->allocs.clear();
   c->cap = 0;
   c->pair_cap = 0;
@@ -196,13 +223,14 @@ void fill(double* p, int64_t n, double v, cudaStream_t s) {
   if (n > 0) fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, v);
 }
 
-int ensure_capacity(sidm_ctx* c, int64_t n) {
-  int64_t want = std::max<int64_t>(n, c->cfg.n_max);
-  if (want <= c->cap && c->allocs.size()) return SIDM_OK;
-  CK(cudaStreamSynchronize(c->stream));
-  free_buffers(c);
-  want = std::max<int64_t>(want, 64);
-  const int64_t pc = c->cfg.pair_capacity > 0 ? c->cfg.pair_capacity : 2 * want + 4096;
+int64_t pair_capacity_for(const sidm_config& cfg, int64_t want) {
+  return cfg.pair_capacity > 0 ? cfg.pair_capacity : 2 * want + 4096;
+}
+
+// Every buffer sized by the particle capacity (dalloc only: with dry_run
+// set it just counts the bytes).
+int alloc_capacity(sidm_ctx* c, int64_t want) {
+  const int64_t pc = pair_capacity_for(c->cfg, want);
   CK(dalloc(c, &c->pos, 3 * want));
   CK(dalloc(c, &c->vel, 3 * want));
   CK(dalloc(c, &c->mass, want));
@@ -264,6 +292,19 @@ int ensure_capacity(sidm_ctx* c, int64_t n) {
   CK(dalloc(c, &c->chg_idx, want));
   CK(dalloc(c, &c->chg_vel, 3 * want));
   CK(dalloc(c, &c->chg_count, 1));
+  return SIDM_OK;
+}
+
+int ensure_capacity(sidm_ctx* c, int64_t n) {
+  int64_t want = std::max<int64_t>(n, c->cfg.n_max);
+  if (want <= c->cap && c->allocs.size()) return SIDM_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  free_buffers(c);
+  want = std::max<int64_t>(want, 64);
+  const int64_t pc = pair_capacity_for(c->cfg, want);
+  const int ra = alloc_capacity(c, want);
+  if (ra != SIDM_OK) return ra;
+  ResolveBuffers& rb = c->rb;
   CK(cudaMemsetAsync(c->chg_stamps, 0, want * sizeof(uint32_t), c->stream));
   CK(cudaMemsetAsync(rb.mult, 0, want * sizeof(int32_t), c->stream));
   CK(cudaMemsetAsync(rb.seg_off, 0xFF, want * sizeof(int32_t), c->stream));
@@ -284,7 +325,7 @@ cudaError_t grow(sidm_ctx* c, T** p, int64_t* have, int64_t need) {
   if (*p) {
     auto it = std::find(c->allocs.begin(), c->allocs.end(), (void*)*p);
     if (it != c->allocs.end()) c->allocs.erase(it);
-    cudaFree(*p);
+    raw_free(c, *p);
     *p = nullptr;
   }
   return dalloc(c, p, (size_t)need);
@@ -652,7 +693,8 @@ int sidm_create(const sidm_config* cfg, sidm_ctx** out) {
       (cfg->precision != SIDM_FP64_PLAIN && cfg->precision != SIDM_FP32_SPLIT) ||
       !(cfg->fixed_h >= 0.0) || cfg->n_max < 0 ||
       cfg->pair_capacity < 0 || cfg->rebuild_every < 0 || cfg->max_resolver_passes < 0 ||
-      (cfg->estimator != SIDM_ESTIMATOR_ONE_SIDED && cfg->estimator != SIDM_ESTIMATOR_OVERLAP))
+      (cfg->estimator != SIDM_ESTIMATOR_ONE_SIDED && cfg->estimator != SIDM_ESTIMATOR_OVERLAP) ||
+      (!cfg->alloc) != (!cfg->free))
     return SIDM_ERR_INVALID_ARG;
   sidm_ctx* c = new (std::nothrow) sidm_ctx();
   if (!c) return SIDM_ERR_OOM;
@@ -801,6 +843,89 @@ int sidm_set_velocities(sidm_ctx* c, const double* vel, int ptr_kind) {
     CK(cudaEventRecord(c->ev_vdone, c->vstream));
     c->vel_pending = true;
   }
+  return SIDM_OK;
+}
+
+int sidm_write_particles(sidm_ctx* c, int64_t offset, int64_t count, const double* pos,
+                         const double* vel, const double* mass, double mass_scalar,
+                         const uint32_t* ids, int ptr_kind) {
+  if (!c || !c->loaded || offset < 0 || count < 0 || offset > c->n ||
+      offset + count > c->cap || (count > 0 && (!pos || !vel || !ids)) ||
+      (ptr_kind != SIDM_HOST && ptr_kind != SIDM_DEVICE) || (!mass && !(mass_scalar > 0.0)))
+    return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  CK(join_velocities(c));
+  if (count == 0) return SIDM_OK;
+  const cudaMemcpyKind k = copy_kind_in(ptr_kind);
+  cudaStream_t s = c->stream;
+  CK(cudaMemcpyAsync(c->pos + 3 * offset, pos, 3 * count * sizeof(double), k, s));
+  CK(cudaMemcpyAsync(c->vel + 3 * offset, vel, 3 * count * sizeof(double), k, s));
+  CK(cudaMemcpyAsync(c->ids + offset, ids, count * sizeof(uint32_t), k, s));
+  if (mass) CK(cudaMemcpyAsync(c->mass + offset, mass, count * sizeof(double), k, s));
+  else fill(c->mass + offset, count, mass_scalar, s);
+  fill(c->h_user + offset, count, 0.0, s);
+  fill(c->dtlim + offset, count, INFINITY, s);
+  c->stepped = false;
+  if (offset + count > c->n) {
+    // the loaded set grows: one halo over all particles until sidm_set_haloes
+    const int64_t n = offset + count;
+    const int64_t off[2] = {0, n};
+    c->n = n;
+    const int r = layout_haloes(c, 1, off);
+    if (r != SIDM_OK) return r;
+  }
+  if (c->cfg.box > 0.0) {
+    const int r = check_in_box(c);
+    if (r != SIDM_OK) return r;
+  }
+  CK(cudaGetLastError());
+  return SIDM_OK;
+}
+
+int sidm_set_count(sidm_ctx* c, int64_t n) {
+  if (!c || !c->loaded || n < 0 || n > c->n) return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  CK(join_velocities(c));
+  if (n == c->n) return SIDM_OK;
+  c->n = n;
+  c->stepped = false;
+  const int64_t off[2] = {0, n};
+  return layout_haloes(c, 1, off);
+}
+
+int sidm_read_particles(sidm_ctx* c, int64_t offset, int64_t count, double* vel_out,
+                        double* h_out, int ptr_kind) {
+  if (!c || !c->loaded || offset < 0 || count < 0 || offset + count > c->n ||
+      (count > 0 && !vel_out && !h_out) || (ptr_kind != SIDM_HOST && ptr_kind != SIDM_DEVICE))
+    return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  CK(join_velocities(c));
+  const cudaMemcpyKind k = copy_kind_out(ptr_kind);
+  if (count > 0) {
+    if (vel_out)
+      CK(cudaMemcpyAsync(vel_out, c->vel + 3 * offset, 3 * count * sizeof(double), k, c->stream));
+    if (h_out)
+      CK(cudaMemcpyAsync(h_out, c->h_user + offset, count * sizeof(double), k, c->stream));
+  }
+  return wait_and_collect(c);
+}
+
+int sidm_context_bytes(const sidm_config* cfg, int64_t n, int64_t* bytes) {
+  if (!cfg || !bytes || n < 0 || n >= (int64_t)1 << 30 || cfg->n_ngb < 1 || cfg->ngb_tol < 0)
+    return SIDM_ERR_INVALID_ARG;
+  sidm_ctx d;
+  d.cfg = *cfg;
+  d.dry_run = true;
+  d.nb_stride = cfg->n_ngb + cfg->ngb_tol;
+  const int64_t want = std::max<int64_t>(n, 64);
+  alloc_capacity(&d, want);
+  // the box tree of one halo of n particles (float4 lower and upper corners)
+  int64_t cnt[MAX_LEVELS] = {};
+  const int levels = tree_levels_for(want, cnt);
+  int64_t nodes = 0;
+  for (int l = 0; l < levels; ++l) nodes += cnt[l];
+  d.dry_bytes += 2 * (((std::max<int64_t>(nodes, 1) * (int64_t)sizeof(float4)) + 255) & ~255ll);
+  *bytes = d.dry_bytes;
   return SIDM_OK;
 }
 
@@ -995,11 +1120,11 @@ int sidm_set_overlap_table(sidm_ctx* c, int32_t na, int32_t ns, const double* t)
     hf[k] = y;
   }
   CK(cudaStreamSynchronize(c->stream));
-  if (c->ov_mem) cudaFree(c->ov_mem);
+  if (c->ov_mem) raw_free(c, c->ov_mem);
   c->ov_mem = nullptr;
   c->ov = OverlapTable{};
   void* d = nullptr;
-  CK(cudaMalloc(&d, host.size()));
+  CK(raw_alloc(c, &d, host.size()));
   c->ov_mem = d;
   CK(cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice));
   c->ov.na = na;
@@ -1046,11 +1171,11 @@ int sidm_set_sigma_table(sidm_ctx* c, int32_t n, const double* v, const double* 
     f[3 * n + k] = ru(sg[k]);
   }
   CK(cudaStreamSynchronize(c->stream));
-  if (c->table_mem) cudaFree(c->table_mem);
+  if (c->table_mem) raw_free(c, c->table_mem);
   c->table_mem = nullptr;
   c->table = SigmaTable{};
   void* d = nullptr;
-  CK(cudaMalloc(&d, host.size()));
+  CK(raw_alloc(c, &d, host.size()));
   c->table_mem = d;
   CK(cudaMemcpy(d, host.data(), host.size(), cudaMemcpyHostToDevice));
   SigmaTable& T = c->table;
@@ -1107,7 +1232,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
                     params[k].step);
   // the state the candidates start from, and restore at the end
   double* save = nullptr;
-  CK(cudaMalloc(&save, 5 * n * sizeof(double)));
+  CK(raw_alloc(c, (void**)&save, 5 * n * sizeof(double)));
   double *v0 = save, *h0 = save + 3 * n, *d0 = save + 4 * n;
   const uint64_t step0 = c->step;
   const int64_t since0 = c->since_rebuild;
@@ -1164,7 +1289,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
   c->order_version = order0;
   c->stepped = false;   // the pair buffer holds a trial step's pairs
   const int st = wait_and_collect(c);
-  cudaFree(save);
+  raw_free(c, save);
   if (rc != SIDM_OK) return rc;
   if (st < 0) return st;
   if (best) to_public(cur, best);
@@ -1326,8 +1451,8 @@ void sidm_destroy(sidm_ctx* c) {
     if (c->h_chg_count) cudaFreeHost(c->h_chg_count);
     if (c->h_chg_idx) cudaFreeHost(c->h_chg_idx);
     if (c->h_chg_vel) cudaFreeHost(c->h_chg_vel);
-    if (c->table_mem) cudaFree(c->table_mem);
-    if (c->ov_mem) cudaFree(c->ov_mem);
+    if (c->table_mem) raw_free(c, c->table_mem);
+    if (c->ov_mem) raw_free(c, c->ov_mem);
     for (int k = 0; k <= SIDM_N_PHASES; ++k)
       if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -40,13 +40,19 @@ class SidmError(RuntimeError):
         self.status = status
 
 
+# allocator hooks of sidm_config: alloc(bytes, stream, user) -> ptr, free(ptr, stream, user)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
 class Config(C.Structure):
     _fields_ = [("n_ngb", C.c_int), ("ngb_tol", C.c_int), ("c_sidm", C.c_double),
                 ("box", C.c_double), ("kernel", C.c_int), ("precision", C.c_int),
                 ("fixed_h", C.c_double), ("n_max", C.c_int64), ("pair_capacity", C.c_int64),
                 ("stream", C.c_void_p), ("device", C.c_int), ("profile", C.c_int),
                 ("use_graph", C.c_int), ("estimator", C.c_int), ("rebuild_every", C.c_int),
-                ("max_resolver_passes", C.c_int)]
+                ("max_resolver_passes", C.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_user", C.c_void_p)]
 
 
 class Tuning(C.Structure):
@@ -91,7 +97,9 @@ ENTRY_POINTS = ("sidm_default_config", "sidm_create", "sidm_set_particles",
                 "sidm_phase_times", "sidm_kernel_launches", "sidm_error_string", "sidm_destroy",
                 "sidm_apply_pairs_noalloc", "sidm_set_haloes", "sidm_step_haloes",
                 "sidm_set_tuning", "sidm_get_tuning", "sidm_autotune", "sidm_graph_state",
-                "sidm_set_sigma_table", "sidm_set_overlap_table", "sidm_overlap_table")
+                "sidm_set_sigma_table", "sidm_set_overlap_table", "sidm_overlap_table",
+                "sidm_write_particles", "sidm_set_count", "sidm_read_particles",
+                "sidm_context_bytes")
 
 N_PHASES = 6
 PHASES = ("keys", "sort", "structure", "search", "pairs", "resolve")
@@ -151,6 +159,10 @@ def lib():
         L.sidm_set_sigma_table.argtypes = [vp, C.c_int32, vp, vp]
         L.sidm_set_overlap_table.argtypes = [vp, C.c_int32, C.c_int32, vp]
         L.sidm_overlap_table.argtypes = [C.c_int, C.c_int32, C.c_int32, vp]
+        L.sidm_write_particles.argtypes = [vp, i64, i64, vp, vp, vp, dp, vp, C.c_int]
+        L.sidm_set_count.argtypes = [vp, i64]
+        L.sidm_read_particles.argtypes = [vp, i64, i64, vp, vp, C.c_int]
+        L.sidm_context_bytes.argtypes = [C.POINTER(Config), i64, C.POINTER(i64)]
         for name in ENTRY_POINTS:
             fn = getattr(L, name)
             if name not in ("sidm_default_config", "sidm_error_string", "sidm_destroy"):
@@ -215,6 +227,49 @@ def sidm_set_velocities(ctx, vel) -> int:
 def sidm_set_positions(ctx, pos) -> int:
     p, kind = _ptr(pos)
     return _check(lib().sidm_set_positions(ctx, p, kind), "sidm_set_positions")
+
+
+def sidm_write_particles(ctx, offset, pos, vel, mass, mass_scalar, ids) -> int:
+    n = int(pos.shape[0])
+    pp, kind = _ptr(pos)
+    return _check(lib().sidm_write_particles(ctx, int(offset), n, pp, _ptr(vel)[0], _ptr(mass)[0],
+                                             float(mass_scalar), _ptr(ids)[0], kind),
+                  "sidm_write_particles")
+
+
+def sidm_set_count(ctx, n) -> int:
+    return _check(lib().sidm_set_count(ctx, int(n)), "sidm_set_count")
+
+
+def sidm_read_particles(ctx, offset, count, vel_out, h_out=None) -> int:
+    p, kind = _ptr(vel_out if vel_out is not None else h_out)
+    return _check(lib().sidm_read_particles(ctx, int(offset), int(count), _ptr(vel_out)[0],
+                                            _ptr(h_out)[0], kind), "sidm_read_particles")
+
+
+def sidm_context_bytes(cfg: Config, n) -> int:
+    b = C.c_int64(0)
+    _check(lib().sidm_context_bytes(C.byref(cfg), int(n), C.byref(b)), "sidm_context_bytes")
+    return b.value
+
+
+def torch_allocator(device: int):
+    """(alloc, free) hooks that take the context's device memory from
+    PyTorch's caching allocator on `device` (kept alive by the caller)."""
+    import torch
+
+    @ALLOC_FN
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+        except Exception:
+            return None
+
+    @FREE_FN
+    def _free(ptr, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return _alloc, _free
 
 
 def sidm_step(ctx, active_mask, dt_bins, dt_max, sigma: SigmaModel, seed, stats=None) -> int:
@@ -368,7 +423,9 @@ class Context:
     def __init__(self, n_ngb=32, ngb_tol=5, c_sidm=0.1, box=0.0, kernel=KERNEL_CUBIC,
                  fixed_h=0.0, n_max=0, pair_capacity=0, stream=None, device=-1, profile=False,
                  precision=FP64_PLAIN, use_graph=False, rebuild_every=0,
-                 estimator=ESTIMATOR_ONE_SIDED, max_resolver_passes=0):
+                 estimator=ESTIMATOR_ONE_SIDED, max_resolver_passes=0, allocator=None):
+        """allocator: None (the library's cudaMalloc) or "torch" (PyTorch's
+        caching allocator on the context's device)."""
         cfg = sidm_default_config()
         cfg.n_ngb, cfg.ngb_tol, cfg.c_sidm, cfg.box = int(n_ngb), int(ngb_tol), float(c_sidm), float(box)
         cfg.kernel, cfg.fixed_h, cfg.n_max = int(kernel), float(fixed_h), int(n_max)
@@ -381,6 +438,14 @@ class Context:
         cfg.rebuild_every = int(rebuild_every)
         cfg.estimator = int(estimator)
         cfg.max_resolver_passes = int(max_resolver_passes)
+        self._hooks = None
+        if allocator == "torch":
+            import torch
+            dev = int(device) if int(device) >= 0 else torch.cuda.current_device()
+            self._hooks = torch_allocator(dev)
+            cfg.alloc, cfg.free = self._hooks
+        elif allocator is not None:
+            raise ValueError(f"unknown allocator {allocator!r}")
         self.cfg = cfg
         self.handle = sidm_create(cfg)
         self.n = 0
@@ -411,6 +476,28 @@ class Context:
         self._keep = (pos, vel, ids, mass)
         sidm_set_particles(self.handle, pos, vel, mass, mass_scalar, ids)
         self.n = int(pos.shape[0])
+
+    def write_particles(self, offset, pos, vel, ids, mass=None, mass_scalar=0.0):
+        """Replaces particles [offset, offset + len(pos)) (growing the loaded
+        count when it reaches past it); the other particles are kept."""
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, np.float64)
+            vel = np.ascontiguousarray(vel, np.float64)
+            ids = np.ascontiguousarray(ids, np.uint32)
+            mass = None if mass is None else np.ascontiguousarray(mass, np.float64)
+        sidm_write_particles(self.handle, offset, pos, vel, mass, mass_scalar, ids)
+        self.n = max(self.n, int(offset) + int(pos.shape[0]))
+
+    def set_count(self, n):
+        sidm_set_count(self.handle, n)
+        self.n = int(n)
+
+    def read_velocities(self, offset, count, out=None):
+        """Velocities of particles [offset, offset + count) (numpy unless a
+        device tensor `out` is given)."""
+        v = np.empty((int(count), 3)) if out is None else out
+        sidm_read_particles(self.handle, offset, count, v)
+        return v
 
     def set_velocities(self, vel):
         if isinstance(vel, np.ndarray):
