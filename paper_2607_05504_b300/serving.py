@@ -2,24 +2,32 @@
 
 A request is one isolated halo (particles, power-of-two bins, dt_max,
 cross-section model, seed) to be advanced by n_steps scattering steps.
-Requests that arrive while others are on the GPU are admitted as soon as the
-device-memory budget allows; every tick runs ONE multi-halo scattering step
-(sidm_step_haloes) over all resident requests, each at its own step counter
-and active set, so their work overlaps on the device; finished requests
-retire and free their share of the budget.
+Requests that arrive while others are on the GPU are admitted as soon as a
+free segment of the device-resident particle range can hold them; every tick
+runs ONE multi-halo scattering step (sidm_step_haloes) over all resident
+requests, each at its own step counter and active set, so their work
+overlaps on the device; finished requests retire and free their segment.
 
 Because every halo of a batch is stepped exactly as it would be alone (its
 own tree, start radius, random key and step counter -- see sidm.h), a
 request's result does not depend on what else is resident.
 
 Layers:
-  Scheduler  host logic only (queue, FIFO admission under the budget,
-             retirement); no device access.
-  GpuEngine  device state: each resident request's arrays as device tensors,
-             packed into one library context whenever the resident set
-             changes; the active mask of a tick is formed on the device.
-  Server     the loop: arrivals -> admission -> one step of all resident
-             haloes -> retirement, with per-request latency.
+  SegmentMap  host logic: the context's particle range [0, capacity) as
+              segments, each a resident request or a hole; first-fit
+              placement, holes merged, the unused tail trimmed.
+  Scheduler   host logic only (FIFO queue, admission into free segments,
+              retirement); no device access.
+  GpuEngine   device state: ONE library context sized once for the memory
+              budget.  Admission writes only the new request's particles
+              into its segment (sidm_write_particles); retirement reads only
+              the finished request's velocities (sidm_read_particles); the
+              resident haloes never move.  The active mask of a tick is
+              formed on the device from per-particle admission ticks and bin
+              periods; the tick's update count is known on the host from each
+              request's bin histogram, so a tick needs no device round trip.
+  Server      the loop: arrivals -> admission -> one step of all resident
+              haloes -> retirement, with per-request latency.
 """
 from __future__ import annotations
 
@@ -51,6 +59,7 @@ class Request:
     admitted: float | None = None
     finished: float | None = None
     result_vel: np.ndarray | None = None
+    segment: int | None = None        # first particle of the request's segment
 
     @property
     def n(self) -> int:
@@ -60,32 +69,104 @@ class Request:
     def latency(self) -> float | None:
         return None if self.finished is None else self.finished - self.arrival
 
+    def active_count(self, s: int) -> int:
+        """Active particles at the request's step s (host arithmetic on its
+        bin histogram: bin b is active every 2^(bmax - b) steps)."""
+        if self.n == 0:
+            return 0
+        hist = getattr(self, "_hist", None)
+        if hist is None:
+            hist = np.bincount(self.bins.astype(np.int64))
+            self._hist = hist
+        bmax = hist.shape[0] - 1
+        return int(sum(int(c) for b, c in enumerate(hist) if c and s % (1 << (bmax - b)) == 0))
+
+
+class SegmentMap:
+    """The particle range [0, capacity) of one context as contiguous
+    segments: resident requests (owner = request id) and holes (owner None).
+    `end` is the used extent; segments cover [0, end) exactly."""
+
+    def __init__(self, capacity: int):
+        self.capacity = int(capacity)
+        self.segs: list[list] = []        # [start, n, owner], sorted by start
+        self.end = 0
+
+    def place(self, n: int, owner) -> int | None:
+        """First fit: the lowest hole that holds n particles, else the tail;
+        None if neither can."""
+        for k, (st, m, own) in enumerate(self.segs):
+            if own is None and m >= n:
+                if m > n:
+                    self.segs.insert(k + 1, [st + n, m - n, None])
+                self.segs[k] = [st, n, owner]
+                return st
+        if self.end + n <= self.capacity:
+            st = self.end
+            self.segs.append([st, n, owner])
+            self.end += n
+            return st
+        return None
+
+    def release(self, start: int) -> None:
+        """Turns the segment at `start` into a hole, merges it with hole
+        neighbours and trims a hole at the end of the used range."""
+        k = next(i for i, s in enumerate(self.segs) if s[0] == start)
+        self.segs[k][2] = None
+        if k + 1 < len(self.segs) and self.segs[k + 1][2] is None:
+            self.segs[k][1] += self.segs[k + 1][1]
+            del self.segs[k + 1]
+        if k > 0 and self.segs[k - 1][2] is None:
+            self.segs[k - 1][1] += self.segs[k][1]
+            del self.segs[k]
+        while self.segs and self.segs[-1][2] is None:
+            self.end -= self.segs[-1][1]
+            self.segs.pop()
+
+    def offsets(self) -> np.ndarray:
+        off = np.zeros(len(self.segs) + 1, np.int64)
+        off[1:] = np.cumsum([s[1] for s in self.segs]) if self.segs else []
+        return off
+
+    @property
+    def free(self) -> int:
+        return self.capacity - sum(s[1] for s in self.segs if s[2] is not None)
+
 
 class Scheduler:
-    """FIFO admission under a device-memory budget (bytes)."""
+    """FIFO admission into free segments of a particle range sized by the
+    device-memory budget (bytes) at `bytes_per_particle`."""
 
     def __init__(self, budget_bytes: float, bytes_per_particle: float):
         self.budget = float(budget_bytes)
         self.per_particle = float(bytes_per_particle)
+        self.map = SegmentMap(int(self.budget // self.per_particle))
         self.queue: collections.deque[Request] = collections.deque()
         self.resident: list[Request] = []
-        self.used = 0.0
 
     def cost(self, r: Request) -> float:
         return r.n * self.per_particle
 
+    @property
+    def used(self) -> float:
+        return sum(self.cost(r) for r in self.resident)
+
     def submit(self, r: Request) -> None:
-        if self.cost(r) > self.budget:
+        if r.n > self.map.capacity:
             raise ValueError(f"request {r.rid} needs {self.cost(r):.3g} B > budget {self.budget:.3g} B")
         self.queue.append(r)
 
     def admit(self, now: float) -> list[Request]:
-        """Admits queued requests in arrival order while they fit."""
+        """Admits queued requests in arrival order while each finds a segment."""
         new = []
-        while self.queue and self.used + self.cost(self.queue[0]) <= self.budget:
-            r = self.queue.popleft()
+        while self.queue:
+            r = self.queue[0]
+            st = self.map.place(r.n, r.rid)
+            if st is None:
+                break
+            self.queue.popleft()
+            r.segment = st
             r.admitted = now
-            self.used += self.cost(r)
             self.resident.append(r)
             new.append(r)
         return new
@@ -94,9 +175,15 @@ class Scheduler:
         done = [r for r in self.resident if r.steps_done >= r.n_steps]
         for r in done:
             r.finished = now
-            self.used -= self.cost(r)
+            self.map.release(r.segment)
         self.resident = [r for r in self.resident if r.steps_done < r.n_steps]
         return done
+
+    def layout(self) -> list:
+        """Segments of the used range: (start, n, request or None)."""
+        by_id = {r.rid: r for r in self.resident}
+        return [(st, m, by_id.get(own) if own is not None else None)
+                for st, m, own in self.map.segs]
 
     @property
     def idle(self) -> bool:
@@ -104,95 +191,104 @@ class Scheduler:
 
 
 class GpuEngine:
-    """Device side: one library context over the resident requests."""
+    """Device side: one library context over the whole budget, resident
+    requests in fixed segments."""
 
-    def __init__(self, capacity: int, n_ngb: int = 64, device: int = 0, stream=None):
+    HOLE_PERIOD = 1 << 62             # a hole particle is never active
+
+    def __init__(self, budget_bytes: float, n_ngb: int = 64, device: int = 0, stream=None,
+                 run_ahead: int = 2):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.Stream(self.dev)
-        self.ctx = sidm.Context(n_ngb=n_ngb, box=0.0, n_max=max(int(capacity), 64),
+        cfg = sidm.sidm_default_config()
+        cfg.n_ngb = n_ngb
+        self.bytes_per_particle = sidm.sidm_context_bytes(cfg, 1 << 20) / float(1 << 20)
+        self.capacity = max(int(budget_bytes // self.bytes_per_particle), 64)
+        self.ctx = sidm.Context(n_ngb=n_ngb, box=0.0, n_max=self.capacity, use_graph=True,
                                 stream=self.stream.cuda_stream, device=device)
-        self.resident: list[Request] = []
-        self.dev_state: dict[int, dict] = {}
-        self.off = np.zeros(1, np.int64)
-
-    def _upload(self, r: Request) -> dict:
-        t = self.torch
-        p = r.particles
+        z = np.zeros((0, 3))
+        self.ctx.set_particles(z, z, np.zeros(0, np.uint32), mass_scalar=1.0)
+        t = torch
         with t.cuda.stream(self.stream):
-            return {"pos": t.from_numpy(p.pos).to(self.dev), "vel": t.from_numpy(p.vel).to(self.dev),
-                    "mass": t.from_numpy(p.mass).to(self.dev),
-                    "ids": t.from_numpy(p.ids.view(np.int32)).to(self.dev),
-                    "bins": t.from_numpy(r.bins.astype(np.int8)).to(self.dev),
-                    "bmax": int(r.bins.max()) if r.n else 0}
+            self.bins = t.zeros(self.capacity, dtype=t.int8, device=self.dev)
+            self.period = t.full((self.capacity,), self.HOLE_PERIOD, dtype=t.int64, device=self.dev)
+            self.t0 = t.full((self.capacity,), -1, dtype=t.int64, device=self.dev)
+        self.tick = 0
+        self.layout: list = []
+        self.params: list = []
+        self.run_ahead = run_ahead
+        self.events: collections.deque = collections.deque()
 
-    def _save_velocities(self) -> None:
-        """Current velocities of the resident requests back into their tensors."""
-        if not self.resident or self.off[-1] == 0:
-            return
+    def admit(self, reqs: list[Request], layout: list) -> None:
+        """Writes each new request into its segment (nothing else moves)."""
         t = self.torch
-        v = t.empty((int(self.off[-1]), 3), dtype=t.float64, device=self.dev)
-        sidm.sidm_get_particles(self.ctx.handle, v)
-        with t.cuda.stream(self.stream):
-            for k, r in enumerate(self.resident):
-                self.dev_state[r.rid]["vel"].copy_(v[self.off[k]:self.off[k + 1]])
-
-    def set_resident(self, reqs: list[Request]) -> None:
-        t = self.torch
-        self._save_velocities()
         for r in reqs:
-            if r.rid not in self.dev_state:
-                self.dev_state[r.rid] = self._upload(r)
-        for rid in [rid for rid in self.dev_state if rid not in {r.rid for r in reqs}]:
-            del self.dev_state[rid]
-        self.resident = list(reqs)
-        sizes = [r.n for r in reqs]
-        self.off = np.zeros(len(reqs) + 1, np.int64)
-        self.off[1:] = np.cumsum(sizes)
-        if not reqs:
-            return
-        S = [self.dev_state[r.rid] for r in reqs]
-        with t.cuda.stream(self.stream):
-            self.pos = t.cat([s["pos"] for s in S])
-            self.vel = t.cat([s["vel"] for s in S])
-            self.mass = t.cat([s["mass"] for s in S])
-            self.ids = t.cat([s["ids"] for s in S])
-            self.bins = t.cat([s["bins"] for s in S])
-            sz = t.tensor(sizes, device=self.dev)
-            self.bmax_p = t.repeat_interleave(t.tensor([s["bmax"] for s in S], device=self.dev), sz)
-            self.steps_p = t.repeat_interleave(
-                t.tensor([r.steps_done for r in reqs], dtype=t.int64, device=self.dev), sz)
-            self.period_p = t.bitwise_left_shift(t.ones_like(self.bmax_p),
-                                                 self.bmax_p - self.bins.to(t.int64))
-        self.ctx.set_particles(self.pos, self.vel, self.ids, mass=self.mass)
-        self.ctx.set_haloes(self.off)
+            p, st = r.particles, r.segment
+            self.ctx.write_particles(st, p.pos, p.vel, p.ids, mass=p.mass)
+            bmax = int(r.bins.max()) if r.n else 0
+            with t.cuda.stream(self.stream):
+                b = t.from_numpy(r.bins.astype(np.int8)).to(self.dev, non_blocking=False)
+                self.bins[st:st + r.n].copy_(b)
+                self.period[st:st + r.n] = t.bitwise_left_shift(
+                    t.ones(r.n, dtype=t.int64, device=self.dev), bmax - b.to(t.int64))
+                self.t0[st:st + r.n] = self.tick
+        self.relayout(layout)
+
+    def relayout(self, layout: list) -> None:
+        """Haloes of the context = the segments (holes are haloes whose
+        particles are never active)."""
+        t = self.torch
+        self.layout = layout
+        end = layout[-1][0] + layout[-1][1] if layout else 0
+        if end < self.ctx.n:
+            self.ctx.set_count(end)
+        for st, m, r in layout:
+            if r is None:
+                with t.cuda.stream(self.stream):
+                    self.period[st:st + m] = self.HOLE_PERIOD
+                    self.t0[st:st + m] = -1
+        if end > 0:
+            off = np.zeros(len(layout) + 1, np.int64)
+            off[1:] = np.cumsum([m for _, m, _ in layout])
+            self.ctx.set_haloes(off)
+        hole = sidm.HaloParams(1.0, sidm.SigmaModel(sidm.SIGMA_CONST, 0.0, 1.0, 0.0), 0, 0)
+        self.params = [hole if r is None else
+                       sidm.HaloParams(r.dt_max, sidm.SigmaModel(r.sigma_kind, r.sigma0, r.w, 0.0),
+                                       r.seed, 0) for _, _, r in layout]
 
     def step(self) -> int:
         """One scattering step of every resident request; returns the number
-        of active particles (particle updates) of the tick."""
+        of active particles (particle updates) of the tick, counted on the host."""
         t = self.torch
-        if not self.resident:
+        if not self.layout:
             return 0
+        end = self.ctx.n
+        n_active = 0
+        for k, (_, _, r) in enumerate(self.layout):
+            if r is not None:
+                self.params[k].step = r.steps_done
+                n_active += r.active_count(r.steps_done)
+        while len(self.events) >= self.run_ahead:     # bound the host's lead
+            self.events.popleft().synchronize()
         with t.cuda.stream(self.stream):
-            active = (t.remainder(self.steps_p, self.period_p) == 0).to(t.uint8)
-            n_active = int(active.sum().item())
-        params = [sidm.HaloParams(r.dt_max, sidm.SigmaModel(r.sigma_kind, r.sigma0, r.w),
-                                  r.seed, r.steps_done) for r in self.resident]
-        sidm.sidm_step_haloes(self.ctx.handle, active, self.bins, params, None)
-        with t.cuda.stream(self.stream):
-            self.steps_p += 1
-        for r in self.resident:
-            r.steps_done += 1
+            active = (t.remainder(self.tick - self.t0[:end], self.period[:end]) == 0).to(t.uint8)
+        sidm.sidm_step_haloes(self.ctx.handle, active, self.bins[:end], self.params, None)
+        ev = t.cuda.Event()
+        ev.record(self.stream)
+        self.events.append(ev)
+        self.tick += 1
+        for _, _, r in self.layout:
+            if r is not None:
+                r.steps_done += 1
         return n_active
 
     def collect(self, done: list[Request]) -> None:
-        """Copies the final velocities of finished requests to the host."""
-        if not done:
-            return
-        self._save_velocities()
+        """Copies the final velocities of finished requests to the host
+        (their segments only)."""
         for r in done:
-            r.result_vel = self.dev_state[r.rid]["vel"].cpu().numpy()
+            r.result_vel = self.ctx.read_velocities(r.segment, r.n)
 
     def sync(self) -> int:
         return self.ctx.sync()
@@ -240,14 +336,14 @@ class Server:
                 continue
             new = self.sched.admit(now)
             if new:
-                self.engine.set_resident(self.sched.resident)
+                self.engine.admit(new, self.sched.layout())
             rep.updates += self.engine.step()
             rep.ticks += 1
             done = [r for r in self.sched.resident if r.steps_done >= r.n_steps]
             if done:
                 self.engine.collect(done)
                 self.sched.retire(self.clock() - t0)
-                self.engine.set_resident(self.sched.resident)
+                self.engine.relayout(self.sched.layout())
         self.engine.sync()
         rep.wall = self.clock() - t0
         rep.latencies = [r.latency for r in requests if r.latency is not None]
@@ -255,25 +351,31 @@ class Server:
 
 
 def request_stream(n_req: int, rate: float, seed: int = 3, log2_n=(12.0, 21.0),
-                   steps=(10, 1000), pool: int = 16, n_ngb: int = 64) -> list[Request]:
+                   steps=(10, 1000), pool: int = 0, n_ngb: int = 64) -> list[Request]:
     """Poisson arrivals (rate per second) of halo requests: N log-uniform in
     2^[log2_n], Hernquist or NFW with p = 1/2, constant or Yukawa-like sigma
     with p = 1/2, sigma0/m log-uniform in [0.1, 10], steps log-uniform in
-    [steps].  Particle sets come from a pool of `pool` generated haloes per
-    profile (each request has its own seed, cross-section and step count)."""
+    [steps].  pool = 0: every request is its own halo (its own size and
+    seed); pool > 0: sizes are quantised to `pool` log-spaced values and the
+    particle sets of equal size and profile are shared (faster to generate;
+    each request still has its own seed, cross-section and step count)."""
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
     sizes = np.round(2.0 ** rng.uniform(log2_n[0], log2_n[1], n_req)).astype(np.int64)
-    # quantise sizes to the pool (log-spaced) so that haloes can be reused
-    grid = np.unique(np.round(np.geomspace(2 ** log2_n[0], 2 ** log2_n[1], pool)).astype(np.int64))
+    grid = (np.unique(np.round(np.geomspace(2 ** log2_n[0], 2 ** log2_n[1], pool)).astype(np.int64))
+            if pool > 0 else None)
     cache: dict = {}
     out = []
     for k in range(n_req):
-        nq = int(grid[np.argmin(np.abs(np.log(grid) - math.log(sizes[k])))])
+        if grid is not None:
+            nq = int(grid[np.argmin(np.abs(np.log(grid) - math.log(sizes[k])))])
+        else:
+            nq = int(sizes[k])
         prof = "hernquist" if rng.random() < 0.5 else "nfw"
-        key = (prof, nq)
+        key = (prof, nq) if grid is not None else (prof, nq, k)
         if key not in cache:
-            p = I.hernquist_halo(nq, 11 + nq) if prof == "hernquist" else I.nfw_halo(nq, 13 + nq)
+            hs = 11 + nq if grid is not None else 100003 * (k + 1) + seed
+            p = I.hernquist_halo(nq, hs) if prof == "hernquist" else I.nfw_halo(nq, hs + 2)
             dens = I.hernquist_density if prof == "hernquist" else I.nfw_density
             cache[key] = (p, dens)
         p, dens = cache[key]

@@ -36,12 +36,16 @@ def _alone(r: S.Request) -> np.ndarray:
 def test_each_request_is_the_same_alone_and_in_the_mix():
     reqs = S.request_stream(7, rate=60.0, seed=5, log2_n=(10.0, 13.5), steps=(3, 9), pool=4)
     biggest = max(r.n for r in reqs)
-    sched = S.Scheduler(budget_bytes=2.2 * biggest, bytes_per_particle=1.0)
-    eng = S.GpuEngine(capacity=int(2.2 * biggest) + 64)
+    probe = S.GpuEngine(budget_bytes=1e6)
+    bpp = probe.bytes_per_particle
+    probe.close()
+    eng = S.GpuEngine(budget_bytes=2.2 * biggest * bpp)
+    sched = S.Scheduler(budget_bytes=2.2 * biggest * bpp, bytes_per_particle=bpp)
     rep = S.Server(eng, sched, clock=FakeClock()).run(reqs)
     eng.close()
     assert rep.requests == 7 and len(rep.latencies) == 7
     assert any(r.admitted > r.arrival + 1e-9 for r in reqs)       # some waited for memory
+    assert rep.updates == sum(sum(r.active_count(s) for s in range(r.n_steps)) for r in reqs)
     for r in reqs:
         assert r.result_vel is not None and r.steps_done == r.n_steps
         v = _alone(r)

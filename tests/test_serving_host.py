@@ -1,6 +1,7 @@
 """Host logic of the continuous-batching service (no GPU): admission in
-arrival order under the memory budget, admission of waiting requests as
-memory frees up, retirement after n_steps, latency bookkeeping."""
+arrival order into free segments of the budget's particle range, admission
+of waiting requests as segments free up, retirement after n_steps, hole
+merging, latency bookkeeping."""
 import numpy as np
 import pytest
 
@@ -12,16 +13,28 @@ class FakeEngine:
     def __init__(self):
         self.resident_history = []
         self.steps = 0
+        self.layout = []
+        self.writes = []
 
-    def set_resident(self, reqs):
-        self.resident = list(reqs)
-        self.resident_history.append([r.rid for r in reqs])
+    def admit(self, reqs, layout):
+        self.writes += [(r.rid, r.segment, r.n) for r in reqs]
+        self.relayout(layout)
+
+    def relayout(self, layout):
+        self.layout = list(layout)
+        self.resident_history.append([r.rid for _, _, r in layout if r is not None])
+        # segments tile [0, end) in order
+        pos = 0
+        for st, m, _ in layout:
+            assert st == pos
+            pos += m
 
     def step(self):
         self.steps += 1
-        for r in self.resident:
+        res = [r for _, _, r in self.layout if r is not None]
+        for r in res:
             r.steps_done += 1
-        return sum(r.n for r in self.resident)
+        return sum(r.n for r in res)
 
     def collect(self, done):
         for r in done:
@@ -79,6 +92,46 @@ def test_server_serves_every_request_and_overlaps_them():
     assert rep.percentile(50) <= rep.percentile(99)
 
 
+def test_segment_map_first_fit_merge_and_trim():
+    m = S.SegmentMap(1000)
+    assert m.place(300, "a") == 0 and m.place(300, "b") == 300 and m.place(300, "c") == 600
+    assert m.place(200, "x") is None                     # 100 left at the tail
+    m.release(300)                                       # hole [300, 600) in the middle
+    assert m.end == 900 and m.free == 400
+    assert m.place(200, "d") == 300                      # first fit: into the hole
+    assert [s[2] for s in m.segs] == ["a", "d", None, "c"]
+    assert m.place(250, "e") is None                     # 100 + 100 apart: no fit
+    m.release(600)                                       # c: merges with the hole, then trimmed
+    assert m.end == 500 and [s[2] for s in m.segs] == ["a", "d"]
+    assert m.place(250, "e") == 500
+    m.release(0)
+    m.release(300)                                       # d: merges with a's hole on the left
+    assert [(s[0], s[1], s[2]) for s in m.segs] == [(0, 500, None), (500, 250, "e")]
+    assert list(m.offsets()) == [0, 500, 750]
+    m.release(500)
+    assert m.end == 0 and m.segs == [] and m.free == 1000
+
+
+def test_resident_requests_never_move():
+    reqs = [_req(0, 400, 2, 0.0), _req(1, 300, 6, 0.0), _req(2, 200, 3, 0.0),
+            _req(3, 350, 2, 0.05)]
+    eng = FakeEngine()
+    S.Server(eng, S.Scheduler(1000.0, 1.0), clock=FakeClock()).run(reqs)
+    # each request was written once, at its segment, and kept it while resident
+    assert sorted(w[0] for w in eng.writes) == [0, 1, 2, 3]
+    seg = {w[0]: w[1] for w in eng.writes}
+    assert seg[1] == 400                                 # behind request 0
+    assert seg[3] == 0                                   # into the hole request 0 left
+    assert all(r.result_vel is not None for r in reqs)
+
+
+def test_active_count_from_bins():
+    r = _req(0, 64, 5, 0.0)
+    r.bins = np.array([0] * 10 + [1] * 20 + [3] * 34, np.int8)
+    for s in range(9):
+        assert r.active_count(s) == int(I.active_at_step(r.bins, s).sum())
+
+
 def test_request_stream_recipe():
     rs = S.request_stream(40, rate=200.0, seed=3, log2_n=(10.0, 12.0), steps=(10, 1000), pool=4)
     arr = np.array([r.arrival for r in rs])
@@ -87,3 +140,5 @@ def test_request_stream_recipe():
     assert {r.sigma_kind for r in rs} == {0, 1}
     assert len({r.seed for r in rs}) == len(rs)
     assert all(2 ** 10 * 0.9 <= r.n <= 2 ** 12 * 1.1 for r in rs)
+    own = S.request_stream(6, rate=200.0, seed=4, log2_n=(10.0, 12.0), steps=(10, 20))
+    assert len({r.particles.pos[0, 0] for r in own}) == 6      # every request its own halo
