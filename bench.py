@@ -1,17 +1,29 @@
 """Benchmark of the SIDM scattering step on one B300 (or N independent replicas).
 
-Workload: isolated Hernquist halo, N = 2^20, N_ngb = 64 +- 5, constant
-sigma/m = 1, open boundaries, FP64, power-of-two timestep bins with ~10 % of
-the particles active per finest step (step s of a 100-step cycle uses the
-active set of finest step s).  One bench step = one complete scattering step
-(keys, sort, structure, h_SI search, pairs + draws + Eq. 18, kicks) on the
-step's active set.  Metric: particle updates (active particles) per second.
+Headline workload: isolated Hernquist halo, N = 2^20, N_ngb = 64 +- 5,
+constant sigma/m = 1, open boundaries, FP64, power-of-two timestep bins with
+~10 % of the particles active per finest step (step s of a 100-step cycle
+uses the active set of finest step s).  One bench step = one complete
+scattering step (keys, sort, structure, h_SI search, pairs + draws + Eq. 18,
+kicks) on the step's active set.  Metric: particle updates (active
+particles) per second.
 
-    python bench.py [--steps K] [--warmup W] [--impl ours|reference]
+The default run also measures, as sub-objects of its one JSON line:
+  c2_eq18_bins  the same halo with bins from its own Eq. 18 limits (no bin
+                clipped, so no pair reaches P = 1);
+  c3_precision  NFW 2^23 with the Yukawa-like cross-section: the FP32-split
+                form against the FP64 plain form, step by step;
+  c4_batch      512 Hernquist haloes of uneven size stepped together, against
+                the plain per-halo loop (graph-replayed too);
+  c5_serving    halo requests served with continuous batching: p50/p99
+                latency at the offered rate and at fractions of capacity.
+
+    python bench.py [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
 
 Under torchrun (N > 1) every rank runs its own halo replica on its own GPU
 (independent problems, no data-path collective): value = all ranks'
-updates / the slowest rank's time ("scaling": "weak").
+updates / the slowest rank's time ("scaling": "weak"); the sub-objects are
+measured at N = 1 only.
 """
 from __future__ import annotations
 
@@ -22,6 +34,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -33,21 +46,23 @@ METRIC = "SIDM particle-updates/s (search+scatter)"
 UNIT = "particle-updates/s"
 CYCLE = 100
 
-# Algorithmic HBM bytes of each phase, per particle (n) and per active
-# particle (a): the data the phase must read and write once (FP64 state,
-# 4-byte ids/indices, 1-byte flags).
-PHASE_BYTES = {
-    "keys": (56.0, 0.0),        # bbox read 24, keys read 24, key+index write 8
-    "sort": (68.0, 0.0),        # one histogram read 4 + 4 passes x (read 8 + write 8)
-    "structure": (190.0, 0.0),  # gather 66 read, key-order state 97 written, leaf boxes ~27
-    "search": (16.0, 56.0),     # FP32 positions once; own state 40 read, h 16 written
-    "pairs": (0.0, 92.0),       # own state 84 read, Eq. 18 limit 8 written
-    "resolve": (0.0, 0.0),      # per accepted pair, reported separately
-}
+# Algorithmic HBM bytes of the step (FP64 state; what the method must move
+# once), per particle (N) and per active particle (A):
+#   build (keys, sort, structure): 24 B position read, 12 B key + index
+#     written, 4 radix passes x 24 B, 2 x 60 B permutation, ~8 B cells
+#     = 260 B x N;
+#   neighbour search + pair/scatter kernels: own position and velocity read,
+#     h and the Eq. 18 limit written = 64 B x A, plus the neighbour data
+#     reached from HBM once, 48 B x N;
+#   kicks ~100 B per accepted pair (not counted).
+BUILD_BYTES_N = 260.0
+NEIGHBOUR_SCATTER_BYTES = (48.0, 64.0)      # (per N, per A)
+STEP_BYTES = (BUILD_BYTES_N + 48.0, 64.0)   # 308 B x N + 64 B x A
 
-
-SEARCH_DRAM_BYTES = 6.573568e6 + 1.042432e6   # dram read + write of the captured launch
-SEARCH_DRAM_QUERIES = 51520
+# DRAM read + write of the neighbour-search and pair kernels per step of the
+# headline workload, from one ncu capture of this bench's own launches
+# (None: no capture of the current kernels).
+NEIGHBOUR_SCATTER_TRAFFIC = None
 
 
 def _peaks():
@@ -85,8 +100,8 @@ class Clocks:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                 f".clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="sidm_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -167,7 +182,8 @@ def run_reference(args) -> None:
         upd += int(a.sum())
     dt = time.perf_counter() - t0
     v = upd / dt
-    cores = os.cpu_count()
+    cpu = host_cpu()
+    cores = cpu["nproc"]
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -176,51 +192,105 @@ def run_reference(args) -> None:
                        "l2": "host run"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"full oracle step per bench step, active set capped at {cap} "
-                                       "(seeded subset) of the step's active particles"},
+                                       "(seeded subset) of the step's active particles",
+                             "cpu_model": cpu["model"], "nproc": cores},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(w, masks, budget_s=12.0) -> dict:
+def host_cpu() -> dict:
+    """The host's CPU model and the cores this process may use."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"model": model, "nproc": usable, "logical_cpus": os.cpu_count()}
+
+
+def cpu_baseline(w, masks, budget_s=10.0, budget_1core_s=8.0) -> dict:
+    """The oracle as it stands on the host cores: all cores on finest steps
+    1, 2, ... of the cycle for about budget_s, then one core on steps from 1
+    for about budget_1core_s (at least one whole step each)."""
     import oracle
     oracle.build()
     p, bins = w["particles"], w["bins"]
-    upd, t0, k = 0, time.perf_counter(), 0
-    vel = p.vel.copy()
-    while k < CYCLE - 1 and (time.perf_counter() - t0) < budget_s:
-        s = 1 + k
-        r = oracle.step(p.pos, vel, p.mass, p.ids, masks[s], bins, w["dt_max"], n_ngb=64, seed=0, step=s)
-        vel = r["vel"]
-        upd += int(masks[s].sum())
-        k += 1
-    dt = time.perf_counter() - t0
-    return {"value": upd / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"finest steps 1..{k} of the 100-step cycle ({upd} active updates, {dt:.1f} s)"}
+    cpu = host_cpu()
+
+    def run(n_threads, budget):
+        upd, t0, k = 0, time.perf_counter(), 0
+        vel = p.vel.copy()
+        while k < CYCLE - 1 and (k == 0 or (time.perf_counter() - t0) < budget):
+            s = 1 + k
+            r = oracle.step(p.pos, vel, p.mass, p.ids, masks[s], bins, w["dt_max"], n_ngb=64,
+                            seed=0, step=s, n_threads=n_threads)
+            vel = r["vel"]
+            upd += int(masks[s].sum())
+            k += 1
+        return upd, time.perf_counter() - t0, k
+
+    u_all, t_all, k_all = run(0, budget_s)
+    u_one, t_one, k_one = run(1, budget_1core_s)
+    return {"value": u_all / t_all, "unit": UNIT, "cores": cpu["nproc"], "kind": "oracle",
+            "sample": f"finest steps 1..{k_all} of the 100-step cycle ({u_all} active updates, "
+                      f"{t_all:.1f} s, all {cpu['nproc']} cores)",
+            "one_core": {"value": u_one / t_one, "unit": UNIT, "cores": 1,
+                         "sample": f"finest steps 1..{k_one} ({u_one} active updates, "
+                                   f"{t_one:.1f} s, one OpenMP thread)"},
+            "cpu_model": cpu["model"], "nproc": cpu["nproc"]}
 
 
-def run_batch(args) -> None:
-    """512 independent Hernquist haloes (N log-uniform in [2^12, 2^18], sigma/m
-    log-uniform in [0.1, 10], own seeds, bins and step counters) stepped
-    together (one sidm_step_haloes per step), against the plain per-halo form
-    (one sidm_step per halo) on the same haloes and steps."""
+def _setup_stream(local=0):
     import torch
-    from paper_2607_05504_b300 import inputs as I
-    from paper_2607_05504_b300 import sidm
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    haloes = I.hernquist_batch(args.n_halos)
+    return torch, dev, stream
+
+
+def _pair_keys(ctx) -> np.ndarray:
+    """Accepted pairs of the context's last step as sorted (a << 32 | b) keys."""
+    from paper_2607_05504_b300 import sidm
+    total = sidm.sidm_get_pairs(ctx.handle, None, None, 0)
+    ab = np.zeros((max(total, 1), 2), np.uint32)
+    ords = np.zeros(max(total, 1), np.uint64)
+    sidm.sidm_get_pairs(ctx.handle, ab, ords, total)
+    return np.sort((ab[:total, 0].astype(np.uint64) << np.uint64(32)) | ab[:total, 1])
+
+
+def batch_run(n_halos=512, steps=10, warmup=3, workers=0, precision=None) -> dict:
+    """c4: independent Hernquist haloes (N log-uniform in [2^12, 2^18],
+    sigma/m log-uniform in [0.1, 10], own seeds, bins and step counters)
+    stepped together (one sidm_step_haloes per tick, graph-replayed, launch
+    shapes autotuned), against the plain per-halo form on the same haloes and
+    ticks: one context per halo, one sidm_step per halo, graph-replayed with
+    the same launch shapes.  Both forms run the same precision."""
+    from paper_2607_05504_b300 import inputs as I
+    from paper_2607_05504_b300 import sidm
+    torch, dev, stream = _setup_stream()
+    prec = sidm.FP32_SPLIT if precision is None else precision
+    t0 = time.perf_counter()
+    haloes = I.hernquist_batch(n_halos, workers=workers)
+    t_gen = time.perf_counter() - t0
     p, off, bins = I.pack(haloes)
     n = p.n
-    bmax = [int(h["bins"].max()) for h in haloes]
+    ticks = warmup + steps
 
     def masks_for(s):
         return np.concatenate([I.active_at_step(h["bins"], s) for h in haloes])
 
-    steps = args.steps
-    cyc = [masks_for(s) for s in range(args.warmup + steps)]
-    ctx = sidm.Context(n_ngb=64, box=0.0, stream=stream.cuda_stream, n_max=n, use_graph=True)
+    cyc = [masks_for(s) for s in range(ticks)]
+    n_active = [int(cyc[s].sum()) for s in range(ticks)]
+    ctx = sidm.Context(n_ngb=64, box=0.0, stream=stream.cuda_stream, n_max=n, use_graph=True,
+                       precision=prec)
     ctx.set_particles(torch.from_numpy(p.pos).to(dev), torch.from_numpy(p.vel).to(dev),
                       torch.from_numpy(p.ids.view(np.int32)).to(dev),
                       mass=torch.from_numpy(p.mass).to(dev))
@@ -232,79 +302,91 @@ def run_batch(args) -> None:
         return [sidm.HaloParams(h["dt_max"], sidm.SigmaModel(0, h["sigma0"], 1.0), h["seed"], s)
                 for h in haloes]
 
-    prm = [params(s) for s in range(args.warmup + steps)]
-    for s in range(args.warmup):
+    prm = [params(s) for s in range(ticks)]
+    for s in range(warmup):
         sidm.sidm_step_haloes(ctx.handle, masks_d[s], bins_d, prm[s], None)
-    tuning = ctx.autotune(prm[args.warmup], masks_d[args.warmup], bins_d, reps=1)
+    tuning = ctx.autotune(prm[warmup], masks_d[warmup], bins_d, reps=1)
+    sidm.sidm_step_haloes(ctx.handle, masks_d[warmup - 1], bins_d, prm[warmup - 1], None)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    upd = 0
-    n_active = [int(cyc[args.warmup + k].sum()) for k in range(steps)]   # host bookkeeping, untimed
     e0.record(stream)
-    for k in range(steps):
-        s = args.warmup + k
+    for s in range(warmup, ticks):
         sidm.sidm_step_haloes(ctx.handle, masks_d[s], bins_d, prm[s], None)
     e1.record(stream)
-    upd = sum(n_active)
     torch.cuda.synchronize()
     t_batch = e0.elapsed_time(e1) * 1e-3
     graph_state = ctx.graph_state
     ctx.close()
-    # plain per-halo form: one context, each halo loaded then stepped alone
-    pc = sidm.Context(n_ngb=64, box=0.0, stream=stream.cuda_stream, n_max=int(np.diff(off).max()))
-    dev_h = [(torch.from_numpy(h["particles"].pos).to(dev), torch.from_numpy(h["particles"].vel).to(dev),
-              torch.from_numpy(h["particles"].ids.view(np.int32)).to(dev),
-              torch.from_numpy(h["particles"].mass).to(dev), torch.from_numpy(h["bins"]).to(dev))
-             for h in haloes]
-    t_plain, upd_plain = 0.0, 0
-    for k in range(min(steps, 3)):
-        s = args.warmup + k
-        for j, h in enumerate(haloes):
-            pos, vel, ids, mass, hb = dev_h[j]
-            pc.set_particles(pos, vel, ids, mass=mass)
-            mk = torch.from_numpy(I.active_at_step(h["bins"], s)).to(dev)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            pc.step_counter = s
-            sidm.sidm_step(pc.handle, mk, hb, h["dt_max"], sidm.SigmaModel(0, h["sigma0"], 1.0),
-                           h["seed"], None)
-            b.record(stream)
-            b.synchronize()
-            t_plain += a.elapsed_time(b) * 1e-3
-            upd_plain += int(mk.sum().item())
-    pc.close()
-    line = {"metric": METRIC, "value": upd / t_batch, "unit": UNIT, "n_gpus": 1, "steps": steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"batch of {args.n_halos} Hernquist haloes, N log-uniform in "
-                                   "[2^12, 2^18], sigma/m log-uniform in [0.1, 10], N_ngb 64",
-                       "n": n, "n_halos": args.n_halos, "mean_active": upd / steps},
-            "launch": {"graph": graph_state, "tuning": tuning,
-                       "form": "one multi-halo step per tick (sidm_step_haloes)"},
-            "plain_per_halo": {"value": upd_plain / t_plain, "unit": UNIT,
-                               "steps": min(steps, 3),
-                               "note": "same haloes, one sidm_step per halo (kernel time only)"}}
-    print(json.dumps(line), flush=True)
+    del masks_d
+    torch.cuda.empty_cache()
+    # plain per-halo form: a context per halo, stepped one after another
+    plain = []
+    for h in haloes:
+        hp = h["particles"]
+        c = sidm.Context(n_ngb=64, box=0.0, stream=stream.cuda_stream, n_max=hp.n, use_graph=True,
+                         precision=prec)
+        c.set_particles(torch.from_numpy(hp.pos).to(dev), torch.from_numpy(hp.vel).to(dev),
+                        torch.from_numpy(hp.ids.view(np.int32)).to(dev),
+                        mass=torch.from_numpy(hp.mass).to(dev))
+        c.set_tuning(**tuning)
+        mk = [torch.from_numpy(I.active_at_step(h["bins"], s)).to(dev) for s in range(ticks)]
+        plain.append((c, mk, torch.from_numpy(h["bins"]).to(dev),
+                      sidm.SigmaModel(0, h["sigma0"], 1.0)))
+    for s in range(warmup):
+        for (c, mk, hb, sg), h in zip(plain, haloes):
+            c.step_counter = s
+            sidm.sidm_step(c.handle, mk[s], hb, h["dt_max"], sg, h["seed"], None)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for s in range(warmup, ticks):
+        for (c, mk, hb, sg), h in zip(plain, haloes):
+            c.step_counter = s
+            sidm.sidm_step(c.handle, mk[s], hb, h["dt_max"], sg, h["seed"], None)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_plain = a.elapsed_time(b) * 1e-3
+    plain_graphs = sum(1 for c, *_ in plain if c.graph_state == 1)
+    for c, *_ in plain:
+        c.close()
+    del plain
+    torch.cuda.empty_cache()
+    upd = sum(n_active[warmup:])
+    return {"value": upd / t_batch, "unit": UNIT, "ms_per_tick": 1e3 * t_batch / steps,
+            "ticks": steps, "warmup": warmup,
+            "workload": f"{n_halos} Hernquist haloes, N log-uniform in [2^12, 2^18] (sum {n}), "
+                        "sigma/m log-uniform in [0.1, 10], own seeds, bins and step counters, "
+                        "N_ngb 64",
+            "precision": "fp32_split" if prec == sidm.FP32_SPLIT else "fp64_plain",
+            "n": n, "n_halos": n_halos, "mean_active": upd / steps,
+            "form": "one multi-halo step per tick (sidm_step_haloes), graph-replayed",
+            "graph": graph_state, "tuning": tuning,
+            "plain_per_halo": {"value": upd / t_plain, "unit": UNIT,
+                               "ms_per_tick": 1e3 * t_plain / steps,
+                               "graphs": plain_graphs,
+                               "note": "same haloes and ticks, one context and one sidm_step per "
+                                       "halo, graph-replayed, the batch's launch shapes"},
+            "speedup_vs_plain": t_plain / t_batch,
+            "timing": "CUDA events on the launch stream around all ticks; inputs resident",
+            "input_generation_s": round(t_gen, 1)}
 
 
-def run_precision(args) -> None:
-    """NFW halo (c = 10, r_s = 1, N = 2^23), Yukawa-like sigma0/m = 1 with w =
-    v_c(r_s), N_ngb 64, power-of-two bins: the FP32-split form against the
-    FP64 plain form, step by step from the same state.  Reports both forms'
-    throughput, the accepted-pair mismatch |A32 xor A64| / |A64| and the
-    split form's relative energy / momentum change per step."""
-    import torch
+def precision_run(log2_n=23, steps=10) -> dict:
+    """c3: NFW halo (c = 10, r_s = 1, N = 2^log2_n), Yukawa-like sigma0/m = 1
+    with w = v_c(r_s), N_ngb 64, power-of-two bins: the FP32-split form
+    against the FP64 plain form, step by step from the same state (the FP64
+    form's).  Reports both forms' throughput (CUDA events, one step at a time),
+    the accepted-pair mismatch |A32 xor A64| / |A64|, and the split form's
+    relative energy / momentum change per step, against its own start and
+    against the FP64 form's result."""
     from paper_2607_05504_b300 import inputs as I
     from paper_2607_05504_b300 import sidm
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
-    p = I.nfw_halo(1 << args.log2_n, 2)
+    torch, dev, stream = _setup_stream()
+    p = I.nfw_halo(1 << log2_n, 2)
     w = p.meta["v_c_rs"]
     bins, dt = I.timestep_bins(p, I.nfw_density, 1.0, 64)
-    ctxs = {k: sidm.Context(n_ngb=64, stream=stream.cuda_stream, n_max=p.n, precision=v)
+    ctxs = {k: sidm.Context(n_ngb=64, stream=stream.cuda_stream, n_max=p.n, precision=v,
+                            use_graph=True)
             for k, v in (("fp64", sidm.FP64_PLAIN), ("split", sidm.FP32_SPLIT))}
     pos, vel = torch.from_numpy(p.pos).to(dev), torch.from_numpy(p.vel).to(dev)
     ids, mass = torch.from_numpy(p.ids.view(np.int32)).to(dev), torch.from_numpy(p.mass).to(dev)
@@ -312,108 +394,192 @@ def run_precision(args) -> None:
         c.set_particles(pos, vel, ids, mass=mass)
     bins_d = torch.from_numpy(bins).to(dev)
     sg = sidm.SigmaModel(sidm.SIGMA_YUKAWA, 1.0, w)
+    # warm-up: capture both forms' graphs on step 1's active set
+    act1 = torch.from_numpy(I.active_at_step(bins, 1)).to(dev)
+    for c in ctxs.values():
+        c.step_counter = 1
+        sidm.sidm_step(c.handle, act1, bins_d, dt, sg, 7, None)
+        c.set_velocities(vel)
+    torch.cuda.synchronize()
     t = {"fp64": 0.0, "split": 0.0}
     n64 = nx = upd = 0
-    drift_e, drift_p = 0.0, 0.0
-    vcur = torch.empty_like(vel)
-    for s in range(args.steps):
+    d_e, d_p, d_e64 = 0.0, 0.0, 0.0
+    m64 = mass.to(torch.float64)
+    vcur = vel.clone()
+    vout = {k: torch.empty_like(vel) for k in ctxs}
+
+    def energy_momentum(v):
+        e = 0.5 * float(torch.sum(m64 * torch.sum(v * v, 1)).item())
+        pm = torch.sum(m64[:, None] * v, 0).cpu().numpy()
+        return e, pm
+
+    pscale = float((m64[:, None] * vel.abs()).sum().item())
+    for s in range(steps):
         act = torch.from_numpy(I.active_at_step(bins, s)).to(dev)
-        res = {}
+        keys = {}
         for k, c in ctxs.items():
+            c.set_velocities(vcur)
             c.step_counter = s
-            torch.cuda.synchronize()
+            c.sync()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             sidm.sidm_step(c.handle, act, bins_d, dt, sg, 7, None)
             b.record(stream)
             b.synchronize()
             t[k] += a.elapsed_time(b) * 1e-3
-            st = sidm.StepStats()
-            res[k] = set(map(tuple, c.pairs()[0].tolist()))
+            keys[k] = _pair_keys(c)
+            sidm.sidm_get_particles(c.handle, vout[k])
         upd += int(act.sum().item())
-        n64 += len(res["fp64"])
-        nx += len(res["fp64"] ^ res["split"])
-        # conservation of the split step: recompute with statistics
-        sidm.sidm_get_particles(ctxs["fp64"].handle, vcur)
-        c = ctxs["split"]
-        c.set_velocities(vcur)
-        c.step_counter = s
-        st = c.step(dt, act, bins_d, sigma0=1.0, sigma_kind=sidm.SIGMA_YUKAWA, w=w, seed=7)
-        drift_e = max(drift_e, abs(st["e_after"] - st["e_before"]) / st["e_before"])
-        pscale = float((mass[:, None] * vcur.abs()).sum().item())
-        drift_p = max(drift_p, float(np.max(np.abs(np.subtract(st["p_after"], st["p_before"])))) / pscale)
-        c.set_velocities(vcur)
+        n64 += keys["fp64"].size
+        nx += np.setxor1d(keys["fp64"], keys["split"], assume_unique=True).size
+        e0, p0 = energy_momentum(vcur)
+        e32, p32 = energy_momentum(vout["split"])
+        e64, _ = energy_momentum(vout["fp64"])
+        d_e = max(d_e, abs(e32 - e0) / e0)
+        d_e64 = max(d_e64, abs(e32 - e64) / e0)
+        d_p = max(d_p, float(np.max(np.abs(p32 - p0))) / pscale)
+        vcur.copy_(vout["fp64"])
     for c in ctxs.values():
         c.close()
-    line = {"metric": METRIC, "value": upd / t["split"], "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 * t["split"] / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
-            "data": "synthetic",
-            "config": {"workload": f"NFW c=10 N=2^{args.log2_n}, Yukawa sigma0/m=1 w=v_c(r_s), "
-                                   "N_ngb 64, FP32-split vs FP64 plain", "n": p.n},
+    torch.cuda.empty_cache()
+    return {"value": upd / t["split"], "unit": UNIT, "steps": steps,
+            "workload": f"NFW c=10 N=2^{log2_n}, Yukawa sigma0/m=1 w=v_c(r_s), N_ngb 64, "
+                        "power-of-two bins, finest steps 0..{}".format(steps - 1),
+            "n": p.n, "mean_active": upd / steps,
             "fp64_plain": {"value": upd / t["fp64"], "unit": UNIT},
-            "pair_mismatch": {"rate": nx / max(n64, 1), "pairs_fp64": n64, "differing": nx},
-            "drift_per_step": {"energy_rel": drift_e, "momentum_rel": drift_p}}
-    print(json.dumps(line), flush=True)
+            "speedup_split_vs_fp64": t["fp64"] / t["split"],
+            "pair_mismatch": {"rate": nx / max(n64, 1), "pairs_fp64": int(n64),
+                              "differing": int(nx), "target": 1e-5},
+            "drift_per_step": {"energy_rel": d_e, "energy_rel_vs_fp64": d_e64,
+                               "momentum_rel": d_p, "target_energy": 1e-10},
+            "timing": "CUDA events around each step (graph-replayed), both forms from the "
+                      "same state; energies from the returned velocities (FP64 sums)"}
 
 
-def run_serving(args) -> None:
-    """Poisson streams of halo requests served with continuous batching under
-    a device-memory budget.  First the saturated throughput (every request
-    present at t = 0), which gives the capacity in requests/s; then Poisson
-    arrivals at fractions of that capacity, each with p50/p99 latency.  A rate
-    is stable when the last third of the requests waits no longer than 1.5x
-    the first third (no backlog builds up)."""
+def serving_run(requests=32, log2_nmax=21.0, max_steps=1000, budget_gb=120.0,
+                offered_rate=200.0, fracs=(0.5, 0.9)) -> dict:
+    """c5: Poisson streams of halo requests served with continuous batching
+    under a device-memory budget.  First the saturated throughput (every
+    request present at t = 0), which gives the capacity in requests/s; then
+    Poisson arrivals at the offered rate and at fractions of capacity, each
+    with p50/p99 latency.  A rate is stable when the last third of the
+    requests waits no longer than 1.5x the first third (no backlog)."""
     import dataclasses
-    import torch
-    from paper_2607_05504_b300 import inputs as I
     from paper_2607_05504_b300 import serving as S
-    torch.cuda.set_device(0)
-    base = S.request_stream(args.requests, rate=1.0, seed=3, log2_n=(12.0, args.log2_nmax),
-                            steps=(10, args.max_steps))
+    torch, dev, stream = _setup_stream()
+    t0 = time.perf_counter()
+    base = S.request_stream(requests, rate=1.0, seed=3, log2_n=(12.0, log2_nmax),
+                            steps=(10, max_steps), pool=0)
+    t_gen = time.perf_counter() - t0
     unit_arrivals = [r.arrival for r in base]
-    budget = args.budget_gb * 1e9
-    per_particle = 700.0
+    budget = budget_gb * 1e9
 
     def serve(rate):
         reqs = [dataclasses.replace(r, arrival=(0.0 if rate is None else a / rate), steps_done=0,
                                     admitted=None, finished=None, result_vel=None)
                 for r, a in zip(base, unit_arrivals)]
-        eng = S.GpuEngine(capacity=int(budget / per_particle))
-        rep = S.Server(eng, S.Scheduler(budget, per_particle)).run(reqs)
+        eng = S.GpuEngine(budget_bytes=budget, stream=stream)
+        rep = S.Server(eng, S.Scheduler(budget, eng.bytes_per_particle)).run(reqs)
         eng.close()
         lat = [r.latency for r in sorted(reqs, key=lambda r: r.arrival)]
         third = max(len(lat) // 3, 1)
         growth = float(np.mean(lat[-third:]) / max(np.mean(lat[:third]), 1e-9))
         return rep, growth
 
+    serve(None)                                  # first pass: host code and graphs warm
     sat, _ = serve(None)
     work = sat.updates / len(base)               # active-particle updates per request
     cap_rate = sat.throughput / work             # requests/s the device sustains
-    sweep = []
-    for frac in (0.25, 0.5, 0.75, 0.9):
-        rate = frac * cap_rate
+    rows = []
+    for frac, rate in [(None, offered_rate)] + [(f, f * cap_rate) for f in fracs]:
         rep, growth = serve(rate)
-        sweep.append({"rate_per_s": rate, "load": frac, "throughput": rep.throughput,
-                      "p50_s": rep.percentile(50), "p99_s": rep.percentile(99),
-                      "backlog_growth": growth, "stable": growth <= 1.5})
-    stable = [x for x in sweep if x["stable"]]
-    op = stable[-1] if stable else sweep[0]
-    line = {"metric": METRIC, "value": sat.throughput, "unit": UNIT, "n_gpus": 1,
-            "steps": sat.ticks, "warmup": 0, "ms_per_step": 1e3 * sat.wall / max(sat.ticks, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "serving: halo requests (Hernquist/NFW, const/Yukawa sigma), "
-                                   f"N log-uniform in [2^12, 2^{args.log2_nmax:g}], steps "
-                                   f"log-uniform in [10, {args.max_steps}]",
-                       "requests": args.requests, "hbm_budget_gb": args.budget_gb},
+        rows.append({"rate_per_s": rate, "load": (rate / cap_rate), "throughput": rep.throughput,
+                     "p50_s": rep.percentile(50), "p99_s": rep.percentile(99),
+                     "backlog_growth": growth, "stable": growth <= 1.5})
+    stable = [x for x in rows[1:] if x["stable"]]
+    torch.cuda.empty_cache()
+    return {"value": sat.throughput, "unit": UNIT,
+            "workload": "halo requests: Hernquist or NFW, constant or Yukawa sigma, N log-uniform "
+                        f"in [2^12, 2^{log2_nmax:g}], steps log-uniform in [10, {max_steps}], "
+                        f"{requests} requests, {budget_gb:g} GB budget",
             "saturation": {"throughput": sat.throughput, "requests_per_s": cap_rate,
                            "p50_s": sat.percentile(50), "p99_s": sat.percentile(99),
-                           "wall_s": sat.wall},
-            "stable_rate_per_s": op["rate_per_s"] if stable else None,
-            "latency_s": {"rate_per_s": op["rate_per_s"], "p50": op["p50_s"], "p99": op["p99_s"]},
-            "sweep": sweep}
-    print(json.dumps(line), flush=True)
+                           "wall_s": sat.wall, "ticks": sat.ticks},
+            "offered": rows[0], "sweep": rows[1:],
+            "stable_rate_per_s": stable[-1]["rate_per_s"] if stable else None,
+            "timing": "host clock from each request's arrival to its result on the host",
+            "input_generation_s": round(t_gen, 1)}
+
+
+def eq18_run(w, tuning, steps=20, warmup=5, local=0) -> dict:
+    """The headline halo with bins from its own Eq. 18 limits (Sec. 4.4): an
+    all-active step gives every particle's limit, each particle takes the
+    smallest bin whose step lies below its limit (no clipping), and dt_max is
+    set for a mean active fraction of 0.10 over the 100-step cycle.  Times
+    the same cycle steps as the headline, and counts pairs at P >= 1."""
+    from paper_2607_05504_b300 import inputs as I
+    from paper_2607_05504_b300 import sidm
+    torch, dev, stream = _setup_stream(local)
+    p = w["particles"]
+    n = p.n
+    pos_d, vel_d = torch.from_numpy(p.pos).to(dev), torch.from_numpy(p.vel).to(dev)
+    ids_d, mass_d = torch.from_numpy(p.ids.view(np.int32)).to(dev), torch.from_numpy(p.mass).to(dev)
+    sg = sidm.SigmaModel(sidm.SIGMA_CONST, 1.0, 1.0)
+    lc = sidm.Context(n_ngb=64, box=0.0, stream=stream.cuda_stream, device=local, n_max=n)
+    lc.set_particles(pos_d, vel_d, ids_d, mass=mass_d)
+    # every particle active; the limits do not depend on the step's dt, so
+    # the headline's bins keep the step's probabilities in range
+    sidm.sidm_step(lc.handle, None, torch.from_numpy(w["bins"]).to(dev), w["dt_max"], sg, 0, None)
+    lim = torch.empty(n, dtype=torch.float64, device=dev)
+    sidm.sidm_timestep_limits(lc.handle, lim)
+    lc.close()
+    bins, dt_max = I.eq18_bins(lim.cpu().numpy())
+    masks = np.stack([I.active_at_step(bins, s) for s in range(CYCLE)])
+    n_act = [int(m.sum()) for m in masks]
+    masks_d = torch.from_numpy(masks).to(dev)
+    bins_d = torch.from_numpy(bins).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ctx = sidm.Context(n_ngb=64, box=0.0, stream=stream.cuda_stream, device=local, n_max=n,
+                       use_graph=True)
+    ctx.set_particles(pos_d, vel_d, ids_d, mass=mass_d)
+    ctx.set_tuning(**tuning)
+    for k in range(warmup):
+        sidm.sidm_step(ctx.handle, masks_d[k % CYCLE], bins_d, dt_max, sg, 0, None)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    upd = 0
+    for k in range(steps):
+        s = (warmup + k) % CYCLE
+        flush.zero_()
+        ev[k][0].record(stream)
+        sidm.sidm_step(ctx.handle, masks_d[s], bins_d, dt_max, sg, 0, None)
+        ev[k][1].record(stream)
+        upd += n_act[s]
+    torch.cuda.synchronize()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    ctx.close()
+    # pair statistics of the same steps (untimed, from the same start state)
+    sc = sidm.Context(n_ngb=64, box=0.0, stream=stream.cuda_stream, device=local, n_max=n)
+    sc.set_particles(pos_d, vel_d, ids_d, mass=mass_d)
+    pge1 = acc = mmax = 0
+    for k in range(warmup + steps):
+        st = sc.step(dt_max, masks_d[k % CYCLE], bins_d, seed=0)
+        if k >= warmup:
+            pge1 += st["n_p_ge_1"]
+            acc += st["n_accepted"]
+            mmax = max(mmax, st["max_multiplicity"])
+    sc.close()
+    del flush
+    torch.cuda.empty_cache()
+    return {"value": upd / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms / steps,
+            "steps": steps, "warmup": warmup, "mean_active": upd / steps,
+            "bins": int(bins.max()) + 1, "dt_max": dt_max,
+            "mean_active_fraction_cycle": float(np.mean(n_act)) / n,
+            "n_p_ge_1": int(pge1), "n_accepted": int(acc), "max_multiplicity": int(mmax),
+            "workload": "hernquist-2^20 with bins from its own step-0 Eq. 18 limits (smallest bin "
+                        "below each limit, none clipped), dt_max set for 10 % mean activity",
+            "timing": "as the headline: CUDA events per step, L2 flushed between steps"}
 
 
 def main():
@@ -434,14 +600,26 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--reuse-every", type=int, default=8,
                     help="also time the steps with the tree rebuilt every k steps (0: skip)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the c2-Eq.18, c3, c4 and c5 sub-objects of the default run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.impl == "ours" and args.workload == "batch":
-        return run_batch(args)
-    if args.impl == "ours" and args.workload == "serving":
-        return run_serving(args)
-    if args.impl == "ours" and args.workload == "precision":
-        return run_precision(args)
+    workers = max(1, min(16, (host_cpu()["nproc"] or 1)))
+    if args.impl == "ours" and args.workload != "hernquist":
+        if args.workload == "batch":
+            d = batch_run(args.n_halos, args.steps, args.warmup, workers=workers)
+        elif args.workload == "precision":
+            d = precision_run(args.log2_n, args.steps)
+        else:
+            d = serving_run(args.requests, args.log2_nmax, args.max_steps, args.budget_gb)
+        line = {"metric": METRIC, "value": d["value"], "unit": UNIT, "n_gpus": 1,
+                "steps": d.get("steps", d.get("ticks", 0)), "warmup": args.warmup,
+                "ms_per_step": d.get("ms_per_tick", d.get("ms_per_step")),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": d["workload"]}, args.workload: d}
+        print(json.dumps(line), flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -574,23 +752,35 @@ def main():
         n_act_sum += int(masks[s].sum())
     pctx.close()
     hbm_peak, peak_kind = _peaks()
-    dom = max(phase_sum, key=phase_sum.get)
-    per_n, per_a = PHASE_BYTES[dom]
-    bytes_per_step = per_n * n + per_a * (n_act_sum / reps)
-    avg_ms = phase_sum[dom] / reps
-    achieved = bytes_per_step / (avg_ms * 1e-3) / 1e9
-    # DRAM bytes of the search kernel from one ncu capture of the current
-    # kernel (7.57 MB on a launch of 51,520 queries of this workload),
-    # scaled to this run's mean queries per step
-    traffic = (SEARCH_DRAM_BYTES * (n_act_sum / reps) / SEARCH_DRAM_QUERIES
-               if dom == "search" else None)
+    ph = {k: v / reps for k, v in phase_sum.items()}
+    a_mean = n_act_sum / reps
+    # the neighbour-search and pair/scatter kernels (the dominant share of
+    # the step): 48 B x N + 64 B x A over their summed phase time
+    ns_bytes = NEIGHBOUR_SCATTER_BYTES[0] * n + NEIGHBOUR_SCATTER_BYTES[1] * a_mean
+    ns_ms = ph["search"] + ph["pairs"]
+    achieved = ns_bytes / (ns_ms * 1e-3) / 1e9
+    step_bytes = STEP_BYTES[0] * n + STEP_BYTES[1] * a_mean
+    step_ms = sum(ph.values())
+    build_ms = ph["keys"] + ph["sort"] + ph["structure"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic,
-                "traffic_note": "bytes per launch, scaled by queries from a 51,520-query capture",
-                "kernel": dom,
+                "frac": achieved / hbm_peak, "traffic": NEIGHBOUR_SCATTER_TRAFFIC,
+                "kernel": "search + pairs (search_kernel, pairs_kernel, pairs_exact_kernel, "
+                          "limits_kernel, permute_vel_kernel)",
+                "algorithmic_bytes": ns_bytes,
+                "bytes_model": "48 B x N + 64 B x A (N particles, A active per step)",
                 "peak_kind": peak_kind,
-                "phase_ms_per_step": {k: v / reps for k, v in phase_sum.items()},
-                "phase_share": {k: v / sum(phase_sum.values()) for k, v in phase_sum.items()}}
+                "search_only": {"achieved": ns_bytes / (ph["search"] * 1e-3) / 1e9,
+                                "frac": ns_bytes / (ph["search"] * 1e-3) / 1e9 / hbm_peak},
+                "build": {"bytes": BUILD_BYTES_N * n, "ms": build_ms,
+                          "achieved": BUILD_BYTES_N * n / (build_ms * 1e-3) / 1e9,
+                          "frac": BUILD_BYTES_N * n / (build_ms * 1e-3) / 1e9 / hbm_peak},
+                "step": {"bytes": step_bytes, "bytes_model": "308 B x N + 64 B x A",
+                         "ms": step_ms, "achieved": step_bytes / (step_ms * 1e-3) / 1e9,
+                         "frac": step_bytes / (step_ms * 1e-3) / 1e9 / hbm_peak},
+                "phase_ms_per_step": ph,
+                "phase_share": {k: v / step_ms for k, v in ph.items()},
+                "timing": "CUDA events between phases on the library's stream, the timed steps "
+                          "repeated in a profiling context (same launch shapes, L2 flushed)"}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -656,6 +846,33 @@ def main():
         cb = cpu_baseline(w, masks)
 
     ctx.close()
+    del flush
+    torch.cuda.empty_cache()
+
+    # ---- the other configurations, each bounded in time (N = 1 only)
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        def guarded(name, fn):
+            t0 = time.perf_counter()
+            try:
+                d = fn()
+            except Exception as e:            # reported in the line, never hidden
+                d = {"error": f"{type(e).__name__}: {e}"}
+            d["wall_s"] = round(time.perf_counter() - t0, 1)
+            extras[name] = d
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+
+        guarded("c2_eq18_bins", lambda: eq18_run(w, tuning, args.steps, args.warmup, local))
+        guarded("c3_precision", lambda: precision_run(23, 10))
+        guarded("c4_batch", lambda: batch_run(512, 10, 3, workers=workers))
+        guarded("c5_serving", lambda: serving_run(32, 21.0, 1000, 120.0))
+    vs_plain = None
+    if extras:
+        vs_plain = {"c3_split_over_fp64": extras["c3_precision"].get("speedup_split_vs_fp64"),
+                    "c4_batch_over_per_halo": extras["c4_batch"].get("speedup_vs_plain"),
+                    "c5_saturation_over_c2": (extras["c5_serving"].get("value", 0.0) / value
+                                              if "value" in extras["c5_serving"] else None)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
@@ -669,7 +886,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(),
                 "launch": {"graph": ctx_graph_state, "tuning": tuning}, "step_ms": step_dist,
-                "tree_reuse": reuse}
+                "tree_reuse": reuse, "vs_plain_form": vs_plain, **extras}
         print(json.dumps(line), flush=True)
     if dist:
         import torch.distributed as D

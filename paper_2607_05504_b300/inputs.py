@@ -270,6 +270,41 @@ def timestep_bins(p: Particles, density, sigma_over_m: float, n_ngb: int,
     return bins.astype(np.int8), float(2.0 ** ldt)
 
 
+def eq18_bins(dt_limit: np.ndarray, target_active: float = 0.10, cycle: int = 100,
+              max_bins: int = 40) -> tuple[np.ndarray, float]:
+    """Power-of-two bins from per-particle Eq. 18 limits (Sec. 4.4), the
+    harness rule of an individual-timestep code: particle i takes the
+    smallest bin b >= 0 with dt_max 2^-b < dt_limit_i (strict), so every
+    particle steps below its own limit and no bin is clipped.  dt_max is
+    bisected (in log2) so that the mean active fraction over the first
+    `cycle` finest steps is closest to target_active.  Infinite limits (no
+    neighbour moving relative to the particle) take bin 0.  Returns (bins
+    int8, dt_max)."""
+    lim = np.asarray(dt_limit, np.float64)
+    fin = np.isfinite(lim) & (lim > 0)
+    l2 = np.log2(np.where(fin, lim, 1.0))
+
+    def bins_for(ldt):
+        # smallest b with ldt - b < l2, i.e. b = floor(ldt - l2) + 1, at least 0
+        b = np.floor(ldt - l2) + 1.0
+        return np.where(fin, np.clip(b, 0, max_bins - 1), 0).astype(np.int64)
+
+    def frac(ldt):
+        b = bins_for(ldt)
+        period = np.left_shift(np.int64(1), int(b.max()) - b)
+        return float(np.mean(np.ceil(cycle / period)) / cycle)
+
+    lo, hi = float(l2[fin].min()) - 1.0, float(l2[fin].max()) + max_bins - 2.0
+    for _ in range(60):          # frac decreases as dt_max grows
+        mid = 0.5 * (lo + hi)
+        if frac(mid) > target_active:
+            lo = mid
+        else:
+            hi = mid
+    ldt = lo if abs(frac(lo) - target_active) <= abs(frac(hi) - target_active) else hi
+    return bins_for(ldt).astype(np.int8), float(2.0 ** ldt)
+
+
 def active_at_step(bins: np.ndarray, s: int) -> np.ndarray:
     """Particle i is active at finest step s iff s is a multiple of
     2**(b_max - b_i) (bin 0 is the coarsest)."""
@@ -301,21 +336,30 @@ def hernquist_2pow20(seed: int = 1, n: int = 1 << 20) -> dict:
             "sigma0": 1.0, "dt_max": dt_max, "bins": bins, "steps": 100, "seed": 0}
 
 
+def _batch_member(args) -> dict:
+    n, halo_seed, sigma0, n_ngb, key_seed = args
+    p = hernquist_halo(n, halo_seed)
+    bins, dt = timestep_bins(p, hernquist_density, sigma0, n_ngb)
+    return {"particles": p, "bins": bins, "dt_max": dt, "sigma0": sigma0, "seed": key_seed}
+
+
 def hernquist_batch(n_halos: int = 512, seed: int = 1000, log2_n=(12.0, 18.0),
-                    sigma_range=(0.1, 10.0), n_ngb: int = 64) -> list:
+                    sigma_range=(0.1, 10.0), n_ngb: int = 64, workers: int = 0) -> list:
     """Independent Hernquist haloes with N log-uniform in 2^[log2_n] and
     sigma/m log-uniform in sigma_range; halo k has seed seed + k, its own
-    power-of-two bins and dt_max (10 % mean activity)."""
+    power-of-two bins and dt_max (10 % mean activity).  workers > 1 builds
+    the haloes in that many spawned processes (same result: each halo
+    depends only on its own seeds)."""
     rng = np.random.default_rng(seed)
     sizes = np.round(2.0 ** rng.uniform(log2_n[0], log2_n[1], n_halos)).astype(np.int64)
     sig = 10.0 ** rng.uniform(math.log10(sigma_range[0]), math.log10(sigma_range[1]), n_halos)
-    out = []
-    for k in range(n_halos):
-        p = hernquist_halo(int(sizes[k]), seed + 1 + k)
-        bins, dt = timestep_bins(p, hernquist_density, float(sig[k]), n_ngb)
-        out.append({"particles": p, "bins": bins, "dt_max": dt, "sigma0": float(sig[k]),
-                    "seed": seed + k})
-    return out
+    jobs = [(int(sizes[k]), seed + 1 + k, float(sig[k]), n_ngb, seed + k) for k in range(n_halos)]
+    if workers > 1 and n_halos > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_batch_member, jobs, chunksize=8))
+    return [_batch_member(j) for j in jobs]
 
 
 def pack(haloes: list) -> tuple:

@@ -320,6 +320,33 @@ def test_hernquist_2pow20_full_size(hernquist_full, s):
     ctx.close()
 
 
+def test_eq18_bins_from_the_oracle_limits_keep_every_pair_below_one():
+    """A halo whose bins come from its own Eq. 18 limits (Sec. 4.4; the
+    oracle's limits of an all-active step, smallest bin below each limit):
+    several steps of the hierarchy match the oracle bit for bit, and no pair
+    reaches P = 1."""
+    p = I.hernquist_halo(1 << 14, 31, ids="random")
+    o0 = oracle.step(p.pos, p.vel, p.mass, p.ids, None, np.zeros(p.n, np.int8), 1e-3, n_ngb=32,
+                     seed=1)
+    bins, dt_max = I.eq18_bins(o0["dtlim"], cycle=16)
+    assert int(bins.max()) >= 3
+    stats = []
+    ctx = sidm.Context(n_ngb=32)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    vel, h, dl = p.vel.copy(), np.zeros(p.n), np.full(p.n, np.inf)
+    for k in range(6):
+        a = I.active_at_step(bins, k)
+        o = oracle.step(p.pos, vel, p.mass, p.ids, a, bins, dt_max, n_ngb=32, seed=5, step=k,
+                        h_init=h, dtlim_init=dl)
+        g = _gpu_step(ctx, p, a, bins, dt_max, seed=5)
+        _compare(g, o, a, f"step {k}")
+        stats.append(g["stats"])
+        vel, h, dl = o["vel"], o["h"], o["dtlim"]
+    ctx.close()
+    assert sum(st["n_accepted"] for st in stats) > 100
+    assert all(st["n_p_ge_1"] == 0 for st in stats)
+
+
 def test_tabulated_cross_section_matches_the_oracle():
     """Tabulated sigma/m(v), linear in log v (Sec. 4.1), on a halo with
     partial activity: h, accepted pairs and velocities equal the oracle's;
