@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include "../../include/sidm.h"
+#include "../../include/sidm_model.cuh"
 
 namespace sidm {
 
@@ -76,36 +77,23 @@ struct DevStats {
   unsigned int pad;
 };
 
-struct PairRec {
-  unsigned long long ord;  // words 2,3 of the stream-0 draw
-  uint32_t a, b;           // ids, a < b
-  int32_t ia, ib;          // user-order indices of the a- and b-particle
-};
+// An accepted pair: ord = words 2, 3 of the stream-0 draw; ids a < b;
+// user-order indices ia, ib of the a- and b-particle (the record of the C ABI).
+using PairRec = sidm_pair;
 
 // ------------------------------------------------------------------ Philox
-// Philox-4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds, each two
-// 32x32 -> 64-bit products of counter words 0 and 2 with fixed multipliers;
-// the high halves are xor-ed with counter words 1, 3 and the key, the key is
-// advanced by two Weyl increments between rounds.
+// Philox-4x32-10 and the 53-bit uniform of sidm_model.cuh (one definition
+// for the draws of the pair kernel and the directions of the kicks).
 struct U4 { uint32_t x, y, z, w; };
 
 __device__ __forceinline__ U4 philox10(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
                                        uint32_t c2, uint32_t c3) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-    const uint32_t n0 = hi1 ^ c1 ^ k0;
-    const uint32_t n2 = hi0 ^ c3 ^ k1;
-    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
-    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
-  }
-  return U4{c0, c1, c2, c3};
+  const uint4 w = sidm_model::philox4x32_10(k0, k1, c0, c1, c2, c3);
+  return U4{w.x, w.y, w.z, w.w};
 }
 
-// 53 random bits -> [0, 1), exact in FP64: top 27 bits of one word, top 26 of the other.
 __device__ __forceinline__ double unit53(uint32_t a, uint32_t b) {
-  return ((double)(a >> 5) * 67108864.0 + (double)(b >> 6)) * 0x1.0p-53;
+  return sidm_model::unit53(a, b);
 }
 
 // ---------------------------------------------------------------- geometry
@@ -387,19 +375,12 @@ int launch_pairs(const Sorted& so, const Forest& f, int64_t n, const int32_t* ac
                  int* work, int sms, const LaunchTuning& t, cudaStream_t s);
 
 // resolve.cu
-struct ResolveBuffers {
-  int32_t* mult;      // [n] accepted pairs per particle (0 between steps)
-  int32_t* seg_off;   // [n] start of the particle's pair segment (-1 between steps)
-  int32_t* fill;      // [n] segment fill counter (0 between steps)
-  int32_t* cursor;    // [n] first unapplied entry of the segment (0 between steps)
-  int32_t* seg;       // [2 cap] pair ids, one segment per particle
-  int32_t* seg_e;     // [2 cap] the particle of each segment slot
-  int32_t* touched;   // [2 cap] particles that own a segment
-  int32_t* pending;   // [cap] pairs that share a particle with another pair
-  uint8_t* flags;     // [cap] applied flags
-  int32_t* pos_a;     // [cap] place of the pair in the sorted segment of its particle a
-  int32_t* pos_b;     // [cap] ... and of its particle b
-};
+// per-particle segments and cursors of the kick application (sidm_model.cuh)
+using ResolveBuffers = sidm_model::detail::Buffers;
+static_assert(ST_DIR_FAIL == sidm_model::detail::kDirFail &&
+                  ST_ERR_ROUNDS == sidm_model::detail::kErrRounds &&
+                  ST_ERR_PAIR_OVERFLOW == sidm_model::detail::kErrPairOverflow,
+              "status bits shared with the application templates");
 // max_passes: bound on the dataflow passes (0: the built-in 2^22)
 int launch_resolve(PairRec* pairs, int64_t pair_cap, int max_passes, double* vel,
                    const double* mass, const int32_t* halo_of, const Halo* halos,
