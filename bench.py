@@ -708,6 +708,22 @@ def main():
         torch.cuda.nvtx.range_pop()
     launches = ctx.kernel_launches - l0
     ctx_graph_state = ctx.graph_state
+    # the whole 100-step cycle, step 0 (every particle active) included
+    cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(CYCLE)]
+    torch.cuda.synchronize()
+    for s in range(CYCLE):
+        flush.zero_()
+        cev[s][0].record(stream)
+        step(s)
+        cev[s][1].record(stream)
+    torch.cuda.synchronize()
+    cyc_ms = [a.elapsed_time(b) for a, b in cev]
+    full_cycle = {"value": sum(n_active) / (sum(cyc_ms) * 1e-3), "unit": UNIT,
+                  "ms_per_step": sum(cyc_ms) / CYCLE, "step0_ms": cyc_ms[0],
+                  "step0_active": n_active[0],
+                  "note": "finest steps 0..99 of the bin cycle, the same context and shapes, "
+                          "L2 flushed between steps"}
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_ms = sum(step_ms)
     srt = sorted(range(len(step_ms)), key=lambda i: step_ms[i])
@@ -906,7 +922,8 @@ def main():
                 "roofline": roofline, "cpu_baseline": cb, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk.summary(),
                 "launch": {"graph": ctx_graph_state, "tuning": tuning}, "step_ms": step_dist,
-                "tree_reuse": reuse, "vs_plain_form": vs_plain, **extras}
+                "tree_reuse": reuse, "full_cycle": full_cycle, "vs_plain_form": vs_plain,
+                **extras}
         print(json.dumps(line), flush=True)
     if dist:
         import torch.distributed as D

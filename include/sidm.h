@@ -376,7 +376,7 @@ typedef struct {
   int search_chunk;         /* queries a search warp claims at a time, 1..64 (1)      */
   int search_blocks_per_sm; /* search blocks of 4 warps launched per SM, 1..8 (8)     */
   int pairs_chunk;          /* queries a pair warp claims at a time, 1..64 (4)        */
-  int pairs_blocks_per_sm;  /* pair blocks of 4 warps per SM, 1..6 (6)                */
+  int pairs_blocks_per_sm;  /* pair blocks of 4 warps per SM, 1..7 (7)                */
 } sidm_tuning;
 
 /* Sets / reads the launch shapes of the context.  SIDM_ERR_INVALID_ARG for a

@@ -962,7 +962,7 @@ bool valid_tuning(const LaunchTuning& t) {
           t.search_window == 512) &&
          t.search_chunk >= 1 && t.search_chunk <= 64 && t.search_blocks_per_sm >= 1 &&
          t.search_blocks_per_sm <= 8 && t.pairs_chunk >= 1 && t.pairs_chunk <= 64 &&
-         t.pairs_blocks_per_sm >= 1 && t.pairs_blocks_per_sm <= 6;
+         t.pairs_blocks_per_sm >= 1 && t.pairs_blocks_per_sm <= PAIRS_BLOCKS_MAX;
 }
 
 LaunchTuning from_public(const sidm_tuning& p) {
@@ -1255,7 +1255,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
   const int windows[] = {128, 256, 384, 512};
   const int chunks[] = {1, 2, 4, 8, 16};
   const int sblocks[] = {4, 6, 8};
-  const int pblocks[] = {3, 4, 6};
+  const int pblocks[] = {4, 6, 7};
   auto try_field = [&](int LaunchTuning::*field, const int* vals, int nv) {
     for (int k = 0; k < nv && rc == SIDM_OK; ++k) {
       if (cur.*field == vals[k]) continue;

@@ -18,6 +18,9 @@ namespace {
 
 constexpr int BT = 256;
 constexpr int BB_ITEMS = 16;
+#ifndef BB_GROUP
+#define BB_GROUP 4      // loads in flight per thread (1: 0.051 ms, 4: 0.043 ms for the key phase)
+#endif
 
 __device__ __forceinline__ float warp_minf(float v) {
   for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -91,19 +94,35 @@ __global__ void __launch_bounds__(BT) bbox_kernel(const double* __restrict__ pos
     int cur = -1;
     unsigned long long lo[3] = {ORD_NONE_LO, ORD_NONE_LO, ORD_NONE_LO};
     unsigned long long hi[3] = {ORD_NONE_HI, ORD_NONE_HI, ORD_NONE_HI};
-    for (int j = 0; j < BB_ITEMS; ++j) {
-      const int64_t i = c0 + (int64_t)j * BT + threadIdx.x;
-      if (i >= n) break;
-      const int k = halo_of[i];
-      if (k != cur) {
-        if (cur >= 0) bbox_flush(halos, cur, lo, hi);
-        cur = k;
-        for (int a = 0; a < 3; ++a) { lo[a] = ORD_NONE_LO; hi[a] = ORD_NONE_HI; }
+    // BB_GROUP items' loads are issued together before any is used
+    for (int j0 = 0; j0 < BB_ITEMS; j0 += BB_GROUP) {
+      int kg[BB_GROUP];
+      double pg[BB_GROUP][3];
+#pragma unroll
+      for (int g = 0; g < BB_GROUP; ++g) {
+        const int64_t i = c0 + (int64_t)(j0 + g) * BT + threadIdx.x;
+        kg[g] = -1;
+        if (i < n) {
+          kg[g] = halo_of[i];
+          pg[g][0] = pos[3 * i];
+          pg[g][1] = pos[3 * i + 1];
+          pg[g][2] = pos[3 * i + 2];
+        }
       }
-      for (int a = 0; a < 3; ++a) {
-        const unsigned long long x = dbl_to_ordered(pos[3 * i + a]);
-        lo[a] = x < lo[a] ? x : lo[a];
-        hi[a] = x > hi[a] ? x : hi[a];
+#pragma unroll
+      for (int g = 0; g < BB_GROUP; ++g) {
+        const int k = kg[g];
+        if (k < 0) break;
+        if (k != cur) {
+          if (cur >= 0) bbox_flush(halos, cur, lo, hi);
+          cur = k;
+          for (int a = 0; a < 3; ++a) { lo[a] = ORD_NONE_LO; hi[a] = ORD_NONE_HI; }
+        }
+        for (int a = 0; a < 3; ++a) {
+          const unsigned long long x = dbl_to_ordered(pg[g][a]);
+          lo[a] = x < lo[a] ? x : lo[a];
+          hi[a] = x > hi[a] ? x : hi[a];
+        }
       }
     }
     const int k0 = __shfl_sync(0xffffffffu, cur, 0);

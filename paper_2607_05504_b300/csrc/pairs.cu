@@ -433,7 +433,13 @@ __device__ __forceinline__ void flush_counters(const PairKArgs& A, unsigned long
 }
 
 // Queries with a complete neighbour list (the usual case).
-__global__ void __launch_bounds__(PT, 6) pairs_kernel(PairKArgs A) {
+// 7 resident blocks of 4 warps per SM (72 registers): the kernel waits on
+// dependent L2 gathers, and 7 blocks hide them better than 6 at 80 registers
+// (pair phase 0.238 -> 0.228 ms on the 2^20 halo)
+#ifndef PAIRS_MIN_BLOCKS
+#define PAIRS_MIN_BLOCKS 7
+#endif
+__global__ void __launch_bounds__(PT, PAIRS_MIN_BLOCKS) pairs_kernel(PairKArgs A) {
   __shared__ float s_ghi[PW][MAXR * WARP];
   if (A.a.ov.na > 0) return;  // the overlap estimator's queries all walk the tree
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -338,12 +338,15 @@ int tree_levels_for(int64_t n, int64_t count[MAX_LEVELS]);
 
 // search.cu
 // Launch shapes that leave every result unchanged (see sidm_tuning).
+#ifndef PAIRS_BLOCKS_MAX
+#define PAIRS_BLOCKS_MAX 7       // pair-kernel blocks resident per SM (its register budget)
+#endif
 struct LaunchTuning {
   int search_window = 512;       // key-order window of the search radius (128, 256, 384, 512)
   int search_chunk = 1;          // queries per work-counter increment
   int search_blocks_per_sm = 8;  // 4-warp blocks per SM (at most 8 are resident)
   int pairs_chunk = 4;
-  int pairs_blocks_per_sm = 6;   // at most 6 are resident
+  int pairs_blocks_per_sm = PAIRS_BLOCKS_MAX;
 };
 int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,
                   double box, int n_ngb, int tol, double fixed_h, int kernel, int split,

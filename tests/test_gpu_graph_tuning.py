@@ -67,7 +67,7 @@ def test_invalid_shapes_are_rejected():
     ctx = sidm.Context()
     before = ctx.tuning
     for bad in (dict(search_window=300), dict(search_chunk=65), dict(search_blocks_per_sm=9),
-                dict(pairs_blocks_per_sm=7)):
+                dict(pairs_blocks_per_sm=8)):
         with pytest.raises(sidm.SidmError) as e:
             ctx.set_tuning(**bad)
         assert e.value.status == sidm.ERR_INVALID_ARG
