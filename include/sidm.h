@@ -222,6 +222,16 @@ SIDM_API int sidm_write_particles(sidm_ctx* ctx, int64_t offset, int64_t count, 
  * becomes one halo over the remaining ones (call sidm_set_haloes next). */
 SIDM_API int sidm_set_count(sidm_ctx* ctx, int64_t n);
 
+/* Moves particles [from, from + count) to [to, to + count) with their
+ * positions, velocities, masses, ids, h and dt limits, on the device and in
+ * their order (overlapping ranges are fine); both ranges lie within the
+ * loaded count.  What was at the destination is overwritten; the source
+ * range keeps its old contents.  A serving loop uses it to close a hole left
+ * by a retired halo.  A halo moved as a whole steps exactly as before: its
+ * results depend on its particles and their order, not on where they sit.
+ * The halo layout is not changed (call sidm_set_haloes next). */
+SIDM_API int sidm_move_particles(sidm_ctx* ctx, int64_t from, int64_t to, int64_t count);
+
 /* Copies the velocities (n x 3, if vel_out is non-NULL) and h (if h_out is
  * non-NULL) of particles [offset, offset + count); waits for the stream and
  * returns the latched status, as sidm_get_particles. */

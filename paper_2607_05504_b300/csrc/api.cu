@@ -893,6 +893,49 @@ int sidm_set_count(sidm_ctx* c, int64_t n) {
   return layout_haloes(c, 1, off);
 }
 
+}  // extern "C"
+
+namespace {
+// Copies `count` elements of `width` doubles (or words) from [from, ...) to
+// [to, ...) within one device array; overlapping ranges are copied in
+// chunks of |from - to| in the safe direction (stream-ordered).
+template <class T>
+cudaError_t move_range(T* base, int64_t width, int64_t from, int64_t to, int64_t count,
+                       cudaStream_t s) {
+  if (count <= 0 || from == to) return cudaSuccess;
+  const int64_t d = from > to ? from - to : to - from;
+  const int64_t step = d < count ? d : count;
+  for (int64_t k = 0; k < count; k += step) {
+    const int64_t len = std::min(step, count - k);
+    const int64_t o = from > to ? k : count - k - len;   // front first when moving down
+    const cudaError_t e = cudaMemcpyAsync(base + width * (to + o), base + width * (from + o),
+                                          (size_t)(width * len) * sizeof(T),
+                                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" {
+
+int sidm_move_particles(sidm_ctx* c, int64_t from, int64_t to, int64_t count) {
+  if (!c || !c->loaded || from < 0 || to < 0 || count < 0 || from + count > c->n ||
+      to + count > c->n)
+    return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  CK(join_velocities(c));
+  cudaStream_t s = c->stream;
+  CK(move_range(c->pos, 3, from, to, count, s));
+  CK(move_range(c->vel, 3, from, to, count, s));
+  CK(move_range(c->mass, 1, from, to, count, s));
+  CK(move_range(c->ids, 1, from, to, count, s));
+  CK(move_range(c->h_user, 1, from, to, count, s));
+  CK(move_range(c->dtlim, 1, from, to, count, s));
+  if (count > 0 && from != to) c->stepped = false;
+  return SIDM_OK;
+}
+
 int sidm_read_particles(sidm_ctx* c, int64_t offset, int64_t count, double* vel_out,
                         double* h_out, int ptr_kind) {
   if (!c || !c->loaded || offset < 0 || count < 0 || offset + count > c->n ||

@@ -15,14 +15,17 @@ request's result does not depend on what else is resident.
 Layers:
   SegmentMap  host logic: the context's particle range [0, capacity) as
               segments, each a resident request or a hole; first-fit
-              placement, holes merged, the unused tail trimmed.
+              placement, holes merged, the unused tail trimmed, and the last
+              resident moved into a hole that holds it (the build work of a
+              tick covers the used range, holes included).
   Scheduler   host logic only (FIFO queue, admission into free segments,
               retirement); no device access.
   GpuEngine   device state: ONE library context sized once for the memory
               budget.  Admission writes only the new request's particles
               into its segment (sidm_write_particles); retirement reads only
-              the finished request's velocities (sidm_read_particles); the
-              resident haloes never move.  The active mask of a tick is
+              the finished request's velocities (sidm_read_particles); a
+              resident moves only to close a hole, device to device
+              (sidm_move_particles).  The active mask of a tick is
               formed on the device from per-particle admission ticks and bin
               periods; the tick's update count is known on the host from each
               request's bin histogram, so a tick needs no device round trip.
@@ -74,12 +77,19 @@ class Request:
         bin histogram: bin b is active every 2^(bmax - b) steps)."""
         if self.n == 0:
             return 0
-        hist = getattr(self, "_hist", None)
-        if hist is None:
-            hist = np.bincount(self.bins.astype(np.int64))
-            self._hist = hist
+        hist = np.bincount(self.bins.astype(np.int64))
         bmax = hist.shape[0] - 1
         return int(sum(int(c) for b, c in enumerate(hist) if c and s % (1 << (bmax - b)) == 0))
+
+    def active_counts(self) -> np.ndarray:
+        """active_count(s) for every step s < n_steps, at once."""
+        if self.n == 0:
+            return np.zeros(self.n_steps, np.int64)
+        hist = np.bincount(self.bins.astype(np.int64))
+        bmax = hist.shape[0] - 1
+        s = np.arange(self.n_steps, dtype=np.int64)[:, None]
+        period = np.left_shift(np.int64(1), bmax - np.arange(hist.shape[0], dtype=np.int64))
+        return ((s % period[None, :]) == 0).astype(np.int64) @ hist.astype(np.int64)
 
 
 class SegmentMap:
@@ -122,6 +132,27 @@ class SegmentMap:
         while self.segs and self.segs[-1][2] is None:
             self.end -= self.segs[-1][1]
             self.segs.pop()
+
+    def compact(self) -> list:
+        """Closes holes: while the last segment (a resident, since a hole at
+        the end is trimmed) fits into a hole before it, it moves into the
+        lowest such hole.  Returns the moves as (owner, old start, new
+        start, n), in order."""
+        moves = []
+        while len(self.segs) > 1:
+            st, m, own = self.segs[-1]
+            k = next((i for i, (hs, hm, ho) in enumerate(self.segs[:-1])
+                      if ho is None and hm >= m), None)
+            if k is None:
+                break
+            new = self.segs[k][0]
+            hole_n = self.segs[k][1]
+            self.segs[k] = [new, m, own]
+            if hole_n > m:
+                self.segs.insert(k + 1, [new + m, hole_n - m, None])
+            self.release(st)
+            moves.append((own, st, new, m))
+        return moves
 
     def offsets(self) -> np.ndarray:
         off = np.zeros(len(self.segs) + 1, np.int64)
@@ -179,6 +210,17 @@ class Scheduler:
         self.resident = [r for r in self.resident if r.steps_done < r.n_steps]
         return done
 
+    def compact(self) -> list:
+        """Moves resident requests from the end of the range into holes (see
+        SegmentMap.compact); returns (request, old start, new start)."""
+        by_id = {r.rid: r for r in self.resident}
+        out = []
+        for own, old, new, _ in self.map.compact():
+            r = by_id[own]
+            r.segment = new
+            out.append((r, old, new))
+        return out
+
     def layout(self) -> list:
         """Segments of the used range: (start, n, request or None)."""
         by_id = {r.rid: r for r in self.resident}
@@ -217,7 +259,9 @@ class GpuEngine:
             self.t0 = t.full((self.capacity,), -1, dtype=t.int64, device=self.dev)
         self.tick = 0
         self.layout: list = []
-        self.params: list = []
+        self.params = None               # ctypes array of HaloParams, one per segment
+        self.resident_k: list = []       # (segment index, request) of the resident requests
+        self.counts: dict = {}           # request id -> active particles at each of its steps
         self.run_ahead = run_ahead
         self.events: collections.deque = collections.deque()
 
@@ -226,6 +270,7 @@ class GpuEngine:
         t = self.torch
         for r in reqs:
             p, st = r.particles, r.segment
+            self.counts[r.rid] = r.active_counts()
             self.ctx.write_particles(st, p.pos, p.vel, p.ids, mass=p.mass)
             bmax = int(r.bins.max()) if r.n else 0
             with t.cuda.stream(self.stream):
@@ -235,6 +280,16 @@ class GpuEngine:
                     t.ones(r.n, dtype=t.int64, device=self.dev), bmax - b.to(t.int64))
                 self.t0[st:st + r.n] = self.tick
         self.relayout(layout)
+
+    def move(self, moves: list) -> None:
+        """Moves resident requests to new segments, on the device (their
+        particles, bins and step phases; their results do not change)."""
+        t = self.torch
+        for r, old, new in moves:
+            self.ctx.move_particles(old, new, r.n)
+            with t.cuda.stream(self.stream):
+                for a in (self.bins, self.period, self.t0):
+                    a[new:new + r.n].copy_(a[old:old + r.n].clone())
 
     def relayout(self, layout: list) -> None:
         """Haloes of the context = the segments (holes are haloes whose
@@ -254,9 +309,14 @@ class GpuEngine:
             off[1:] = np.cumsum([m for _, m, _ in layout])
             self.ctx.set_haloes(off)
         hole = sidm.HaloParams(1.0, sidm.SigmaModel(sidm.SIGMA_CONST, 0.0, 1.0, 0.0), 0, 0)
-        self.params = [hole if r is None else
-                       sidm.HaloParams(r.dt_max, sidm.SigmaModel(r.sigma_kind, r.sigma0, r.w, 0.0),
-                                       r.seed, 0) for _, _, r in layout]
+        self.params = (sidm.HaloParams * max(len(layout), 1))(
+            *[hole if r is None else
+              sidm.HaloParams(r.dt_max, sidm.SigmaModel(r.sigma_kind, r.sigma0, r.w, 0.0),
+                              r.seed, 0) for _, _, r in layout])
+        self.resident_k = [(k, r) for k, (_, _, r) in enumerate(layout) if r is not None]
+        live = {r.rid for _, r in self.resident_k}
+        for rid in [rid for rid in self.counts if rid not in live]:
+            del self.counts[rid]
 
     def step(self) -> int:
         """One scattering step of every resident request; returns the number
@@ -266,22 +326,23 @@ class GpuEngine:
             return 0
         end = self.ctx.n
         n_active = 0
-        for k, (_, _, r) in enumerate(self.layout):
-            if r is not None:
-                self.params[k].step = r.steps_done
-                n_active += r.active_count(r.steps_done)
+        params = self.params
+        for k, r in self.resident_k:
+            params[k].step = r.steps_done
+            n_active += int(self.counts[r.rid][r.steps_done])
         while len(self.events) >= self.run_ahead:     # bound the host's lead
             self.events.popleft().synchronize()
         with t.cuda.stream(self.stream):
             active = (t.remainder(self.tick - self.t0[:end], self.period[:end]) == 0).to(t.uint8)
-        sidm.sidm_step_haloes(self.ctx.handle, active, self.bins[:end], self.params, None)
+        sidm._check(sidm.lib().sidm_step_haloes(self.ctx.handle, active.data_ptr(),
+                                                self.bins[:end].data_ptr(), params, None),
+                    "sidm_step_haloes")
         ev = t.cuda.Event()
         ev.record(self.stream)
         self.events.append(ev)
         self.tick += 1
-        for _, _, r in self.layout:
-            if r is not None:
-                r.steps_done += 1
+        for _, r in self.resident_k:
+            r.steps_done += 1
         return n_active
 
     def collect(self, done: list[Request]) -> None:
@@ -314,10 +375,14 @@ class ServeReport:
 
 
 class Server:
-    def __init__(self, engine, scheduler: Scheduler, clock=time.perf_counter):
+    def __init__(self, engine, scheduler: Scheduler, clock=time.perf_counter, compact=True):
+        """compact: after a retirement, move resident requests from the end of
+        the range into the holes it left (the step's build work follows the
+        used range, holes included)."""
         self.engine = engine
         self.sched = scheduler
         self.clock = clock
+        self.compact = compact
 
     def run(self, requests: list[Request], max_ticks: int = 10 ** 9) -> ServeReport:
         """Serves requests whose .arrival are offsets (s) from the start."""
@@ -343,6 +408,10 @@ class Server:
             if done:
                 self.engine.collect(done)
                 self.sched.retire(self.clock() - t0)
+                if self.compact:
+                    moves = self.sched.compact()
+                    if moves:
+                        self.engine.move(moves)
                 self.engine.relayout(self.sched.layout())
         self.engine.sync()
         rep.wall = self.clock() - t0

@@ -99,7 +99,7 @@ ENTRY_POINTS = ("sidm_default_config", "sidm_create", "sidm_set_particles",
                 "sidm_set_tuning", "sidm_get_tuning", "sidm_autotune", "sidm_graph_state",
                 "sidm_set_sigma_table", "sidm_set_overlap_table", "sidm_overlap_table",
                 "sidm_write_particles", "sidm_set_count", "sidm_read_particles",
-                "sidm_context_bytes")
+                "sidm_context_bytes", "sidm_move_particles")
 
 N_PHASES = 6
 PHASES = ("keys", "sort", "structure", "search", "pairs", "resolve")
@@ -161,6 +161,7 @@ def lib():
         L.sidm_overlap_table.argtypes = [C.c_int, C.c_int32, C.c_int32, vp]
         L.sidm_write_particles.argtypes = [vp, i64, i64, vp, vp, vp, dp, vp, C.c_int]
         L.sidm_set_count.argtypes = [vp, i64]
+        L.sidm_move_particles.argtypes = [vp, i64, i64, i64]
         L.sidm_read_particles.argtypes = [vp, i64, i64, vp, vp, C.c_int]
         L.sidm_context_bytes.argtypes = [C.POINTER(Config), i64, C.POINTER(i64)]
         for name in ENTRY_POINTS:
@@ -239,6 +240,11 @@ def sidm_write_particles(ctx, offset, pos, vel, mass, mass_scalar, ids) -> int:
 
 def sidm_set_count(ctx, n) -> int:
     return _check(lib().sidm_set_count(ctx, int(n)), "sidm_set_count")
+
+
+def sidm_move_particles(ctx, src, dst, count) -> int:
+    return _check(lib().sidm_move_particles(ctx, int(src), int(dst), int(count)),
+                  "sidm_move_particles")
 
 
 def sidm_read_particles(ctx, offset, count, vel_out, h_out=None) -> int:
@@ -491,6 +497,10 @@ class Context:
     def set_count(self, n):
         sidm_set_count(self.handle, n)
         self.n = int(n)
+
+    def move_particles(self, src, dst, count):
+        """Moves particles [src, src + count) to [dst, dst + count)."""
+        sidm_move_particles(self.handle, src, dst, count)
 
     def read_velocities(self, offset, count, out=None):
         """Velocities of particles [offset, offset + count) (numpy unless a

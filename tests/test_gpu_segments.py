@@ -71,3 +71,45 @@ def test_segment_written_into_a_resident_context_steps_as_alone():
     with pytest.raises(sidm.SidmError):
         ctx.write_particles(ctx.n + 1, a.pos[:2], a.vel[:2], a.ids[:2])        # a gap
     ctx.close()
+
+
+def test_a_halo_moved_into_a_hole_steps_as_before():
+    """sidm_move_particles: a halo moved as a whole (to close a hole left by
+    a retired one) continues exactly as if it had stayed."""
+    a = I.hernquist_halo(5000, 31)
+    gone = I.hernquist_halo(7000, 32)
+    b = I.nfw_halo(3000, 33)
+    ba, dta = I.timestep_bins(a, I.hernquist_density, 1.0, 32)
+    bg, dtg = I.timestep_bins(gone, I.hernquist_density, 1.0, 32)
+    bb, dtb = I.timestep_bins(b, I.nfw_density, 2.0, 32)
+    ctx = sidm.Context(n_ngb=32, n_max=20000)
+    z = np.zeros((0, 3))
+    ctx.set_particles(z, z, np.zeros(0, np.uint32), mass_scalar=1.0)
+    for off, h in ((0, a), (a.n, gone), (a.n + gone.n, b)):
+        ctx.write_particles(off, h.pos, h.vel, h.ids, mass=h.mass)
+    ctx.set_haloes([0, a.n, a.n + gone.n, a.n + gone.n + b.n])
+
+    def params(s, sb, three=True):
+        p = [sidm.HaloParams(dta, sidm.SigmaModel(0, 1.0, 1.0), 1, s)]
+        if three:
+            p.append(sidm.HaloParams(dtg, sidm.SigmaModel(0, 1.0, 1.0), 2, s))
+        p.append(sidm.HaloParams(dtb, sidm.SigmaModel(0, 1.0, 1.0), 3, sb))
+        return p
+
+    for s in range(3):
+        act = np.concatenate([I.active_at_step(ba, s), I.active_at_step(bg, s),
+                              I.active_at_step(bb, s)])
+        sidm.sidm_step_haloes(ctx.handle, act, np.concatenate([ba, bg, bb]), params(s, s), None)
+    # the middle halo retires; b moves down into its place and the tail goes
+    ctx.move_particles(a.n + gone.n, a.n, b.n)
+    ctx.set_count(a.n + b.n)
+    ctx.set_haloes([0, a.n, a.n + b.n])
+    for s in range(3, 6):
+        act = np.concatenate([I.active_at_step(ba, s), I.active_at_step(bb, s)])
+        sidm.sidm_step_haloes(ctx.handle, act, np.concatenate([ba, bb]), params(s, s, False),
+                              None)
+    va = ctx.read_velocities(0, a.n)
+    vb = ctx.read_velocities(a.n, b.n)
+    ctx.close()
+    assert np.array_equal(va, _alone(a, ba, dta, 6, 1)[0])
+    assert np.array_equal(vb, _alone(b, bb, dtb, 6, 3)[0])

@@ -15,6 +15,7 @@ class FakeEngine:
         self.steps = 0
         self.layout = []
         self.writes = []
+        self.moves = []
 
     def admit(self, reqs, layout):
         self.writes += [(r.rid, r.segment, r.n) for r in reqs]
@@ -28,6 +29,9 @@ class FakeEngine:
         for st, m, _ in layout:
             assert st == pos
             pos += m
+
+    def move(self, moves):
+        self.moves += [(r.rid, old, new) for r, old, new in moves]
 
     def step(self):
         self.steps += 1
@@ -112,11 +116,34 @@ def test_segment_map_first_fit_merge_and_trim():
     assert m.end == 0 and m.segs == [] and m.free == 1000
 
 
-def test_resident_requests_never_move():
+def test_compaction_moves_the_last_resident_into_the_lowest_hole():
+    m = S.SegmentMap(1000)
+    for o, n in (("a", 300), ("b", 200), ("c", 100), ("d", 150)):
+        m.place(n, o)
+    m.release(0)                                         # a: hole [0, 300)
+    # d into the hole (the tail trims), then c into what is left of it
+    assert m.compact() == [("d", 600, 0, 150), ("c", 500, 150, 100)]
+    assert [(s[0], s[1], s[2]) for s in m.segs] == [(0, 150, "d"), (150, 100, "c"),
+                                                    (250, 50, None), (300, 200, "b")]
+    assert m.end == 500 and m.compact() == []            # b does not fit into 50
+
+
+def test_resident_requests_move_only_to_close_holes():
     reqs = [_req(0, 400, 2, 0.0), _req(1, 300, 6, 0.0), _req(2, 200, 3, 0.0),
             _req(3, 350, 2, 0.05)]
     eng = FakeEngine()
     S.Server(eng, S.Scheduler(1000.0, 1.0), clock=FakeClock()).run(reqs)
+    # the only moves are into holes below the mover's old segment
+    assert all(new < old for _, old, new in eng.moves)
+    assert all(r.result_vel is not None for r in reqs)
+
+
+def test_resident_requests_never_move_without_compaction():
+    reqs = [_req(0, 400, 2, 0.0), _req(1, 300, 6, 0.0), _req(2, 200, 3, 0.0),
+            _req(3, 350, 2, 0.05)]
+    eng = FakeEngine()
+    S.Server(eng, S.Scheduler(1000.0, 1.0), clock=FakeClock(), compact=False).run(reqs)
+    assert eng.moves == []
     # each request was written once, at its segment, and kept it while resident
     assert sorted(w[0] for w in eng.writes) == [0, 1, 2, 3]
     seg = {w[0]: w[1] for w in eng.writes}
