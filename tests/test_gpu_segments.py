@@ -113,3 +113,19 @@ def test_a_halo_moved_into_a_hole_steps_as_before():
     ctx.close()
     assert np.array_equal(va, _alone(a, ba, dta, 6, 1)[0])
     assert np.array_equal(vb, _alone(b, bb, dtb, 6, 3)[0])
+
+
+@pytest.mark.parametrize("src,dst,count", [(100, 50, 1000), (50, 100, 1000), (0, 3, 997),
+                                           (2000, 0, 700), (10, 10, 5)])
+def test_move_particles_with_overlapping_ranges(src, dst, count):
+    p = I.uniform_box(3000, 1.0, 1.0, 41)
+    ctx = sidm.Context(n_max=3000)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    ctx.move_particles(src, dst, count)
+    v = ctx.read_velocities(0, p.n)
+    want = p.vel.copy()
+    want[dst:dst + count] = p.vel[src:src + count]
+    assert np.array_equal(v, want)
+    with pytest.raises(sidm.SidmError):
+        ctx.move_particles(2500, 0, 600)            # source past the loaded count
+    ctx.close()
