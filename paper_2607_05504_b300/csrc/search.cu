@@ -12,12 +12,18 @@
 //      rounding of coordinates, differences, squares, sums).  Every test
 //      "surely inside / surely outside radius H" becomes one comparison of
 //      the FP32 squared separation with a threshold computed once per H.
-//   2. Radius T: from the key-order window of 128-512 particles around i
-//      (a launch shape, 512 by default; at least K + 1 particles, so 256
-//      where 128 would be too few), an upper bound (within ~2 % above) of
-//      the K-th smallest hi, K = N_ngb + tol + 1: K particles have r <= T.
-//      A halo with at most K particles besides i has no bound: T is
-//      infinite and the whole halo (fewer than SEARCH_CAP) is gathered.
+//   2. Radius T, such that K = N_ngb + tol + 1 particles have r <= T.
+//      First, when i has an h from an earlier search (h_prev, kept in the
+//      h output between steps): T = G h_prev (G = 9/8), kept only when the
+//      gather below finds K entries surely within it; the standard SPH
+//      practice of starting from the last smoothing length, used here to
+//      size the gather only.  Otherwise, from the key-order window of
+//      128-512 particles around i (a launch shape, 512 by default; at least
+//      K + 1 particles, so 256 where 128 would be too few): an upper bound
+//      (within ~2 % above) of the K-th smallest hi.  A halo with at most K
+//      particles besides i has no bound: T is infinite and the whole halo
+//      (fewer than SEARCH_CAP) is gathered.  Every certified T gives the
+//      same h and neighbour list (step 4 counts exactly below T).
 //   3. Gather: every particle whose lower bound is <= T goes into a
 //      shared-memory list (FP32 squared separation, index).  If more than
 //      SEARCH_CAP qualify, T shrinks (count-verified) and the gather repeats.
@@ -52,6 +58,9 @@ constexpr float SQ = 4.76837158203125e-07f;   // 2^-21: slack on squared thresho
 constexpr int WALK_STACK = 128;
 #ifndef LIST_REGS
 #define LIST_REGS 8                            // candidates per lane held in registers
+#endif
+#ifndef SEARCH_HINT_GROW
+#define SEARCH_HINT_GROW 1.125f                // first gather radius / h of the last search
 #endif
 #ifndef SEARCH_LEAF_BATCH
 #define SEARCH_LEAF_BATCH 2                    // leaves per L2 round trip in the gather walk
@@ -171,127 +180,159 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
     const float eq = ABS * (fmaxf(fmaxf(fabsf(fi.x), fabsf(fi.y)), fabsf(fi.z)) + boxf);
     double h;
     int len = 0;
-    float T = INFINITY;  // every j with r <= T (and more) is in the list
+    float T0 = INFINITY;  // radius when no bound is known (fixed h: h itself)
     // the key-order window bounds T only when it holds K particles besides i
     const int64_t W = (int64_t)NWIN * 32 < hn ? (int64_t)NWIN * 32 : hn;
     const bool window_bound = !(A.fixed_h > 0.0) && W - 1 >= K;
-
     if (A.fixed_h > 0.0) {
       h = A.fixed_h;
       float hl, hu;
       float_bounds(h, &hl, &hu);
-      T = hu;
-    } else if (window_bound) {
-      // ---- 2. radius T from the key-order window
-      int64_t w0 = s - W / 2;
-      if (w0 > hs + hn - W) w0 = hs + hn - W;
-      if (w0 < hs) w0 = hs;
-      float wv[NWIN];
-      float vmin = INFINITY, vmax = 0.0f;
-#pragma unroll
-      for (int k = 0; k < NWIN; ++k) {
-        wv[k] = INFINITY;
-        const int64_t j = w0 + k * 32 + lane;
-        if (j < w0 + W && j != s) {
-          wv[k] = sep2f<PERIODIC>(fi, so.f[j], boxf);
-          vmin = fminf(vmin, wv[k]);
-          vmax = fmaxf(vmax, wv[k]);
-        }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
-        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-      }
-      // bit-pattern bisection for t with #{wv <= t} >= K; stop within 2^-6
-      uint32_t blo = __float_as_uint(vmin), bhi = __float_as_uint(vmax);
-      if (blo > 0) --blo;
-      for (int it = 0; it < 32 && bhi - blo > (1u << 17); ++it) {
-        const uint32_t mid = blo + ((bhi - blo) >> 1);
-        const float tm = __uint_as_float(mid);
-        int c = 0;
-#pragma unroll
-        for (int k = 0; k < NWIN; ++k) c += wv[k] <= tm ? 1 : 0;
-        c = warp_sum(c);
-        if (c >= K) bhi = mid; else blo = mid;
-      }
-      T = upper_from_s2(__uint_as_float(bhi), eq);
+      T0 = hu;
     }
+    // h of the particle's last search (0 before its first): the first
+    // gather tries G h_prev, kept only if K entries are surely within it
+    double hp = 0.0;
+    if (SEARCH_HINT_GROW > 0.0f && window_bound) hp = A.h_user[so.orig[s]];
+    bool use_hint = hp > 0.0 && hp < INFINITY;
 
-    // ---- 3. gather every j whose lower bound is <= T
+    // ---- 2-3. radius T and gather of every j whose lower bound is <= T
+    float T = T0;         // every j with r <= T (and more) is in the list
+    bool t_bound = false;  // K particles besides i lie within T
     bool complete = true;
-    for (int attempt = 0;; ++attempt) {
-      len = 0;
-      const float g2 = T < INFINITY ? thr_out2(T * (1.0f + REL), eq) : INFINITY;
-      const float rad = (T + 2.0f * eq) * (1.0f + 4.0f * REL);
-      const float rad2 = rad < INFINITY ? rad * rad : INFINITY;
-      const bool ok = traverse<PERIODIC, false, SEARCH_LEAF_BATCH, WALK_STACK>(
-          A.f, H, hpos, fi, rad2, boxf, stack,
-          [&](const int* kk, const bool* valid, const float4* pj, const bool* on) {
-        // every slot's separation first (independent work), then the appends
-        float s2[SEARCH_LEAF_BATCH];
-        bool keep[SEARCH_LEAF_BATCH];
+    for (;;) {
+      if (use_hint) {
+        float hpl, hpu;
+        float_bounds(hp, &hpl, &hpu);
+        T = __fmul_ru(hpu, SEARCH_HINT_GROW);
+      } else if (window_bound) {
+        // radius from the key-order window: an upper bound (within ~2 %
+        // above) of the K-th smallest hi over the window's particles
+        int64_t w0 = s - W / 2;
+        if (w0 > hs + hn - W) w0 = hs + hn - W;
+        if (w0 < hs) w0 = hs;
+        float wv[NWIN];
+        float vmin = INFINITY, vmax = 0.0f;
 #pragma unroll
-        for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
-          s2[b] = sep2f<PERIODIC>(fi, pj[b], boxf);
-          keep[b] = valid[b] && kk[b] != sl && s2[b] < g2;
-        }
-#pragma unroll
-        for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
-          if (!on[b]) break;
-          const uint32_t m = __ballot_sync(0xffffffffu, keep[b]);
-          if (keep[b]) {
-            const int at = len + __popc(m & lt);
-            if (at < SEARCH_CAP) {
-              lst_r2[at] = s2[b];
-              lst_j[at] = (int32_t)(hs + kk[b]);
-            }
+        for (int k = 0; k < NWIN; ++k) {
+          wv[k] = INFINITY;
+          const int64_t j = w0 + k * 32 + lane;
+          if (j < w0 + W && j != s) {
+            wv[k] = sep2f<PERIODIC>(fi, so.f[j], boxf);
+            vmin = fminf(vmin, wv[k]);
+            vmax = fmaxf(vmax, wv[k]);
           }
-          len += __popc(m);
         }
-      });
-      __syncwarp();
-      if (!ok) { status |= ST_ERR_STACK; complete = false; break; }
-      if (len <= SEARCH_CAP) break;
-      // too many candidates.  With a fixed h the pair kernel walks the tree
-      // itself; otherwise shrink T, keeping a new T only once at least K
-      // particles are certainly within it.
-      if (A.fixed_h > 0.0) {
-        complete = false;
-        len = SEARCH_CAP;
-        break;
+        for (int o = 16; o > 0; o >>= 1) {
+          vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+          vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        }
+        // bit-pattern bisection for t with #{wv <= t} >= K; stop within 2^-6
+        uint32_t blo = __float_as_uint(vmin), bhi = __float_as_uint(vmax);
+        if (blo > 0) --blo;
+        for (int it = 0; it < 32 && bhi - blo > (1u << 17); ++it) {
+          const uint32_t mid = blo + ((bhi - blo) >> 1);
+          const float tm = __uint_as_float(mid);
+          int c = 0;
+#pragma unroll
+          for (int k = 0; k < NWIN; ++k) c += wv[k] <= tm ? 1 : 0;
+          c = warp_sum(c);
+          if (c >= K) bhi = mid; else blo = mid;
+        }
+        T = upper_from_s2(__uint_as_float(bhi), eq);
+      } else {
+        T = T0;
       }
-      if (attempt >= RADIUS_MAX_ITERS) {
-        status |= ST_ERR_SEARCH_CAP;
-        complete = false;
-        len = SEARCH_CAP;
-        break;
-      }
-      float Tn = T * cbrtf(0.5f * (float)SEARCH_CAP / (float)len);
-      bool verified = false;
-      for (int inner = 0; inner < RADIUS_MAX_ITERS; ++inner) {
-        const float in2 = thr_in2(Tn, eq);
-        const float radn = (Tn + 2.0f * eq) * (1.0f + 4.0f * REL);
-        int c = 0;
-        const bool ok2 = traverse<PERIODIC, false, SEARCH_LEAF_BATCH, WALK_STACK>(
-            A.f, H, hpos, fi, radn * radn, boxf, stack,
+      bool ok = true;
+      for (int attempt = 0;; ++attempt) {
+        len = 0;
+        const float g2 = T < INFINITY ? thr_out2(T * (1.0f + REL), eq) : INFINITY;
+        const float rad = (T + 2.0f * eq) * (1.0f + 4.0f * REL);
+        const float rad2 = rad < INFINITY ? rad * rad : INFINITY;
+        ok = traverse<PERIODIC, false, SEARCH_LEAF_BATCH, WALK_STACK>(
+            A.f, H, hpos, fi, rad2, boxf, stack,
             [&](const int* kk, const bool* valid, const float4* pj, const bool* on) {
+          // every slot's separation first (independent work), then the appends
+          float s2[SEARCH_LEAF_BATCH];
+          bool keep[SEARCH_LEAF_BATCH];
 #pragma unroll
           for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
-            const bool in = valid[b] && kk[b] != sl && sep2f<PERIODIC>(fi, pj[b], boxf) < in2;
-            c += __popc(__ballot_sync(0xffffffffu, in));   // invalid slots add 0
+            s2[b] = sep2f<PERIODIC>(fi, pj[b], boxf);
+            keep[b] = valid[b] && kk[b] != sl && s2[b] < g2;
+          }
+#pragma unroll
+          for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
+            if (!on[b]) break;
+            const uint32_t m = __ballot_sync(0xffffffffu, keep[b]);
+            if (keep[b]) {
+              const int at = len + __popc(m & lt);
+              if (at < SEARCH_CAP) {
+                lst_r2[at] = s2[b];
+                lst_j[at] = (int32_t)(hs + kk[b]);
+              }
+            }
+            len += __popc(m);
           }
         });
-        if (!ok2) { status |= ST_ERR_STACK; break; }
-        if (c >= K) { verified = true; break; }
-        Tn = sqrtf(Tn * T);   // too small: move towards the valid T
+        __syncwarp();
+        // the hinted radius is judged once, below
+        if (use_hint) break;
+        if (!ok) { status |= ST_ERR_STACK; complete = false; break; }
+        if (len <= SEARCH_CAP) break;
+        // too many candidates.  With a fixed h the pair kernel walks the tree
+        // itself; otherwise shrink T, keeping a new T only once at least K
+        // particles are certainly within it.
+        if (A.fixed_h > 0.0) {
+          complete = false;
+          len = SEARCH_CAP;
+          break;
+        }
+        if (attempt >= RADIUS_MAX_ITERS) {
+          status |= ST_ERR_SEARCH_CAP;
+          complete = false;
+          len = SEARCH_CAP;
+          break;
+        }
+        float Tn = T * cbrtf(0.5f * (float)SEARCH_CAP / (float)len);
+        bool verified = false;
+        for (int inner = 0; inner < RADIUS_MAX_ITERS; ++inner) {
+          const float in2 = thr_in2(Tn, eq);
+          const float radn = (Tn + 2.0f * eq) * (1.0f + 4.0f * REL);
+          int c = 0;
+          const bool ok2 = traverse<PERIODIC, false, SEARCH_LEAF_BATCH, WALK_STACK>(
+              A.f, H, hpos, fi, radn * radn, boxf, stack,
+              [&](const int* kk, const bool* valid, const float4* pj, const bool* on) {
+#pragma unroll
+            for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
+              const bool in = valid[b] && kk[b] != sl && sep2f<PERIODIC>(fi, pj[b], boxf) < in2;
+              c += __popc(__ballot_sync(0xffffffffu, in));   // invalid slots add 0
+            }
+          });
+          if (!ok2) { status |= ST_ERR_STACK; break; }
+          if (c >= K) { verified = true; break; }
+          Tn = sqrtf(Tn * T);   // too small: move towards the valid T
+        }
+        if (!verified) {
+          status |= ST_ERR_RADIUS;
+          complete = false;
+          len = SEARCH_CAP;
+          break;
+        }
+        T = Tn;
       }
-      if (!verified) {
-        status |= ST_ERR_RADIUS;
-        complete = false;
-        len = SEARCH_CAP;
-        break;
+      if (use_hint) {
+        // kept when the whole list fits and K entries are surely within T
+        use_hint = false;
+        if (ok && len <= SEARCH_CAP) {
+          const float in2 = thr_in2(T, eq);
+          int c = 0;
+          for (int k = lane; k < len; k += 32) c += lst_r2[k] < in2 ? 1 : 0;
+          if (warp_sum(c) >= K) { t_bound = true; break; }
+        }
+        continue;   // the window's radius instead
       }
-      T = Tn;
+      t_bound = window_bound;
+      break;
     }
 
     // ---- 4. bisection on the exact neighbour count
@@ -354,7 +395,7 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
         float hl, hu;
         float_bounds(h, &hl, &hu);
         int c;
-        if (window_bound && hl > T) {
+        if (t_bound && hl > T) {
           c = hi_band + 1;   // K particles lie within T < h
         } else {
           c = count_below(h, hl, hu);
@@ -377,7 +418,7 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
     float_bounds(h, &hl, &hu);
     int* out = A.nb_list + qi * (int64_t)A.nb_stride;
     int cnt = -1;
-    const bool list_covers = complete && (!window_bound || !(hl > T));
+    const bool list_covers = complete && (!t_bound || !(hl > T));
     if (list_covers) {
       float in2, out2;
       thresholds(h, hl, hu, &in2, &out2);
