@@ -57,7 +57,7 @@ constexpr float SQ = 4.76837158203125e-07f;   // 2^-21: slack on squared thresho
 // 1 KB reserved per block).
 constexpr int WALK_STACK = 128;
 #ifndef LIST_REGS
-#define LIST_REGS 8                            // candidates per lane held in registers
+#define LIST_REGS 4                            // candidates per lane held in registers
 #endif
 #ifndef SEARCH_HINT_GROW
 #define SEARCH_HINT_GROW 1.125f                // first gather radius / h of the last search
@@ -142,6 +142,45 @@ __device__ __forceinline__ double half_of(double h) {
   return hw_mul(h, 0.5);
 }
 
+// Radius from the key-order window [w0, w0 + W) around s (warp-collective):
+// an upper bound (within ~2 % above) of the K-th smallest separation from s
+// over the window's particles.  Out of line: it is the rare path once most
+// queries start from their last h, and its registers stay out of the walk's.
+template <bool PERIODIC, int NWIN>
+__device__ __noinline__ float window_radius(const float4* __restrict__ f, int64_t s, int64_t w0,
+                                            int64_t W, float4 fi, float boxf, int K, float eq) {
+  const int lane = threadIdx.x & 31;
+  float wv[NWIN];
+  float vmin = INFINITY, vmax = 0.0f;
+#pragma unroll
+  for (int k = 0; k < NWIN; ++k) {
+    wv[k] = INFINITY;
+    const int64_t j = w0 + k * 32 + lane;
+    if (j < w0 + W && j != s) {
+      wv[k] = sep2f<PERIODIC>(fi, f[j], boxf);
+      vmin = fminf(vmin, wv[k]);
+      vmax = fmaxf(vmax, wv[k]);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  }
+  // bit-pattern bisection for t with #{wv <= t} >= K; stop within 2^-6
+  uint32_t blo = __float_as_uint(vmin), bhi = __float_as_uint(vmax);
+  if (blo > 0) --blo;
+  for (int it = 0; it < 32 && bhi - blo > (1u << 17); ++it) {
+    const uint32_t mid = blo + ((bhi - blo) >> 1);
+    const float tm = __uint_as_float(mid);
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < NWIN; ++k) c += wv[k] <= tm ? 1 : 0;
+    c = warp_sum(c);
+    if (c >= K) bhi = mid; else blo = mid;
+  }
+  return upper_from_s2(__uint_as_float(bhi), eq);
+}
+
 // NWIN: the key-order window of the search radius is 32 NWIN particles.
 template <bool PERIODIC, int NWIN>
 __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
@@ -162,12 +201,16 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
   uint32_t status = 0;
   int nonconv = 0;
 
-  int q = 0, q_end = 0;
+  // queries are claimed a chunk at a time from the work counter; the next
+  // claim is issued as the current chunk starts, so that its round trip
+  // overlaps the chunk's work
+  int q = 0, q_end = 0, q_next = 0;
+  if (lane == 0) q_next = atomicAdd(A.work, A.chunk);
   for (;;) {
     if (q >= q_end) {
-      if (lane == 0) q = atomicAdd(A.work, A.chunk);
-      q = __shfl_sync(0xffffffffu, q, 0);
+      q = __shfl_sync(0xffffffffu, q_next, 0);
       q_end = q + A.chunk;
+      if (lane == 0 && q < n_act) q_next = atomicAdd(A.work, A.chunk);
     }
     if (q >= n_act) break;
     const int64_t qi = q++;
@@ -206,40 +249,10 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
         float_bounds(hp, &hpl, &hpu);
         T = __fmul_ru(hpu, SEARCH_HINT_GROW);
       } else if (window_bound) {
-        // radius from the key-order window: an upper bound (within ~2 %
-        // above) of the K-th smallest hi over the window's particles
         int64_t w0 = s - W / 2;
         if (w0 > hs + hn - W) w0 = hs + hn - W;
         if (w0 < hs) w0 = hs;
-        float wv[NWIN];
-        float vmin = INFINITY, vmax = 0.0f;
-#pragma unroll
-        for (int k = 0; k < NWIN; ++k) {
-          wv[k] = INFINITY;
-          const int64_t j = w0 + k * 32 + lane;
-          if (j < w0 + W && j != s) {
-            wv[k] = sep2f<PERIODIC>(fi, so.f[j], boxf);
-            vmin = fminf(vmin, wv[k]);
-            vmax = fmaxf(vmax, wv[k]);
-          }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
-          vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        }
-        // bit-pattern bisection for t with #{wv <= t} >= K; stop within 2^-6
-        uint32_t blo = __float_as_uint(vmin), bhi = __float_as_uint(vmax);
-        if (blo > 0) --blo;
-        for (int it = 0; it < 32 && bhi - blo > (1u << 17); ++it) {
-          const uint32_t mid = blo + ((bhi - blo) >> 1);
-          const float tm = __uint_as_float(mid);
-          int c = 0;
-#pragma unroll
-          for (int k = 0; k < NWIN; ++k) c += wv[k] <= tm ? 1 : 0;
-          c = warp_sum(c);
-          if (c >= K) bhi = mid; else blo = mid;
-        }
-        T = upper_from_s2(__uint_as_float(bhi), eq);
+        T = window_radius<PERIODIC, NWIN>(so.f, s, w0, W, fi, boxf, K, eq);
       } else {
         T = T0;
       }
@@ -391,13 +404,39 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
       h = H.h0;
       double blo = 0.0, bhi = 0.0;
       bool have_hi = false, conv = false;
-      for (int it = 0; it < BISECT_MAX_EVALS; ++it) {
-        float hl, hu;
-        float_bounds(h, &hl, &hu);
+      // h > T means c(h) >= K: K particles lie within T.  h and T are
+      // positive, so their bit patterns compare as integers.
+      const long long t_bits =
+          t_bound ? __double_as_longlong((double)T) : 0x7FFFFFFFFFFFFFFFll;
+      int it = 0;
+      // While h > T and no lower end is known, each step sets bhi = h and
+      // halves h (the midpoint of 0 and h): the opening run from h0 down to
+      // the first h0 2^-k <= T follows from the exponents.  Taken at once
+      // when every halving is an exact exponent step, as in the loop.
+      {
+        const long long hb = __double_as_longlong(h);
+        if (hb > t_bits) {
+          int k = (int)((hb >> 52) & 0x7FF) - (int)((t_bits >> 52) & 0x7FF);
+          long long hk = hb - ((long long)k << 52);   // h0 2^-k: T's exponent
+          if (hk > t_bits) {
+            ++k;
+            hk -= 1ll << 52;
+          }
+          if (((hk >> 52) & 0x7FF) >= 1 && k < BISECT_MAX_EVALS) {
+            bhi = __longlong_as_double(hk + (1ll << 52));
+            have_hi = true;
+            h = __longlong_as_double(hk);
+            it = k;
+          }
+        }
+      }
+      for (; it < BISECT_MAX_EVALS; ++it) {
         int c;
-        if (t_bound && hl > T) {
-          c = hi_band + 1;   // K particles lie within T < h
+        if (__double_as_longlong(h) > t_bits) {
+          c = hi_band + 1;
         } else {
+          float hl, hu;
+          float_bounds(h, &hl, &hu);
           c = count_below(h, hl, hu);
         }
         if (c >= lo_band && c <= hi_band) { conv = true; break; }
