@@ -255,6 +255,68 @@ struct IsotropicKick {
   __device__ __forceinline__ State overwrite_state(const State&, const State& out) const {
     return out;
   }
+
+  // The prepared kick with its arithmetic spread over a group of GROUP
+  // lanes (lanes GROUP g .. GROUP g + GROUP - 1 of a warp, all of them
+  // calling together): lane s < 3 of the group takes component s (the
+  // difference, v_com and both new velocities), lane 3 takes (m_b g) / M,
+  // lane 4 (m_a g) / M, and every lane the square root.  A warp's FP64
+  // instruction serves all of its lanes at once, so the pair's FP64
+  // instruction stream shrinks from ~70 to ~25; each value is made by the
+  // operations of kick_values, in the same order, so the result is
+  // bit-identical.  The group holds the pair (ia, ib, r) when `active`;
+  // otherwise it only takes part in the shuffles.  Loads and stores as
+  // get_state / set_state.
+  static constexpr int GROUP = 8;
+  __device__ __forceinline__ void scatter_group(const Particles& P, int32_t ia, int32_t ib,
+                                                const Prepared& r, bool active) const {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, sub = lane & (GROUP - 1), base = lane & ~(GROUP - 1);
+    const int k = sub < 3 ? sub : 2;
+    const detail::KickTerms& t = r.kt;
+    double a = 0.0, b = 0.0;
+    if (active) {
+      a = __ldcg(P.vel + 3 * (int64_t)ia + k);
+      b = __ldcg(P.vel + 3 * (int64_t)ib + k);
+    }
+    const double d = __dsub_rn(a, b);
+    const double sq = __dmul_rn(d, d);
+    const double s0 = __shfl_sync(full, sq, base), s1 = __shfl_sync(full, sq, base + 1),
+                 s2 = __shfl_sync(full, sq, base + 2);
+    double g = __dsqrt_rn(__dadd_rn(__dadd_rn(s0, s1), s2));
+    if (!t.elastic) g = __dmul_rn(g, t.eps);
+    // x = m_a v_a + m_b v_b (lanes 0-2), m_b g (lane 3), m_a g (lanes 4-7);
+    // the second product is +0 on lanes 3-7 and adding +0 to m g >= +0
+    // changes nothing
+    const bool comp = sub < 3;
+    const double m1 = comp ? t.ma : (sub == 3 ? t.mb : t.ma);
+    const double v1 = comp ? a : g;
+    const double x = __dadd_rn(__dmul_rn(m1, v1), __dmul_rn(t.mb, comp ? b : 0.0));
+    // x / M, correctly rounded (div_m: Markstein's step, checked)
+    const double q0 = __dmul_rn(x, t.y);
+    double q = __fma_rn(__fma_rn(-t.M, q0, x), t.y, q0);
+    {
+      const double rr = __fma_rn(-t.M, q, x);
+      const unsigned long long qb = (unsigned long long)__double_as_longlong(q);
+      const unsigned long long rb = (unsigned long long)__double_as_longlong(rr);
+      const bool toward0 = ((qb ^ rb) >> 63) != 0;
+      const bool pow2 = (qb & 0xFFFFFFFFFFFFFull) == 0;
+      const long long kk = (long long)((qb >> 52) & 0x7FFu) - 1076 - ((toward0 && pow2) ? 1 : 0);
+      const unsigned long long half_gap =
+          (unsigned long long)__double_as_longlong(t.M) + ((unsigned long long)kk << 52);
+      const bool ok = t.rcp && detail::in_rcp_range(x, false) &&
+                      (rb & 0x7FFFFFFFFFFFFFFFull) < half_gap;
+      if (!ok) q = __ddiv_rn(x, t.M);
+    }
+    const double fa = __shfl_sync(full, q, base + 3), fb = __shfl_sync(full, q, base + 4);
+    const double ek = sub == 0 ? r.e[0] : (sub == 1 ? r.e[1] : r.e[2]);
+    const double na = __dadd_rn(q, __dmul_rn(fa, ek));
+    const double nb = __dsub_rn(q, __dmul_rn(fb, ek));
+    if (active && comp) {
+      __stcg(P.vel + 3 * (int64_t)ia + k, na);
+      __stcg(P.vel + 3 * (int64_t)ib + k, nb);
+    }
+  }
 };
 
 // ------------------------------------------------- application order
@@ -267,6 +329,17 @@ struct has_prepare<M, std::void_t<typename M::Prepared,
                                       std::declval<const PairInfo&>(),
                                       std::declval<const typename M::Particles&>()))>>
     : std::true_type {};
+
+// Detection of the optional group form of scatter_prepared (scatter_group,
+// with GROUP lanes per pair).
+template <class M, class = void>
+struct has_group : std::false_type {};
+template <class M>
+struct has_group<M, std::void_t<decltype(M::GROUP),
+                                decltype(std::declval<const M&>().scatter_group(
+                                    std::declval<const typename M::Particles&>(), int32_t(0),
+                                    int32_t(0), std::declval<const typename M::Prepared&>(),
+                                    true))>> : std::true_type {};
 
 }  // namespace sidm_model
 

@@ -82,6 +82,19 @@ __device__ __forceinline__ void fence_acq_rel() {
   asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
+// A trivially copyable value of lane src, word by word.
+template <class T>
+__device__ __forceinline__ T shfl_value(const T& v, int src) {
+  constexpr int W = (int)((sizeof(T) + 3) / 4);
+  uint32_t w[W] = {};
+  memcpy(w, &v, sizeof(T));
+#pragma unroll
+  for (int i = 0; i < W; ++i) w[i] = __shfl_sync(0xffffffffu, w[i], src);
+  T out;
+  memcpy(&out, w, sizeof(T));
+  return out;
+}
+
 // One interaction through the model: states in, scatter on copies,
 // overwrite_state(in, out) back.
 template <class M>
@@ -238,6 +251,9 @@ __global__ void __launch_bounds__(kThreads) rank_kernel(const sidm_pair* __restr
 // A pending pair, its data gathered (and, where the model allows, its
 // interaction prepared) before its turn; a turn is two acquire loads of the
 // cursors, then the interaction through L2 and the release of both cursors.
+// apply_ready is called by the whole warp each pass, `ready` set on the
+// lanes whose pair has its turn: it applies those pairs, then releases
+// their cursors (one fence, then relaxed stores).
 template <class B, bool PREP = has_prepare<decltype(std::declval<B>().model(sidm_pair{}))>::value>
 struct Turn;
 
@@ -256,12 +272,48 @@ struct Turn<B, true> {
     m = bind.model(r);
     prep = m.prepare(bind.info(r, dirfail), bind.parts);
   }
-  __device__ void apply(const B& bind, unsigned*) const {
-    const typename M::State ia = m.get_state(bind.parts, r.ia), ib = m.get_state(bind.parts, r.ib);
-    typename M::State oa = ia, ob = ib;
-    m.scatter_prepared(oa, ob, prep);
-    m.set_state(bind.parts, r.ia, m.overwrite_state(ia, oa));
-    m.set_state(bind.parts, r.ib, m.overwrite_state(ib, ob));
+  __device__ void release(const Buffers& b) const {
+    st_relaxed(&b.cursor[r.ia], pa + 1);
+    st_relaxed(&b.cursor[r.ib], pb + 1);
+  }
+  __device__ void apply_ready(const B& bind, const Buffers& b, bool ready, unsigned*) const {
+    if constexpr (has_group<M>::value) {
+      // the ready pairs of the warp, 32 / GROUP at a time, each by a group
+      // of GROUP lanes (M::scatter_group)
+      constexpr int G = M::GROUP, NG = 32 / G;
+      const int lane = threadIdx.x & 31, grp = lane / G;
+      __syncwarp();   // the owners' acquire loads come before the group's loads
+      uint32_t rm = __ballot_sync(0xffffffffu, ready);
+      while (rm) {
+        uint32_t mine = rm;
+        for (int i = 0; i < grp; ++i) mine &= mine - 1u;
+        const int owner = mine ? __ffs(mine) - 1 : -1;
+        uint32_t rest = rm;
+#pragma unroll
+        for (int i = 0; i < NG; ++i) rest &= rest - 1u;
+        const int src = owner >= 0 ? owner : lane;
+        const int32_t ia = __shfl_sync(0xffffffffu, r.ia, src);
+        const int32_t ib = __shfl_sync(0xffffffffu, r.ib, src);
+        const typename M::Prepared pr = shfl_value(prep, src);
+        const M mo = shfl_value(m, src);
+        mo.scatter_group(bind.parts, ia, ib, pr, owner >= 0);
+        __syncwarp();   // the group's stores come before the owner's release
+        if ((rm & ~rest) & (1u << lane)) {
+          fence_acq_rel();
+          release(b);
+        }
+        rm = rest;
+      }
+    } else if (ready) {
+      const typename M::State ia = m.get_state(bind.parts, r.ia),
+                              ib = m.get_state(bind.parts, r.ib);
+      typename M::State oa = ia, ob = ib;
+      m.scatter_prepared(oa, ob, prep);
+      m.set_state(bind.parts, r.ia, m.overwrite_state(ia, oa));
+      m.set_state(bind.parts, r.ib, m.overwrite_state(ib, ob));
+      fence_acq_rel();   // release: one fence covers both cursor stores
+      release(b);
+    }
   }
 };
 
@@ -274,8 +326,13 @@ struct Turn<B, false> {
     pa = b.pos_a[p];
     pb = b.pos_b[p];
   }
-  __device__ void apply(const B& bind, unsigned* dirfail) const {
+  __device__ void apply_ready(const B& bind, const Buffers& b, bool ready,
+                              unsigned* dirfail) const {
+    if (!ready) return;
     interact(bind.model(r), bind.parts, bind.info(r, dirfail));
+    fence_acq_rel();
+    st_relaxed(&b.cursor[r.ia], pa + 1);
+    st_relaxed(&b.cursor[r.ib], pb + 1);
   }
 };
 
@@ -290,7 +347,9 @@ __global__ void __launch_bounds__(kThreads) dataflow_kernel(const sidm_pair* __r
   if (!overflowed(st, cap)) {
     const int64_t np = (int64_t)st->n_pending;
     const int64_t gsize = (int64_t)gridDim.x * kThreads;
-    const int64_t t0 = blockIdx.x * (int64_t)kThreads + threadIdx.x;
+    // pending pair k to block k mod G: the pairs (and their FP64 kicks)
+    // spread over every SM, each warp still holding 32 of them
+    const int64_t t0 = threadIdx.x * (int64_t)gridDim.x + blockIdx.x;
     // the thread's first pair, prepared before its turn
     bool first = t0 < np;
     Turn<B> f0;
@@ -298,23 +357,21 @@ __global__ void __launch_bounds__(kThreads) dataflow_kernel(const sidm_pair* __r
       const int32_t p = b.pending[t0];
       f0.load(bind, pairs[p], b, p, &s_dirfail);
     }
+    // passes of the whole warp (apply_ready may work across its lanes)
     int pass = 0;
     bool left = first;
-    for (; left && pass < max_passes; ++pass) {
+    for (; pass < max_passes; ++pass) {
+      if (!__any_sync(0xffffffffu, left)) break;
       left = false;
+      bool ready = false;
       if (first) {
         const int ca = ld_acquire(&b.cursor[f0.r.ia]);
         const int cb = ld_acquire(&b.cursor[f0.r.ib]);
-        if (ca == f0.pa && cb == f0.pb) {
-          f0.apply(bind, &s_dirfail);
-          fence_acq_rel();   // release: one fence covers both cursor stores
-          st_relaxed(&b.cursor[f0.r.ia], f0.pa + 1);
-          st_relaxed(&b.cursor[f0.r.ib], f0.pb + 1);
-          first = false;
-        } else {
-          left = true;
-        }
+        ready = ca == f0.pa && cb == f0.pb;
+        left = !ready;
       }
+      f0.apply_ready(bind, b, ready, &s_dirfail);
+      if (ready) first = false;
       // further pairs of this thread (more pending pairs than threads)
       for (int64_t k = t0 + gsize; k < np; k += gsize) {
         const int32_t p = b.pending[k];

@@ -28,8 +28,11 @@ def _sources():
 
 
 def _deps():
+    # every source and every header the sources include (csrc/*.cuh and the
+    # public headers, sidm_model*.cuh among them)
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + \
-        [os.path.join(ROOT, "include", "sidm.h")]
+        glob.glob(os.path.join(ROOT, "include", "*.h")) + \
+        glob.glob(os.path.join(ROOT, "include", "*.cuh"))
 
 
 def up_to_date() -> bool:
