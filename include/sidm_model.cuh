@@ -258,12 +258,15 @@ struct IsotropicKick {
 
   // The prepared kick with its arithmetic spread over a group of GROUP
   // lanes (lanes GROUP g .. GROUP g + GROUP - 1 of a warp, all of them
-  // calling together): lane s < 3 of the group takes component s (the
-  // difference, v_com and both new velocities), lane 3 takes (m_b g) / M,
-  // lane 4 (m_a g) / M, and every lane the square root.  A warp's FP64
-  // instruction serves all of its lanes at once, so the pair's FP64
-  // instruction stream shrinks from ~70 to ~25; each value is made by the
-  // operations of kick_values, in the same order, so the result is
+  // calling together).  Lane s of the group:
+  //   s = 0, 1, 2: component s of the a-side (m_a v_a, v_com, v_a');
+  //   s = 5, 6, 7: component s - 5 of the b-side (m_b v_b, v_com, v_b');
+  //   s = 3: (m_b g) / M;  s = 4: (m_a g) / M;
+  // every lane the differences and the square root.  A warp's FP64
+  // instruction costs the same for one lane or 32, so the pair's FP64
+  // instruction stream shrinks from ~62 to ~23.  Each value is made by the
+  // operations of kick_values in the same order (v_b' = v_com - (f_b e) as
+  // v_com + (f_b (-e)), which rounds identically), so the result is
   // bit-identical.  The group holds the pair (ia, ib, r) when `active`;
   // otherwise it only takes part in the shuffles.  Loads and stores as
   // get_state / set_state.
@@ -272,7 +275,8 @@ struct IsotropicKick {
                                                 const Prepared& r, bool active) const {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, sub = lane & (GROUP - 1), base = lane & ~(GROUP - 1);
-    const int k = sub < 3 ? sub : 2;
+    const bool side_a = sub < 3, side_b = sub >= 5, comp = side_a || side_b;
+    const int k = side_a ? sub : (side_b ? sub - 5 : 0);
     const detail::KickTerms& t = r.kt;
     double a = 0.0, b = 0.0;
     if (active) {
@@ -285,13 +289,12 @@ struct IsotropicKick {
                  s2 = __shfl_sync(full, sq, base + 2);
     double g = __dsqrt_rn(__dadd_rn(__dadd_rn(s0, s1), s2));
     if (!t.elastic) g = __dmul_rn(g, t.eps);
-    // x = m_a v_a + m_b v_b (lanes 0-2), m_b g (lane 3), m_a g (lanes 4-7);
-    // the second product is +0 on lanes 3-7 and adding +0 to m g >= +0
-    // changes nothing
-    const bool comp = sub < 3;
-    const double m1 = comp ? t.ma : (sub == 3 ? t.mb : t.ma);
-    const double v1 = comp ? a : g;
-    const double x = __dadd_rn(__dmul_rn(m1, v1), __dmul_rn(t.mb, comp ? b : 0.0));
+    // one product per lane: m_a v_a (a-side), m_b v_b (b-side), m_b g, m_a g
+    const double pm = __dmul_rn(side_a || sub == 4 ? t.ma : t.mb, comp ? (side_a ? a : b) : g);
+    // the partner's product (a-side lane s <-> b-side lane s + 5)
+    const double po = __shfl_sync(full, pm, side_a ? lane + 5 : (side_b ? lane - 5 : lane));
+    // x = m_a v_a + m_b v_b on both sides; m g + 0 (exact) on lanes 3, 4
+    const double x = __dadd_rn(side_b ? po : pm, comp ? (side_b ? pm : po) : 0.0);
     // x / M, correctly rounded (div_m: Markstein's step, checked)
     const double q0 = __dmul_rn(x, t.y);
     double q = __fma_rn(__fma_rn(-t.M, q0, x), t.y, q0);
@@ -309,13 +312,9 @@ struct IsotropicKick {
       if (!ok) q = __ddiv_rn(x, t.M);
     }
     const double fa = __shfl_sync(full, q, base + 3), fb = __shfl_sync(full, q, base + 4);
-    const double ek = sub == 0 ? r.e[0] : (sub == 1 ? r.e[1] : r.e[2]);
-    const double na = __dadd_rn(q, __dmul_rn(fa, ek));
-    const double nb = __dsub_rn(q, __dmul_rn(fb, ek));
-    if (active && comp) {
-      __stcg(P.vel + 3 * (int64_t)ia + k, na);
-      __stcg(P.vel + 3 * (int64_t)ib + k, nb);
-    }
+    const double ek = k == 0 ? r.e[0] : (k == 1 ? r.e[1] : r.e[2]);
+    const double nv = __dadd_rn(q, __dmul_rn(side_a ? fa : fb, side_a ? ek : -ek));
+    if (active && comp) __stcg(P.vel + 3 * (int64_t)(side_a ? ia : ib) + k, nv);
   }
 };
 
