@@ -63,10 +63,10 @@ STEP_BYTES = (BUILD_BYTES_N + 48.0, 64.0)   # 308 B x N + 64 B x A
 # pairs_kernel, pairs_walk_kernel, pairs_exact_kernel, limits_kernel) per
 # step of the headline workload, from an ncu capture of this bench's own
 # timed steps (10 graph-replayed steps, tuned shapes, L2 flushed between
-# steps): 16.67 + 36.38 + 0.44 + 10.62 + 9.44 MB.  The velocity permutation
+# steps): 18.28 + 36.46 + 0.44 + 10.62 + 9.44 MB.  The velocity permutation
 # that shares their phase time (40.8 MB) is a build term of the byte model.
 # None once those kernels change and until they are captured again.
-NEIGHBOUR_SCATTER_TRAFFIC = 73.56e6
+NEIGHBOUR_SCATTER_TRAFFIC = 75.24e6
 
 
 def _peaks():
