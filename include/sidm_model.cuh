@@ -307,8 +307,14 @@ struct IsotropicKick {
       const long long kk = (long long)((qb >> 52) & 0x7FFu) - 1076 - ((toward0 && pow2) ? 1 : 0);
       const unsigned long long half_gap =
           (unsigned long long)__double_as_longlong(t.M) + ((unsigned long long)kk << 52);
-      const bool ok = t.rcp && detail::in_rcp_range(x, false) &&
-                      (rb & 0x7FFFFFFFFFFFFFFFull) < half_gap;
+      // a zero numerator is its own quotient (M is positive and in range
+      // when t.rcp); a group without a pair needs no quotient.  Either way
+      // the division below is skipped: a lane that takes it holds the
+      // whole warp for the division's ~650 cycles.
+      const bool xzero = ((unsigned long long)__double_as_longlong(x) << 1) == 0ull;
+      if (t.rcp && xzero) q = x;
+      const bool ok = !active || (t.rcp && (xzero || (detail::in_rcp_range(x, false) &&
+                                                      (rb & 0x7FFFFFFFFFFFFFFFull) < half_gap)));
       if (!ok) q = __ddiv_rn(x, t.M);
     }
     const double fa = __shfl_sync(full, q, base + 3), fb = __shfl_sync(full, q, base + 4);
