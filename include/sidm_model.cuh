@@ -143,8 +143,11 @@ __device__ __forceinline__ KickTerms kick_terms(double ma, double mb, double eps
 // a double, and rounding is monotone, so a kept q lies within half a
 // spacing of x/M: it is the correctly rounded quotient (a quotient of two
 // doubles is never a midpoint).  Otherwise, or when x or M lies outside
-// [2^-500, 2^500) (where a step could under- or overflow), the division.
+// [2^-500, 2^500) (where a step could under- or overflow), the division;
+// a zero x is returned as it is.
 __device__ __forceinline__ double div_m(double x, const KickTerms& t) {
+  // +-0 / M = +-0 exactly for M positive and in range
+  if (t.rcp && ((unsigned long long)__double_as_longlong(x) << 1) == 0ull) return x;
   if (t.rcp && in_rcp_range(x, false)) {
     const double q0 = __dmul_rn(x, t.y);
     const double q = __fma_rn(__fma_rn(-t.M, q0, x), t.y, q0);
