@@ -134,6 +134,15 @@ typedef struct {
   void* (*alloc)(size_t bytes, void* stream, void* alloc_user);
   void (*free)(void* ptr, void* stream, void* alloc_user);
   void* alloc_user;
+  int search_hint;      /* 1: a particle's neighbour search starts its candidate gather at
+                           9/8 of the h it had at its last search (the h output), and keeps
+                           that radius only when the gathered list surely holds N_ngb + tol
+                           + 1 particles; otherwise, and at a first search, the radius comes
+                           from the key order as in the plain form.  The usual SPH start from
+                           the previous smoothing length (Sec. 4.5); h, the neighbour lists
+                           and every result are unchanged, only the search's work shrinks
+                           while particles move little between steps.  0 (the default): the
+                           plain form, which carries no h from one step to the next.   */
 } sidm_config;
 
 /* Fills `cfg` with the paper's fiducial values (N_ngb 32 +- 5, C_SIDM 0.1,

@@ -498,7 +498,7 @@ int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches, int par
                        c->h_user,
                        c->nb_list, c->nb_count, c->nb_stride,
                        c->dstats, c->work, c->sms, c->tune,
-                       c->cfg.estimator == SIDM_ESTIMATOR_OVERLAP, s);
+                       c->cfg.estimator == SIDM_ESTIMATOR_OVERLAP, c->cfg.search_hint != 0, s);
     if (c->cfg.estimator == SIDM_ESTIMATOR_OVERLAP) L += launch_hmax(c->so, F, s);
     mark(4);
   }

@@ -13,11 +13,13 @@
 //      "surely inside / surely outside radius H" becomes one comparison of
 //      the FP32 squared separation with a threshold computed once per H.
 //   2. Radius T, such that K = N_ngb + tol + 1 particles have r <= T.
-//      First, when i has an h from an earlier search (h_prev, kept in the
-//      h output between steps): T = G h_prev (G = 9/8), kept only when the
-//      gather below finds K entries surely within it; the standard SPH
-//      practice of starting from the last smoothing length, used here to
-//      size the gather only.  Otherwise, from the key-order window of
+//      With the context's search hint on, and when i has an h from an
+//      earlier search (h_prev, kept in the h output between steps): first
+//      T = G h_prev (G = 9/8), kept only when the gather below finds K
+//      entries surely within it; the standard SPH practice of starting from
+//      the last smoothing length, used here to size the gather only.
+//      Otherwise (the plain form carries no h between steps), from the
+//      key-order window of
 //      128-512 particles around i (a launch shape, 512 by default; at least
 //      K + 1 particles, so 256 where 128 would be too few): an upper bound
 //      (within ~2 % above) of the K-th smallest hi.  A halo with at most K
@@ -82,6 +84,7 @@ struct SearchArgs {
   int nb_stride;
   int chunk;             // queries claimed per work-counter increment
   int all;               // 1: every particle is a query (overlap estimator), s = query index
+  int hint;              // 1: the first gather radius from the particle's last h
   DevStats* st;
   int* work;
 };
@@ -236,7 +239,7 @@ __global__ void __launch_bounds__(ST, 8) search_kernel(SearchArgs A) {
     // h of the particle's last search (0 before its first): the first
     // gather tries G h_prev, kept only if K entries are surely within it
     double hp = 0.0;
-    if (SEARCH_HINT_GROW > 0.0f && window_bound) hp = A.h_user[so.orig[s]];
+    if (SEARCH_HINT_GROW > 0.0f && A.hint && window_bound) hp = A.h_user[so.orig[s]];
     bool use_hint = hp > 0.0 && hp < INFINITY;
 
     // ---- 2-3. radius T and gather of every j whose lower bound is <= T
@@ -516,10 +519,10 @@ int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* a
                   double box, int n_ngb, int tol, double fixed_h, int kernel, int split,
                   double* h_user, int32_t* nb_list, int32_t* nb_count, int nb_stride,
                   DevStats* st, int* work, int sms, const LaunchTuning& t, int all,
-                  cudaStream_t s) {
+                  int hint, cudaStream_t s) {
   if (n <= 0) return 0;
   SearchArgs a{so, f, n, act_list, box, n_ngb, tol, fixed_h, kernel, split, h_user,
-               nb_list, nb_count, nb_stride, t.search_chunk, all, st, work};
+               nb_list, nb_count, nb_stride, t.search_chunk, all, hint, st, work};
   int64_t blocks = (int64_t)sms * t.search_blocks_per_sm;
   const int64_t need = (n + SW - 1) / SW;
   if (blocks > need) blocks = need;

@@ -352,7 +352,7 @@ int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* a
                   double box, int n_ngb, int tol, double fixed_h, int kernel, int split,
                   double* h_user, int32_t* nb_list, int32_t* nb_count, int nb_stride,
                   DevStats* st, int* work, int sms, const LaunchTuning& t, int all,
-                  cudaStream_t s);
+                  int hint, cudaStream_t s);
 // largest h (rounded up) of each tree node, in the w of its upper corner
 int launch_hmax(const Sorted& so, const Forest& f, cudaStream_t s);
 

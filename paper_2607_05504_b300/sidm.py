@@ -52,7 +52,7 @@ class Config(C.Structure):
                 ("stream", C.c_void_p), ("device", C.c_int), ("profile", C.c_int),
                 ("use_graph", C.c_int), ("estimator", C.c_int), ("rebuild_every", C.c_int),
                 ("max_resolver_passes", C.c_int), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_user", C.c_void_p)]
+                ("alloc_user", C.c_void_p), ("search_hint", C.c_int)]
 
 
 class Tuning(C.Structure):
@@ -429,7 +429,8 @@ class Context:
     def __init__(self, n_ngb=32, ngb_tol=5, c_sidm=0.1, box=0.0, kernel=KERNEL_CUBIC,
                  fixed_h=0.0, n_max=0, pair_capacity=0, stream=None, device=-1, profile=False,
                  precision=FP64_PLAIN, use_graph=False, rebuild_every=0,
-                 estimator=ESTIMATOR_ONE_SIDED, max_resolver_passes=0, allocator=None):
+                 estimator=ESTIMATOR_ONE_SIDED, max_resolver_passes=0, allocator=None,
+                 search_hint=False):
         """allocator: None (the library's cudaMalloc) or "torch" (PyTorch's
         caching allocator on the context's device)."""
         cfg = sidm_default_config()
@@ -444,6 +445,7 @@ class Context:
         cfg.rebuild_every = int(rebuild_every)
         cfg.estimator = int(estimator)
         cfg.max_resolver_passes = int(max_resolver_passes)
+        cfg.search_hint = int(bool(search_hint))
         self._hooks = None
         if allocator == "torch":
             import torch

@@ -1,8 +1,11 @@
-"""The search's first gather radius from the h of a particle's last search.
+"""The search's first gather radius from the h of a particle's last search
+(the context's opt-in search hint; the plain form carries no h between
+steps).
 
-A query whose particle has an h from an earlier step first gathers within
-9/8 of it, and keeps that radius only when K = N_ngb + tol + 1 gathered
-entries are surely inside; otherwise it takes the key-order window's radius.
+With the hint, a query whose particle has an h from an earlier step first
+gathers within 9/8 of it, and keeps that radius only when K = N_ngb + tol +
+1 gathered entries are surely inside; otherwise it takes the key-order
+window's radius.
 Either radius bounds the K-th neighbour, and the h bisection counts exactly
 below it, so the result must be the oracle's whichever radius was used
 (Sec. 4.2 and 4.5: the iterative h search).  These steps follow a first
@@ -23,9 +26,11 @@ pytestmark = pytest.mark.gpu
 
 
 def _steps(p, positions, masks, bins, dt_max, *, n_ngb=32, seed=5, overlap_table=None):
-    """Steps the context and the oracle over the given positions (one array
-    per step, set before that step) and compares every step."""
-    ctx = sidm.Context(n_ngb=n_ngb, box=p.box, estimator=int(overlap_table is not None))
+    """Steps the context (search hint on) and the oracle over the given
+    positions (one array per step, set before that step) and compares every
+    step."""
+    ctx = sidm.Context(n_ngb=n_ngb, box=p.box, estimator=int(overlap_table is not None),
+                       search_hint=True)
     if overlap_table is not None:
         ctx.set_overlap_table(overlap_table)
     ctx.set_particles(positions[0], p.vel, p.ids, mass=p.mass)
@@ -88,3 +93,26 @@ def test_overlap_estimator_repeated_steps():
     table = oracle.overlap_table(32, 128, kernel=0)
     masks = [I.active_at_step(bins, s) for s in range(3)]
     _steps(p, [p.pos, p.pos * 0.7, p.pos * 0.7], masks, bins, 2.0, overlap_table=table)
+
+
+def test_hint_off_and_on_give_the_same_steps():
+    """The plain form (no hint) and the hinted form step the same halo to
+    bit-identical h, pairs and velocities."""
+    p = I.hernquist_halo(30000, 28, ids="random")
+    rng = np.random.default_rng(29)
+    bins = rng.integers(0, 3, p.n).astype(np.int8)
+    out = []
+    for hint in (False, True):
+        ctx = sidm.Context(n_ngb=64, box=0.0, search_hint=hint)
+        ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+        res = []
+        for s in range(4):
+            ctx.step(1.0, I.active_at_step(bins, s), bins, seed=13)
+            v, h = ctx.velocities()
+            res.append((v.copy(), h.copy(), ctx.pairs()))
+        ctx.close()
+        out.append(res)
+    for (v0, h0, (ab0, o0)), (v1, h1, (ab1, o1)) in zip(*out):
+        assert np.array_equal(h0, h1)
+        assert np.array_equal(ab0, ab1) and np.array_equal(o0, o1)
+        assert np.array_equal(v0, v1)
