@@ -389,7 +389,7 @@ SIDM_API int sidm_overlap_table(int kernel, int32_t na, int32_t ns, double* out)
  * results; only the time changes.  Zero fields take the defaults. */
 typedef struct {
   int search_window;        /* key-order window that bounds each search radius:
-                               128, 256, 384 or 512 (default) particles; a window
+                               128, 256, 384, 512 (default), 768 or 1024 particles; a window
                                of fewer than n_ngb + ngb_tol + 2 particles runs as
                                256                                                   */
   int search_chunk;         /* queries a search warp claims at a time, 1..64 (1)      */

@@ -1002,7 +1002,7 @@ namespace {
 
 bool valid_tuning(const LaunchTuning& t) {
   return (t.search_window == 128 || t.search_window == 256 || t.search_window == 384 ||
-          t.search_window == 512) &&
+          t.search_window == 512 || t.search_window == 768 || t.search_window == 1024) &&
          t.search_chunk >= 1 && t.search_chunk <= 64 && t.search_blocks_per_sm >= 1 &&
          t.search_blocks_per_sm <= 8 && t.pairs_chunk >= 1 && t.pairs_chunk <= 64 &&
          t.pairs_blocks_per_sm >= 1 && t.pairs_blocks_per_sm <= PAIRS_BLOCKS_MAX;
@@ -1295,7 +1295,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
   float cur_ms = 0.f;
   if (rc == SIDM_OK) rc = time_candidate(c, active_mask, dt_bins, reps, v0, h0, d0, step0, &cur_ms);
   // coordinate search over the launch shapes
-  const int windows[] = {128, 256, 384, 512};
+  const int windows[] = {128, 256, 384, 512, 768, 1024};
   const int chunks[] = {1, 2, 4, 8, 16};
   const int sblocks[] = {4, 6, 8};
   const int pblocks[] = {4, 6, 7};
@@ -1314,7 +1314,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
       }
     }
   };
-  try_field(&LaunchTuning::search_window, windows, 4);
+  try_field(&LaunchTuning::search_window, windows, (int)(sizeof(windows) / sizeof(windows[0])));
   try_field(&LaunchTuning::search_chunk, chunks, 5);
   try_field(&LaunchTuning::search_blocks_per_sm, sblocks, 3);
   try_field(&LaunchTuning::pairs_chunk, chunks, 5);

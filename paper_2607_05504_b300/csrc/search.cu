@@ -512,7 +512,9 @@ void launch_search_window(const SearchArgs& a, int window, unsigned blocks, cuda
   if (window <= 128) search_kernel<PERIODIC, 4><<<blocks, ST, 0, s>>>(a);
   else if (window <= 256) search_kernel<PERIODIC, 8><<<blocks, ST, 0, s>>>(a);
   else if (window <= 384) search_kernel<PERIODIC, 12><<<blocks, ST, 0, s>>>(a);
-  else search_kernel<PERIODIC, 16><<<blocks, ST, 0, s>>>(a);
+  else if (window <= 512) search_kernel<PERIODIC, 16><<<blocks, ST, 0, s>>>(a);
+  else if (window <= 768) search_kernel<PERIODIC, 24><<<blocks, ST, 0, s>>>(a);
+  else search_kernel<PERIODIC, 32><<<blocks, ST, 0, s>>>(a);
 }
 
 int launch_search(const Sorted& so, const Forest& f, int64_t n, const int32_t* act_list,

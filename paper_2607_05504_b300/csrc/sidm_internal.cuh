@@ -342,7 +342,7 @@ int tree_levels_for(int64_t n, int64_t count[MAX_LEVELS]);
 #define PAIRS_BLOCKS_MAX 7       // pair-kernel blocks resident per SM (its register budget)
 #endif
 struct LaunchTuning {
-  int search_window = 512;       // key-order window of the search radius (128, 256, 384, 512)
+  int search_window = 512;       // key-order window of the search radius (128 .. 1024)
   int search_chunk = 1;          // queries per work-counter increment
   int search_blocks_per_sm = 8;  // 4-warp blocks per SM (at most 8 are resident)
   int pairs_chunk = 4;

@@ -55,6 +55,8 @@ def test_graph_replay_is_bit_identical():
          pairs_blocks_per_sm=3),
     dict(search_window=512, search_chunk=16, search_blocks_per_sm=6, pairs_chunk=1,
          pairs_blocks_per_sm=4),
+    dict(search_window=768, search_chunk=2),
+    dict(search_window=1024, search_chunk=4, search_blocks_per_sm=8),
 ])
 def test_launch_shapes_do_not_change_results(tune):
     p, bins, dt = _halo(seed=22)
@@ -82,7 +84,7 @@ def test_autotune_leaves_the_state_and_results_unchanged():
     ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
     prm = [sidm.HaloParams(dt, sidm.SigmaModel(0, 1.0, 1.0), 5, 0)]
     best = ctx.autotune(prm, I.active_at_step(bins, 0), bins, reps=2)
-    assert best["search_window"] in (128, 256, 384, 512)
+    assert best["search_window"] in (128, 256, 384, 512, 768, 1024)
     assert ctx.tuning == best
     assert ctx.step_counter == 0
     v, _ = ctx.velocities()
