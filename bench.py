@@ -68,6 +68,13 @@ STEP_BYTES = (BUILD_BYTES_N + 48.0, 64.0)   # 308 B x N + 64 B x A
 # None once those kernels change and until they are captured again.
 NEIGHBOUR_SCATTER_TRAFFIC = 73.51e6
 
+# Warp instructions the search kernel issues per query on this workload, from
+# an ncu capture of the bench's first timed launch (smsp__inst_executed.sum /
+# queries: 230.7 M / 51,520), and the B300's issue rate: one warp instruction
+# per scheduler per clock, 4 schedulers per SM, 148 SMs, 2032 MHz maximum.
+SEARCH_INST_PER_QUERY = 4478.0
+ISSUE_PEAK = 148 * 4 * 2032e6          # warp instructions per second
+
 
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -847,6 +854,15 @@ def main():
                 "peak_kind": peak_kind,
                 "search_only": {"achieved": ns_bytes / (ph["search"] * 1e-3) / 1e9,
                                 "frac": ns_bytes / (ph["search"] * 1e-3) / 1e9 / hbm_peak},
+                # the search's binding resource is instruction issue, not HBM
+                "search_issue": {"bound": "issue",
+                                 "achieved": SEARCH_INST_PER_QUERY * a_mean / (ph["search"] * 1e-3),
+                                 "peak": ISSUE_PEAK, "unit": "warp instructions/s",
+                                 "frac": SEARCH_INST_PER_QUERY * a_mean / (ph["search"] * 1e-3)
+                                 / ISSUE_PEAK,
+                                 "note": "ncu warp instructions per query x active queries per "
+                                         "step / live search time, against 148 SMs x 4 "
+                                         "schedulers x 2032 MHz"},
                 "build": {"bytes": BUILD_BYTES_N * n, "ms": build_ms,
                           "achieved": BUILD_BYTES_N * n / (build_ms * 1e-3) / 1e9,
                           "frac": BUILD_BYTES_N * n / (build_ms * 1e-3) / 1e9 / hbm_peak},
