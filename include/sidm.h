@@ -319,10 +319,15 @@ SIDM_API int sidm_get_changed(sidm_ctx* ctx, int32_t* idx_out, double* vel_out, 
 /* Brings a host copy of the velocities up to date after a step: vel_inout
  * (host memory, n x 3) holds the velocities before the last step; the
  * velocities the step changed are written into it, and nothing else is
- * touched.  Only the changed particles cross the bus (as with
- * sidm_get_changed, into pinned staging of the context's own, allocated on
- * the first call), then a host loop scatters them.  Waits for the stream;
- * returns the latched status of the last step. */
+ * touched.  Only the changed particles cross the bus.  If vel_inout is
+ * pinned host memory that the device can address (cudaHostAlloc or
+ * cudaHostRegister memory on a system with unified addressing, such as
+ * PyTorch's pinned tensors), a kernel writes each changed particle's
+ * velocity straight into it; the pinned range must then cover all n x 3
+ * doubles.  Otherwise they go, as with sidm_get_changed, into pinned staging
+ * of the context's own (allocated on the first such call), and a host loop
+ * scatters them.  Waits for the stream; returns the latched status of the
+ * last step. */
 SIDM_API int sidm_update_velocities(sidm_ctx* ctx, double* vel_inout);
 
 /* Copies the Eq. 18 limit of every particle from its last active step

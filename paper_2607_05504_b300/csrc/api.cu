@@ -1393,6 +1393,21 @@ int sidm_update_velocities(sidm_ctx* c, double* vel_inout) {
   if (!c->loaded || c->n <= 0 || !c->stepped) return SIDM_OK;
   DeviceGuard g(c->device);
   const int64_t n = c->n;
+  // pinned host memory that the device addresses: the changed particles are
+  // written into it from the device, with no staging and no host loop
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, vel_inout) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+      pa.devicePointer) {
+    CK(join_velocities(c));
+    if (++c->chg_call == 0) c->chg_call = 1;   // stamps start at 0
+    c->launches += launch_changed_to_host(c->pairs, c->pair_cap, c->dstats, c->chg_call,
+                                          c->chg_stamps, c->vel,
+                                          static_cast<double*>(pa.devicePointer), c->sms,
+                                          c->stream);
+    CK(cudaGetLastError());
+    return wait_and_collect(c);
+  }
+  cudaGetLastError();   // a pointer the runtime does not know is not an error here
   if (c->h_chg_cap < n) {
     if (c->h_chg_idx) cudaFreeHost(c->h_chg_idx);
     if (c->h_chg_vel) cudaFreeHost(c->h_chg_vel);

@@ -400,5 +400,8 @@ int conserved_blocks();
 int launch_changed(const PairRec* pairs, int64_t cap, const DevStats* st, uint32_t stamp,
                    uint32_t* stamps, const double* vel, int32_t* idx_out, double* vel_out,
                    unsigned long long* count, int sms, cudaStream_t s);
+int launch_changed_to_host(const PairRec* pairs, int64_t cap, const DevStats* st,
+                           uint32_t stamp, uint32_t* stamps, const double* vel,
+                           double* host_vel, int sms, cudaStream_t s);
 
 }  // namespace sidm

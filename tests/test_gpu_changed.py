@@ -74,3 +74,45 @@ def test_update_velocities_keeps_a_host_copy_current():
     with pytest.raises(sidm.SidmError):
         sidm.sidm_update_velocities(ctx.handle, host.astype(np.float32))
     ctx.close()
+
+
+def test_update_velocities_into_pinned_memory_writes_from_the_device():
+    """A pinned host array (device-addressable) takes the changed particles'
+    velocities straight from the device: it stays equal to the full
+    read-back, and entries of particles the step did not change keep
+    whatever they held."""
+    torch = pytest.importorskip("torch")
+    p = I.hernquist_halo(15000, 49, ids="random")
+    bins = np.random.default_rng(50).integers(0, 3, p.n).astype(np.int8)
+    ctx = sidm.Context(n_ngb=32, use_graph=True)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    host = torch.from_numpy(p.vel.copy()).pin_memory().numpy()
+    pageable = p.vel.copy()
+    marked = torch.full((p.n, 3), np.nan, dtype=torch.float64).pin_memory().numpy()
+    # the same, 8 bytes past a 16-byte boundary (one store per component)
+    shifted = torch.from_numpy(np.concatenate([[0.0], p.vel.ravel()])).pin_memory().numpy()
+    shifted = shifted[1:].reshape(p.n, 3)
+    assert shifted.ctypes.data % 16 == 8
+    launches = ctx.kernel_launches
+    sidm.sidm_update_velocities(ctx.handle, host)       # no step yet: untouched
+    assert np.array_equal(host, p.vel)
+    assert ctx.kernel_launches == launches
+    for k in range(5):
+        ctx.step(2.0, I.active_at_step(bins, k), bins, seed=51, stats=False)
+        before = ctx.kernel_launches
+        sidm.sidm_update_velocities(ctx.handle, host)
+        assert ctx.kernel_launches == before + 1       # the direct write, no staging
+        sidm.sidm_update_velocities(ctx.handle, pageable)
+        sidm.sidm_update_velocities(ctx.handle, marked)
+        sidm.sidm_update_velocities(ctx.handle, shifted)
+        after = ctx.velocities()[0]
+        assert np.array_equal(host, after), k
+        assert np.array_equal(shifted, after), k
+        assert np.array_equal(pageable, after), k
+        idx, v = ctx.changed()
+        hit = np.zeros(p.n, bool)
+        hit[idx] = True
+        assert np.array_equal(marked[hit], after[hit])
+        assert np.isnan(marked[~hit]).all()
+        marked[:] = np.nan
+    ctx.close()
