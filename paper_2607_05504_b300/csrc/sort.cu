@@ -13,8 +13,9 @@
 //      already holds an inclusive prefix) and publishes its own inclusive
 //      prefix.  Each of the 16 warps ranks the keys of its own 256-key part
 //      of the tile among the earlier keys of the same digit (peers found by
-//      one vote per digit bit, warp-private counters, no block barrier), so
-//      a tile needs four barriers.
+//      one vote per digit bit, warp-private counters, no block barrier),
+//      the tile is put in digit order in shared memory, and runs of equal
+//      digits are written out by consecutive threads.
 // A slot is one 32-bit word holding a 2-bit state and a 30-bit count, so a
 // reader sees the state and the count together without a fence.  Six
 // launches per sort (a memset, the histogram, four passes) instead of a
@@ -77,27 +78,40 @@ __global__ void __launch_bounds__(OS_THREADS) os_hist_kernel(const uint32_t* __r
 
 // A pass runs PASS_THREADS threads on each 4096-key tile: warp w ranks keys
 // [w 32 PASS_ITEMS, (w + 1) 32 PASS_ITEMS) of the tile; the per-digit work
-// (tile counts, look-back, digit starts) is done by the first RADIX threads.
+// (tile counts, scans, look-back) is done by the first RADIX threads.  The
+// tile is put in digit order in shared memory before the look-back (which
+// then runs with the keys out of registers), and written out in runs of
+// equal digits, so that neighbouring threads write neighbouring places.
 constexpr int PASS_THREADS = 512;
 constexpr int PASS_ITEMS = OS_TILE / PASS_THREADS;
 constexpr int PASS_WARPS = PASS_THREADS / WARP;
+constexpr int DIGIT_WARPS = RADIX / WARP;
 static_assert(PASS_THREADS >= RADIX && PASS_ITEMS * PASS_THREADS == OS_TILE, "pass tiling");
+static_assert(PASS_WARPS * RADIX == OS_TILE, "the warp counters and the tile's keys share memory");
 
-__global__ void __launch_bounds__(PASS_THREADS) os_pass_kernel(
+__global__ void __launch_bounds__(PASS_THREADS, 2) os_pass_kernel(
     const uint32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int64_t n, int pass,
     const uint32_t* __restrict__ counts, uint32_t* tile_ctr, uint32_t* slots, unsigned* status) {
   __shared__ uint32_t s_tile;
-  __shared__ uint32_t s_cnt[PASS_WARPS][RADIX];   // per warp: keys of each digit, then their start
-  __shared__ uint32_t s_wsum[RADIX / WARP];
+  // per warp: keys of each digit, then the warp's start within the digit;
+  // afterwards the tile's keys in digit order
+  __shared__ uint32_t s_cnt_key[PASS_WARPS * RADIX];
+  __shared__ int32_t s_val[OS_TILE];
+  __shared__ uint32_t s_wsum[2][DIGIT_WARPS];
+  __shared__ uint32_t s_tstart[RADIX];   // start of each digit within the tile
+  __shared__ int32_t s_off[RADIX];       // output place minus tile place, per digit
+  uint32_t(*s_cnt)[RADIX] = reinterpret_cast<uint32_t(*)[RADIX]>(s_cnt_key);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const bool digit_thread = t < RADIX;               // thread t owns digit t
   const int shift = 8 * pass;
   if (t == 0) s_tile = atomicAdd(&tile_ctr[pass], 1u);
-  for (int i = t; i < PASS_WARPS * RADIX; i += PASS_THREADS) (&s_cnt[0][0])[i] = 0;
+  for (int i = t; i < PASS_WARPS * RADIX; i += PASS_THREADS) s_cnt_key[i] = 0;
   __syncthreads();
   const int64_t tile = s_tile;
-  const int64_t base = tile * OS_TILE + (int64_t)warp * (PASS_ITEMS * WARP);
+  const int64_t tbase = tile * OS_TILE;
+  const int64_t base = tbase + (int64_t)warp * (PASS_ITEMS * WARP);
+  const int tn = (int)(n - tbase < OS_TILE ? n - tbase : OS_TILE);   // keys in the tile
 
   // 1. rank every key among the earlier keys of its digit in the warp's
   //    part of the tile (warp-private counters, no block barrier)
@@ -131,80 +145,111 @@ __global__ void __launch_bounds__(PASS_THREADS) os_pass_kernel(
   }
   __syncthreads();
 
-  // 2. the tile's count of digit t; publish it, then look back over the
-  //    earlier tiles
-  uint32_t cnt = 0, excl = 0;
+  // 2. the tile's count of digit t, published at once; each warp's start
+  //    within the digit; scans over the digits of the tile's counts and of
+  //    the global counts
+  uint32_t cnt = 0, g = 0, ic = 0, ig = 0;
   if (digit_thread) {
-#pragma unroll
-    for (int w = 0; w < PASS_WARPS; ++w) cnt += s_cnt[w][t];
-    uint32_t* my = slots + tile * RADIX + t;
-    st_relaxed_u32(my, (tile == 0 ? SLOT_PRE : SLOT_AGG) | cnt);
-    if (tile > 0) {
-      // slots j, j-1, ... are loaded LOOKBACK_BATCH at a time and consumed in
-      // order until an inclusive prefix; a slot not yet published is
-      // reloaded (the earlier tile's block is resident and publishes before
-      // it waits on anything; the wait is bounded nonetheless)
-      int64_t j = tile - 1;
-      int spins = 0;
-      bool done = false;
-      while (!done) {
-        uint32_t v[LOOKBACK_BATCH];
-#pragma unroll
-        for (int k = 0; k < LOOKBACK_BATCH; ++k)
-          v[k] = j - k >= 0 ? ld_relaxed_u32(slots + (j - k) * RADIX + t) : 0u;
-        bool stall = false;
-#pragma unroll
-        for (int k = 0; k < LOOKBACK_BATCH; ++k) {
-          if (done || stall) continue;
-          const uint32_t state = v[k] & SLOT_STATE;
-          if (state == 0u) { stall = true; continue; }
-          excl += v[k] & SLOT_VALUE;
-          if (state == SLOT_PRE || j == 0) done = true;
-          else --j;
-        }
-        if (stall && ++spins > LOOKBACK_MAX_SPINS) {
-          atomicOr(status, (unsigned)ST_ERR_SORT);
-          break;
-        }
-      }
-      st_relaxed_u32(my, SLOT_PRE | (excl + cnt));
-    }
-  }
-
-  // 3. start of digit t in the output (keys of smaller digits, then the
-  //    earlier tiles' keys of digit t), then of each warp's run of it
-  uint32_t g = 0, inc = 0;
-  if (digit_thread) {
-    g = counts[pass * RADIX + t];
-    inc = g;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_wsum[warp] = inc;
-  }
-  __syncthreads();
-  if (digit_thread) {
-    uint32_t run = inc - g + excl;
-    for (int w = 0; w < warp; ++w) run += s_wsum[w];
 #pragma unroll
     for (int w = 0; w < PASS_WARPS; ++w) {
       const uint32_t c = s_cnt[w][t];
-      s_cnt[w][t] = run;
-      run += c;
+      s_cnt[w][t] = cnt;
+      cnt += c;
+    }
+    st_relaxed_u32(slots + tile * RADIX + t, (tile == 0 ? SLOT_PRE : SLOT_AGG) | cnt);
+    g = counts[pass * RADIX + t];
+    ic = cnt;
+    ig = g;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t yc = __shfl_up_sync(0xffffffffu, ic, o);
+      const uint32_t yg = __shfl_up_sync(0xffffffffu, ig, o);
+      if (lane >= o) {
+        ic += yc;
+        ig += yg;
+      }
+    }
+    if (lane == 31) {
+      s_wsum[0][warp] = ic;
+      s_wsum[1][warp] = ig;
     }
   }
   __syncthreads();
+  if (digit_thread) {
+    uint32_t tc = ic - cnt, tg = ig - g;
+    for (int w = 0; w < warp; ++w) {
+      tc += s_wsum[0][w];
+      tg += s_wsum[1][w];
+    }
+    s_tstart[t] = tc;
+    ig = tg;   // keys of smaller digits, over all tiles
+  }
+  __syncthreads();
 
-  // 4. scatter (stable: warp, then round, then lane is the input order)
+  // 3. each key's place in the tile's digit order, then the tile in that
+  //    order (the keys over the counters, which are no longer needed)
 #pragma unroll
   for (int r = 0; r < PASS_ITEMS; ++r) {
-    const int64_t i = base + (int64_t)r * WARP + lane;
-    if (i < n) {
-      const uint32_t pos = s_cnt[warp][(key[r] >> shift) & 255u] + rank[r];
-      keys_out[pos] = key[r];
-      vals_out[pos] = val[r];
+    const uint32_t d = (key[r] >> shift) & 255u;
+    rank[r] += s_tstart[d] + s_cnt[warp][d];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < PASS_ITEMS; ++r) {
+    if (base + (int64_t)r * WARP + lane < n) {
+      s_cnt_key[rank[r]] = key[r];
+      s_val[rank[r]] = val[r];
+    }
+  }
+
+  // 4. look back over the earlier tiles: slots j, j-1, ... are loaded
+  //    LOOKBACK_BATCH at a time and consumed in order until an inclusive
+  //    prefix; a slot not yet published is reloaded (the earlier tile's
+  //    block is resident and publishes before it waits on anything; the
+  //    wait is bounded nonetheless)
+  uint32_t excl = 0;
+  if (digit_thread && tile > 0) {
+    int64_t j = tile - 1;
+    int spins = 0;
+    bool done = false;
+    while (!done) {
+      uint32_t v[LOOKBACK_BATCH];
+#pragma unroll
+      for (int k = 0; k < LOOKBACK_BATCH; ++k)
+        v[k] = j - k >= 0 ? ld_relaxed_u32(slots + (j - k) * RADIX + t) : 0u;
+      bool stall = false;
+#pragma unroll
+      for (int k = 0; k < LOOKBACK_BATCH; ++k) {
+        if (done || stall) continue;
+        const uint32_t state = v[k] & SLOT_STATE;
+        if (state == 0u) {
+          stall = true;
+          continue;
+        }
+        excl += v[k] & SLOT_VALUE;
+        if (state == SLOT_PRE || j == 0) done = true;
+        else --j;
+      }
+      if (stall && ++spins > LOOKBACK_MAX_SPINS) {
+        atomicOr(status, (unsigned)ST_ERR_SORT);
+        break;
+      }
+    }
+    st_relaxed_u32(slots + tile * RADIX + t, SLOT_PRE | (excl + cnt));
+  }
+  // output place of tile place i with digit t: keys of smaller digits, the
+  // earlier tiles' keys of digit t, then i's place within the digit's run
+  if (digit_thread) s_off[t] = (int32_t)(ig + excl) - (int32_t)s_tstart[t];
+  __syncthreads();
+
+  // 5. scatter (stable: warp, then round, then lane is the input order);
+  //    consecutive threads write consecutive places of a digit's run
+  for (int i = t; i < tn; i += PASS_THREADS) {
+    const uint32_t k = s_cnt_key[i];
+    const int64_t pos = (int64_t)s_off[(k >> shift) & 255u] + i;
+    if (pos >= 0 && pos < n) {
+      keys_out[pos] = k;
+      vals_out[pos] = s_val[i];
     }
   }
 }
