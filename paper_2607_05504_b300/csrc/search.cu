@@ -54,9 +54,9 @@ constexpr float CREL = REL + ABS;             // relative part of the bounds
 constexpr float SQ = 4.76837158203125e-07f;   // 2^-21: slack on squared thresholds
 // The gather walk visits leaves without stacking them, so its stack holds at
 // most 31 entries for each internal level below the root except the lowest,
-// plus one: 31 * 4 + 1 = 125 for the 6 levels of n < 2^30.  128 entries keep
-// a block's shared memory at 26 KB, so that 8 blocks fit on an SM (228 KB,
-// 1 KB reserved per block).
+// plus one: 31 * 4 + 1 = 125 for the 6 levels of n < 2^30.  128 entries (2 KB
+// per block) beside the candidate lists keep a block's shared memory at
+// 18 KB.
 constexpr int WALK_STACK = 128;
 #ifndef LIST_REGS
 #define LIST_REGS 4                            // candidates per lane held in registers

@@ -19,7 +19,15 @@ constexpr int WARP = 32;
 constexpr int LEAF = 32;                 // particles per tree leaf (one per lane)
 constexpr int MAX_LEVELS = 8;            // 32-ary levels: 32^8 leaves >> any n
 constexpr int BISECT_MAX_EVALS = 128;    // neighbour-count evaluations per particle
-constexpr int SEARCH_CAP = 768;          // gathered candidates per query (shared memory)
+// Gathered candidates per query (shared memory; a query that gathers more
+// shrinks its radius and gathers again).  512 entries keep a search block at
+// 18 KB of shared memory, which leaves ~80 KB of each SM's L1 to the walk's
+// position and box loads at 8 blocks per SM (768 entries: 27 KB per block,
+// ~30 KB of L1, and a search ~4.5 % slower on the 2^20 halo).
+#ifndef SEARCH_CAP_ENTRIES
+#define SEARCH_CAP_ENTRIES 512
+#endif
+constexpr int SEARCH_CAP = SEARCH_CAP_ENTRIES;
 constexpr int SEARCH_STACK = 256;        // traversal stack per warp (>= 31 MAX_LEVELS + 1)
 constexpr int RADIUS_MAX_ITERS = 24;     // gather-radius adjustments per query
 constexpr int RESOLVE_MAX_ROUNDS = 4096; // resolver rounds
