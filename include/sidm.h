@@ -397,8 +397,11 @@ typedef struct {
                                128, 256, 384, 512 (default), 768 or 1024 particles; a window
                                of fewer than n_ngb + ngb_tol + 2 particles runs as
                                256                                                   */
-  int search_chunk;         /* queries a search warp claims at a time, 1..64 (1)      */
-  int search_blocks_per_sm; /* search blocks of 4 warps launched per SM, 1..8 (8)     */
+  int search_chunk;         /* a search block (32 warps, one query per warp at a time)
+                               claims ranges of 32 x search_chunk consecutive queries,
+                               1..64 (1)                                             */
+  int search_blocks_per_sm; /* search blocks launched per SM, 1..8 (1); one is resident
+                               at a time, the others start as blocks finish          */
   int pairs_chunk;          /* queries a pair warp claims at a time, 1..64 (4)        */
   int pairs_blocks_per_sm;  /* pair blocks of 4 warps per SM, 1..7 (7)                */
 } sidm_tuning;

@@ -1297,7 +1297,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
   // coordinate search over the launch shapes
   const int windows[] = {128, 256, 384, 512, 768, 1024};
   const int chunks[] = {1, 2, 4, 8, 16};
-  const int sblocks[] = {4, 6, 8};
+  const int sranges[] = {1, 2};   // ranges of 32 and 64 queries per search block
   const int pblocks[] = {4, 6, 7};
   auto try_field = [&](int LaunchTuning::*field, const int* vals, int nv) {
     for (int k = 0; k < nv && rc == SIDM_OK; ++k) {
@@ -1315,8 +1315,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
     }
   };
   try_field(&LaunchTuning::search_window, windows, (int)(sizeof(windows) / sizeof(windows[0])));
-  try_field(&LaunchTuning::search_chunk, chunks, 5);
-  try_field(&LaunchTuning::search_blocks_per_sm, sblocks, 3);
+  try_field(&LaunchTuning::search_chunk, sranges, 2);
   try_field(&LaunchTuning::pairs_chunk, chunks, 5);
   try_field(&LaunchTuning::pairs_blocks_per_sm, pblocks, 3);
   // leave the simulation where it was

@@ -44,6 +44,7 @@ enum : uint32_t {
   ST_ERR_PAIR_OVERFLOW = 1u << 11,// accepted-pair buffer full
   ST_ERR_ROUNDS = 1u << 12,       // resolver did not finish within its round cap
   ST_ERR_SORT = 1u << 13,         // key sort: a look-back wait gave up (order not valid)
+  ST_ERR_CLAIM = 1u << 15,        // search: a block's wait for its next query range gave up
   ST_ERR_MASK = 0xFF00u
 };
 
@@ -351,8 +352,8 @@ int tree_levels_for(int64_t n, int64_t count[MAX_LEVELS]);
 #endif
 struct LaunchTuning {
   int search_window = 512;       // key-order window of the search radius (128 .. 1024)
-  int search_chunk = 1;          // queries per work-counter increment
-  int search_blocks_per_sm = 8;  // 4-warp blocks per SM (at most 8 are resident)
+  int search_chunk = 1;          // a search block claims ranges of 32 search_chunk queries
+  int search_blocks_per_sm = 1;  // 32-warp blocks per SM (one is resident at a time)
   int pairs_chunk = 4;
   int pairs_blocks_per_sm = PAIRS_BLOCKS_MAX;
 };
