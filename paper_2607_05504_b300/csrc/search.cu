@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(ST, 1) search_kernel(SearchArgs A) {
 
 }  // namespace
 
-constexpr size_t SEARCH_SMEM = (size_t)SW * (SEARCH_CAP * 8 + WALK_STACK * 4);   // 147 KB
+constexpr size_t SEARCH_SMEM = (size_t)SW * (SEARCH_CAP * 8 + WALK_STACK * 4);   // 131 KB
 template <bool PERIODIC, int NWIN>
 void launch_one(const SearchArgs& a, unsigned blocks, cudaStream_t s) {
   // above the default 48 KB of dynamic shared memory (set for the current

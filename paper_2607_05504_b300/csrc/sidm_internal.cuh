@@ -20,12 +20,13 @@ constexpr int LEAF = 32;                 // particles per tree leaf (one per lan
 constexpr int MAX_LEVELS = 8;            // 32-ary levels: 32^8 leaves >> any n
 constexpr int BISECT_MAX_EVALS = 128;    // neighbour-count evaluations per particle
 // Gathered candidates per query (shared memory; a query that gathers more
-// shrinks its radius and gathers again).  512 entries keep a search block at
-// 18 KB of shared memory, which leaves ~80 KB of each SM's L1 to the walk's
-// position and box loads at 8 blocks per SM (768 entries: 27 KB per block,
-// ~30 KB of L1, and a search ~4.5 % slower on the 2^20 halo).
+// shrinks its radius and gathers again).  With 448 entries the 32 warps of
+// an SM's search block hold 131 KB of shared memory, which leaves ~120 KB of
+// L1 to the walks' position and box loads.  On the 2^20 halo: 768 entries
+// 0.576 ms per search (4-warp blocks, ~30 KB of L1), 512 entries 0.550, and
+// with the 32-warp blocks 512 entries 0.507, 384 or 448 entries 0.500.
 #ifndef SEARCH_CAP_ENTRIES
-#define SEARCH_CAP_ENTRIES 512
+#define SEARCH_CAP_ENTRIES 448
 #endif
 constexpr int SEARCH_CAP = SEARCH_CAP_ENTRIES;
 constexpr int SEARCH_STACK = 256;        // traversal stack per warp (>= 31 MAX_LEVELS + 1)
