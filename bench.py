@@ -902,25 +902,40 @@ def main():
             sidm.sidm_get_particles(ectx.handle, out_v)   # waits for the step
             eu += n_active[s]
         et_full = time.perf_counter() - t0
-        # (b) the host holds the simulation's velocities: they go in, and only
-        # the particles the step changed come back, written by the device
-        # straight into the same (pinned) host array (sidm_update_velocities)
-        host_v = pin(vel_h.copy())
+        # (b) the host holds the simulation's velocities in one pinned array:
+        # they go in each step, and the kicks write every velocity they change
+        # straight back into it (sidm_set_velocity_mirror); the step's result
+        # is on the host once the stream is done
+        def host_loop(host_v, readback):
+            eu_, t0_ = 0, time.perf_counter()
+            for k in range(K2):
+                s = (args.warmup + k) % CYCLE
+                sidm.sidm_set_positions(ectx.handle, pos_h)
+                sidm.sidm_set_velocities(ectx.handle, host_v)
+                sidm.sidm_step(ectx.handle, masks_h[s], bins_h, w["dt_max"], sg, 0, None)
+                readback(host_v)                                 # waits for the step
+                eu_ += n_active[s]
+            return eu_, time.perf_counter() - t0_
+
         step0 = ectx.step_counter
+        host_v = pin(vel_h.copy())
+        ectx.set_velocity_mirror(host_v)
         for k in range(2):                                     # warm-up, untimed
             sidm.sidm_step(ectx.handle, masks_h[1 + k], bins_h, w["dt_max"], sg, 0, None)
-            sidm.sidm_update_velocities(ectx.handle, host_v)
+        sidm.sidm_sync(ectx.handle)
         ectx.step_counter = step0
         host_v[:] = vel_h
-        eu2, t0 = 0, time.perf_counter()
-        for k in range(K2):
-            s = (args.warmup + k) % CYCLE
-            sidm.sidm_set_positions(ectx.handle, pos_h)
-            sidm.sidm_set_velocities(ectx.handle, host_v)
-            sidm.sidm_step(ectx.handle, masks_h[s], bins_h, w["dt_max"], sg, 0, None)
-            sidm.sidm_update_velocities(ectx.handle, host_v)   # waits for the step
-            eu2 += n_active[s]
-        et = time.perf_counter() - t0
+        eu2, et = host_loop(host_v, lambda hv: sidm.sidm_sync(ectx.handle))
+        ectx.set_velocity_mirror(None)
+        # (c) the same through sidm_update_velocities after each step (the
+        # changed particles written by one kernel after the step)
+        host_u = pin(vel_h.copy())
+        for k in range(2):                                     # warm-up, untimed
+            sidm.sidm_step(ectx.handle, masks_h[1 + k], bins_h, w["dt_max"], sg, 0, None)
+            sidm.sidm_update_velocities(ectx.handle, host_u)
+        ectx.step_counter = step0
+        host_u[:] = vel_h
+        eu3, et3 = host_loop(host_u, lambda hv: sidm.sidm_update_velocities(ectx.handle, hv))
         # the same steps again, untimed, from the same step counter: the
         # particles that crossed the bus, and the host array they give
         ectx.step_counter = step0
@@ -940,10 +955,15 @@ def main():
         e2e = {"value": eu2 / et, "unit": UNIT,
                "h2d_bytes_per_step": int(n * (24 + 24) + n + n),
                "d2h_bytes_per_step": int(4 + 24 * nchg / K2),
-               "readback": "sidm_update_velocities into the host's pinned velocity array: the "
-                           "device writes the velocities of the particles the step changed "
-                           "(the two particles of each accepted pair) into it",
-               "replay_identical": bool(np.array_equal(host_c, host_v)),
+               "readback": "sidm_set_velocity_mirror: the kicks write the final velocity of "
+                           "every particle the step changes into the host's pinned velocity "
+                           "array, which is uploaded from and kept current in place",
+               "replay_identical": bool(np.array_equal(host_c, host_v) and
+                                        np.array_equal(host_c, host_u)),
+               "update_velocities": {"value": eu3 / et3,
+                                     "readback": "sidm_update_velocities after each step: one "
+                                                 "kernel writes the changed particles into the "
+                                                 "pinned array"},
                "full_readback": {"value": eu / et_full, "d2h_bytes_per_step": int(4 + n * 24),
                                  "readback": "all velocities (sidm_get_particles)"}}
 

@@ -316,6 +316,22 @@ SIDM_API int sidm_get_particles(sidm_ctx* ctx, double* vel_out, double* h_out, i
 SIDM_API int sidm_get_changed(sidm_ctx* ctx, int32_t* idx_out, double* vel_out, int64_t cap,
                               int64_t* n_out, int ptr_kind);
 
+/* Keeps a host copy of the velocities current from the device: from the
+ * next step on, each step writes the velocity of every particle it changes
+ * into host_vel (user order, n x 3 doubles) as soon as that particle's last
+ * kick of the step is applied, so the copy is complete when the step's work
+ * on the stream is (sidm_sync, or any call that waits for the stream).
+ * Entries of particles a step does not change are not touched: host_vel
+ * must already hold the velocities the step starts from (those set or
+ * loaded, as uploaded from this same array by sidm_set_velocities).
+ * host_vel must be pinned host memory the device can address (cudaHostAlloc
+ * or cudaHostRegister memory on a system with unified addressing, such as
+ * PyTorch's pinned tensors) and hold n particles; a step of a context with
+ * more particles than n returns SIDM_ERR_INVALID_ARG.  NULL stops the
+ * writes.  Waits for the stream; sidm_autotune's trial steps do not write
+ * the copy.  SIDM_ERR_INVALID_ARG if host_vel is not such memory. */
+SIDM_API int sidm_set_velocity_mirror(sidm_ctx* ctx, double* host_vel, int64_t n);
+
 /* Brings a host copy of the velocities up to date after a step: vel_inout
  * (host memory, n x 3) holds the velocities before the last step; the
  * velocities the step changed are written into it, and nothing else is

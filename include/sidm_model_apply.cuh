@@ -19,6 +19,10 @@
  *      resident), the globally first unapplied pair is always ready, and a
  *      bounded number of passes guards against a stuck state (error flag);
  *   5. reset of the per-particle arrays that were touched.
+ * A binder may define publish(e): it is called once for every particle an
+ * application changes, right after that particle's last interaction of the
+ * application (its state is then final), by the thread that applied it;
+ * the step uses it to copy velocities into a host-side mirror.
  * This is the single-device counterpart of the paper's rule that no particle
  * is modified concurrently (Sec. 4.5).
  */
@@ -93,6 +97,22 @@ __device__ __forceinline__ T shfl_value(const T& v, int src) {
   T out;
   memcpy(&out, w, sizeof(T));
   return out;
+}
+
+// Detection of the binder's optional publish(e) (see the top of this file).
+template <class B, class = void>
+struct has_publish : std::false_type {};
+template <class B>
+struct has_publish<B, std::void_t<decltype(std::declval<const B&>().publish(int32_t(0)))>>
+    : std::true_type {};
+
+// publish(e) of a particle whose pair at place `place` of its segment of
+// `mult` pairs has just been applied, if that was its last pair
+template <class B>
+__device__ __forceinline__ void publish_if_last(const B& bind, int32_t e, int place, int mult) {
+  if constexpr (has_publish<B>::value) {
+    if (place + 1 == mult) bind.publish(e);
+  }
 }
 
 // One interaction through the model: states in, scatter on copies,
@@ -176,6 +196,8 @@ __global__ void __launch_bounds__(kThreads, 4) split_kernel(const sidm_pair* __r
         mm = max(mm, max(ma, mb));
         if (ma == 1 && mb == 1) {
           interact(bind.model(r), bind.parts, bind.info(r, &s_dirfail));
+          publish_if_last(bind, r.ia, 0, 1);
+          publish_if_last(bind, r.ib, 0, 1);
         } else {
           pend = true;
           b.flags[p] = 0;
@@ -262,6 +284,7 @@ struct Turn<B, true> {
   using M = decltype(std::declval<B>().model(sidm_pair{}));
   sidm_pair r;
   int pa, pb;
+  int ma = 0, mb = 0;   // pairs of each particle (read only for publish)
   typename M::Prepared prep;
   M m;
   __device__ void load(const B& bind, const sidm_pair& rr, const Buffers& b, int32_t p,
@@ -269,12 +292,20 @@ struct Turn<B, true> {
     r = rr;
     pa = b.pos_a[p];
     pb = b.pos_b[p];
+    if constexpr (has_publish<B>::value) {
+      ma = b.mult[r.ia];
+      mb = b.mult[r.ib];
+    }
     m = bind.model(r);
     prep = m.prepare(bind.info(r, dirfail), bind.parts);
   }
   __device__ void release(const Buffers& b) const {
     st_relaxed(&b.cursor[r.ia], pa + 1);
     st_relaxed(&b.cursor[r.ib], pb + 1);
+  }
+  __device__ void publish(const B& bind) const {
+    publish_if_last(bind, r.ia, pa, ma);
+    publish_if_last(bind, r.ib, pb, mb);
   }
   __device__ void apply_ready(const B& bind, const Buffers& b, bool ready, unsigned*) const {
     if constexpr (has_group<M>::value) {
@@ -301,6 +332,7 @@ struct Turn<B, true> {
         if ((rm & ~rest) & (1u << lane)) {
           fence_acq_rel();
           release(b);
+          publish(bind);
         }
         rm = rest;
       }
@@ -313,6 +345,7 @@ struct Turn<B, true> {
       m.set_state(bind.parts, r.ib, m.overwrite_state(ib, ob));
       fence_acq_rel();   // release: one fence covers both cursor stores
       release(b);
+      publish(bind);
     }
   }
 };
@@ -321,10 +354,15 @@ template <class B>
 struct Turn<B, false> {
   sidm_pair r;
   int pa, pb;
+  int ma = 0, mb = 0;   // pairs of each particle (read only for publish)
   __device__ void load(const B&, const sidm_pair& rr, const Buffers& b, int32_t p, unsigned*) {
     r = rr;
     pa = b.pos_a[p];
     pb = b.pos_b[p];
+    if constexpr (has_publish<B>::value) {
+      ma = b.mult[r.ia];
+      mb = b.mult[r.ib];
+    }
   }
   __device__ void apply_ready(const B& bind, const Buffers& b, bool ready,
                               unsigned* dirfail) const {
@@ -333,6 +371,8 @@ struct Turn<B, false> {
     fence_acq_rel();
     st_relaxed(&b.cursor[r.ia], pa + 1);
     st_relaxed(&b.cursor[r.ib], pb + 1);
+    publish_if_last(bind, r.ia, pa, ma);
+    publish_if_last(bind, r.ib, pb, mb);
   }
 };
 
@@ -386,6 +426,10 @@ __global__ void __launch_bounds__(kThreads) dataflow_kernel(const sidm_pair* __r
           st_relaxed(&b.cursor[r.ia], pa + 1);
           st_relaxed(&b.cursor[r.ib], pb + 1);
           b.flags[p] = 1;
+          if constexpr (has_publish<B>::value) {
+            publish_if_last(bind, r.ia, pa, b.mult[r.ia]);
+            publish_if_last(bind, r.ib, pb, b.mult[r.ib]);
+          }
         } else {
           left = true;
         }

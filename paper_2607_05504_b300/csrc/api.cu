@@ -101,6 +101,10 @@ struct sidm_ctx {
   int32_t* h_chg_idx = nullptr;     // pinned staging of sidm_update_velocities
   double* h_chg_vel = nullptr;
   int64_t h_chg_cap = 0;
+  // pinned host copy of the velocities kept current by the kicks
+  // (sidm_set_velocity_mirror): its device address and its length in particles
+  double* mirror = nullptr;
+  int64_t mirror_n = 0;
   bool stepped = false;             // a step ran since the particles were loaded
   // key order kept between full rebuilds
   uint64_t order_version = 0;   // layout of the last full rebuild
@@ -520,8 +524,8 @@ int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches, int par
                       c->pairs, c->dtlim, c->dstats, c->work + 1, c->sms, c->tune, s);
     mark(5);
     const int nr = launch_resolve(c->pairs, c->pair_cap, c->cfg.max_resolver_passes, c->vel,
-                                  c->mass, c->halo_of,
-                                  c->d_halos, c->rb, c->dstats, c->sms, s);
+                                  c->mass, c->halo_of, c->d_halos, c->mirror, c->rb, c->dstats,
+                                  c->sms, s);
     if (nr < 0) return SIDM_ERR_CUDA;
     L += nr;
     mark(6);
@@ -578,6 +582,7 @@ void capture_core(sidm_ctx* c, int rebuild) {
 int run_step(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins,
              sidm_step_stats* stats) {
   if (c->cfg.estimator == SIDM_ESTIMATOR_OVERLAP && c->ov.na <= 0) return SIDM_ERR_NOT_READY;
+  if (c->mirror && c->n > c->mirror_n) return SIDM_ERR_INVALID_ARG;   // the copy is too short
   const int64_t n = c->n;
   cudaStream_t s = c->stream;
   if (n > 0) {
@@ -1281,8 +1286,10 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
   const int64_t since0 = c->since_rebuild;
   const uint64_t order0 = c->order_version;
   const int use_graph = c->cfg.use_graph, rebuild_every = c->cfg.rebuild_every;
+  double* const mirror = c->mirror;
   c->cfg.use_graph = 0;      // candidates launch directly
   c->cfg.rebuild_every = 0;  // and rebuild fully, like the steps they stand for
+  c->mirror = nullptr;       // and leave the host copy of the velocities alone
   int rc = SIDM_OK;
   if (cudaMemcpyAsync(v0, c->vel, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream) !=
           cudaSuccess ||
@@ -1323,6 +1330,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
   ++c->layout_version;
   c->cfg.use_graph = use_graph;
   c->cfg.rebuild_every = rebuild_every;
+  c->mirror = mirror;
   cudaMemcpyAsync(c->vel, v0, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   cudaMemcpyAsync(c->h_user, h0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
   cudaMemcpyAsync(c->dtlim, d0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
@@ -1385,6 +1393,26 @@ int sidm_get_changed(sidm_ctx* c, int32_t* idx_out, double* vel_out, int64_t cap
   }
   *n_out = cnt;
   return wait_and_collect(c);
+}
+
+int sidm_set_velocity_mirror(sidm_ctx* c, double* host_vel, int64_t n) {
+  if (!c || (host_vel && n < 0)) return SIDM_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  double* dev = nullptr;
+  if (host_vel) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, host_vel) != cudaSuccess || pa.type != cudaMemoryTypeHost ||
+        !pa.devicePointer || (reinterpret_cast<uintptr_t>(pa.devicePointer) & 7) != 0) {
+      cudaGetLastError();
+      return SIDM_ERR_INVALID_ARG;
+    }
+    dev = static_cast<double*>(pa.devicePointer);
+  }
+  CK(cudaStreamSynchronize(c->stream));   // no earlier step still writes the old copy
+  c->mirror = dev;
+  c->mirror_n = host_vel ? n : 0;
+  ++c->layout_version;                     // a captured step holds the old address
+  return SIDM_OK;
 }
 
 int sidm_update_velocities(sidm_ctx* c, double* vel_inout) {

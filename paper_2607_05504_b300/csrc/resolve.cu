@@ -29,6 +29,18 @@ struct HaloBinder {
   IsotropicKick::Particles parts;
   const int32_t* halo_of;
   const Halo* halos;
+  double* mirror;        // device address of a pinned host copy of the velocities, or null
+  // a particle's final velocity of the step into the host copy, read back
+  // from L2 (the kick stores there); three 8-byte stores
+  __device__ __forceinline__ void publish(int32_t e) const {
+    if (!mirror) return;
+    const double* v = parts.vel + 3 * (int64_t)e;
+    const double v0 = __ldcg(v), v1 = __ldcg(v + 1), v2 = __ldcg(v + 2);
+    double* d = mirror + 3 * (int64_t)e;
+    d[0] = v0;
+    d[1] = v1;
+    d[2] = v2;
+  }
   __device__ __forceinline__ IsotropicKick model(const PairRec& r) const {
     IsotropicKick m;
     m.eps = halos[halo_of[r.ia]].eps;
@@ -137,8 +149,9 @@ __global__ void __launch_bounds__(RT) resolve_kernel(const PairRec* __restrict__
 
 int launch_resolve(PairRec* pairs, int64_t pair_cap, int max_passes, double* vel,
                    const double* mass, const int32_t* halo_of, const Halo* halos,
-                   const ResolveBuffers& b, DevStats* st, int sms, cudaStream_t s) {
-  const HaloBinder bind{IsotropicKick::Particles{vel, mass}, halo_of, halos};
+                   double* mirror, const ResolveBuffers& b, DevStats* st, int sms,
+                   cudaStream_t s) {
+  const HaloBinder bind{IsotropicKick::Particles{vel, mass}, halo_of, halos, mirror};
   return sidm_model::detail::launch_apply(pairs, pair_cap, max_passes, bind, b, st, sms, s);
 }
 
@@ -151,5 +164,6 @@ void launch_resolve_with_scratch(const PairRec* pairs, int64_t pair_cap, double*
   resolve_kernel<<<1, RT, 0, s>>>(pairs, pair_cap, vel, mass, head, next, flags, mult,
                                   (uint32_t)seed, (uint32_t)(seed >> 32), step, st);
 }
+
 
 }  // namespace sidm

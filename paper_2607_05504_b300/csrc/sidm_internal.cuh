@@ -395,9 +395,12 @@ static_assert(ST_DIR_FAIL == sidm_model::detail::kDirFail &&
                   ST_ERR_PAIR_OVERFLOW == sidm_model::detail::kErrPairOverflow,
               "status bits shared with the application templates");
 // max_passes: bound on the dataflow passes (0: the built-in 2^22)
+// mirror: device address of a pinned host copy of the velocities that the
+// kicks keep current (null: none)
 int launch_resolve(PairRec* pairs, int64_t pair_cap, int max_passes, double* vel,
                    const double* mass, const int32_t* halo_of, const Halo* halos,
-                   const ResolveBuffers& b, DevStats* st, int sms, cudaStream_t s);
+                   double* mirror, const ResolveBuffers& b, DevStats* st, int sms,
+                   cudaStream_t s);
 void launch_resolve_with_scratch(const PairRec* pairs, int64_t pair_cap, double* vel,
                                  const double* mass, int32_t* head, int32_t* next, uint8_t* flags,
                                  int32_t* mult, uint64_t seed, uint32_t step, DevStats* st,

@@ -92,7 +92,8 @@ class StepStats(C.Structure):
 
 # names of every entry point declared in include/sidm.h
 ENTRY_POINTS = ("sidm_default_config", "sidm_create", "sidm_set_particles",
-                "sidm_set_velocities", "sidm_set_positions", "sidm_get_changed", "sidm_update_velocities", "sidm_step", "sidm_sync", "sidm_get_particles",
+                "sidm_set_velocities", "sidm_set_positions", "sidm_get_changed", "sidm_update_velocities",
+                "sidm_set_velocity_mirror", "sidm_step", "sidm_sync", "sidm_get_particles",
                 "sidm_timestep_limits", "sidm_get_pairs", "sidm_get_step", "sidm_set_step",
                 "sidm_phase_times", "sidm_kernel_launches", "sidm_error_string", "sidm_destroy",
                 "sidm_apply_pairs_noalloc", "sidm_set_haloes", "sidm_step_haloes",
@@ -134,6 +135,7 @@ def lib():
         L.sidm_set_positions.argtypes = [vp, vp, C.c_int]
         L.sidm_get_changed.argtypes = [vp, vp, vp, i64, C.POINTER(i64), C.c_int]
         L.sidm_update_velocities.argtypes = [vp, vp]
+        L.sidm_set_velocity_mirror.argtypes = [vp, vp, i64]
         L.sidm_step.argtypes = [vp, vp, vp, dp, C.POINTER(SigmaModel), C.c_uint64,
                                 C.POINTER(StepStats)]
         L.sidm_sync.argtypes = [vp]
@@ -374,6 +376,21 @@ def sidm_update_velocities(ctx, vel_inout) -> int:
                   "sidm_update_velocities")
 
 
+def sidm_set_velocity_mirror(ctx, host_vel) -> int:
+    """From the next step on, the device writes every changed velocity into
+    host_vel (n x 3 float64, C-contiguous, pinned memory the device can
+    address, e.g. a numpy view of a pinned torch tensor); None stops it.
+    The array must stay alive while it is set."""
+    if host_vel is None:
+        return _check(lib().sidm_set_velocity_mirror(ctx, None, 0), "sidm_set_velocity_mirror")
+    if not (isinstance(host_vel, np.ndarray) and host_vel.dtype == np.float64 and
+            host_vel.flags.c_contiguous and host_vel.ndim == 2 and host_vel.shape[1] == 3):
+        raise SidmError(ERR_INVALID_ARG, "sidm_set_velocity_mirror: host float64 (n, 3) array")
+    return _check(lib().sidm_set_velocity_mirror(ctx, host_vel.ctypes.data_as(C.c_void_p),
+                                                 int(host_vel.shape[0])),
+                  "sidm_set_velocity_mirror")
+
+
 def sidm_timestep_limits(ctx, out) -> int:
     p, kind = _ptr(out)
     return _check(lib().sidm_timestep_limits(ctx, p, kind), "sidm_timestep_limits")
@@ -598,6 +615,12 @@ class Context:
     @property
     def graph_state(self) -> int:
         return sidm_graph_state(self.handle)
+
+    def set_velocity_mirror(self, host_vel):
+        """Pinned host (n, 3) array the device keeps current with every
+        velocity a step changes (None: stop); the context holds a reference."""
+        sidm_set_velocity_mirror(self.handle, host_vel)
+        self._mirror = host_vel
 
     def changed(self):
         """(indices, velocities) of the particles the last step changed."""

@@ -116,3 +116,61 @@ def test_update_velocities_into_pinned_memory_writes_from_the_device():
         assert np.isnan(marked[~hit]).all()
         marked[:] = np.nan
     ctx.close()
+
+
+def test_velocity_mirror_is_kept_current_by_the_kicks():
+    """sidm_set_velocity_mirror: a pinned host array into which the step's
+    kicks write each changed particle's final velocity.  After every step
+    (and a wait for the stream) it equals the full read-back; only the
+    particles the step changed are written; the velocities are bit for bit
+    those of a context without the mirror (multiple scatters per particle
+    at dt_max = 2); a mirror shorter than the particle set stops the step,
+    autotuning leaves it alone, and pageable memory is refused."""
+    torch = pytest.importorskip("torch")
+    p = I.hernquist_halo(20000, 52, ids="random")
+    bins = np.random.default_rng(53).integers(0, 3, p.n).astype(np.int8)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    ref = sidm.Context(n_ngb=32, use_graph=True)
+    ref.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    ctx = sidm.Context(n_ngb=32, use_graph=True)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    mirror = pin(p.vel.copy())
+    ctx.set_velocity_mirror(mirror)
+    multi = 0
+    for k in range(6):
+        act = I.active_at_step(bins, k)
+        ref.step(2.0, act, bins, seed=54, stats=False)
+        st = ctx.step(2.0, act, bins, seed=54)
+        multi = max(multi, st["max_multiplicity"])
+        ctx.sync()
+        after = ctx.velocities()[0]
+        assert np.array_equal(after, ref.velocities()[0]), k
+        assert np.array_equal(mirror, after), k
+    assert multi >= 3
+    # only the changed particles are written
+    marked = pin(np.full((p.n, 3), np.nan))
+    ctx.set_velocity_mirror(marked)
+    ctx.step(2.0, I.active_at_step(bins, 6), bins, seed=54, stats=False)
+    ctx.sync()
+    after = ctx.velocities()[0]
+    idx, _ = ctx.changed()
+    hit = np.zeros(p.n, bool)
+    hit[idx] = True
+    assert hit.sum() > 100
+    assert np.array_equal(marked[hit], after[hit])
+    assert np.isnan(marked[~hit]).all()
+    # trial steps of the autotuner leave the mirror alone
+    marked[:] = np.nan
+    ctx.autotune([sidm.HaloParams(2.0, sidm.SigmaModel(0, 1.0, 1.0), 54, ctx.step_counter)],
+                 I.active_at_step(bins, 7), bins, reps=1)
+    assert np.isnan(marked).all()
+    # too short for the particle set: the step is refused
+    ctx.set_velocity_mirror(pin(np.zeros((p.n - 1, 3))))
+    with pytest.raises(sidm.SidmError):
+        ctx.step(2.0, I.active_at_step(bins, 7), bins, seed=54, stats=False)
+    ctx.set_velocity_mirror(None)
+    ctx.step(2.0, I.active_at_step(bins, 7), bins, seed=54, stats=False)
+    with pytest.raises(sidm.SidmError):
+        ctx.set_velocity_mirror(np.zeros((p.n, 3)))   # pageable
+    ctx.close()
+    ref.close()
