@@ -1424,7 +1424,7 @@ int sidm_update_velocities(sidm_ctx* c, double* vel_inout) {
   // written into it from the device, with no staging and no host loop
   cudaPointerAttributes pa{};
   if (cudaPointerGetAttributes(&pa, vel_inout) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-      pa.devicePointer) {
+      pa.devicePointer && (reinterpret_cast<uintptr_t>(pa.devicePointer) & 7) == 0) {
     CK(join_velocities(c));
     if (++c->chg_call == 0) c->chg_call = 1;   // stamps start at 0
     c->launches += launch_changed_to_host(c->pairs, c->pair_cap, c->dstats, c->chg_call,

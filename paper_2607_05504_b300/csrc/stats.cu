@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(CT) changed_to_host_kernel(const PairRec* __re
                                                              int64_t cap, const DevStats* st,
                                                              uint32_t stamp, uint32_t* stamps,
                                                              const double* __restrict__ vel,
-                                                             double* host_vel, bool aligned16) {
+                                                             double* host_vel) {
   const unsigned long long na = st->n_acc;
   if (na > (unsigned long long)cap || st->n_deferred > (unsigned long long)cap) return;
   for (int64_t t = blockIdx.x * (int64_t)CT + threadIdx.x; t < 2 * (int64_t)na;
@@ -124,20 +124,9 @@ __global__ void __launch_bounds__(CT) changed_to_host_kernel(const PairRec* __re
     if (atomicExch(&stamps[e], stamp) == stamp) continue;
     const double* v = vel + 3 * (int64_t)e;
     double* d = host_vel + 3 * (int64_t)e;
-    const double v0 = v[0], v1 = v[1], v2 = v[2];
-    // two stores per particle instead of three when the array is 16-byte
-    // aligned: 24 e bytes is 0 mod 16 for even e and 8 mod 16 for odd e
-    if (!aligned16) {
-      d[0] = v0;
-      d[1] = v1;
-      d[2] = v2;
-    } else if ((e & 1) == 0) {
-      *reinterpret_cast<double2*>(d) = make_double2(v0, v1);
-      d[2] = v2;
-    } else {
-      d[0] = v0;
-      *reinterpret_cast<double2*>(d + 1) = make_double2(v1, v2);
-    }
+    d[0] = v[0];
+    d[1] = v[1];
+    d[2] = v[2];
   }
 }
 
@@ -152,9 +141,8 @@ int launch_changed(const PairRec* pairs, int64_t cap, const DevStats* st, uint32
 int launch_changed_to_host(const PairRec* pairs, int64_t cap, const DevStats* st,
                            uint32_t stamp, uint32_t* stamps, const double* vel,
                            double* host_vel, int sms, cudaStream_t s) {
-  const bool a16 = (reinterpret_cast<uintptr_t>(host_vel) & 15) == 0;
   changed_to_host_kernel<<<(unsigned)(sms * 4), CT, 0, s>>>(pairs, cap, st, stamp, stamps, vel,
-                                                            host_vel, a16);
+                                                            host_vel);
   return 1;
 }
 
