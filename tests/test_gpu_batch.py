@@ -128,3 +128,29 @@ def test_hernquist_batch_512_sampled_haloes(batch512):
         assert np.array_equal(vb[sl], va), f"halo {k}"
         assert np.array_equal(hb[sl], ha), f"halo {k}"
         assert np.array_equal(db[sl], da), f"halo {k}"
+
+
+def test_velocity_mirror_over_a_batch():
+    """The velocity mirror (sidm_set_velocity_mirror) over many haloes in
+    one context: after each multi-halo step it equals the full read-back,
+    with an empty halo and a tiny one in the batch."""
+    torch = pytest.importorskip("torch")
+    haloes = _small_batch()
+    p, off, bins = I.pack(haloes)
+    ctx = sidm.Context(n_ngb=64, box=0.0, use_graph=True)
+    ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
+    ctx.set_haloes(off)
+    mirror = torch.from_numpy(p.vel.copy()).pin_memory().numpy()
+    ctx.set_velocity_mirror(mirror)
+    changed = 0
+    for t in range(3):
+        params = [_params(h, k, 1 + t) for k, h in enumerate(haloes)]
+        act = np.concatenate([I.active_at_step(h["bins"], 1 + t) if h["particles"].n else
+                              np.zeros(0, np.uint8) for k, h in enumerate(haloes)])
+        ctx.step_haloes(params, act, bins)
+        ctx.sync()
+        v, _ = ctx.velocities()
+        assert np.array_equal(mirror, v), t
+        changed += ctx.changed()[0].size
+    assert changed > 50
+    ctx.close()
