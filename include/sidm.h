@@ -410,7 +410,7 @@ SIDM_API int sidm_overlap_table(int kernel, int32_t na, int32_t ns, double* out)
  * results; only the time changes.  Zero fields take the defaults. */
 typedef struct {
   int search_window;        /* key-order window that bounds each search radius:
-                               128, 256, 384, 512 (default), 768 or 1024 particles; a window
+                               128, 256, 384 (default), 512, 768 or 1024 particles; a window
                                of fewer than n_ngb + ngb_tol + 2 particles runs as
                                256                                                   */
   int search_chunk;         /* a search block (32 warps, one query per warp at a time)

@@ -20,7 +20,7 @@
 //      the last smoothing length, used here to size the gather only.
 //      Otherwise (the plain form carries no h between steps), from the
 //      key-order window of
-//      128-512 particles around i (a launch shape, 512 by default; at least
+//      128-1024 particles around i (a launch shape, 384 by default; at least
 //      K + 1 particles, so 256 where 128 would be too few): an upper bound
 //      (within ~2 % above) of the K-th smallest hi.  A halo with at most K
 //      particles besides i has no bound: T is infinite and the whole halo

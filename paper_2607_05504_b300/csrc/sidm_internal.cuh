@@ -352,7 +352,7 @@ int tree_levels_for(int64_t n, int64_t count[MAX_LEVELS]);
 #define PAIRS_BLOCKS_MAX 7       // pair-kernel blocks resident per SM (its register budget)
 #endif
 struct LaunchTuning {
-  int search_window = 512;       // key-order window of the search radius (128 .. 1024)
+  int search_window = 384;       // key-order window of the search radius (128 .. 1024)
   int search_chunk = 1;          // a search block claims ranges of 32 search_chunk queries
   int search_blocks_per_sm = 1;  // 32-warp blocks per SM (one is resident at a time)
   int pairs_chunk = 4;
