@@ -411,8 +411,13 @@ def precision_run(log2_n=23, steps=10) -> dict:
         c.set_particles(pos, vel, ids, mass=mass)
     bins_d = torch.from_numpy(bins).to(dev)
     sg = sidm.SigmaModel(sidm.SIGMA_YUKAWA, 1.0, w)
-    # warm-up: capture both forms' graphs on step 1's active set
+    # launch shapes of each form tuned on step 1's active set (the state is
+    # restored), then warm-up: both forms' graphs captured on that set
     act1 = torch.from_numpy(I.active_at_step(bins, 1)).to(dev)
+    tunings = {}
+    for k, c in ctxs.items():
+        c.step_counter = 1
+        tunings[k] = c.autotune([sidm.HaloParams(dt, sg, 7, 1)], act1, bins_d, reps=1)
     for c in ctxs.values():
         c.step_counter = 1
         sidm.sidm_step(c.handle, act1, bins_d, dt, sg, 7, None)
@@ -465,6 +470,7 @@ def precision_run(log2_n=23, steps=10) -> dict:
             "n": p.n, "mean_active": upd / steps,
             "fp64_plain": {"value": upd / t["fp64"], "unit": UNIT},
             "speedup_split_vs_fp64": t["fp64"] / t["split"],
+            "tuning": tunings,
             "pair_mismatch": {"rate": nx / max(n64, 1), "pairs_fp64": int(n64),
                               "differing": int(nx), "target": 1e-5},
             "drift_per_step": {"energy_rel": d_e, "energy_rel_vs_fp64": d_e64,
