@@ -481,14 +481,20 @@ int launch_core(sidm_ctx* c, bool prof, bool rebuild, int64_t* launches, int par
     mark(0);
     L += launch_bbox(c->pos, c->halo_of, n, c->d_halos, nh, s);
     L += launch_params(c->d_halos, nh, c->cfg.box, s);
+    // the key's width sets the sort's passes; an odd count starts from the
+    // alternate buffers, so that the sorted order lands in keys / vals
+    const int key_bits = F.halo_bits + 3 * key_axis_bits(F.halo_bits);
+    const bool odd = (sort_passes(key_bits) & 1) != 0;
+    uint32_t* k_in = odd ? c->keys_alt : c->keys;
+    int32_t* v_in = odd ? c->vals_alt : c->vals;
+    uint32_t* k_out = odd ? c->keys : c->keys_alt;
+    int32_t* v_out = odd ? c->vals : c->vals_alt;
     if (rebuild)
-      L += launch_keys(c->pos, c->halo_of, n, c->d_halos, F.halo_bits, c->cfg.box, c->keys,
-                       c->vals, s);
+      L += launch_keys(c->pos, c->halo_of, n, c->d_halos, F.halo_bits, c->cfg.box, k_in, v_in, s);
     mark(1);
     if (rebuild) {
-      const int mb = (30 - F.halo_bits) / 3;
-      const int sl = radix_sort_pairs(c->keys, c->vals, c->keys_alt, c->vals_alt, n,
-                                      F.halo_bits + 3 * mb, c->sort_tmp, &c->dstats->status, s);
+      const int sl = radix_sort_pairs(k_in, v_in, k_out, v_out, n, key_bits, c->sort_tmp,
+                                      &c->dstats->status, s);
       if (sl < 0) return SIDM_ERR_CUDA;
       L += sl;
     }

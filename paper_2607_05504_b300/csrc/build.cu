@@ -248,7 +248,7 @@ __device__ __forceinline__ uint32_t hilbert_key(uint32_t x0, uint32_t x1, uint32
   return (spread10(x0) << 2) | (spread10(x1) << 1) | spread10(x2);
 }
 
-// Key = halo index above a Hilbert key with mb = (30 - halo_bits)/3 bits per
+// Key = halo index above a Hilbert key with mb = key_axis_bits(halo_bits) bits per
 // axis.  Periodic box: 2^mb cells per axis.  Open boundaries: the offset
 // from the halo's centre is compressed radially by asinh(r/s)/asinh(R/s)
 // (s = R/1024) before 2^mb cells per axis, so that cells stay small relative
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(BT) keys_kernel(const double* __restrict__ pos
   const int64_t i = blockIdx.x * (int64_t)BT + threadIdx.x;
   if (i >= n) return;
   const int k = halo_of[i];
-  const int mb = (30 - halo_bits) / 3;
+  const int mb = key_axis_bits(halo_bits);
   const float cells = (float)(1u << mb);
   uint32_t c[3];
   if (box > 0.0) {

@@ -18,7 +18,7 @@
 //      digits are written out by consecutive threads.
 // A slot is one 32-bit word holding a 2-bit state and a 30-bit count, so a
 // reader sees the state and the count together without a fence.  Six
-// launches per sort (a memset, the histogram, four passes) instead of a
+// launches per sort at most (a memset, the histogram, up to four passes) instead of a
 // histogram, scan and scatter per pass.
 #include "sidm_internal.cuh"
 
@@ -256,22 +256,30 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) os_pass_kernel(
 
 }  // namespace
 
+// 8-bit digit passes for a key width: an odd count leaves the result in the
+// alternate buffers (the caller then starts from them, see sort_passes' users)
+int sort_passes(int key_bits) {
+  int passes = (key_bits + 7) / 8;
+  if (passes > MAX_PASSES) passes = MAX_PASSES;
+  return passes;
+}
+
 size_t radix_sort_temp_bytes(int64_t n) {
   const int64_t tiles = (n + OS_TILE - 1) / OS_TILE;
   return (size_t)(HEAD_WORDS + (int64_t)MAX_PASSES * tiles * RADIX) * sizeof(uint32_t);
 }
 
-// Sorts (keys, vals) by the low `key_bits` bits of the keys; the result is
-// left in (keys, vals).  keys_alt / vals_alt are scratch of n entries;
+// Sorts (keys, vals) by the low `key_bits` bits of the keys in
+// sort_passes(key_bits) passes; the result is left in (keys, vals) after an
+// even number of passes and in (keys_alt, vals_alt) after an odd number.
+// keys_alt / vals_alt are scratch of n entries;
 // n < 2^30.  A look-back that gives up sets ST_ERR_SORT in *status (the
 // order is then not valid; every index written stays below n).
 int radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_alt, int32_t* vals_alt,
                      int64_t n, int key_bits, void* temp, unsigned* status, cudaStream_t s) {
   if (n <= 1) return 0;
   const int tiles = (int)((n + OS_TILE - 1) / OS_TILE);
-  int passes = (key_bits + 7) / 8;
-  if (passes & 1) ++passes;  // even number of passes: the result lands back in keys/vals
-  if (passes > MAX_PASSES) passes = MAX_PASSES;
+  int passes = sort_passes(key_bits);
   uint32_t* counts = (uint32_t*)temp;
   uint32_t* tile_ctr = counts + MAX_PASSES * RADIX;
   uint32_t* slots = counts + HEAD_WORDS;
