@@ -413,13 +413,16 @@ typedef struct {
                                128, 256, 384 (default), 512, 768 or 1024 particles; a window
                                of fewer than n_ngb + ngb_tol + 2 particles runs as
                                256                                                   */
-  int search_chunk;         /* a search block (32 warps, one query per warp at a time)
-                               claims ranges of 32 x search_chunk consecutive queries,
-                               1..64 (1)                                             */
+  int search_chunk;         /* a search block (32 warps, one run of search_run queries
+                               per warp at a time) claims ranges of 32 x search_chunk
+                               consecutive runs, 1..64 (1)                           */
   int search_blocks_per_sm; /* search blocks launched per SM, 1..8 (1); one is resident
                                at a time, the others start as blocks finish          */
   int pairs_chunk;          /* queries a pair warp claims at a time, 1..64 (4)        */
   int pairs_blocks_per_sm;  /* pair blocks of 4 warps per SM, 1..7 (7)                */
+  int search_run;           /* consecutive active queries a search warp takes in a row,
+                               1..16 (2); each query of a run after the first sizes
+                               its first gather from the previous one's h            */
 } sidm_tuning;
 
 /* Sets / reads the launch shapes of the context.  SIDM_ERR_INVALID_ARG for a
@@ -435,7 +438,7 @@ SIDM_API int sidm_get_tuning(const sidm_ctx* ctx, sidm_tuning* t);
  * replaces the current one only if it is at least 2 % faster.  Afterwards
  * the velocities, h, timestep limits
  * and the step counter are restored, so the call leaves the simulation
- * where it was.  Coordinate search: window, then search chunk and blocks,
+ * where it was.  Coordinate search: window, then search run, chunk and blocks,
  * then pair chunk and blocks.  Writes the chosen shapes to `best` (nullable).
  * Synchronises the stream; allocates one temporary copy of the state. */
 SIDM_API int sidm_autotune(sidm_ctx* ctx, const uint8_t* active_mask, const int8_t* dt_bins,

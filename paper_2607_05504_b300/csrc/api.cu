@@ -1016,7 +1016,8 @@ bool valid_tuning(const LaunchTuning& t) {
           t.search_window == 512 || t.search_window == 768 || t.search_window == 1024) &&
          t.search_chunk >= 1 && t.search_chunk <= 64 && t.search_blocks_per_sm >= 1 &&
          t.search_blocks_per_sm <= 8 && t.pairs_chunk >= 1 && t.pairs_chunk <= 64 &&
-         t.pairs_blocks_per_sm >= 1 && t.pairs_blocks_per_sm <= PAIRS_BLOCKS_MAX;
+         t.pairs_blocks_per_sm >= 1 && t.pairs_blocks_per_sm <= PAIRS_BLOCKS_MAX &&
+         t.search_run >= 1 && t.search_run <= 16;
 }
 
 LaunchTuning from_public(const sidm_tuning& p) {
@@ -1026,6 +1027,7 @@ LaunchTuning from_public(const sidm_tuning& p) {
   if (p.search_blocks_per_sm) t.search_blocks_per_sm = p.search_blocks_per_sm;
   if (p.pairs_chunk) t.pairs_chunk = p.pairs_chunk;
   if (p.pairs_blocks_per_sm) t.pairs_blocks_per_sm = p.pairs_blocks_per_sm;
+  if (p.search_run) t.search_run = p.search_run;
   return t;
 }
 
@@ -1035,6 +1037,7 @@ void to_public(const LaunchTuning& t, sidm_tuning* p) {
   p->search_blocks_per_sm = t.search_blocks_per_sm;
   p->pairs_chunk = t.pairs_chunk;
   p->pairs_blocks_per_sm = t.pairs_blocks_per_sm;
+  p->search_run = t.search_run;
 }
 
 // Median time (ms) of `reps` steps, each from the saved state.
@@ -1310,7 +1313,8 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
   // coordinate search over the launch shapes
   const int windows[] = {128, 256, 384, 512, 768, 1024};
   const int chunks[] = {1, 2, 4, 8, 16};
-  const int sranges[] = {1, 2};   // ranges of 32 and 64 queries per search block
+  const int sranges[] = {1, 2};   // ranges of 32 and 64 runs per search block
+  const int sruns[] = {1, 2, 4};
   const int pblocks[] = {4, 6, 7};
   auto try_field = [&](int LaunchTuning::*field, const int* vals, int nv) {
     for (int k = 0; k < nv && rc == SIDM_OK; ++k) {
@@ -1328,6 +1332,7 @@ int sidm_autotune(sidm_ctx* c, const uint8_t* active_mask, const int8_t* dt_bins
     }
   };
   try_field(&LaunchTuning::search_window, windows, (int)(sizeof(windows) / sizeof(windows[0])));
+  try_field(&LaunchTuning::search_run, sruns, 3);
   try_field(&LaunchTuning::search_chunk, sranges, 2);
   try_field(&LaunchTuning::pairs_chunk, chunks, 5);
   try_field(&LaunchTuning::pairs_blocks_per_sm, pblocks, 3);

@@ -367,6 +367,7 @@ struct LaunchTuning {
   int search_window = 384;       // key-order window of the search radius (128 .. 1024)
   int search_chunk = 1;          // a search block claims ranges of 32 search_chunk queries
   int search_blocks_per_sm = 1;  // 32-warp blocks per SM (one is resident at a time)
+  int search_run = 2;            // consecutive queries a search warp takes in a row
   int pairs_chunk = 4;
   int pairs_blocks_per_sm = PAIRS_BLOCKS_MAX;
 };

@@ -58,7 +58,7 @@ class Config(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("search_window", C.c_int), ("search_chunk", C.c_int),
                 ("search_blocks_per_sm", C.c_int), ("pairs_chunk", C.c_int),
-                ("pairs_blocks_per_sm", C.c_int)]
+                ("pairs_blocks_per_sm", C.c_int), ("search_run", C.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

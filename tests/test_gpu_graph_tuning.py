@@ -57,6 +57,11 @@ def test_graph_replay_is_bit_identical():
          pairs_blocks_per_sm=4),
     dict(search_window=768, search_chunk=2),
     dict(search_window=1024, search_chunk=4, search_blocks_per_sm=8),
+    # runs of consecutive queries per warp: each query after a run's first
+    # sizes its gather from its predecessor's h (1: every query on its own)
+    dict(search_run=1),
+    dict(search_run=3, search_blocks_per_sm=2),
+    dict(search_run=16, search_chunk=2, search_window=256),
 ])
 def test_launch_shapes_do_not_change_results(tune):
     p, bins, dt = _halo(seed=22)
@@ -69,7 +74,7 @@ def test_invalid_shapes_are_rejected():
     ctx = sidm.Context()
     before = ctx.tuning
     for bad in (dict(search_window=300), dict(search_chunk=65), dict(search_blocks_per_sm=9),
-                dict(pairs_blocks_per_sm=8)):
+                dict(pairs_blocks_per_sm=8), dict(search_run=17)):
         with pytest.raises(sidm.SidmError) as e:
             ctx.set_tuning(**bad)
         assert e.value.status == sidm.ERR_INVALID_ARG
