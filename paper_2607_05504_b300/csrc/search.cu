@@ -282,312 +282,334 @@ __global__ void __launch_bounds__(ST, 1) search_kernel(SearchArgs A) {
 
   __shared__ unsigned long long s_claim;
   __shared__ int s_next;
+  __shared__ long long s_qnext[SW], s_qend[SW];
+  __shared__ float s_hpred[SW];
+  __shared__ int s_halopred[SW];
   if (threadIdx.x == 0) {
     const int a = atomicAdd(A.work, 2);   // the block's first range and the one after
     s_claim = (unsigned long long)a << 32;
     s_next = a + 1;
   }
   __syncthreads();
-  // runs of A.run consecutive queries are the unit of the claims
+  // Runs of A.run consecutive queries are the unit of the claims; lane 0
+  // keeps the warp's place in its run (next query, end) and the run's
+  // previous h (an FP32 upper bound; 0: none yet) and halo in shared memory,
+  // so that the loop below carries no state from one query to the next.
   const int64_t n_runs = (n_act + A.run - 1) / A.run;
+  if (lane == 0) {
+    s_qnext[warp] = 0;
+    s_qend[warp] = 0;
+  }
   for (;;) {
-    int64_t rc = 0;
-    if (lane == 0) rc = claim_in_block(&s_claim, &s_next, A.work, n_runs, A.range, &status);
-    const int64_t run = __shfl_sync(0xffffffffu, rc, 0);
-    if (run >= n_runs) break;
-    const int64_t q_end = (run + 1) * A.run < n_act ? (run + 1) * A.run : n_act;
-    double h_pred = 0.0;   // h of the run's previous query (0: none yet)
-    int halo_pred = -1;    // and its halo
-    for (int64_t qi = run * A.run; qi < q_end; ++qi) {
-      const int64_t s = A.all ? qi : (int64_t)A.act_list[qi];
-      const int halo_s = so.halo[s];
-      const Halo& H = A.f.halos[halo_s];
-      const int64_t hs = H.start, hn = H.n;   // the query's halo: [hs, hs + hn)
-      const float4* hpos = so.f + hs;         // its FP32 positions
-      const int sl = (int)(s - hs);           // the query's halo-local index
-      const float4 fi = so.f[s];
-      const float eq = ABS * (fmaxf(fmaxf(fabsf(fi.x), fabsf(fi.y)), fabsf(fi.z)) + boxf);
-      double h;
-      int len = 0;
-      float T0 = INFINITY;  // radius when no bound is known (fixed h: h itself)
-      // the key-order window bounds T only when it holds K particles besides i
-      const int64_t W = (int64_t)NWIN * 32 < hn ? (int64_t)NWIN * 32 : hn;
-      const bool window_bound = !(A.fixed_h > 0.0) && W - 1 >= K;
-      if (A.fixed_h > 0.0) {
-        h = A.fixed_h;
-        float hl, hu;
-        float_bounds(h, &hl, &hu);
-        T0 = hu;
+    int64_t qc = 0;
+    if (lane == 0) {
+      if (s_qnext[warp] < s_qend[warp]) {
+        qc = s_qnext[warp]++;
+      } else {
+        const int64_t run = claim_in_block(&s_claim, &s_next, A.work, n_runs, A.range, &status);
+        qc = run < n_runs ? run * A.run : n_act;
+        s_qnext[warp] = qc + 1;
+        s_qend[warp] = qc + A.run < n_act ? qc + A.run : n_act;
+        s_hpred[warp] = 0.0f;
+        s_halopred[warp] = -1;
       }
-      // h of the particle's last search (0 before its first): the first
-      // gather tries G h_prev, kept only if K entries are surely within it
-      double hp = 0.0;
-      if (SEARCH_HINT_GROW > 0.0f && A.hint && window_bound) hp = A.h_user[so.orig[s]];
-      bool use_hint = hp > 0.0 && hp < INFINITY;
-      float grow = SEARCH_HINT_GROW;
-      // else the h of the run's previous query, a neighbour in space
-      if (!use_hint && window_bound && halo_pred == halo_s && h_pred > 0.0 && h_pred < INFINITY) {
-        hp = h_pred;
-        use_hint = true;
-        grow = SEARCH_RUN_GROW;
-      }
-
-      // ---- 2-3. radius T and gather of every j whose lower bound is <= T
-      float T = T0;         // every j with r <= T (and more) is in the list
-      bool t_bound = false;  // K particles besides i lie within T
-      bool complete = true;
-      for (;;) {
-        if (use_hint) {
-          float hpl, hpu;
-          float_bounds(hp, &hpl, &hpu);
-          T = __fmul_ru(hpu, grow);
-        } else if (window_bound) {
-          int64_t w0 = s - W / 2;
-          if (w0 > hs + hn - W) w0 = hs + hn - W;
-          if (w0 < hs) w0 = hs;
-          T = window_radius<PERIODIC, NWIN>(so.f, s, w0, W, fi, boxf, K, eq);
-        } else {
-          T = T0;
-        }
-        bool ok = true;
-        for (int attempt = 0;; ++attempt) {
-          len = 0;
-          const float g2 = T < INFINITY ? thr_out2(T * (1.0f + REL), eq) : INFINITY;
-          const float rad = (T + 2.0f * eq) * (1.0f + 4.0f * REL);
-          const float rad2 = rad < INFINITY ? rad * rad : INFINITY;
-          ok = traverse<PERIODIC, false, SEARCH_LEAF_BATCH, WALK_STACK>(
-              A.f, H, hpos, fi, rad2, boxf, stack,
-              [&](const int* kk, const bool* valid, const float4* pj, const bool* on) {
-            // every slot's separation first (independent work), then the appends
-            float s2[SEARCH_LEAF_BATCH];
-            bool keep[SEARCH_LEAF_BATCH];
-  #pragma unroll
-            for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
-              s2[b] = sep2f<PERIODIC>(fi, pj[b], boxf);
-              keep[b] = valid[b] && kk[b] != sl && s2[b] < g2;
-            }
-  #pragma unroll
-            for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
-              if (!on[b]) break;
-              const uint32_t m = __ballot_sync(0xffffffffu, keep[b]);
-              if (keep[b]) {
-                const int at = len + __popc(m & lt);
-                if (at < SEARCH_CAP) {
-                  lst_r2[at] = s2[b];
-                  lst_j[at] = (int32_t)(hs + kk[b]);
-                }
-              }
-              len += __popc(m);
-            }
-          });
-          __syncwarp();
-          // the hinted radius is judged once, below
-          if (use_hint) break;
-          if (!ok) { status |= ST_ERR_STACK; complete = false; break; }
-          if (len <= SEARCH_CAP) break;
-          // too many candidates.  With a fixed h the pair kernel walks the tree
-          // itself; otherwise shrink T, keeping a new T only once at least K
-          // particles are certainly within it.
-          if (A.fixed_h > 0.0) {
-            complete = false;
-            len = SEARCH_CAP;
-            break;
-          }
-          if (attempt >= RADIUS_MAX_ITERS) {
-            status |= ST_ERR_SEARCH_CAP;
-            complete = false;
-            len = SEARCH_CAP;
-            break;
-          }
-          float Tn = T * cbrtf(0.5f * (float)SEARCH_CAP / (float)len);
-          bool verified = false;
-          for (int inner = 0; inner < RADIUS_MAX_ITERS; ++inner) {
-            const float in2 = thr_in2(Tn, eq);
-            const float radn = (Tn + 2.0f * eq) * (1.0f + 4.0f * REL);
-            int c = 0;
-            const bool ok2 = traverse<PERIODIC, false, SEARCH_LEAF_BATCH, WALK_STACK>(
-                A.f, H, hpos, fi, radn * radn, boxf, stack,
-                [&](const int* kk, const bool* valid, const float4* pj, const bool* on) {
-  #pragma unroll
-              for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
-                const bool in = valid[b] && kk[b] != sl && sep2f<PERIODIC>(fi, pj[b], boxf) < in2;
-                c += __popc(__ballot_sync(0xffffffffu, in));   // invalid slots add 0
-              }
-            });
-            if (!ok2) { status |= ST_ERR_STACK; break; }
-            if (c >= K) { verified = true; break; }
-            Tn = sqrtf(Tn * T);   // too small: move towards the valid T
-          }
-          if (!verified) {
-            status |= ST_ERR_RADIUS;
-            complete = false;
-            len = SEARCH_CAP;
-            break;
-          }
-          T = Tn;
-        }
-        if (use_hint) {
-          // kept when the whole list fits and K entries are surely within T
-          use_hint = false;
-          if (ok && len <= SEARCH_CAP) {
-            const float in2 = thr_in2(T, eq);
-            int c = 0;
-            for (int k = lane; k < len; k += 32) c += lst_r2[k] < in2 ? 1 : 0;
-            if (warp_sum(c) >= K) { t_bound = true; break; }
-          }
-          continue;   // the window's radius instead
-        }
-        t_bound = window_bound;
-        break;
-      }
-
-      // ---- 4. bisection on the exact neighbour count
-      const double xi = so.x[s], yi = so.y[s], zi = so.z[s];
-      auto exact_r2 = [&](int k) {
-        const int64_t j = lst_j[k];
-        return sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half);
-      };
-      // #{r^2 < h h} over the list (exact); requires h <= T (1 + 2^-22)
-      // FP32-split form: the counts compare FP32 r^2 with the FP32 h^2 directly
-      auto thresholds = [&](double hv, float hl, float hu, float* in2, float* out2) {
-        if (A.split) {
-          const float hf = (float)hv;
-          *in2 = *out2 = hf * hf;
-        } else {
-          *in2 = thr_in2(hl, eq);
-          *out2 = thr_out2(hu, eq);
-        }
-      };
-      // a short list (the usual case) is held in registers for the bisection
-      const bool in_regs = len <= LIST_REGS * 32;
-      float rv[LIST_REGS];
-  #pragma unroll
-      for (int i = 0; i < LIST_REGS; ++i) {
-        const int k = lane + 32 * i;
-        rv[i] = (in_regs && k < len) ? lst_r2[k] : INFINITY;
-      }
-      auto count_below = [&](double hv, float hl, float hu) {
-        float in2, out2;
-        thresholds(hv, hl, hu, &in2, &out2);
-        int c = 0;
-        bool amb = false;
-        if (in_regs) {
-  #pragma unroll
-          for (int i = 0; i < LIST_REGS; ++i) {
-            c += rv[i] < in2 ? 1 : 0;
-            amb |= (rv[i] >= in2) && (rv[i] < out2);
-          }
-        } else {
-          for (int k = lane; k < len; k += 32) {
-            const float v = lst_r2[k];
-            c += v < in2 ? 1 : 0;
-            amb |= (v >= in2) && (v < out2);
-          }
-        }
-        if (__any_sync(0xffffffffu, amb)) {
-          const double hh = hv * hv;
-          for (int k = lane; k < len; k += 32) {
-            const float v = lst_r2[k];
-            if (v >= in2 && v < out2) c += exact_r2(k) < hh ? 1 : 0;
-          }
-        }
-        return warp_sum(c);
-      };
-      if (!(A.fixed_h > 0.0)) {
-        h = H.h0;
-        double blo = 0.0, bhi = 0.0;
-        bool have_hi = false, conv = false;
-        // h > T means c(h) >= K: K particles lie within T.  h and T are
-        // positive, so their bit patterns compare as integers.
-        const long long t_bits =
-            t_bound ? __double_as_longlong((double)T) : 0x7FFFFFFFFFFFFFFFll;
-        int it = 0;
-        // While h > T and no lower end is known, each step sets bhi = h and
-        // halves h (the midpoint of 0 and h): the opening run from h0 down to
-        // the first h0 2^-k <= T follows from the exponents.  Taken at once
-        // when every halving is an exact exponent step, as in the loop.
-        {
-          const long long hb = __double_as_longlong(h);
-          if (hb > t_bits) {
-            int k = (int)((hb >> 52) & 0x7FF) - (int)((t_bits >> 52) & 0x7FF);
-            long long hk = hb - ((long long)k << 52);   // h0 2^-k: T's exponent
-            if (hk > t_bits) {
-              ++k;
-              hk -= 1ll << 52;
-            }
-            if (((hk >> 52) & 0x7FF) >= 1 && k < BISECT_MAX_EVALS) {
-              bhi = __longlong_as_double(hk + (1ll << 52));
-              have_hi = true;
-              h = __longlong_as_double(hk);
-              it = k;
-            }
-          }
-        }
-        for (; it < BISECT_MAX_EVALS; ++it) {
-          int c;
-          if (__double_as_longlong(h) > t_bits) {
-            c = hi_band + 1;
-          } else {
-            float hl, hu;
-            float_bounds(h, &hl, &hu);
-            c = count_below(h, hl, hu);
-          }
-          if (c >= lo_band && c <= hi_band) { conv = true; break; }
-          if (c < lo_band) {
-            blo = h;
-            h = have_hi ? half_of(blo + bhi) : twice(h);
-          } else {
-            bhi = h;
-            have_hi = true;
-            h = half_of(blo + bhi);
-          }
-        }
-        if (!conv) ++nonconv;
-      }
-
-      // ---- 5. neighbour list
+    }
+    __syncwarp();
+    const int64_t qi = __shfl_sync(0xffffffffu, qc, 0);
+    if (qi >= n_act) break;
+    const int64_t s = A.all ? qi : (int64_t)A.act_list[qi];
+    const int halo_s = so.halo[s];
+    const Halo& H = A.f.halos[halo_s];
+    const int64_t hs = H.start, hn = H.n;   // the query's halo: [hs, hs + hn)
+    const float4* hpos = so.f + hs;         // its FP32 positions
+    const int sl = (int)(s - hs);           // the query's halo-local index
+    const float4 fi = so.f[s];
+    const float eq = ABS * (fmaxf(fmaxf(fabsf(fi.x), fabsf(fi.y)), fabsf(fi.z)) + boxf);
+    double h;
+    int len = 0;
+    float T0 = INFINITY;  // radius when no bound is known (fixed h: h itself)
+    // the key-order window bounds T only when it holds K particles besides i
+    const int64_t W = (int64_t)NWIN * 32 < hn ? (int64_t)NWIN * 32 : hn;
+    const bool window_bound = !(A.fixed_h > 0.0) && W - 1 >= K;
+    if (A.fixed_h > 0.0) {
+      h = A.fixed_h;
       float hl, hu;
       float_bounds(h, &hl, &hu);
-      int* out = A.nb_list + qi * (int64_t)A.nb_stride;
-      int cnt = -1;
-      const bool list_covers = complete && (!t_bound || !(hl > T));
-      if (list_covers) {
-        float in2, out2;
-        thresholds(h, hl, hu, &in2, &out2);
-        cnt = 0;
-        for (int k0 = 0; k0 < len; k0 += 32) {
-          const int k = k0 + lane;
-          bool in = false;
-          if (k < len) {
-            const float v = lst_r2[k];
-            if (v < in2) in = true;
-            else if (v < out2) in = hw_within(so.x, so.y, so.z, s, lst_j[k], box, h);
-          }
-          const uint32_t m = __ballot_sync(0xffffffffu, in);
-          if (in) {
-            const int at = cnt + __popc(m & lt);
-            if (at < A.nb_stride) out[at] = lst_j[k];
-          }
-          cnt += __popc(m);
-        }
-        if (cnt > A.nb_stride) cnt = -1;
-      }
-      if (lane == 0) {
-        A.nb_count[qi] = cnt;
-        so.h[s] = h;
-        // bounds used by the pair kernel: 1/h from below, K/h^3 from above
-        // K = 8/pi or 3/(4 pi) (the FP64 constants) rounded up to FP32
-        const float knorm_up = A.kernel == SIDM_KERNEL_TOPHAT ? 0x1.e8ec8cp-3f : 0x1.45f308p+1f;
-        // (__frcp_rn is within 2^-24 of the reciprocal; 2^-23 covers it)
-        const float h3 = __fmul_rd(__fmul_rd(hl, hl), hl);
-        so.hb[s] = make_float4(hl, hu, __fmul_rd(__frcp_rn(hu), 1.0f - ULP1),
-                               __fmul_ru(__fmul_ru(knorm_up, __frcp_rn(h3)), 1.0f + ULP1));
-        A.h_user[so.orig[s]] = h;
-      }
-      h_pred = h;
-      halo_pred = halo_s;
-      __syncwarp();
+      T0 = hu;
     }
+    // h of the particle's last search (0 before its first): the first
+    // gather tries G h_prev, kept only if K entries are surely within it
+    double hp = 0.0;
+    if (SEARCH_HINT_GROW > 0.0f && A.hint && window_bound) hp = A.h_user[so.orig[s]];
+    bool use_hint = hp > 0.0 && hp < INFINITY;
+    float T = T0;         // every j with r <= T (and more) is in the list
+    if (use_hint) {
+      float hpl, hpu;
+      float_bounds(hp, &hpl, &hpu);
+      T = __fmul_ru(hpu, SEARCH_HINT_GROW);
+    }
+    // else the h of the run's previous query, a neighbour in space (lane 0
+    // records this query's halo now and its h at the end)
+    const float h_pred = s_hpred[warp];
+    if (!use_hint && window_bound && s_halopred[warp] == halo_s && h_pred > 0.0f &&
+        h_pred < INFINITY) {
+      use_hint = true;
+      T = __fmul_ru(h_pred, SEARCH_RUN_GROW);
+    }
+    __syncwarp();
+    if (lane == 0) s_halopred[warp] = halo_s;
+
+    // ---- 2-3. radius T and gather of every j whose lower bound is <= T
+    bool t_bound = false;  // K particles besides i lie within T
+    bool complete = true;
+    for (;;) {
+      if (use_hint) {
+        // T: the hinted radius, set above
+      } else if (window_bound) {
+        int64_t w0 = s - W / 2;
+        if (w0 > hs + hn - W) w0 = hs + hn - W;
+        if (w0 < hs) w0 = hs;
+        T = window_radius<PERIODIC, NWIN>(so.f, s, w0, W, fi, boxf, K, eq);
+      } else {
+        T = T0;
+      }
+      bool ok = true;
+      for (int attempt = 0;; ++attempt) {
+        len = 0;
+        const float g2 = T < INFINITY ? thr_out2(T * (1.0f + REL), eq) : INFINITY;
+        const float rad = (T + 2.0f * eq) * (1.0f + 4.0f * REL);
+        const float rad2 = rad < INFINITY ? rad * rad : INFINITY;
+        ok = traverse<PERIODIC, false, SEARCH_LEAF_BATCH, WALK_STACK>(
+            A.f, H, hpos, fi, rad2, boxf, stack,
+            [&](const int* kk, const bool* valid, const float4* pj, const bool* on) {
+          // every slot's separation first (independent work), then the appends
+          float s2[SEARCH_LEAF_BATCH];
+          bool keep[SEARCH_LEAF_BATCH];
+#pragma unroll
+          for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
+            s2[b] = sep2f<PERIODIC>(fi, pj[b], boxf);
+            keep[b] = valid[b] && kk[b] != sl && s2[b] < g2;
+          }
+#pragma unroll
+          for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
+            if (!on[b]) break;
+            const uint32_t m = __ballot_sync(0xffffffffu, keep[b]);
+            if (keep[b]) {
+              const int at = len + __popc(m & lt);
+              if (at < SEARCH_CAP) {
+                lst_r2[at] = s2[b];
+                lst_j[at] = (int32_t)(hs + kk[b]);
+              }
+            }
+            len += __popc(m);
+          }
+        });
+        __syncwarp();
+        // the hinted radius is judged once, below
+        if (use_hint) break;
+        if (!ok) { status |= ST_ERR_STACK; complete = false; break; }
+        if (len <= SEARCH_CAP) break;
+        // too many candidates.  With a fixed h the pair kernel walks the tree
+        // itself; otherwise shrink T, keeping a new T only once at least K
+        // particles are certainly within it.
+        if (A.fixed_h > 0.0) {
+          complete = false;
+          len = SEARCH_CAP;
+          break;
+        }
+        if (attempt >= RADIUS_MAX_ITERS) {
+          status |= ST_ERR_SEARCH_CAP;
+          complete = false;
+          len = SEARCH_CAP;
+          break;
+        }
+        float Tn = T * cbrtf(0.5f * (float)SEARCH_CAP / (float)len);
+        bool verified = false;
+        for (int inner = 0; inner < RADIUS_MAX_ITERS; ++inner) {
+          const float in2 = thr_in2(Tn, eq);
+          const float radn = (Tn + 2.0f * eq) * (1.0f + 4.0f * REL);
+          int c = 0;
+          const bool ok2 = traverse<PERIODIC, false, SEARCH_LEAF_BATCH, WALK_STACK>(
+              A.f, H, hpos, fi, radn * radn, boxf, stack,
+              [&](const int* kk, const bool* valid, const float4* pj, const bool* on) {
+#pragma unroll
+            for (int b = 0; b < SEARCH_LEAF_BATCH; ++b) {
+              const bool in = valid[b] && kk[b] != sl && sep2f<PERIODIC>(fi, pj[b], boxf) < in2;
+              c += __popc(__ballot_sync(0xffffffffu, in));   // invalid slots add 0
+            }
+          });
+          if (!ok2) { status |= ST_ERR_STACK; break; }
+          if (c >= K) { verified = true; break; }
+          Tn = sqrtf(Tn * T);   // too small: move towards the valid T
+        }
+        if (!verified) {
+          status |= ST_ERR_RADIUS;
+          complete = false;
+          len = SEARCH_CAP;
+          break;
+        }
+        T = Tn;
+      }
+      if (use_hint) {
+        // kept when the whole list fits and K entries are surely within T
+        use_hint = false;
+        if (ok && len <= SEARCH_CAP) {
+          const float in2 = thr_in2(T, eq);
+          int c = 0;
+          for (int k = lane; k < len; k += 32) c += lst_r2[k] < in2 ? 1 : 0;
+          if (warp_sum(c) >= K) { t_bound = true; break; }
+        }
+        continue;   // the window's radius instead
+      }
+      t_bound = window_bound;
+      break;
+    }
+
+    // ---- 4. bisection on the exact neighbour count
+    const double xi = so.x[s], yi = so.y[s], zi = so.z[s];
+    auto exact_r2 = [&](int k) {
+      const int64_t j = lst_j[k];
+      return sep2(xi, yi, zi, so.x[j], so.y[j], so.z[j], box, half);
+    };
+    // #{r^2 < h h} over the list (exact); requires h <= T (1 + 2^-22)
+    // FP32-split form: the counts compare FP32 r^2 with the FP32 h^2 directly
+    auto thresholds = [&](double hv, float hl, float hu, float* in2, float* out2) {
+      if (A.split) {
+        const float hf = (float)hv;
+        *in2 = *out2 = hf * hf;
+      } else {
+        *in2 = thr_in2(hl, eq);
+        *out2 = thr_out2(hu, eq);
+      }
+    };
+    // a short list (the usual case) is held in registers for the bisection
+    const bool in_regs = len <= LIST_REGS * 32;
+    float rv[LIST_REGS];
+#pragma unroll
+    for (int i = 0; i < LIST_REGS; ++i) {
+      const int k = lane + 32 * i;
+      rv[i] = (in_regs && k < len) ? lst_r2[k] : INFINITY;
+    }
+    auto count_below = [&](double hv, float hl, float hu) {
+      float in2, out2;
+      thresholds(hv, hl, hu, &in2, &out2);
+      int c = 0;
+      bool amb = false;
+      if (in_regs) {
+#pragma unroll
+        for (int i = 0; i < LIST_REGS; ++i) {
+          c += rv[i] < in2 ? 1 : 0;
+          amb |= (rv[i] >= in2) && (rv[i] < out2);
+        }
+      } else {
+        for (int k = lane; k < len; k += 32) {
+          const float v = lst_r2[k];
+          c += v < in2 ? 1 : 0;
+          amb |= (v >= in2) && (v < out2);
+        }
+      }
+      if (__any_sync(0xffffffffu, amb)) {
+        const double hh = hv * hv;
+        for (int k = lane; k < len; k += 32) {
+          const float v = lst_r2[k];
+          if (v >= in2 && v < out2) c += exact_r2(k) < hh ? 1 : 0;
+        }
+      }
+      return warp_sum(c);
+    };
+    if (!(A.fixed_h > 0.0)) {
+      h = H.h0;
+      double blo = 0.0, bhi = 0.0;
+      bool have_hi = false, conv = false;
+      // h > T means c(h) >= K: K particles lie within T.  h and T are
+      // positive, so their bit patterns compare as integers.
+      const long long t_bits =
+          t_bound ? __double_as_longlong((double)T) : 0x7FFFFFFFFFFFFFFFll;
+      int it = 0;
+      // While h > T and no lower end is known, each step sets bhi = h and
+      // halves h (the midpoint of 0 and h): the opening run from h0 down to
+      // the first h0 2^-k <= T follows from the exponents.  Taken at once
+      // when every halving is an exact exponent step, as in the loop.
+      {
+        const long long hb = __double_as_longlong(h);
+        if (hb > t_bits) {
+          int k = (int)((hb >> 52) & 0x7FF) - (int)((t_bits >> 52) & 0x7FF);
+          long long hk = hb - ((long long)k << 52);   // h0 2^-k: T's exponent
+          if (hk > t_bits) {
+            ++k;
+            hk -= 1ll << 52;
+          }
+          if (((hk >> 52) & 0x7FF) >= 1 && k < BISECT_MAX_EVALS) {
+            bhi = __longlong_as_double(hk + (1ll << 52));
+            have_hi = true;
+            h = __longlong_as_double(hk);
+            it = k;
+          }
+        }
+      }
+      for (; it < BISECT_MAX_EVALS; ++it) {
+        int c;
+        if (__double_as_longlong(h) > t_bits) {
+          c = hi_band + 1;
+        } else {
+          float hl, hu;
+          float_bounds(h, &hl, &hu);
+          c = count_below(h, hl, hu);
+        }
+        if (c >= lo_band && c <= hi_band) { conv = true; break; }
+        if (c < lo_band) {
+          blo = h;
+          h = have_hi ? half_of(blo + bhi) : twice(h);
+        } else {
+          bhi = h;
+          have_hi = true;
+          h = half_of(blo + bhi);
+        }
+      }
+      if (!conv) ++nonconv;
+    }
+
+    // ---- 5. neighbour list
+    float hl, hu;
+    float_bounds(h, &hl, &hu);
+    int* out = A.nb_list + qi * (int64_t)A.nb_stride;
+    int cnt = -1;
+    const bool list_covers = complete && (!t_bound || !(hl > T));
+    if (list_covers) {
+      float in2, out2;
+      thresholds(h, hl, hu, &in2, &out2);
+      cnt = 0;
+      for (int k0 = 0; k0 < len; k0 += 32) {
+        const int k = k0 + lane;
+        bool in = false;
+        if (k < len) {
+          const float v = lst_r2[k];
+          if (v < in2) in = true;
+          else if (v < out2) in = hw_within(so.x, so.y, so.z, s, lst_j[k], box, h);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, in);
+        if (in) {
+          const int at = cnt + __popc(m & lt);
+          if (at < A.nb_stride) out[at] = lst_j[k];
+        }
+        cnt += __popc(m);
+      }
+      if (cnt > A.nb_stride) cnt = -1;
+    }
+    if (lane == 0) {
+      A.nb_count[qi] = cnt;
+      so.h[s] = h;
+      // bounds used by the pair kernel: 1/h from below, K/h^3 from above
+      // K = 8/pi or 3/(4 pi) (the FP64 constants) rounded up to FP32
+      const float knorm_up = A.kernel == SIDM_KERNEL_TOPHAT ? 0x1.e8ec8cp-3f : 0x1.45f308p+1f;
+      // (__frcp_rn is within 2^-24 of the reciprocal; 2^-23 covers it)
+      const float h3 = __fmul_rd(__fmul_rd(hl, hl), hl);
+      so.hb[s] = make_float4(hl, hu, __fmul_rd(__frcp_rn(hu), 1.0f - ULP1),
+                             __fmul_ru(__fmul_ru(knorm_up, __frcp_rn(h3)), 1.0f + ULP1));
+      A.h_user[so.orig[s]] = h;
+      s_hpred[warp] = hu;
+    }
+    __syncwarp();
   }
   if (lane == 0) {
     if (nonconv) {
