@@ -63,16 +63,16 @@ STEP_BYTES = (BUILD_BYTES_N + 48.0, 64.0)   # 308 B x N + 64 B x A
 # pairs_kernel, pairs_walk_kernel, pairs_exact_kernel, limits_kernel) per
 # step of the headline workload, from an ncu capture of this bench's own
 # timed steps (10 graph-replayed steps, tuned shapes, L2 flushed between
-# steps): 16.10 + 36.47 + 0.44 + 10.63 + 9.44 MB.  The velocity permutation
+# steps): 16.16 + 36.47 + 0.44 + 10.63 + 9.44 MB.  The velocity permutation
 # that shares their phase time (40.8 MB) is a build term of the byte model.
 # None once those kernels change and until they are captured again.
-NEIGHBOUR_SCATTER_TRAFFIC = 73.08e6
+NEIGHBOUR_SCATTER_TRAFFIC = 73.14e6
 
 # Warp instructions the search kernel issues per query on this workload, from
 # an ncu capture of the bench's first timed launch (smsp__inst_executed.sum /
-# queries: 235.6 M / 51,520), and the B300's issue rate: one warp instruction
+# queries: 206.6 M / 51,520), and the B300's issue rate: one warp instruction
 # per scheduler per clock, 4 schedulers per SM, 148 SMs, 2032 MHz maximum.
-SEARCH_INST_PER_QUERY = 4572.0
+SEARCH_INST_PER_QUERY = 4010.0
 ISSUE_PEAK = 148 * 4 * 2032e6          # warp instructions per second
 
 
