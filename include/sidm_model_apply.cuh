@@ -7,9 +7,9 @@
  * order (records with equal keys in the order given), each interaction on
  * the states the earlier ones left (Sec. 4.4).  On the device:
  *   1. count: pairs per particle;
- *   2. split: a pair whose particles are in no other pair commutes with all
- *      the others and is applied at once; the rest are "pending", and each
- *      of their particles gets a segment for its pairs;
+ *   2. split: a pair whose particles are in no other pair ("isolated")
+ *      commutes with all the others; the rest are "pending", and each of
+ *      their particles gets a segment for its pairs;
  *   3. fill + rank: segments filled, each pending pair's place in key order
  *      at both of its particles;
  *   4. dataflow: a pending pair is applied once it sits at the cursor of both
@@ -17,7 +17,10 @@
  *      stores, one release fence, then the cursor stores; cursors are polled
  *      with acquire loads.  The grid is launched cooperatively (all blocks
  *      resident), the globally first unapplied pair is always ready, and a
- *      bounded number of passes guards against a stuck state (error flag);
+ *      bounded number of passes guards against a stuck state (error flag).
+ *      The isolated pairs are applied in the same kernel by the warps that
+ *      hold no pending pair, while the chains of pending pairs run (or, when
+ *      every warp holds one, by every thread after its pending pairs);
  *   5. reset of the per-particle arrays that were touched.
  * A binder may define publish(e): it is called once for every particle an
  * application changes, right after that particle's last interaction of the
@@ -169,15 +172,14 @@ __device__ __forceinline__ void claim_segments(bool want, int32_t e, const int32
   }
 }
 
-// B (the binder) gives, for an accepted pair, the model that applies it
-// (B::model), its PairInfo (B::info) and the particle arrays (B::parts).
+// Marks the pending pairs and claims their particles' segments (B, the
+// binder, is the dataflow kernel's; the isolated pairs are applied there).
 template <class B, class S>
 __global__ void __launch_bounds__(kThreads, 4) split_kernel(const sidm_pair* __restrict__ pairs,
                                                             int64_t cap, B bind, Buffers b,
                                                             S* st) {
-  __shared__ unsigned s_dirfail;
   __shared__ int s_max;
-  if (threadIdx.x == 0) { s_dirfail = 0; s_max = 0; }
+  if (threadIdx.x == 0) s_max = 0;
   __syncthreads();
   const unsigned long long nall = st->n_acc;
   const int lane = threadIdx.x & 31;
@@ -194,11 +196,7 @@ __global__ void __launch_bounds__(kThreads, 4) split_kernel(const sidm_pair* __r
         r = pairs[p];
         const int ma = b.mult[r.ia], mb = b.mult[r.ib];
         mm = max(mm, max(ma, mb));
-        if (ma == 1 && mb == 1) {
-          interact(bind.model(r), bind.parts, bind.info(r, &s_dirfail));
-          publish_if_last(bind, r.ia, 0, 1);
-          publish_if_last(bind, r.ib, 0, 1);
-        } else {
+        if (ma != 1 || mb != 1) {   // isolated pairs wait for the dataflow kernel
           pend = true;
           b.flags[p] = 0;
         }
@@ -217,13 +215,7 @@ __global__ void __launch_bounds__(kThreads, 4) split_kernel(const sidm_pair* __r
   }
   atomicMax(&s_max, mm);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    if (s_max) atomicMax(&st->max_mult, (unsigned long long)s_max);
-    if (s_dirfail) {
-      atomicAdd(&st->n_dirfail, (unsigned long long)s_dirfail);
-      atomicOr(&st->status, kDirFail);
-    }
-  }
+  if (threadIdx.x == 0 && s_max) atomicMax(&st->max_mult, (unsigned long long)s_max);
 }
 
 template <class S>
@@ -376,6 +368,22 @@ struct Turn<B, false> {
   }
 };
 
+// The isolated pairs among accepted pairs first, first + stride, ...: each
+// is applied by its thread (its particles are in no other pair).
+template <class B>
+__device__ __forceinline__ void apply_isolated(const sidm_pair* __restrict__ pairs, int64_t na,
+                                               int64_t first, int64_t stride, const B& bind,
+                                               const Buffers& b, unsigned* dirfail) {
+  for (int64_t p = first; p < na; p += stride) {
+    const sidm_pair r = pairs[p];
+    if (b.mult[r.ia] == 1 && b.mult[r.ib] == 1) {
+      interact(bind.model(r), bind.parts, bind.info(r, dirfail));
+      publish_if_last(bind, r.ia, 0, 1);
+      publish_if_last(bind, r.ib, 0, 1);
+    }
+  }
+}
+
 template <class B, class S>
 __global__ void __launch_bounds__(kThreads) dataflow_kernel(const sidm_pair* __restrict__ pairs,
                                                             int64_t cap, int max_passes, B bind,
@@ -386,10 +394,19 @@ __global__ void __launch_bounds__(kThreads) dataflow_kernel(const sidm_pair* __r
   __syncthreads();
   if (!overflowed(st, cap)) {
     const int64_t np = (int64_t)st->n_pending;
+    const int64_t na = (int64_t)st->n_acc;
     const int64_t gsize = (int64_t)gridDim.x * kThreads;
     // pending pair k to block k mod G: the pairs (and their FP64 kicks)
     // spread over every SM, each warp still holding 32 of them
     const int64_t t0 = threadIdx.x * (int64_t)gridDim.x + blockIdx.x;
+    // warps 0 .. busy-1 of every block hold the pending pairs; the others
+    // apply the isolated pairs meanwhile
+    constexpr int kWarps = kThreads / 32;
+    const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+    const int64_t busy = (np + 32 * (int64_t)gridDim.x - 1) / (32 * (int64_t)gridDim.x);
+    if (busy < kWarps && warp >= busy)
+      apply_isolated(pairs, na, ((warp - busy) * 32 + lane) * (int64_t)gridDim.x + blockIdx.x,
+                     (kWarps - busy) * 32 * (int64_t)gridDim.x, bind, b, &s_dirfail);
     // the thread's first pair, prepared before its turn
     bool first = t0 < np;
     Turn<B> f0;
@@ -437,6 +454,7 @@ __global__ void __launch_bounds__(kThreads) dataflow_kernel(const sidm_pair* __r
     }
     if (left) atomicOr(&st->status, kErrRounds);
     atomicMax(&s_passes, pass);
+    if (busy >= kWarps) apply_isolated(pairs, na, t0, gsize, bind, b, &s_dirfail);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
