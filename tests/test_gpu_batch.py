@@ -35,11 +35,13 @@ def _alone(h, k, starts, n_steps, n_ngb=64):
     return v, hh, dl
 
 
-def _batch(haloes, starts, n_steps, n_ngb=64):
+def _batch(haloes, starts, n_steps, n_ngb=64, tune=None):
     p, off, bins = I.pack(haloes)
     ctx = sidm.Context(n_ngb=n_ngb, box=0.0)
     ctx.set_particles(p.pos, p.vel, p.ids, mass=p.mass)
     ctx.set_haloes(off)
+    if tune:
+        ctx.set_tuning(**tune)
     for t in range(n_steps):
         params = [_params(h, k, starts[k] + t) for k, h in enumerate(haloes)]
         act = np.concatenate([I.active_at_step(h["bins"], starts[k] + t) if h["particles"].n else
@@ -75,6 +77,21 @@ def test_batch_equals_each_halo_alone():
         assert np.array_equal(vb[sl], va), f"halo {k}: velocities"
         assert np.array_equal(hb[sl], ha), f"halo {k}: h"
         assert np.array_equal(db[sl], da), f"halo {k}: dt limits"
+
+
+@pytest.mark.parametrize("run", [1, 16])
+def test_search_runs_across_halo_boundaries(run):
+    """A search warp takes runs of consecutive active queries, and a query
+    whose predecessor in the run lies in the same halo first gathers within
+    6/5 of that query's h.  Runs of 16 cross many halo boundaries of the
+    batch (empty and tiny haloes among them); runs of 1 use no such radius.
+    Both must give the default shape's results bit for bit."""
+    haloes = _small_batch()
+    starts = [(5 * k) % 7 for k in range(len(haloes))]
+    ref = _batch(haloes, starts, 2)
+    got = _batch(haloes, starts, 2, tune={"search_run": run})
+    for a, b in zip(ref[:3], got[:3]):
+        assert np.array_equal(a, b)
 
 
 def test_batch_halo_matches_oracle():
