@@ -417,7 +417,7 @@ def precision_run(log2_n=23, steps=10) -> dict:
     tunings = {}
     for k, c in ctxs.items():
         c.step_counter = 1
-        tunings[k] = c.autotune([sidm.HaloParams(dt, sg, 7, 1)], act1, bins_d, reps=1)
+        tunings[k] = c.autotune([sidm.HaloParams(dt, sg, 7, 1)], act1, bins_d, reps=3)
     for c in ctxs.values():
         c.step_counter = 1
         sidm.sidm_step(c.handle, act1, bins_d, dt, sg, 7, None)
