@@ -179,6 +179,20 @@ def test_ragged_and_tiny_sizes(n, box):
     run_pair(p, None, np.zeros(n, np.int8), 0.1)
 
 
+def test_every_kick_warp_busy_with_pending_pairs():
+    """More pending pairs than the kick application's cooperative grid has
+    warps to spare (at most 7 x 32 x 1184 = 265,216 on a B300): every warp
+    holds pending pairs, so each thread applies its share of the isolated
+    pairs after its pending ones.  An all-active periodic box of 2^20
+    particles at unit density, with dt for about 1.2 expected scatters per
+    particle (~6e5 accepted pairs, most sharing a particle with another),
+    against the oracle."""
+    n = 1 << 20
+    p = I.uniform_box(n, 1.0, 1.0, 31)
+    g, o = run_pair(p, None, np.zeros(n, np.int8), 1.2 * math.sqrt(math.pi) / 4.0)
+    assert o["n_pairs"] > 400_000
+
+
 def test_no_active_particles():
     p = I.uniform_box(3000, 1.0, 1.0, 6)
     g, o = run_pair(p, np.zeros(p.n, np.uint8), np.zeros(p.n, np.int8), 0.1)
